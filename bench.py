@@ -1,0 +1,364 @@
+"""Benchmark: SO(3) FFT forward + inverse transforms per second on the GB300.
+
+One step = one forward transform (2-D FFTs + DWT) and one inverse transform
+(iDWT + 2-D FFTs) of one band-limited function at bandwidth B, through the C
+ABI.  Default workload: B = 64 in FP64 (128^3 complex128 grid, 32 MiB;
+coefficients complex Gaussian scaled by 1/(l+1)).  The inputs rotate over
+enough distinct grids/coefficient vectors that one pass over them exceeds the
+129 MB L2, so no step starts with its input cached.
+
+Printed JSON line (rank 0):
+  value        device-timed fwd+inv pairs/s over the timed steps (CUDA events)
+  e2e          the same through soft_forward_host / soft_inverse_host with
+               pinned host buffers, host<->device copies inside the timing
+  roofline     dominant kernel (the FP64 DWT or iDWT) against the FP64 pipe
+  cpu_baseline the FP64 CPU oracle on a bounded sample, single core
+
+Multi-GPU (torchrun): the transforms are independent, so every rank runs its
+own replica of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (B, coefficient kind, description)
+    "b16": (16, "uniform", "FP64 SOFT forward+inverse, B=16, 32^3 complex128 grid, U(-1,1) coefficients"),
+    "b64": (64, "gauss_decay", "FP64 SOFT forward+inverse, B=64, 128^3 complex128 grid (32 MiB), "
+                               "complex Gaussian coefficients x 1/(l+1)"),
+    "b128": (128, "gauss_decay", "FP64 SOFT forward+inverse, B=128, 256^3 complex128 grid (256 MiB)"),
+    "b256": (256, "gauss_decay", "FP64 SOFT forward+inverse, B=256, 512^3 complex128 grid (2 GiB)"),
+    "b512": (512, "gauss_decay", "FP64 SOFT forward+inverse, B=512, 1024^3 complex128 grid (16 GiB)"),
+}
+METRIC = "SOFT fwd+inv transforms/s"
+UNIT = "fwd+inv pairs/s"
+L2_BYTES = 129 * 2 ** 20
+
+# FP64 pipe peak, derived: the GB300's nominal 1.25 TFLOP/s FP64 at the maximum
+# SM clock of 2070 MHz over 152 SMs is 4 FP64 flops (2 DFMA) per SM per clock.
+FP64_FLOPS_PER_SM_CLK = 4
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+# DRAM traffic per launch of the dominant kernels from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel, bandwidth and
+# the SHA-256 of the kernel source it was taken on; reported as null when the
+# source has changed since.  Filled in from profiles/.
+TRAFFIC = {}
+
+
+def kernel_source_sha() -> str:
+    path = os.path.join(ROOT, "paper_1808_00896_gb300", "csrc", "dwt_fp64.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def dwt_flops(B: int) -> dict:
+    """Algorithmic FP64 flops of one DWT (or iDWT) launch at bandwidth B:
+    contraction 8B per coefficient (2B real FMAs on re and im), plus the
+    recurrence, 5 flops (2 FMA + 1 MUL) per generated T entry; one T column
+    block per symmetry cluster: sum over m = 0..B-1 of (m+1) clusters with
+    B-m degrees and 2B samples."""
+    nc = B * (4 * B * B - 1) // 3
+    t_entries = 2 * B * sum((m + 1) * (B - m) for m in range(B))
+    return {"contraction": 8 * B * nc, "recurrence": 5 * t_entries, "t_entries": t_entries}
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_oracle(B: int, kind: str, budget_s: float) -> dict:
+    """The FP64 oracle, as it stands, on one host core: full forward+inverse
+    round trips at bandwidth B until `budget_s` seconds have elapsed (>= 1)."""
+    import numpy as np
+
+    import oracle
+    from paper_1808_00896_gb300 import synth
+    oracle.build()
+    coef = synth.coefficients(B, kind, seed=synth.BASE_SEED + 7)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        g = oracle.inverse(B, coef)
+        oracle.forward(B, g)
+        k += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} full B={B} FP64 forward+inverse round trip(s) in {dt:.1f} s, single thread"}
+
+
+def run_reference(args) -> None:
+    """--impl reference: the CPU oracle timed as it stands on one host core, on
+    the same workload, metric and unit.  One oracle round trip at B = 64 takes
+    seconds, so the run is bounded: one untimed warm-up round trip, then at
+    most --steps round trips and at most --ref-seconds of timed work."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    B, kind, desc = WORKLOADS[args.workload]
+    import oracle
+    from paper_1808_00896_gb300 import synth
+    oracle.build()
+    coef = synth.coefficients(B, kind, seed=synth.BASE_SEED + 7)
+    oracle.forward(B, oracle.inverse(B, coef))  # warm-up (page-in, caches)
+    t0 = time.perf_counter()
+    k = 0
+    while k < args.steps:
+        oracle.forward(B, oracle.inverse(B, coef))
+        k += 1
+        if time.perf_counter() - t0 >= args.ref_seconds:
+            break
+    dt = time.perf_counter() - t0
+    value = k / dt
+    sample = (f"{k} of the requested {args.steps} full B={B} FP64 forward+inverse round trips "
+              f"(capped at {args.ref_seconds:.0f} s), single thread, after 1 untimed warm-up round trip")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "executed_steps": k, "warmup": args.warmup, "ms_per_step": 1000 * dt / k,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "B": B, "coefficients": kind},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+
+    from paper_1808_00896_gb300 import Plan, capi, synth
+    from paper_1808_00896_gb300 import build as build_mod
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    build_mod.build()
+
+    B, kind, desc = WORKLOADS[args.workload]
+    n = 2 * B
+    grid_bytes = 16 * n ** 3
+    coef_bytes = 16 * synth.num_coeffs(B)
+    R = max(1, min(8, math.ceil(2 * L2_BYTES / (grid_bytes + coef_bytes))))
+    if B >= 256:
+        R = 1  # one input already exceeds L2 several times over
+
+    plan = Plan(B, "fp64", device=dev)
+    coefs = [torch.from_numpy(synth.coefficients(B, kind, seed=synth.BASE_SEED + 100 * rank + r)).to(dev)
+             for r in range(R)]
+    grids = [plan.inverse(c) for c in coefs]
+    coef_out = plan.empty_coef()
+    grid_out = plan.empty_grid()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(r):
+        plan.forward(grids[r], out=coef_out)
+        plan.inverse(coefs[r], out=grid_out)
+
+    for w in range(args.warmup):
+        step(w % R)
+    plan.sync()
+    capi.soft_plan_read_timing(plan.handle)  # discard
+    capi.soft_plan_enable_timing(plan.handle, True)
+
+    sampler = ClockSampler(dev.index if world == 1 else local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)  # let the sampler attach before the timed region
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(args.steps):
+        step(s % R)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    plan.sync()
+    phase_ms, phase_cnt = capi.soft_plan_read_timing(plan.handle)
+    capi.soft_plan_enable_timing(plan.handle, False)
+
+    ms_per_step = ms_total / args.steps
+    value = world * 1000.0 / ms_per_step
+
+    # e2e through the host-buffer entry points with pinned host memory.
+    e2e_steps = max(3, min(args.steps, int(args.e2e_steps)))
+    g_host = torch.empty((n, n, n), dtype=torch.complex128, pin_memory=True)
+    g_host.copy_(grids[0].cpu())
+    c_host = torch.empty(synth.num_coeffs(B), dtype=torch.complex128, pin_memory=True)
+    c_host.copy_(coefs[0].cpu())
+    c_res = torch.empty_like(c_host, pin_memory=True)
+    g_res = torch.empty_like(g_host, pin_memory=True)
+    gh, ch, cr, gr = g_host.numpy(), c_host.numpy(), c_res.numpy(), g_res.numpy()
+    plan.forward_host(gh, cr)
+    plan.inverse_host(ch, gr)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.forward_host(gh, cr)
+        plan.inverse_host(ch, gr)
+    e2e_dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_dt, "unit": UNIT,
+           "h2d_bytes_per_step": grid_bytes + coef_bytes, "d2h_bytes_per_step": coef_bytes + grid_bytes,
+           "steps": e2e_steps}
+
+    # Roofline of the dominant kernel, from the library's CUDA events.
+    fl = dwt_flops(B)
+    algo = fl["contraction"] + fl["recurrence"]
+    fwd_ms = phase_ms[1] / max(1, phase_cnt[1])
+    inv_ms = phase_ms[2] / max(1, phase_cnt[2])
+    dom, dom_ms = ("dwt_forward_fp64_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else \
+        ("dwt_inverse_fp64_kernel", inv_ms)
+    peak_gflops = FP64_FLOPS_PER_SM_CLK * N_SM * SM_MAX_MHZ * 1e6 / 1e9
+    achieved = algo / (dom_ms * 1e-3) / 1e9
+    tr = TRAFFIC.get((dom, B))
+    traffic = tr[0] if (tr and tr[1] == kernel_source_sha()) else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s",
+                "frac": achieved / peak_gflops, "traffic": traffic, "kernel": dom,
+                "peak_source": "derived: nominal FP64 1.25 TFLOP/s = 4 flop/clk/SM x 152 SM x 2070 MHz",
+                "algorithmic_flops_per_launch": algo,
+                "phase_ms_per_launch": {"fft_forward": phase_ms[0] / max(1, phase_cnt[0]),
+                                        "dwt_forward": fwd_ms, "dwt_inverse": inv_ms,
+                                        "fft_inverse": phase_ms[3] / max(1, phase_cnt[3])}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle(min(B, 64), kind, args.cpu_seconds)
+        if B > 64:
+            cpu["sample"] += f" (B={B} oracle is O(B^4); sample taken at B=64, not rescaled)"
+            cpu["value"] = None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "B": B, "coefficients": kind, "inputs_rotated": R,
+                       "l2": f"{R} rotating input sets of {(grid_bytes + coef_bytes) / 2**20:.1f} MiB "
+                             f"(> 129 MB L2 per pass)" if R > 1 else "single input larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roofline, "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="b64")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.steps is None:
+        args.steps = {"ours": {"b16": 2000, "b64": 400, "b128": 60, "b256": 10, "b512": 3},
+                      "reference": {"b16": 50, "b64": 20, "b128": 4, "b256": 1, "b512": 1}}[args.impl][args.workload]
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,136 @@
+/*
+ * soft.h -- C ABI of the GB300 library for the fast Fourier transform on SO(3)
+ * (the Kostelec-Rockmore FSOFT and its inverse, as reviewed and parallelised in
+ * Lux, Wuelker, Chirikjian, "Parallelization of the FFT on SO(3)",
+ * arXiv:1808.00896).
+ *
+ * Every entry point takes plain pointers and sizes; there are no C++ or torch
+ * types in the signatures.  Errors are reported by return code only: nothing
+ * aborts, throws or traps.  Unless an entry point says otherwise, all data
+ * pointers are DEVICE pointers on the plan's device, owned by the caller,
+ * 16-byte aligned, and must not overlap each other.  Inputs are never
+ * modified.  Calls are asynchronous on the given stream (a cudaStream_t passed
+ * as void*; NULL = the legacy default stream); the returned status covers
+ * argument checks and launch errors, and a device-side error word is checked
+ * by soft_plan_sync().
+ *
+ * Data layouts (the paper fixes the math, not the memory layout):
+ *
+ *   grid  -- (2B)^3 complex doubles (interleaved re, im), index [j][i][k]:
+ *            grid[(j*2B + i)*2B + k] = f(alpha_i, beta_j, gamma_k) with the
+ *            sampling angles of Eq. (quadrature): alpha_i = i*pi/B,
+ *            beta_j = (2j+1)*pi/(4B), gamma_k = k*pi/B.  beta is slowest, so
+ *            each beta slice is one contiguous 2B x 2B array.
+ *
+ *   coef  -- B(4B^2-1)/3 complex doubles, the Fourier coefficients f(l,m,m')
+ *            of Eq. (fourier_representation).  For m = 1-B..B-1 (outer) and
+ *            m' = 1-B..B-1 (inner) the run l = max(|m|,|m'|)..B-1 is
+ *            contiguous; soft_coef_index() gives the offset of any entry.
+ *
+ *   S     -- (2B)^3 complex doubles, index [j][m mod 2B][m' mod 2B]: the
+ *            separated sums S(m,m';j) of Sec. 2.4 (the output of the 2-D FFT
+ *            of each beta slice); entries with m or m' = -B (index B) are 0.
+ */
+#ifndef SOFT_GB300_SOFT_H
+#define SOFT_GB300_SOFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct soft_plan_s *soft_plan; /* opaque; created and owned by the library */
+
+typedef enum {
+    SOFT_OK = 0,
+    SOFT_ERR_INVALID_ARG = 1,   /* bad B, NULL or misaligned pointer, bad dtype, stale plan */
+    SOFT_ERR_OUT_OF_MEMORY = 2, /* device or pinned-host allocation failed */
+    SOFT_ERR_CUDA = 3,          /* a CUDA runtime or cuFFT call failed */
+    SOFT_ERR_UNSUPPORTED = 4,   /* B above soft_max_bandwidth(), or a mode not built */
+    SOFT_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    SOFT_ERR_DEVICE = 6         /* a kernel flagged an internal inconsistency */
+} soft_status;
+
+typedef enum {
+    SOFT_FP64 = 0,         /* every step in FP64 */
+    SOFT_MIXED_BF16X3 = 1, /* reserved: contraction on tensor cores, split BF16 x3 */
+    SOFT_MIXED_TF32 = 2    /* reserved: contraction on tensor cores, TF32 */
+} soft_dtype;
+
+/* Largest bandwidth B the kernels accept. */
+int soft_max_bandwidth(void);
+
+/* Number of Fourier coefficients with l < B: B(4B^2-1)/3 (Sec. 2.4).
+ * Returns -1 for B < 1. */
+int64_t soft_num_coeffs(int B);
+
+/* Offset of f(l,m,m') in the coefficient array for bandwidth B, or -1 when
+ * not (max(|m|,|m'|) <= l < B). Host function, no device work. */
+int64_t soft_coef_index(int B, int l, int m, int mp);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *soft_status_string(int status);
+
+/* Create a plan for bandwidth B on the current CUDA device.  Allocates the
+ * plan's device workspace ((2B)^3 complex doubles for S plus small tables),
+ * builds the cuFFT plan and computes the quadrature weights of Eq. (weights)
+ * and the other beta tables on the device.  *out receives the handle, or NULL
+ * on failure.  Returns SOFT_ERR_INVALID_ARG for B < 1 or out == NULL,
+ * SOFT_ERR_UNSUPPORTED for B > soft_max_bandwidth() or an unbuilt dtype. */
+soft_status soft_plan_create(soft_plan *out, int B, int dtype);
+
+/* Release a plan and everything it owns.  NULL is accepted (no-op).
+ * Synchronises the plan's device first. */
+soft_status soft_destroy(soft_plan p);
+
+/* Bandwidth of a plan, or -1 for NULL. */
+int soft_plan_bandwidth(soft_plan p);
+
+/* Wait for all work on the plan's device and read the device error word.
+ * Returns SOFT_ERR_DEVICE if a kernel flagged an error since the last call. */
+soft_status soft_plan_sync(soft_plan p);
+
+/* Forward transform (FSOFT, Sec. 2.4): grid (device, (2B)^3 complex) ->
+ * coef (device, B(4B^2-1)/3 complex), f(l,m,m') of Eq. (quadrature):
+ *   2-D FFT of every beta slice (cuFFT, exp(+i...)) into the plan's S,
+ *   then the DWT f = V_B T_B W_B S for every order pair (m,m').       */
+soft_status soft_forward(soft_plan p, const double *grid, double *coef, void *stream);
+
+/* Inverse transform (iFSOFT, Sec. 2.4): coef -> grid, the function values of
+ * Eq. (fourier_representation) on the sampling grid:
+ *   iDWT S = T_B^T f for every (m,m') into the plan's S, then 2-D FFT of
+ *   every beta slice (cuFFT, exp(-i...)).                               */
+soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *stream);
+
+/* The DWT step alone (Sec. 2.4, matrix form V_B T_B W_B): S (device, layout
+ * above) -> coef.  S is read only. */
+soft_status soft_dwt_forward(soft_plan p, const double *S, double *coef, void *stream);
+
+/* The iDWT step alone (Sec. 2.4, T_B^T): coef -> S (device, layout above,
+ * every entry written, the -B rows/columns set to 0). */
+soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *stream);
+
+/* Host-buffer forms: grid_host / coef_host are HOST pointers (pageable or
+ * pinned).  The call copies the input to plan-owned device staging buffers
+ * (allocated on first use), runs the transform on `stream`, copies the
+ * result back and synchronises the stream before returning. */
+soft_status soft_forward_host(soft_plan p, const double *grid_host, double *coef_host, void *stream);
+soft_status soft_inverse_host(soft_plan p, const double *coef_host, double *grid_host, void *stream);
+
+/* Per-phase timing.  When enabled, every soft_forward / soft_inverse records
+ * CUDA events (on the call's stream) around its 2-D FFT and its (i)DWT
+ * kernel(s); soft_plan_read_timing() waits for them, adds up the elapsed
+ * times since the last read and resets the sums.  ms_out[4] receives the
+ * milliseconds spent in {forward FFT, DWT, iDWT (with the S clearing),
+ * inverse FFT}; counts_out[4] the number of timed launches of each (either
+ * pointer may be NULL).  Up to 4096 calls are held between two reads; a call
+ * that finds 4096 pending first waits for them and folds them into the sums. */
+soft_status soft_plan_enable_timing(soft_plan p, int on);
+soft_status soft_plan_read_timing(soft_plan p, double *ms_out, int64_t *counts_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOFT_GB300_SOFT_H */

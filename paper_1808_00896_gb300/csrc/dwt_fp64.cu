@@ -1,0 +1,369 @@
+// dwt_fp64.cu -- FP64 discrete Wigner transform (DWT) and its inverse (iDWT)
+// on the GB300, plus the small table and S-clearing kernels.
+//
+// The DWT of orders (m,m') (Sec. 2.4, matrix form):
+//   [f(l,m,m')]_l = V_B T_B W_B [S(m,m';j)]_j,   V = diag((2l+1)/(8 pi B)),
+//   T = [d(l,m,m';beta_j)], W = diag(w_B(j)),     l = l0..B-1, j = 0..2B-1;
+// the iDWT is [S(m,m';j)]_j = T_B^T [f(l,m,m')]_l.
+//
+// GB300 design.  One CTA per symmetry cluster (Sec. 3): the representative's
+// column block T is generated ONCE, on the fly, by the three-term recurrence
+// in FP64 (never stored in HBM) and serves the cluster's up to 8 partners,
+// which become the 16 real right-hand sides of a skinny GEMM.  The path is
+// bound by the FP64 pipe, so the kernels keep FP64 work to the contraction's
+// 16 FMAs plus the recurrence's 3 operations per (l, j) entry; every table
+// (weights, logs, recurrence coefficients) is computed once per CTA or plan.
+#include "soft_internal.cuh"
+
+#include <algorithm>
+#include <mutex>
+
+namespace softgb {
+
+namespace {
+
+__device__ __forceinline__ int mod_n(int a, int n) { return a < 0 ? a + n : a; }
+
+// ---------------------------------------------------------------------------
+// Plan tables: w_B(j) (Eq. (weights)), cos(beta_j), log cos(beta_j/2),
+// log sin(beta_j/2) and log(k!).  Angles are formed as exact rationals of pi
+// (sinpi/cospi) so that no rounded multiple of pi enters the arguments.
+// ---------------------------------------------------------------------------
+__global__ void tables_kernel(int B, double *w, double *cosb, double *lcos, double *lsin, double *lfact) {
+    const int n = 2 * B;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        const int64_t q = 2 * t + 1;  // beta_t = q pi / (4B)
+        const int64_t per = 8LL * B;  // sin(r pi/(4B)) has period 8B in r
+        double s = 0.0;
+        for (int i = 0; i < B; ++i) {
+            const int64_t r = ((2LL * i + 1) * q) % per;
+            s += sinpi((double)r / (4.0 * B)) / (2.0 * i + 1.0);
+        }
+        w[t] = 2.0 * M_PI * sinpi((double)q / (4.0 * B)) / ((double)B * B) * s;
+        cosb[t] = cospi((double)q / (4.0 * B));
+        lcos[t] = log(cospi((double)q / (8.0 * B)));
+        lsin[t] = log(sinpi((double)q / (8.0 * B)));
+    }
+    if (t <= n) lfact[t] = lgamma(t + 1.0);
+}
+
+// Zero the S entries of frequency -B (index B) in either order, which the
+// iDWT never writes and the 2-D FFT of the inverse must see as 0.
+__global__ void zero_nyquist_kernel(int B, double2 *S) {
+    const int n = 2 * B;
+    const int64_t total = (int64_t)n * (2 * n - 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / (2 * n - 1));
+        const int r = (int)(e % (2 * n - 1));
+        int64_t idx;
+        if (r < n) idx = ((int64_t)j * n + B) * n + r;                      // m = -B row
+        else { const int c = r - n; idx = ((int64_t)j * n + (c < B ? c : c + 1)) * n + B; }  // m' = -B col
+        S[idx] = make_double2(0.0, 0.0);
+    }
+}
+
+// Per-CTA cluster prologue: partner table, run offsets, recurrence coefficients.
+struct ClusterSmem {
+    int np;
+    int pm[8], pmp[8], mir[8], lpar[8];
+    double sign[8];
+    int64_t off[8];
+};
+
+__device__ void load_cluster(const Tables &tb, int m, int mp, ClusterSmem &cs) {
+    if (threadIdx.x == 0) {
+        const Partners P = make_partners(m, mp);
+        cs.np = P.np;
+        for (int p = 0; p < 8; ++p) {
+            const bool on = p < P.np;
+            cs.pm[p] = on ? P.m[p] : 0;
+            cs.pmp[p] = on ? P.mp[p] : 0;
+            cs.mir[p] = on ? P.mirror[p] : 0;
+            cs.lpar[p] = on ? P.lpar[p] : 0;
+            cs.sign[p] = on ? P.sign[p] : 0.0;
+            cs.off[p] = on ? tb.runoff[runoff_index(tb.B, P.m[p], P.mp[p])] : 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward DWT.  NT threads, LT = NT/16 degrees per tile, JPT beta samples per
+// thread in the recurrence phase.
+//   dynamic smem: X[2B][16] (w_B(j') S_p(j'), partner p in columns 2p, 2p+1),
+//                 T[LT][2B] (the current tile of T_B), rec[4][B] (A, Ac, Bc, V).
+// Phase A: every thread advances the recurrence of its beta samples LT steps,
+//          writing the tile of T.
+// Phase B: thread (t, c) forms sum_j T[t][j] X[j][c] for output column c.
+// ---------------------------------------------------------------------------
+template <int NT, int JPT>
+__global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const double2 *__restrict__ S,
+                                                               double *__restrict__ coef) {
+    constexpr int LT = NT / 16;
+    extern __shared__ __align__(16) double smem[];
+    __shared__ ClusterSmem cs;
+    const int B = tb.B, n = 2 * B, tid = threadIdx.x;
+    const int2 rep = tb.clusters[blockIdx.x];
+    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+
+    double *X = smem;              // [n][16]
+    double *T = X + (size_t)n * 16; // [LT][n]
+    double *rA = T + (size_t)LT * n;
+    double *rAc = rA + B;
+    double *rBc = rAc + B;
+    double *rV = rBc + B;
+
+    load_cluster(tb, m, mp, cs);
+    for (int t = tid; t < L; t += NT) {
+        const int l = l0 + t;
+        double A, Ac, Bc;
+        recurrence_coeffs(l, m, mp, A, Ac, Bc);
+        rA[t] = A; rAc[t] = Ac; rBc[t] = Bc;
+        rV[t] = (2.0 * l + 1.0) / (8.0 * M_PI * B);
+    }
+    __syncthreads();
+    const int np = cs.np;
+
+    // X: weighted S of every partner, beta index mirrored where the partner's
+    // column is d(.; pi - beta).
+    for (int e = tid; e < n * 8; e += NT) {
+        const int j = e >> 3, p = e & 7;
+        double2 v = make_double2(0.0, 0.0);
+        if (p < np) {
+            const int src = cs.mir[p] ? n - 1 - j : j;
+            const double2 s = S[((int64_t)src * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)];
+            const double wj = tb.w[src];
+            v = make_double2(wj * s.x, wj * s.y);
+        }
+        *reinterpret_cast<double2 *>(&X[j * 16 + 2 * p]) = v;
+    }
+
+    // Recurrence state of this thread's beta samples.
+    double x[JPT], dcur[JPT], dprev[JPT];
+    {
+        const double lognorm = seed_lognorm(tb, m, mp);
+#pragma unroll
+        for (int k = 0; k < JPT; ++k) {
+            const int j = tid + k * NT;
+            x[k] = 0.0; dcur[k] = 0.0; dprev[k] = 0.0;
+            if (j < n) {
+                x[k] = tb.cosb[j];
+                dcur[k] = seed_rep(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
+            }
+        }
+    }
+    __syncthreads();
+
+    const int pt = tid >> 4, pc = tid & 15;  // phase-B output (degree in tile, column)
+    const int pp = pc >> 1;
+    for (int lb = l0; lb < B; lb += LT) {
+        const int nt = min(LT, B - lb);
+        // Phase A
+#pragma unroll
+        for (int k = 0; k < JPT; ++k) {
+            const int j = tid + k * NT;
+            if (j < n) {
+                for (int t = 0; t < nt; ++t) {
+                    T[t * n + j] = dcur[k];
+                    const int r = lb + t - l0;
+                    const double nx = fma(fma(rA[r], x[k], -rAc[r]), dcur[k], -rBc[r] * dprev[k]);
+                    dprev[k] = dcur[k];
+                    dcur[k] = nx;
+                }
+            }
+        }
+        __syncthreads();
+        // Phase B
+        if (pt < nt && pp < np) {
+            const double *Tr = T + pt * n;
+            const double *Xc = X + pc;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int j = 0;
+            for (; j + 4 <= n; j += 4) {
+                a0 = fma(Tr[j], Xc[j * 16], a0);
+                a1 = fma(Tr[j + 1], Xc[(j + 1) * 16], a1);
+                a2 = fma(Tr[j + 2], Xc[(j + 2) * 16], a2);
+                a3 = fma(Tr[j + 3], Xc[(j + 3) * 16], a3);
+            }
+            for (; j < n; ++j) a0 = fma(Tr[j], Xc[j * 16], a0);
+            const int l = lb + pt;
+            const double sg = (cs.lpar[pp] && (l & 1)) ? -cs.sign[pp] : cs.sign[pp];
+            coef[2 * (cs.off[pp] + (l - l0)) + (pc & 1)] = rV[l - l0] * sg * ((a0 + a1) + (a2 + a3));
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse DWT.  Every thread owns JPT beta samples, walks l = l0..B-1 with the
+// recurrence in registers and accumulates NC real columns:
+//   acc[c] += d(l; beta_j) * F[l][c],  F = sign-folded coefficients of the partners.
+//   dynamic smem: F[B][16], rec[3][B].
+// ---------------------------------------------------------------------------
+template <int NT, int JPT, int NC>
+__device__ __forceinline__ void idwt_walk(const double *F, const double *rA, const double *rAc, const double *rBc,
+                                          int L, double (&x)[JPT], double (&dcur)[JPT], double (&dprev)[JPT],
+                                          double (&acc)[JPT][16]) {
+    for (int t = 0; t < L; ++t) {
+        const double *Fr = F + t * 16;
+        const double A = rA[t], Ac = rAc[t], Bc = rBc[t];
+#pragma unroll
+        for (int c = 0; c < NC; c += 2) {
+            const double2 f = *reinterpret_cast<const double2 *>(Fr + c);
+#pragma unroll
+            for (int k = 0; k < JPT; ++k) {
+                acc[k][c] = fma(dcur[k], f.x, acc[k][c]);
+                acc[k][c + 1] = fma(dcur[k], f.y, acc[k][c + 1]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < JPT; ++k) {
+            const double nx = fma(fma(A, x[k], -Ac), dcur[k], -Bc * dprev[k]);
+            dprev[k] = dcur[k];
+            dcur[k] = nx;
+        }
+    }
+}
+
+template <int NT, int JPT>
+__global__ void __launch_bounds__(NT) dwt_inverse_fp64_kernel(Tables tb, const double *__restrict__ coef,
+                                                               double2 *__restrict__ S) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ ClusterSmem cs;
+    const int B = tb.B, n = 2 * B, tid = threadIdx.x;
+    const int2 rep = tb.clusters[blockIdx.x];
+    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+
+    double *F = smem;                  // [B][16]
+    double *rA = F + (size_t)B * 16;
+    double *rAc = rA + B;
+    double *rBc = rAc + B;
+
+    load_cluster(tb, m, mp, cs);
+    for (int t = tid; t < L; t += NT) {
+        double A, Ac, Bc;
+        recurrence_coeffs(l0 + t, m, mp, A, Ac, Bc);
+        rA[t] = A; rAc[t] = Ac; rBc[t] = Bc;
+    }
+    __syncthreads();
+    const int np = cs.np;
+    for (int e = tid; e < L * 8; e += NT) {
+        const int t = e >> 3, p = e & 7;
+        double2 v = make_double2(0.0, 0.0);
+        if (p < np) {
+            const int l = l0 + t;
+            const double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
+            const double2 c = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + t));
+            v = make_double2(sg * c.x, sg * c.y);
+        }
+        *reinterpret_cast<double2 *>(&F[t * 16 + 2 * p]) = v;
+    }
+
+    double x[JPT], dcur[JPT], dprev[JPT];
+    double acc[JPT][16];
+    {
+        const double lognorm = seed_lognorm(tb, m, mp);
+#pragma unroll
+        for (int k = 0; k < JPT; ++k) {
+            const int j = tid + k * NT;
+            x[k] = 0.0; dcur[k] = 0.0; dprev[k] = 0.0;
+            if (j < n) {
+                x[k] = tb.cosb[j];
+                dcur[k] = seed_rep(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[k][c] = 0.0;
+        }
+    }
+    __syncthreads();
+
+    if (np == 8) idwt_walk<NT, JPT, 16>(F, rA, rAc, rBc, L, x, dcur, dprev, acc);
+    else         idwt_walk<NT, JPT, 8>(F, rA, rAc, rBc, L, x, dcur, dprev, acc);
+
+#pragma unroll
+    for (int k = 0; k < JPT; ++k) {
+        const int j = tid + k * NT;
+        if (j < n) {
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                if (p < np) {
+                    const int jj = cs.mir[p] ? n - 1 - j : j;
+                    S[((int64_t)jj * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)] =
+                        make_double2(acc[k][2 * p], acc[k][2 * p + 1]);
+                }
+            }
+        }
+    }
+}
+
+template <typename K>
+cudaError_t set_smem_once(K kernel, size_t bytes, std::once_flag &flag) {
+    cudaError_t err = cudaSuccess;
+    std::call_once(flag, [&] {
+        err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+    (void)bytes;
+    return err;
+}
+
+template <int NT, int JPT>
+cudaError_t run_forward(const Tables &tb, const double2 *S, double *coef, cudaStream_t s) {
+    static std::once_flag flag;
+    const int B = tb.B, n = 2 * B;
+    const size_t bytes = sizeof(double) * ((size_t)n * 16 + (size_t)(NT / 16) * n + 4 * (size_t)B);
+    cudaError_t e = set_smem_once(dwt_forward_fp64_kernel<NT, JPT>, bytes, flag);
+    if (e != cudaSuccess) return e;
+    dwt_forward_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, S, coef);
+    return cudaGetLastError();
+}
+
+template <int NT, int JPT>
+cudaError_t run_inverse(const Tables &tb, const double *coef, double2 *S, cudaStream_t s) {
+    static std::once_flag flag;
+    const int B = tb.B;
+    const size_t bytes = sizeof(double) * ((size_t)B * 16 + 3 * (size_t)B);
+    cudaError_t e = set_smem_once(dwt_inverse_fp64_kernel<NT, JPT>, bytes, flag);
+    if (e != cudaSuccess) return e;
+    dwt_inverse_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, coef, S);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *lsin, double *lfact,
+                          cudaStream_t s) {
+    const int n = 2 * B;
+    tables_kernel<<<(n + 1 + 127) / 128, 128, 0, s>>>(B, w, cosb, lcos, lsin, lfact);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s) {
+    const int n = 2 * B;
+    const int64_t total = (int64_t)n * (2 * n - 1);
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    zero_nyquist_kernel<<<blocks, 256, 0, s>>>(B, S);
+    return cudaGetLastError();
+}
+
+// Shape choice: the forward needs X (2B x 16) and a T tile (LT x 2B) in shared
+// memory; at 2B = 1024 only NT = 128 (LT = 8) fits the 227 KB of a CTA.
+cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s) {
+    const int n = 2 * tb.B;
+    double *c = reinterpret_cast<double *>(coef);
+    if (n <= 256) return run_forward<256, 1>(tb, S, c, s);
+    if (n <= 512) return run_forward<256, 2>(tb, S, c, s);
+    return run_forward<128, 8>(tb, S, c, s);
+}
+
+cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s) {
+    const int n = 2 * tb.B;
+    const double *c = reinterpret_cast<const double *>(coef);
+    if (n <= 64) return run_inverse<64, 1>(tb, c, S, s);
+    if (n <= 128) return run_inverse<128, 1>(tb, c, S, s);
+    if (n <= 256) return run_inverse<256, 1>(tb, c, S, s);
+    if (n <= 512) return run_inverse<256, 2>(tb, c, S, s);
+    return run_inverse<256, 4>(tb, c, S, s);
+}
+
+}  // namespace softgb

@@ -1,0 +1,415 @@
+// soft_api.cu -- plans and the C ABI declared in include/soft.h.
+//
+// A plan owns, on one device: the quadrature and beta tables (computed by a
+// kernel), the cluster work list, the coefficient run-offset table, the S
+// workspace ((2B)^3 complex doubles) and a batched 2-D cuFFT plan over the 2B
+// beta slices.  The transforms are the two steps of Sec. 2.4: a 2-D FFT per
+// beta slice and the DWT per order pair (forward), or the iDWT per order pair
+// and a 2-D FFT per slice (inverse).
+#include "soft.h"
+#include "soft_internal.cuh"
+
+#include <cufft.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace softgb;
+
+namespace {
+
+constexpr uint64_t kPlanMagic = 0x534f46545f504c4eULL;  // "SOFT_PLN"
+
+}  // namespace
+
+struct soft_plan_s {
+    uint64_t magic;
+    int B, dtype, device;
+    double *w, *cosb, *lcos, *lsin, *lfact;
+    int2 *clusters;
+    int ncl;
+    int64_t *runoff;
+    double2 *S;
+    int *err;
+    cufftHandle fft;
+    bool fft_made;
+    double2 *stage_grid, *stage_coef;  // for the host-buffer entry points, allocated on first use
+
+    // Per-phase timing (soft_plan_enable_timing): 3 events per timed call.
+    static constexpr int kMaxRec = 4096;
+    bool timing;
+    int nrec;
+    int rec_kind[kMaxRec];             // 0 = forward, 1 = inverse
+    std::vector<cudaEvent_t> events;   // 3 * kMaxRec, created on first use
+    double ms[4];
+    int64_t counts[4];
+
+    Tables tables() const {
+        Tables t;
+        t.B = B; t.ncl = ncl; t.w = w; t.cosb = cosb; t.lcos = lcos; t.lsin = lsin; t.lfact = lfact;
+        t.clusters = clusters; t.runoff = runoff; t.err = err;
+        return t;
+    }
+};
+
+namespace {
+
+// Keeps the caller's current device unchanged across a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) switched = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+};
+
+bool valid(const soft_plan_s *p) { return p != nullptr && p->magic == kPlanMagic; }
+bool aligned16(const void *ptr) { return ptr != nullptr && (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+soft_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SOFT_OK;
+    if (e == cudaErrorMemoryAllocation) return SOFT_ERR_OUT_OF_MEMORY;
+    return SOFT_ERR_CUDA;
+}
+
+int64_t sum_sq(int64_t x) { return x * (x + 1) * (2 * x + 1) / 6; }  // 1^2 + ... + x^2
+
+// Start of the run of (m, m') in the coefficient array (layout in soft.h), closed form.
+// Row m holds B^2 - m^2 entries; within row m (mu = |m|) the run of m' has length
+// B - max(mu, |m'|).
+int64_t run_start(int B, int m, int mp) {
+    const int64_t BB = (int64_t)B * B;
+    const int64_t sq = m <= 0 ? sum_sq(B - 1) - sum_sq(-m) : sum_sq(B - 1) + sum_sq(m - 1);
+    const int64_t row = (int64_t)(m + B - 1) * BB - sq;
+    const int64_t mu = m < 0 ? -m : m;
+    int64_t in;
+    if (mp <= -mu) {
+        const int64_t K = B + mp - 1;
+        in = K * (K + 1) / 2;
+    } else {
+        const int64_t K1 = B - mu - 1;
+        in = K1 * (K1 + 1) / 2;
+        if (mp <= mu + 1) {
+            in += (mp + mu) * (B - mu);
+        } else {
+            const int64_t c = mp - mu - 1;
+            in += (2 * mu + 1) * (B - mu) + c * (2 * B - mu - mp) / 2;
+        }
+    }
+    return row + in;
+}
+
+soft_status check_plan_args(const soft_plan_s *p, const void *a, const void *b) {
+    if (!valid(p)) return SOFT_ERR_INVALID_ARG;
+    if (!aligned16(a) || !aligned16(b) || a == b) return SOFT_ERR_INVALID_ARG;
+    return SOFT_OK;
+}
+
+size_t grid_elems(int B) { return (size_t)(2 * B) * (2 * B) * (2 * B); }
+
+// Adds the pending timing records to the sums (waits for their events).
+void fold_timing(soft_plan_s *p) {
+    for (int r = 0; r < p->nrec; ++r) {
+        cudaEvent_t *e = &p->events[3 * r];
+        float a = 0.f, b = 0.f;
+        if (cudaEventSynchronize(e[2]) != cudaSuccess) continue;
+        cudaEventElapsedTime(&a, e[0], e[1]);
+        cudaEventElapsedTime(&b, e[1], e[2]);
+        const int k = p->rec_kind[r] == 0 ? 0 : 2;
+        p->ms[k] += a; p->ms[k + 1] += b;
+        p->counts[k] += 1; p->counts[k + 1] += 1;
+    }
+    p->nrec = 0;
+}
+
+// Returns the 3 events of a new timing record, or nullptr when timing is off.
+cudaEvent_t *timing_slot(soft_plan_s *p, int kind) {
+    if (!p->timing) return nullptr;
+    if (p->events.empty()) {
+        p->events.resize(3 * soft_plan_s::kMaxRec);
+        for (auto &e : p->events)
+            if (cudaEventCreate(&e) != cudaSuccess) e = nullptr;
+    }
+    if (p->nrec == soft_plan_s::kMaxRec) fold_timing(p);
+    cudaEvent_t *e = &p->events[3 * p->nrec];
+    if (!e[0] || !e[1] || !e[2]) return nullptr;
+    p->rec_kind[p->nrec++] = kind;
+    return e;
+}
+
+void free_plan(soft_plan_s *p) {
+    if (!p) return;
+    for (auto &e : p->events)
+        if (e) cudaEventDestroy(e);
+    if (p->fft_made) cufftDestroy(p->fft);
+    cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
+    cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
+    cudaFree(p->stage_grid); cudaFree(p->stage_coef);
+    p->magic = 0;
+    delete p;
+}
+
+soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s) {
+    cudaEvent_t *ev = timing_slot(p, 0);
+    if (ev) cudaEventRecord(ev[0], s);
+    if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return SOFT_ERR_CUDA;
+    // S(m,m';j) = sum_{i,k} f exp(+i(m alpha_i + m' gamma_k)): cuFFT's INVERSE direction, unnormalised.
+    cufftDoubleComplex *in = reinterpret_cast<cufftDoubleComplex *>(const_cast<double *>(grid));
+    if (cufftExecZ2Z(p->fft, in, reinterpret_cast<cufftDoubleComplex *>(p->S), CUFFT_INVERSE) != CUFFT_SUCCESS)
+        return SOFT_ERR_CUDA;
+    if (ev) cudaEventRecord(ev[1], s);
+    cudaError_t e = launch_dwt_forward_fp64(p->tables(), p->S, reinterpret_cast<double2 *>(coef), s);
+    if (ev) cudaEventRecord(ev[2], s);
+    return cuda_status(e);
+}
+
+soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s) {
+    cudaEvent_t *ev = timing_slot(p, 1);
+    if (ev) cudaEventRecord(ev[0], s);
+    cudaError_t e = launch_zero_nyquist(p->B, p->S, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = launch_dwt_inverse_fp64(p->tables(), reinterpret_cast<const double2 *>(coef), p->S, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (ev) cudaEventRecord(ev[1], s);
+    if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return SOFT_ERR_CUDA;
+    // f = sum_{m,m'} S exp(-i(m alpha_i + m' gamma_k)): cuFFT's FORWARD direction, unnormalised.
+    if (cufftExecZ2Z(p->fft, reinterpret_cast<cufftDoubleComplex *>(p->S),
+                     reinterpret_cast<cufftDoubleComplex *>(grid), CUFFT_FORWARD) != CUFFT_SUCCESS)
+        return SOFT_ERR_CUDA;
+    if (ev) cudaEventRecord(ev[2], s);
+    return SOFT_OK;
+}
+
+soft_status ensure_staging(soft_plan_s *p) {
+    if (!p->stage_grid) {
+        if (cudaMalloc(&p->stage_grid, sizeof(double2) * grid_elems(p->B)) != cudaSuccess) {
+            p->stage_grid = nullptr;
+            return SOFT_ERR_OUT_OF_MEMORY;
+        }
+    }
+    if (!p->stage_coef) {
+        if (cudaMalloc(&p->stage_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B)) != cudaSuccess) {
+            p->stage_coef = nullptr;
+            return SOFT_ERR_OUT_OF_MEMORY;
+        }
+    }
+    return SOFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int soft_max_bandwidth(void) { return kMaxB; }
+
+int64_t soft_num_coeffs(int B) {
+    if (B < 1) return -1;
+    return (int64_t)B * (4LL * B * B - 1) / 3;
+}
+
+int64_t soft_coef_index(int B, int l, int m, int mp) {
+    if (B < 1) return -1;
+    const int am = m < 0 ? -m : m, amp = mp < 0 ? -mp : mp;
+    const int l0 = am > amp ? am : amp;
+    if (l < l0 || l >= B) return -1;
+    return run_start(B, m, mp) + (l - l0);
+}
+
+const char *soft_status_string(int status) {
+    switch (status) {
+        case SOFT_OK: return "SOFT_OK";
+        case SOFT_ERR_INVALID_ARG: return "SOFT_ERR_INVALID_ARG";
+        case SOFT_ERR_OUT_OF_MEMORY: return "SOFT_ERR_OUT_OF_MEMORY";
+        case SOFT_ERR_CUDA: return "SOFT_ERR_CUDA";
+        case SOFT_ERR_UNSUPPORTED: return "SOFT_ERR_UNSUPPORTED";
+        case SOFT_ERR_TIMEOUT: return "SOFT_ERR_TIMEOUT";
+        case SOFT_ERR_DEVICE: return "SOFT_ERR_DEVICE";
+        default: return "SOFT_ERR_UNKNOWN";
+    }
+}
+
+soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
+    if (!out) return SOFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (B < 1) return SOFT_ERR_INVALID_ARG;
+    if (B > kMaxB) return SOFT_ERR_UNSUPPORTED;
+    if (dtype != SOFT_FP64) return dtype == SOFT_MIXED_BF16X3 || dtype == SOFT_MIXED_TF32 ? SOFT_ERR_UNSUPPORTED
+                                                                                       : SOFT_ERR_INVALID_ARG;
+    soft_plan_s *p = new (std::nothrow) soft_plan_s();
+    if (!p) return SOFT_ERR_OUT_OF_MEMORY;
+    p->magic = kPlanMagic;
+    p->B = B;
+    p->dtype = dtype;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return SOFT_ERR_CUDA; }
+
+    const int n = 2 * B;
+    const int R = 2 * B - 1;
+    // Cluster work list, heaviest first: work ~ (B - m) * number of partners.
+    std::vector<int2> cl;
+    cl.reserve((size_t)B * (B + 1) / 2);
+    for (int m = 0; m < B; ++m)
+        for (int mp = 0; mp <= m; ++mp) cl.push_back(make_int2(m, mp));
+    auto weight = [B](const int2 &c) {
+        const int np = (c.x == 0 && c.y == 0) ? 1 : (c.y == 0 || c.x == c.y) ? 4 : 8;
+        return (int64_t)(B - c.x) * np;
+    };
+    std::stable_sort(cl.begin(), cl.end(), [&](const int2 &a, const int2 &b) { return weight(a) > weight(b); });
+    p->ncl = (int)cl.size();
+    std::vector<int64_t> ro((size_t)R * R);
+    for (int m = 1 - B; m <= B - 1; ++m)
+        for (int mp = 1 - B; mp <= B - 1; ++mp) ro[runoff_index(B, m, mp)] = run_start(B, m, mp);
+
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    };
+    alloc((void **)&p->w, sizeof(double) * n);
+    alloc((void **)&p->cosb, sizeof(double) * n);
+    alloc((void **)&p->lcos, sizeof(double) * n);
+    alloc((void **)&p->lsin, sizeof(double) * n);
+    alloc((void **)&p->lfact, sizeof(double) * (n + 1));
+    alloc((void **)&p->clusters, sizeof(int2) * cl.size());
+    alloc((void **)&p->runoff, sizeof(int64_t) * ro.size());
+    alloc((void **)&p->err, sizeof(int));
+    alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
+    if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+
+    e = cudaMemcpy(p->clusters, cl.data(), sizeof(int2) * cl.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->runoff, ro.data(), sizeof(int64_t) * ro.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = launch_tables(B, p->w, p->cosb, p->lcos, p->lsin, p->lfact, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+
+    // One batched 2-D Z2Z plan over the 2B contiguous beta slices.
+    if (cufftCreate(&p->fft) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
+    p->fft_made = true;
+    long long dims[2] = {n, n};
+    size_t work = 0;
+    if (cufftMakePlanMany64(p->fft, 2, dims, nullptr, 1, (long long)n * n, nullptr, 1, (long long)n * n,
+                            CUFFT_Z2Z, n, &work) != CUFFT_SUCCESS) {
+        free_plan(p);
+        return SOFT_ERR_CUDA;
+    }
+    *out = p;
+    return SOFT_OK;
+}
+
+soft_status soft_destroy(soft_plan p) {
+    if (!p) return SOFT_OK;
+    if (!valid(p)) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return SOFT_OK;
+}
+
+int soft_plan_bandwidth(soft_plan p) { return valid(p) ? p->B : -1; }
+
+soft_status soft_plan_sync(soft_plan p) {
+    if (!valid(p)) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_status(e);
+    int h = 0;
+    e = cudaMemcpy(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (h != 0) {
+        cudaMemset(p->err, 0, sizeof(int));
+        return h == 2 ? SOFT_ERR_TIMEOUT : SOFT_ERR_DEVICE;
+    }
+    return SOFT_OK;
+}
+
+soft_status soft_forward(soft_plan p, const double *grid, double *coef, void *stream) {
+    soft_status st = check_plan_args(p, grid, coef);
+    if (st != SOFT_OK) return st;
+    DeviceGuard g(p->device);
+    return run_forward(p, grid, coef, static_cast<cudaStream_t>(stream));
+}
+
+soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *stream) {
+    soft_status st = check_plan_args(p, coef, grid);
+    if (st != SOFT_OK) return st;
+    DeviceGuard g(p->device);
+    return run_inverse(p, coef, grid, static_cast<cudaStream_t>(stream));
+}
+
+soft_status soft_dwt_forward(soft_plan p, const double *S, double *coef, void *stream) {
+    soft_status st = check_plan_args(p, S, coef);
+    if (st != SOFT_OK) return st;
+    DeviceGuard g(p->device);
+    return cuda_status(launch_dwt_forward_fp64(p->tables(), reinterpret_cast<const double2 *>(S),
+                                               reinterpret_cast<double2 *>(coef), static_cast<cudaStream_t>(stream)));
+}
+
+soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *stream) {
+    soft_status st = check_plan_args(p, coef, S);
+    if (st != SOFT_OK) return st;
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_zero_nyquist(p->B, reinterpret_cast<double2 *>(S), s);
+    if (e == cudaSuccess)
+        e = launch_dwt_inverse_fp64(p->tables(), reinterpret_cast<const double2 *>(coef),
+                                    reinterpret_cast<double2 *>(S), s);
+    return cuda_status(e);
+}
+
+soft_status soft_forward_host(soft_plan p, const double *grid_host, double *coef_host, void *stream) {
+    if (!valid(p) || !grid_host || !coef_host) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    soft_status st = ensure_staging(p);
+    if (st != SOFT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(p->stage_grid, grid_host, sizeof(double2) * grid_elems(p->B),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    st = run_forward(p, reinterpret_cast<const double *>(p->stage_grid), reinterpret_cast<double *>(p->stage_coef), s);
+    if (st != SOFT_OK) return st;
+    e = cudaMemcpyAsync(coef_host, p->stage_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B),
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_status(e);
+}
+
+soft_status soft_inverse_host(soft_plan p, const double *coef_host, double *grid_host, void *stream) {
+    if (!valid(p) || !coef_host || !grid_host) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    soft_status st = ensure_staging(p);
+    if (st != SOFT_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(p->stage_coef, coef_host, sizeof(double2) * (size_t)soft_num_coeffs(p->B),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    st = run_inverse(p, reinterpret_cast<const double *>(p->stage_coef), reinterpret_cast<double *>(p->stage_grid), s);
+    if (st != SOFT_OK) return st;
+    e = cudaMemcpyAsync(grid_host, p->stage_grid, sizeof(double2) * grid_elems(p->B), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_status(e);
+}
+
+soft_status soft_plan_enable_timing(soft_plan p, int on) {
+    if (!valid(p)) return SOFT_ERR_INVALID_ARG;
+    p->timing = on != 0;
+    return SOFT_OK;
+}
+
+soft_status soft_plan_read_timing(soft_plan p, double *ms_out, int64_t *counts_out) {
+    if (!valid(p)) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    fold_timing(p);
+    for (int k = 0; k < 4; ++k) {
+        if (ms_out) ms_out[k] = p->ms[k];
+        if (counts_out) counts_out[k] = p->counts[k];
+        p->ms[k] = 0.0;
+        p->counts[k] = 0;
+    }
+    return SOFT_OK;
+}
+
+}  // extern "C"

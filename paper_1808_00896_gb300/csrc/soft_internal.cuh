@@ -1,0 +1,128 @@
+// soft_internal.cuh -- device-side building blocks shared by the DWT kernels.
+//
+// Notation follows Sec. 2 of Lux, Wuelker, Chirikjian, "Parallelization of
+// the FFT on SO(3)": bandwidth B, n = 2B samples per angle, beta_j =
+// (2j+1)pi/(4B), Wigner-d d(l,m,m';beta), order pairs (m,m') with
+// |m|,|m'| < B, degree l from l0 = max(|m|,|m'|) to B-1.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace softgb {
+
+constexpr int kMaxB = 512;
+
+// Per-plan device tables (all FP64 unless stated).
+struct Tables {
+    int B;
+    int ncl;                  // number of symmetry clusters, B(B+1)/2
+    const double *w;          // [2B]  quadrature weights w_B(j), Eq. (weights)
+    const double *cosb;       // [2B]  cos(beta_j)
+    const double *lcos;       // [2B]  log cos(beta_j / 2)
+    const double *lsin;       // [2B]  log sin(beta_j / 2)
+    const double *lfact;      // [2B+1] log(k!)
+    const int2 *clusters;     // [ncl] representatives (m, m'), m >= m' >= 0, heaviest first
+    const int64_t *runoff;    // [(2B-1)^2] start of the l-run of (m,m') in the coefficient array,
+                              //   index (m + B - 1) * (2B - 1) + (m' + B - 1)
+    int *err;                 // device error word (0 = fine)
+};
+
+__host__ __device__ inline int64_t runoff_index(int B, int m, int mp) {
+    return (int64_t)(m + B - 1) * (2 * B - 1) + (mp + B - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Symmetry clusters (Sec. 3, "Communication"): the order pairs whose Wigner-d
+// columns follow from one representative (m, m'), m >= m' >= 0, by the seven
+// relations of Eq. (Wigner_symmetries).  Partner p satisfies
+//   d(l, m_p, m'_p; beta_j) = sign_p * (lpar_p ? (-1)^l : 1) * d(l, m, m'; beta_{j'}),
+//   j' = mirror_p ? 2B-1-j : j            (beta -> pi - beta is j -> 2B-1-j).
+// Clusters have 8 partners, or 4 when m' = 0 or m = m' (> 0), or 1 for (0,0).
+// ---------------------------------------------------------------------------
+struct Partners {
+    int np;
+    int m[8], mp[8];
+    int mirror[8];
+    int lpar[8];
+    double sign[8];
+};
+
+__host__ __device__ inline double neg1pow(int k) { return (k & 1) ? -1.0 : 1.0; }
+
+__host__ __device__ inline Partners make_partners(int m, int mp) {
+    Partners P;
+    int q = 0;
+    auto add = [&](int a, int b, int mir, int lp, double s) {
+        P.m[q] = a; P.mp[q] = b; P.mirror[q] = mir; P.lpar[q] = lp; P.sign[q] = s; ++q;
+    };
+    const double smm = neg1pow(m - mp);  // (-1)^(m-m')
+    if (m == 0 && mp == 0) {
+        add(0, 0, 0, 0, 1.0);
+    } else if (mp == 0) {
+        add(m, 0, 0, 0, 1.0);        // identity
+        add(-m, 0, 0, 0, smm);       // d(l,-m,-m') = (-1)^(m-m') d(l,m,m')
+        add(0, m, 0, 0, smm);        // d(l,m',m)   = (-1)^(m-m') d(l,m,m')
+        add(0, -m, 0, 0, 1.0);       // d(l,-m',-m) = d(l,m,m')
+    } else if (m == mp) {
+        add(m, m, 0, 0, 1.0);
+        add(-m, -m, 0, 0, 1.0);
+        add(-m, m, 1, 1, neg1pow(m));  // d(l,-m,m';b) = (-1)^(l-m') d(l,m,m';pi-b)
+        add(m, -m, 1, 1, neg1pow(m));  // d(l,m,-m';b) = (-1)^(l+m)  d(l,m,m';pi-b)
+    } else {
+        add(m, mp, 0, 0, 1.0);
+        add(-m, -mp, 0, 0, smm);
+        add(mp, m, 0, 0, smm);
+        add(-mp, -m, 0, 0, 1.0);
+        add(-m, mp, 1, 1, neg1pow(mp));  // (-1)^(l-m')
+        add(m, -mp, 1, 1, neg1pow(m));   // (-1)^(l+m)
+        add(-mp, m, 1, 1, neg1pow(mp));  // d(l,-m',m;b) = (-1)^(l-m') d(l,m,m';pi-b)
+        add(mp, -m, 1, 1, neg1pow(m));   // d(l,m',-m;b) = (-1)^(l+m)  d(l,m,m';pi-b)
+    }
+    P.np = q;
+    return P;
+}
+
+// ---------------------------------------------------------------------------
+// Three-term recurrence, Eq. (Wigner_d_recurrence), for l >= 1:
+//   d(l+1) = A_l (cos b - c_l) d(l) - Bc_l d(l-1)
+//   A_l  = (l+1)(2l+1) / sqrt(((l+1)^2-m^2)((l+1)^2-m'^2)),   c_l = m m' / (l(l+1)),
+//   Bc_l = (l+1) sqrt((l^2-m^2)(l^2-m'^2)) / (l sqrt(((l+1)^2-m^2)((l+1)^2-m'^2))).
+// Stored as (A_l, A_l c_l, Bc_l) so that a step is fma(fma(A,x,-Ac), d, -Bc*dprev).
+// The only cluster starting at l = 0 is (0,0), where d(1,0,0) = cos b: entry (1,0,0).
+// At l = l0 > 0 the d(l0-1) coefficient vanishes, consistent with d(l0-1) := 0.
+// ---------------------------------------------------------------------------
+__device__ inline void recurrence_coeffs(int l, int m, int mp, double &A, double &Ac, double &Bc) {
+    if (l == 0) { A = 1.0; Ac = 0.0; Bc = 0.0; return; }
+    const double L1 = l + 1.0, ll = l, mm = m, nn = mp;
+    const double den = sqrt((L1 * L1 - mm * mm) * (L1 * L1 - nn * nn));  // exact integer product
+    const double a = L1 * (2.0 * ll + 1.0) / den;
+    A = a;
+    Ac = a * (mm * nn / (ll * (ll + 1.0)));
+    Bc = L1 * sqrt((ll * ll - mm * mm) * (ll * ll - nn * nn)) / (ll * den);
+}
+
+// Seed d(l0, m, m'; beta_j), l0 = max(|m|,|m'|), for a representative m >= m' >= 0
+// (the "+" case of the paper's first initial condition):
+//   d(m, m, m') = sqrt((2m)! / ((m+m')!(m-m')!)) cos(b/2)^(m+m') sin(b/2)^(m-m'),
+// evaluated as exp of its logarithm so that neither the factorials nor the
+// powers leave the FP64 range; values below ~1e-308 flush to 0.
+__device__ inline double seed_rep(int m, int mp, double lognorm, double lc, double ls) {
+    double lg = lognorm;
+    if (m + mp > 0) lg = fma((double)(m + mp), lc, lg);
+    if (m - mp > 0) lg = fma((double)(m - mp), ls, lg);
+    return exp(lg);
+}
+
+__device__ inline double seed_lognorm(const Tables &tb, int m, int mp) {
+    return 0.5 * (tb.lfact[2 * m] - tb.lfact[m + mp] - tb.lfact[m - mp]);
+}
+
+// Launchers (dwt_fp64.cu).
+cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s);
+cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s);
+cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s);
+cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *lsin, double *lfact,
+                          cudaStream_t s);
+
+}  // namespace softgb
