@@ -72,6 +72,11 @@ int64_t soft_coef_index(int B, int l, int m, int mp);
 /* Human-readable name of a status code (static string, never NULL). */
 const char *soft_status_string(int status);
 
+/* Detail of the most recent failing call on this host thread (which CUDA or
+ * cuFFT call failed and its error text); "" when none.  Valid until the next
+ * library call on the same thread. */
+const char *soft_last_error(void);
+
 /* Create a plan for bandwidth B on the current CUDA device.  Allocates the
  * plan's device workspace ((2B)^3 complex doubles for S plus small tables),
  * builds the cuFFT plan and computes the quadrature weights of Eq. (weights)

@@ -30,6 +30,7 @@ SIGNATURES = {
     "soft_num_coeffs": (_i64, [_i]),
     "soft_coef_index": (_i64, [_i, _i, _i, _i]),
     "soft_status_string": (ctypes.c_char_p, [_i]),
+    "soft_last_error": (ctypes.c_char_p, []),
     "soft_plan_create": (_i, [ctypes.POINTER(_vp), _i, _i]),
     "soft_destroy": (_i, [_vp]),
     "soft_plan_bandwidth": (_i, [_vp]),
@@ -50,7 +51,8 @@ _lib = None
 class SoftError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {status_string(status)} ({status})")
+        detail = load().soft_last_error().decode()
+        super().__init__(f"{what}: {status_string(status)} ({status})" + (f" [{detail}]" if detail else ""))
 
 
 def load(path: str | None = None) -> ctypes.CDLL:

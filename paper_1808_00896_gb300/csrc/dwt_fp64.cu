@@ -16,7 +16,6 @@
 #include "soft_internal.cuh"
 
 #include <algorithm>
-#include <mutex>
 
 namespace softgb {
 
@@ -297,22 +296,12 @@ __global__ void __launch_bounds__(NT) dwt_inverse_fp64_kernel(Tables tb, const d
     }
 }
 
-template <typename K>
-cudaError_t set_smem_once(K kernel, size_t bytes, std::once_flag &flag) {
-    cudaError_t err = cudaSuccess;
-    std::call_once(flag, [&] {
-        err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    });
-    (void)bytes;
-    return err;
-}
-
 template <int NT, int JPT>
 cudaError_t run_forward(const Tables &tb, const double2 *S, double *coef, cudaStream_t s) {
-    static std::once_flag flag;
     const int B = tb.B, n = 2 * B;
     const size_t bytes = sizeof(double) * ((size_t)n * 16 + (size_t)(NT / 16) * n + 4 * (size_t)B);
-    cudaError_t e = set_smem_once(dwt_forward_fp64_kernel<NT, JPT>, bytes, flag);
+    cudaError_t e = cudaFuncSetAttribute(dwt_forward_fp64_kernel<NT, JPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     dwt_forward_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, S, coef);
     return cudaGetLastError();
@@ -320,10 +309,10 @@ cudaError_t run_forward(const Tables &tb, const double2 *S, double *coef, cudaSt
 
 template <int NT, int JPT>
 cudaError_t run_inverse(const Tables &tb, const double *coef, double2 *S, cudaStream_t s) {
-    static std::once_flag flag;
     const int B = tb.B;
     const size_t bytes = sizeof(double) * ((size_t)B * 16 + 3 * (size_t)B);
-    cudaError_t e = set_smem_once(dwt_inverse_fp64_kernel<NT, JPT>, bytes, flag);
+    cudaError_t e = cudaFuncSetAttribute(dwt_inverse_fp64_kernel<NT, JPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     dwt_inverse_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, coef, S);
     return cudaGetLastError();

@@ -12,6 +12,7 @@
 #include <cufft.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -69,10 +70,29 @@ struct DeviceGuard {
     }
 };
 
+thread_local char g_last_error[256] = "";
+
+void set_error(const char *where, const char *what) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", where, what);
+}
+
+soft_status fail_cuda(const char *where, cudaError_t e) {
+    set_error(where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SOFT_ERR_OUT_OF_MEMORY : SOFT_ERR_CUDA;
+}
+
+soft_status fail_cufft(const char *where, cufftResult r) {
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "cufftResult %d", (int)r);
+    set_error(where, buf);
+    return SOFT_ERR_CUDA;
+}
+
 bool valid(const soft_plan_s *p) { return p != nullptr && p->magic == kPlanMagic; }
 bool aligned16(const void *ptr) { return ptr != nullptr && (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
 soft_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SOFT_OK;
+    set_error("CUDA", cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) return SOFT_ERR_OUT_OF_MEMORY;
     return SOFT_ERR_CUDA;
 }
@@ -157,30 +177,33 @@ void free_plan(soft_plan_s *p) {
 soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s) {
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
-    if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return SOFT_ERR_CUDA;
+    cufftResult r = cufftSetStream(p->fft, s);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
     // S(m,m';j) = sum_{i,k} f exp(+i(m alpha_i + m' gamma_k)): cuFFT's INVERSE direction, unnormalised.
     cufftDoubleComplex *in = reinterpret_cast<cufftDoubleComplex *>(const_cast<double *>(grid));
-    if (cufftExecZ2Z(p->fft, in, reinterpret_cast<cufftDoubleComplex *>(p->S), CUFFT_INVERSE) != CUFFT_SUCCESS)
-        return SOFT_ERR_CUDA;
+    r = cufftExecZ2Z(p->fft, in, reinterpret_cast<cufftDoubleComplex *>(p->S), CUFFT_INVERSE);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (forward slices)", r);
     if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = launch_dwt_forward_fp64(p->tables(), p->S, reinterpret_cast<double2 *>(coef), s);
+    if (e != cudaSuccess) return fail_cuda("DWT kernel launch", e);
     if (ev) cudaEventRecord(ev[2], s);
-    return cuda_status(e);
+    return SOFT_OK;
 }
 
 soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s) {
     cudaEvent_t *ev = timing_slot(p, 1);
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = launch_zero_nyquist(p->B, p->S, s);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return fail_cuda("S clearing kernel launch", e);
     e = launch_dwt_inverse_fp64(p->tables(), reinterpret_cast<const double2 *>(coef), p->S, s);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return fail_cuda("iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
-    if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return SOFT_ERR_CUDA;
+    cufftResult r = cufftSetStream(p->fft, s);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
     // f = sum_{m,m'} S exp(-i(m alpha_i + m' gamma_k)): cuFFT's FORWARD direction, unnormalised.
-    if (cufftExecZ2Z(p->fft, reinterpret_cast<cufftDoubleComplex *>(p->S),
-                     reinterpret_cast<cufftDoubleComplex *>(grid), CUFFT_FORWARD) != CUFFT_SUCCESS)
-        return SOFT_ERR_CUDA;
+    r = cufftExecZ2Z(p->fft, reinterpret_cast<cufftDoubleComplex *>(p->S),
+                     reinterpret_cast<cufftDoubleComplex *>(grid), CUFFT_FORWARD);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (inverse slices)", r);
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
 }
@@ -219,6 +242,8 @@ int64_t soft_coef_index(int B, int l, int m, int mp) {
     if (l < l0 || l >= B) return -1;
     return run_start(B, m, mp) + (l - l0);
 }
+
+const char *soft_last_error(void) { return g_last_error; }
 
 const char *soft_status_string(int status) {
     switch (status) {
