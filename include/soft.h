@@ -116,6 +116,26 @@ soft_status soft_dwt_forward(soft_plan p, const double *S, double *coef, void *s
  * every entry written, the -B rows/columns set to 0). */
 soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *stream);
 
+/* The DWT step alone, without a plan and without allocating any memory
+ * (the paper has no counterpart: this is a deployment variant of
+ * soft_dwt_forward).  For callers that cannot call cudaMalloc -- a plug-in
+ * whose host application owns the whole device memory pool, or a fixed-budget
+ * pipeline that allocates only at start-up and cannot take cudaMalloc's
+ * implicit synchronisation later -- and so cannot create a plan.
+ * S (device, layout above, read only) -> coef (device), bandwidth B on the
+ * current device, asynchronous on `stream`; same result as soft_dwt_forward.
+ * Its working tables live in a fixed 2.3 MiB static device array that every
+ * GPU loading the library keeps until exit; they are rebuilt on `stream` at
+ * every call.  Limits and rules:
+ *   - B must be <= 256; larger B returns SOFT_ERR_UNSUPPORTED (detail in
+ *     soft_last_error()).
+ *   - The first call on a device looks up the array's device address (one-time
+ *     set-up); make that first call before any stream capture.
+ *   - All calls share the array: calls whose GPU work overlaps (different
+ *     streams, or devices sharing it) race and must be serialised by the caller.
+ *   - No cudaMalloc, cudaFree or allocating library call is made. */
+soft_status soft_dwt_forward_noalloc(int B, const double *S, double *coef, void *stream);
+
 /* Host-buffer forms: grid_host / coef_host are HOST pointers (pageable or
  * pinned).  The call copies the input to plan-owned device staging buffers
  * (allocated on first use), runs the transform on `stream`, copies the

@@ -39,6 +39,7 @@ SIGNATURES = {
     "soft_inverse": (_i, [_vp, _vp, _vp, _vp]),
     "soft_dwt_forward": (_i, [_vp, _vp, _vp, _vp]),
     "soft_dwt_inverse": (_i, [_vp, _vp, _vp, _vp]),
+    "soft_dwt_forward_noalloc": (_i, [_i, _vp, _vp, _vp]),
     "soft_forward_host": (_i, [_vp, _vp, _vp, _vp]),
     "soft_inverse_host": (_i, [_vp, _vp, _vp, _vp]),
     "soft_plan_enable_timing": (_i, [_vp, _i]),
@@ -122,6 +123,11 @@ def soft_dwt_forward(plan: int, S_ptr: int, coef_ptr: int, stream: int = 0) -> i
 
 def soft_dwt_inverse(plan: int, coef_ptr: int, S_ptr: int, stream: int = 0) -> int:
     return load().soft_dwt_inverse(plan, coef_ptr, S_ptr, stream)
+
+
+def soft_dwt_forward_noalloc(B: int, S_ptr: int, coef_ptr: int, stream: int = 0) -> int:
+    """Forward DWT without a plan or any allocation (B <= 256); see include/soft.h."""
+    return load().soft_dwt_forward_noalloc(B, S_ptr, coef_ptr, stream)
 
 
 def soft_forward_host(plan: int, grid_ptr: int, coef_ptr: int, stream: int = 0) -> int:

@@ -89,6 +89,14 @@ soft_status fail_cufft(const char *where, cufftResult r) {
 }
 
 bool valid(const soft_plan_s *p) { return p != nullptr && p->magic == kPlanMagic; }
+
+}  // namespace
+
+namespace softgb {
+void set_last_error_message(const char *where, const char *what) { set_error(where, what); }
+}  // namespace softgb
+
+namespace {
 bool aligned16(const void *ptr) { return ptr != nullptr && (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
 soft_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SOFT_OK;

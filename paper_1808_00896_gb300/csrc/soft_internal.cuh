@@ -118,6 +118,9 @@ __device__ inline double seed_lognorm(const Tables &tb, int m, int mp) {
     return 0.5 * (tb.lfact[2 * m] - tb.lfact[m + mp] - tb.lfact[m - mp]);
 }
 
+// Records the detail returned by soft_last_error() on this host thread (soft_api.cu).
+void set_last_error_message(const char *where, const char *what);
+
 // Launchers (dwt_fp64.cu).
 cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s);
 cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s);
