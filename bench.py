@@ -34,14 +34,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # name: (B, coefficient kind, description)
-    "b16": (16, "uniform", "FP64 SOFT forward+inverse, B=16, 32^3 complex128 grid, U(-1,1) coefficients"),
-    "b64": (64, "gauss_decay", "FP64 SOFT forward+inverse, B=64, 128^3 complex128 grid (32 MiB), "
-                               "complex Gaussian coefficients x 1/(l+1)"),
-    "b128": (128, "gauss_decay", "FP64 SOFT forward+inverse, B=128, 256^3 complex128 grid (256 MiB)"),
-    "b256": (256, "gauss_decay", "FP64 SOFT forward+inverse, B=256, 512^3 complex128 grid (2 GiB)"),
-    "b512": (512, "gauss_decay", "FP64 SOFT forward+inverse, B=512, 1024^3 complex128 grid (16 GiB)"),
+    # name: (B, dtype, coefficient kind, description)
+    "b16": (16, "fp64", "uniform", "FP64 SOFT forward+inverse, B=16, 32^3 complex128 grid, U(-1,1) coefficients"),
+    "b64": (64, "fp64", "gauss_decay", "FP64 SOFT forward+inverse, B=64, 128^3 complex128 grid (32 MiB), "
+                                       "complex Gaussian coefficients x 1/(l+1)"),
+    "b128": (128, "fp64", "gauss_decay", "FP64 SOFT forward+inverse, B=128, 256^3 complex128 grid (256 MiB)"),
+    "b256": (256, "fp64", "gauss_decay", "FP64 SOFT forward+inverse, B=256, 512^3 complex128 grid (2 GiB)"),
+    "b512": (512, "fp64", "gauss_decay", "FP64 SOFT forward+inverse, B=512, 1024^3 complex128 grid (16 GiB)"),
 }
+for _B in (64, 128, 256, 512):
+    for _m, _d in (("bf16x3", "split-BF16x3"), ("tf32", "TF32")):
+        WORKLOADS[f"b{_B}_{_m}"] = (_B, _m, "gauss_decay",
+                                    f"mixed SOFT forward+inverse, B={_B}, {_d} contraction on tcgen05 tensor cores, "
+                                    f"FP64 Wigner-d recurrence, FP32 2-D FFTs; complex128 in/out")
 METRIC = "SOFT fwd+inv transforms/s"
 UNIT = "fwd+inv pairs/s"
 L2_BYTES = 129 * 2 ** 20
@@ -170,7 +175,7 @@ def run_reference(args) -> None:
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    B, kind, desc = WORKLOADS[args.workload]
+    B, _, kind, desc = WORKLOADS[args.workload]
     import oracle
     from paper_1808_00896_gb300 import synth
     oracle.build()
@@ -214,7 +219,7 @@ def run_ours(args) -> None:
     torch.cuda.set_device(dev)
     build_mod.build()
 
-    B, kind, desc = WORKLOADS[args.workload]
+    B, dtype, kind, desc = WORKLOADS[args.workload]
     n = 2 * B
     grid_bytes = 16 * n ** 3
     coef_bytes = 16 * synth.num_coeffs(B)
@@ -222,7 +227,7 @@ def run_ours(args) -> None:
     if B >= 256:
         R = 1  # one input already exceeds L2 several times over
 
-    plan = Plan(B, "fp64", device=dev)
+    plan = Plan(B, dtype, device=dev)
     coefs = [torch.from_numpy(synth.coefficients(B, kind, seed=synth.BASE_SEED + 100 * rank + r)).to(dev)
              for r in range(R)]
     grids = [plan.inverse(c) for c in coefs]
@@ -295,12 +300,15 @@ def run_ours(args) -> None:
 
     # Roofline of the dominant kernel, from the library's CUDA events.
     fl = dwt_flops(B)
-    algo = fl["contraction"] + fl["recurrence"]
     fwd_ms = phase_ms[1] / max(1, phase_cnt[1])
     inv_ms = phase_ms[2] / max(1, phase_cnt[2])
-    dom, dom_ms = ("dwt_forward_fp64_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else \
-        ("dwt_inverse_fp64_kernel", inv_ms)
+    kname = "fp64" if dtype == "fp64" else "mixed"
+    dom, dom_ms = (f"dwt_forward_{kname}_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else \
+        (f"dwt_inverse_{kname}_kernel", inv_ms)
     peak_gflops = FP64_FLOPS_PER_SM_CLK * N_SM * SM_MAX_MHZ * 1e6 / 1e9
+    # FP64 path: contraction + recurrence on the FP64 pipe.  Mixed modes: the
+    # FP64 recurrence is the binding term (the contraction runs on tensor cores).
+    algo = fl["contraction"] + fl["recurrence"] if dtype == "fp64" else fl["recurrence"]
     achieved = algo / (dom_ms * 1e-3) / 1e9
     tr = TRAFFIC.get((dom, B))
     traffic = tr[0] if (tr and tr[1] == kernel_source_sha()) else None
@@ -311,6 +319,11 @@ def run_ours(args) -> None:
                 "phase_ms_per_launch": {"fft_forward": phase_ms[0] / max(1, phase_cnt[0]),
                                         "dwt_forward": fwd_ms, "dwt_inverse": inv_ms,
                                         "fft_inverse": phase_ms[3] / max(1, phase_cnt[3])}}
+    if dtype != "fp64":
+        mult = 3 if dtype == "bf16x3" else 1
+        roofline["tensor_tflops_achieved"] = mult * fl["contraction"] / (dom_ms * 1e-3) / 1e12
+        roofline["note"] = ("mixed mode: frac is the FP64 Wigner-d recurrence (5 flop per T entry) against the "
+                            "FP64 pipe; tensor_tflops_achieved counts the contraction's tensor-core flops")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -323,8 +336,8 @@ def run_ours(args) -> None:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "B": B, "coefficients": kind, "inputs_rotated": R,
+            "vs_baseline": None, "dtype": "f64" if dtype == "fp64" else dtype, "data": "synthetic",
+            "config": {"workload": desc, "B": B, "mode": dtype, "coefficients": kind, "inputs_rotated": R,
                        "l2": f"{R} rotating input sets of {(grid_bytes + coef_bytes) / 2**20:.1f} MiB "
                              f"(> 129 MB L2 per pass)" if R > 1 else "single input larger than L2",
                        "parallelism": f"replicas x{world}"},
@@ -352,8 +365,9 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     if args.steps is None:
-        args.steps = {"ours": {"b16": 2000, "b64": 400, "b128": 60, "b256": 10, "b512": 3},
-                      "reference": {"b16": 50, "b64": 20, "b128": 4, "b256": 1, "b512": 1}}[args.impl][args.workload]
+        B = WORKLOADS[args.workload][0]
+        args.steps = {"ours": {16: 2000, 64: 400, 128: 60, 256: 10, 512: 3},
+                      "reference": {16: 50, 64: 20, 128: 4, 256: 1, 512: 1}}[args.impl][B]
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -63,30 +63,6 @@ __global__ void zero_nyquist_kernel(int B, double2 *S) {
     }
 }
 
-// Per-CTA cluster prologue: partner table, run offsets, recurrence coefficients.
-struct ClusterSmem {
-    int np;
-    int pm[8], pmp[8], mir[8], lpar[8];
-    double sign[8];
-    int64_t off[8];
-};
-
-__device__ void load_cluster(const Tables &tb, int m, int mp, ClusterSmem &cs) {
-    if (threadIdx.x == 0) {
-        const Partners P = make_partners(m, mp);
-        cs.np = P.np;
-        for (int p = 0; p < 8; ++p) {
-            const bool on = p < P.np;
-            cs.pm[p] = on ? P.m[p] : 0;
-            cs.pmp[p] = on ? P.mp[p] : 0;
-            cs.mir[p] = on ? P.mirror[p] : 0;
-            cs.lpar[p] = on ? P.lpar[p] : 0;
-            cs.sign[p] = on ? P.sign[p] : 0.0;
-            cs.off[p] = on ? tb.runoff[runoff_index(tb.B, P.m[p], P.mp[p])] : 0;
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Forward DWT.  NT threads, LT = NT/16 degrees per tile, JPT beta samples per
 // thread in the recurrence phase.

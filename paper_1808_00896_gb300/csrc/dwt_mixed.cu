@@ -1,0 +1,430 @@
+// dwt_mixed.cu -- mixed-precision DWT / iDWT on the tcgen05 tensor cores.
+//
+// Same mathematics as dwt_fp64.cu (Sec. 2.4: f = V_B T_B W_B S per order
+// pair, S = T_B^T f), with the contraction moved to the tensor cores:
+//   * the Wigner-d block T is generated on the fly by the FP64 three-term
+//     recurrence of Eq. (Wigner_d_recurrence) from log-domain seeds, one
+//     column block per symmetry cluster (Sec. 3), exactly as in the FP64 path;
+//   * each FP64 entry is narrowed with integer bit operations (the FP64 pipe
+//     stays free for the recurrence) and stored in shared memory as the
+//     tensor-core A operand, either split into BF16 hi + lo (mode BF16X3:
+//     three MMAs hi*hi + hi*lo + lo*hi per K step, ~2^-16 relative products)
+//     or as TF32 (one MMA per K step, ~2^-11);
+//   * the cluster's partners (8 x re/im = the N = 16 columns) are the B operand;
+//   * tcgen05.mma accumulates in FP32 in TMEM (M = 128 rows, N = 16); the
+//     epilogue applies V_l and the partner signs in FP64.
+// Forward: M = degrees l (tiles of 128), K = beta samples (chunks of 128);
+// the recurrence state of every beta sample is carried across degree tiles in
+// shared memory.  Inverse: M = beta samples (tiles of 128), K = degrees
+// (chunks of 128); each thread owns one beta sample and walks l.
+// The quadrature weight w_B(j) is folded into the forward's seeds (the
+// recurrence is linear in d), so the forward reads S unscaled.
+//
+// S here is the mixed plan's FP32 workspace in layout [m mod 2B][m' mod 2B][j]
+// (beta fastest), written and read by cuFFT C2C with strided layouts, so that
+// the per-partner loads and stores of 128 beta samples are contiguous.
+#include "soft.h"
+#include "soft_internal.cuh"
+#include "tcgen05.cuh"
+
+#include <algorithm>
+
+namespace softgb {
+namespace {
+
+constexpr int kNT = 128;       // threads per CTA: one warpgroup = the 128 TMEM lanes of the tile
+constexpr int kTile = 128;     // M rows per tensor-core tile
+constexpr int kChunk = 128;    // K elements staged per round
+constexpr int kNCols = 16;     // N: 8 partners x (re, im)
+constexpr uint32_t kTmemCols = 32;
+constexpr uint32_t kWaitPolls = 1u << 22;
+
+__device__ __forceinline__ int mod_n(int a, int n) { return a < 0 ? a + n : a; }
+
+// Shared operand buffers for one K chunk.
+template <int MODE>
+struct Operands {
+    static constexpr int EB = MODE == SOFT_MIXED_TF32 ? 4 : 2;        // bytes per element
+    static constexpr int A_BYTES = kTile * kChunk * EB;              // one A plane
+    static constexpr int B_BYTES = kNCols * kChunk * EB;             // one B plane
+    static constexpr int PLANES = MODE == SOFT_MIXED_TF32 ? 1 : 2;   // (hi, lo) for BF16X3
+    static constexpr int BYTES = PLANES * (A_BYTES + B_BYTES);
+};
+
+// Store one value into plane(s) of an operand tile at (r, k).
+template <int MODE>
+__device__ __forceinline__ void put(unsigned char *plane0, int plane_bytes, int rows, int r, int k, float v) {
+    if (MODE == SOFT_MIXED_TF32) {
+        *reinterpret_cast<float *>(plane0 + tc::kmajor_offset(r, k, rows, 4)) = tc::round_tf32(v);
+    } else {
+        uint16_t hi, lo;
+        tc::split_bf16(v, hi, lo);
+        const uint32_t o = tc::kmajor_offset(r, k, rows, 2);
+        *reinterpret_cast<uint16_t *>(plane0 + o) = hi;
+        *reinterpret_cast<uint16_t *>(plane0 + plane_bytes + o) = lo;
+    }
+}
+
+// Issue the MMAs of one K chunk (thread 0 only) and commit them to mbar.
+template <int MODE>
+__device__ __forceinline__ void issue_chunk(uint32_t tmem, const unsigned char *A, const unsigned char *Bop,
+                                            bool first, uint64_t *mbar) {
+    using O = Operands<MODE>;
+    tc::fence_after_sync();
+    const uint32_t abase = tc::smem_u32(A), bbase = tc::smem_u32(Bop);
+    constexpr uint32_t LBO_A = kTile * 16, LBO_B = kNCols * 16, SBO = 128;
+    constexpr int KSTEPS = kChunk * O::EB / 32;  // 32 bytes of K per MMA
+    if (MODE == SOFT_MIXED_TF32) {
+        constexpr uint32_t idesc = tc::instr_desc(2, kTile, kNCols);
+        for (int s = 0; s < KSTEPS; ++s) {
+            const uint64_t ad = tc::smem_desc(abase + s * 2 * LBO_A, LBO_A, SBO);
+            const uint64_t bd = tc::smem_desc(bbase + s * 2 * LBO_B, LBO_B, SBO);
+            tc::mma_tf32(tmem, ad, bd, idesc, (first && s == 0) ? 0u : 1u);
+        }
+    } else {
+        constexpr uint32_t idesc = tc::instr_desc(1, kTile, kNCols);
+        const uint32_t alo = abase + O::A_BYTES, blo = bbase + O::B_BYTES;
+        for (int s = 0; s < KSTEPS; ++s) {
+            const uint32_t ao = s * 2 * LBO_A, bo = s * 2 * LBO_B;
+            tc::mma_bf16(tmem, tc::smem_desc(abase + ao, LBO_A, SBO), tc::smem_desc(bbase + bo, LBO_B, SBO), idesc,
+                         (first && s == 0) ? 0u : 1u);
+            tc::mma_bf16(tmem, tc::smem_desc(abase + ao, LBO_A, SBO), tc::smem_desc(blo + bo, LBO_B, SBO), idesc, 1u);
+            tc::mma_bf16(tmem, tc::smem_desc(alo + ao, LBO_A, SBO), tc::smem_desc(bbase + bo, LBO_B, SBO), idesc, 1u);
+        }
+    }
+    tc::mma_commit(mbar);
+}
+
+struct MixedTables {
+    Tables tb;
+    const double *lw;  // [2B] log w_B(j)
+};
+
+// ---------------------------------------------------------------------------
+// Forward DWT (mixed).  One CTA per cluster.
+//   dynamic smem: operands | dprev[2B] | dcur[2B] | rA,rAc,rBc,rV [B each]
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, const float2 *__restrict__ S,
+                                                                 double *__restrict__ coef) {
+    using O = Operands<MODE>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ ClusterSmem cs;
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mbar;
+    const Tables &tb = mt.tb;
+    const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5;
+    const int2 rep = tb.clusters[blockIdx.x];
+    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+
+    unsigned char *A = smem;                    // A planes (T tile), then B planes (X chunk)
+    unsigned char *X = smem + O::PLANES * O::A_BYTES;
+    double *dprev = reinterpret_cast<double *>(smem + O::BYTES);
+    double *dcur = dprev + n;
+    double *rA = dcur + n, *rAc = rA + B, *rBc = rAc + B, *rV = rBc + B;
+
+    load_cluster(tb, m, mp, cs);
+    for (int t = tid; t < L; t += kNT) {
+        double a, ac, bc;
+        recurrence_coeffs(l0 + t, m, mp, a, ac, bc);
+        rA[t] = a; rAc[t] = ac; rBc[t] = bc;
+        rV[t] = (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B);
+    }
+    {
+        const double lognorm = seed_lognorm(tb, m, mp);
+        for (int j = tid; j < n; j += kNT) {
+            // w_B(j) d(l0,m,m';beta_j): the weight enters through the seed's logarithm
+            dcur[j] = seed_rep(m, mp, lognorm + mt.lw[j], tb.lcos[j], tb.lsin[j]);
+            dprev[j] = 0.0;
+        }
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const int np = cs.np;
+    const int nchunks = (n + kChunk - 1) / kChunk;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int lb = l0; lb < B && ok; lb += kTile) {
+        const int rows = min(kTile, B - lb);
+        for (int c = 0; c < nchunks && ok; ++c) {
+            // A: column tid of the tile = beta sample j; rows = degrees lb..lb+rows-1.
+            const int j = c * kChunk + tid;
+            if (j < n) {
+                const double x = tb.cosb[j];
+                double dc = dcur[j], dp = dprev[j];
+                for (int r = 0; r < rows; ++r) {
+                    put<MODE>(A, O::A_BYTES, kTile, r, tid, tc::f64_to_f32_trunc(dc));
+                    const int q = lb + r - l0;
+                    const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -rBc[q] * dp);
+                    dp = dc;
+                    dc = nx;
+                }
+                for (int r = rows; r < kTile; ++r) put<MODE>(A, O::A_BYTES, kTile, r, tid, 0.0f);
+                dcur[j] = dc;
+                dprev[j] = dp;
+            } else {
+                for (int r = 0; r < kTile; ++r) put<MODE>(A, O::A_BYTES, kTile, r, tid, 0.0f);
+            }
+            // B: X chunk, row 2p / 2p+1 = re / im of partner p, k = beta sample in chunk.
+            for (int e = tid; e < 8 * kChunk; e += kNT) {
+                const int p = e / kChunk, k = e % kChunk, jj = c * kChunk + k;
+                float2 v = make_float2(0.f, 0.f);
+                if (p < np && jj < n) {
+                    const int src = cs.mir[p] ? n - 1 - jj : jj;
+                    v = S[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + src];
+                }
+                put<MODE>(X, O::B_BYTES, kNCols, 2 * p, k, v.x);
+                put<MODE>(X, O::B_BYTES, kNCols, 2 * p + 1, k, v.y);
+            }
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) issue_chunk<MODE>(tmem, A, X, c == 0, &mbar);
+            const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
+            phase ^= 1u;
+            ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
+        }
+        if (!ok) break;
+        // Epilogue: TMEM lane = row = degree lb + tid; 16 FP32 columns.
+        tc::fence_after_sync();
+        uint32_t d[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), d);
+        if (tid < rows) {
+            const int l = lb + tid, q = l - l0;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                if (p >= np) break;
+                const double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
+                const double v = rV[q] * sg;
+                double2 out;
+                out.x = v * tc::f32_to_f64(__uint_as_float(d[2 * p]));
+                out.y = v * tc::f32_to_f64(__uint_as_float(d[2 * p + 1]));
+                *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p] + q)) = out;
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (!ok && tid == 0 && tb.err) atomicExch(tb.err, 2);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// Inverse DWT (mixed).  One CTA per cluster, looping over tiles of 128 beta
+// samples; K = degrees in chunks of 128.
+//   dynamic smem: operands | rA,rAc,rBc [B each]
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, const double *__restrict__ coef,
+                                                                 float2 *__restrict__ S) {
+    using O = Operands<MODE>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ ClusterSmem cs;
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mbar;
+    const Tables &tb = mt.tb;
+    const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5;
+    const int2 rep = tb.clusters[blockIdx.x];
+    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+
+    unsigned char *A = smem;
+    unsigned char *F = smem + O::PLANES * O::A_BYTES;
+    double *rA = reinterpret_cast<double *>(smem + O::BYTES), *rAc = rA + B, *rBc = rAc + B;
+
+    load_cluster(tb, m, mp, cs);
+    for (int t = tid; t < L; t += kNT) {
+        double a, ac, bc;
+        recurrence_coeffs(l0 + t, m, mp, a, ac, bc);
+        rA[t] = a; rAc[t] = ac; rBc[t] = bc;
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const int np = cs.np;
+    const double lognorm = seed_lognorm(tb, m, mp);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int jb = 0; jb < n && ok; jb += kTile) {
+        const int j = jb + tid;
+        const bool active = j < n;
+        double x = 0.0, dc = 0.0, dp = 0.0;
+        if (active) {
+            x = tb.cosb[j];
+            dc = seed_rep(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
+        }
+        for (int lb = l0, c = 0; lb < B && ok; lb += kChunk, ++c) {
+            const int cnt = min(kChunk, B - lb);
+            // A: row tid = beta sample j, K = degrees lb..lb+cnt-1.
+            for (int k = 0; k < kChunk; ++k) {
+                float v = 0.f;
+                if (active && k < cnt) {
+                    v = tc::f64_to_f32_trunc(dc);
+                    const int q = lb + k - l0;
+                    const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -rBc[q] * dp);
+                    dp = dc;
+                    dc = nx;
+                }
+                put<MODE>(A, O::A_BYTES, kTile, tid, k, v);
+            }
+            // B: F chunk, row 2p / 2p+1 = sign-folded re / im of partner p at degree lb + k.
+            for (int e = tid; e < 8 * kChunk; e += kNT) {
+                const int p = e / kChunk, k = e % kChunk;
+                float re = 0.f, im = 0.f;
+                if (p < np && k < cnt) {
+                    const int l = lb + k;
+                    const double2 cv = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + (l - l0)));
+                    const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
+                    re = tc::f64_to_f32_rn(neg ? -cv.x : cv.x);
+                    im = tc::f64_to_f32_rn(neg ? -cv.y : cv.y);
+                }
+                put<MODE>(F, O::B_BYTES, kNCols, 2 * p, k, re);
+                put<MODE>(F, O::B_BYTES, kNCols, 2 * p + 1, k, im);
+            }
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) issue_chunk<MODE>(tmem, A, F, c == 0, &mbar);
+            const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
+            phase ^= 1u;
+            ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
+        }
+        if (!ok) break;
+        tc::fence_after_sync();
+        uint32_t d[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), d);
+        if (active) {
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                if (p >= np) break;
+                const int jj = cs.mir[p] ? n - 1 - j : j;
+                S[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + jj] =
+                    make_float2(__uint_as_float(d[2 * p]), __uint_as_float(d[2 * p + 1]));
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (!ok && tid == 0 && tb.err) atomicExch(tb.err, 2);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// log w_B(j) for the forward's weighted seeds.
+__global__ void log_weights_kernel(int n, const double *w, double *lw) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) lw[t] = log(w[t]);
+}
+
+// Entries with m or m' = -B (index B) of the [m][m'][j] FP32 workspace.
+__global__ void zero_nyquist32_kernel(int B, float2 *S) {
+    const int n = 2 * B;
+    const int64_t total = (int64_t)(2 * n - 1) * n;  // row mi = B (n*n entries) is handled as n rows of n
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int rowi = (int)(e / n), j = (int)(e % n);
+        int64_t idx;
+        if (rowi < n) idx = ((int64_t)B * n + rowi) * n + j;                    // mi = B, mk = rowi
+        else { const int c = rowi - n; idx = ((int64_t)(c < B ? c : c + 1) * n + B) * n + j; }  // mk = B
+        S[idx] = make_float2(0.f, 0.f);
+    }
+}
+
+__global__ void f64_to_f32_kernel(const double2 *__restrict__ in, float2 *__restrict__ out, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = in[i];
+        out[i] = make_float2(tc::f64_to_f32_rn(v.x), tc::f64_to_f32_rn(v.y));
+    }
+}
+
+__global__ void f32_to_f64_kernel(const float2 *__restrict__ in, double2 *__restrict__ out, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = in[i];
+        out[i] = make_double2(tc::f32_to_f64(v.x), tc::f32_to_f64(v.y));
+    }
+}
+
+int grid_for(int64_t count) { return (int)std::min<int64_t>((count + 255) / 256, 152 * 16); }
+
+}  // namespace
+
+size_t mixed_forward_smem(int mode, int B) {
+    const size_t ops = mode == SOFT_MIXED_TF32 ? Operands<SOFT_MIXED_TF32>::BYTES : Operands<SOFT_MIXED_BF16X3>::BYTES;
+    return ops + sizeof(double) * (2 * (size_t)(2 * B) + 4 * (size_t)B);
+}
+
+size_t mixed_inverse_smem(int mode, int B) {
+    const size_t ops = mode == SOFT_MIXED_TF32 ? Operands<SOFT_MIXED_TF32>::BYTES : Operands<SOFT_MIXED_BF16X3>::BYTES;
+    return ops + sizeof(double) * 3 * (size_t)B;
+}
+
+cudaError_t launch_log_weights(int B, const double *w, double *lw, cudaStream_t s) {
+    const int n = 2 * B;
+    log_weights_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, w, lw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dwt_forward_mixed(int mode, const Tables &tb, const double *lw, const float2 *S, double *coef,
+                                     cudaStream_t s) {
+    MixedTables mt{tb, lw};
+    const size_t bytes = mixed_forward_smem(mode, tb.B);
+    cudaError_t e;
+    if (mode == SOFT_MIXED_TF32) {
+        e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<SOFT_MIXED_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
+        if (e != cudaSuccess) return e;
+        dwt_forward_mixed_kernel<SOFT_MIXED_TF32><<<tb.ncl, kNT, bytes, s>>>(mt, S, coef);
+    } else {
+        e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<SOFT_MIXED_BF16X3>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        dwt_forward_mixed_kernel<SOFT_MIXED_BF16X3><<<tb.ncl, kNT, bytes, s>>>(mt, S, coef);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s) {
+    MixedTables mt{tb, nullptr};
+    const size_t bytes = mixed_inverse_smem(mode, tb.B);
+    cudaError_t e;
+    if (mode == SOFT_MIXED_TF32) {
+        e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<SOFT_MIXED_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
+        if (e != cudaSuccess) return e;
+        dwt_inverse_mixed_kernel<SOFT_MIXED_TF32><<<tb.ncl, kNT, bytes, s>>>(mt, coef, S);
+    } else {
+        e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<SOFT_MIXED_BF16X3>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        dwt_inverse_mixed_kernel<SOFT_MIXED_BF16X3><<<tb.ncl, kNT, bytes, s>>>(mt, coef, S);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_nyquist32(int B, float2 *S, cudaStream_t s) {
+    const int n = 2 * B;
+    zero_nyquist32_kernel<<<grid_for((int64_t)(2 * n - 1) * n), 256, 0, s>>>(B, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_f32(const double2 *in, float2 *out, int64_t count, cudaStream_t s) {
+    f64_to_f32_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const float2 *in, double2 *out, int64_t count, cudaStream_t s) {
+    f32_to_f64_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+}  // namespace softgb

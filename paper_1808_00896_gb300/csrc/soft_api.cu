@@ -37,6 +37,11 @@ struct soft_plan_s {
     int *err;
     cufftHandle fft;
     bool fft_made;
+    // Mixed-precision plans: FP32 grid staging and S in layout [m][m'][j], FP32 cuFFT plans.
+    double *lw;
+    float2 *g32, *S32;
+    cufftHandle fft32f, fft32i;
+    bool fft32f_made, fft32i_made;
     double2 *stage_grid, *stage_coef;  // for the host-buffer entry points, allocated on first use
 
     // Per-phase timing (soft_plan_enable_timing): 3 events per timed call.
@@ -175,6 +180,9 @@ void free_plan(soft_plan_s *p) {
     for (auto &e : p->events)
         if (e) cudaEventDestroy(e);
     if (p->fft_made) cufftDestroy(p->fft);
+    if (p->fft32f_made) cufftDestroy(p->fft32f);
+    if (p->fft32i_made) cufftDestroy(p->fft32i);
+    cudaFree(p->lw); cudaFree(p->g32); cudaFree(p->S32);
     cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
     cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
     cudaFree(p->stage_grid); cudaFree(p->stage_coef);
@@ -182,7 +190,45 @@ void free_plan(soft_plan_s *p) {
     delete p;
 }
 
+soft_status run_forward_mixed(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s) {
+    cudaEvent_t *ev = timing_slot(p, 0);
+    if (ev) cudaEventRecord(ev[0], s);
+    cudaError_t e = launch_f64_to_f32(reinterpret_cast<const double2 *>(grid), p->g32, (int64_t)grid_elems(p->B), s);
+    if (e != cudaSuccess) return fail_cuda("grid conversion kernel launch", e);
+    cufftResult r = cufftSetStream(p->fft32f, s);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
+    // S(m,m';j) with exp(+i...) = cuFFT INVERSE, written in layout [m][m'][j].
+    r = cufftExecC2C(p->fft32f, reinterpret_cast<cufftComplex *>(p->g32), reinterpret_cast<cufftComplex *>(p->S32),
+                     CUFFT_INVERSE);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecC2C (forward slices)", r);
+    if (ev) cudaEventRecord(ev[1], s);
+    e = launch_dwt_forward_mixed(p->dtype, p->tables(), p->lw, p->S32, coef, s);
+    if (e != cudaSuccess) return fail_cuda("mixed DWT kernel launch", e);
+    if (ev) cudaEventRecord(ev[2], s);
+    return SOFT_OK;
+}
+
+soft_status run_inverse_mixed(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s) {
+    cudaEvent_t *ev = timing_slot(p, 1);
+    if (ev) cudaEventRecord(ev[0], s);
+    cudaError_t e = launch_zero_nyquist32(p->B, p->S32, s);
+    if (e != cudaSuccess) return fail_cuda("S clearing kernel launch", e);
+    e = launch_dwt_inverse_mixed(p->dtype, p->tables(), coef, p->S32, s);
+    if (e != cudaSuccess) return fail_cuda("mixed iDWT kernel launch", e);
+    if (ev) cudaEventRecord(ev[1], s);
+    cufftResult r = cufftSetStream(p->fft32i, s);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
+    r = cufftExecC2C(p->fft32i, reinterpret_cast<cufftComplex *>(p->S32), reinterpret_cast<cufftComplex *>(p->g32),
+                     CUFFT_FORWARD);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecC2C (inverse slices)", r);
+    e = launch_f32_to_f64(p->g32, reinterpret_cast<double2 *>(grid), (int64_t)grid_elems(p->B), s);
+    if (e != cudaSuccess) return fail_cuda("grid conversion kernel launch", e);
+    if (ev) cudaEventRecord(ev[2], s);
+    return SOFT_OK;
+}
+
 soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s) {
+    if (p->dtype != SOFT_FP64) return run_forward_mixed(p, grid, coef, s);
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
     cufftResult r = cufftSetStream(p->fft, s);
@@ -199,6 +245,7 @@ soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaSt
 }
 
 soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s) {
+    if (p->dtype != SOFT_FP64) return run_inverse_mixed(p, coef, grid, s);
     cudaEvent_t *ev = timing_slot(p, 1);
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = launch_zero_nyquist(p->B, p->S, s);
@@ -271,8 +318,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     *out = nullptr;
     if (B < 1) return SOFT_ERR_INVALID_ARG;
     if (B > kMaxB) return SOFT_ERR_UNSUPPORTED;
-    if (dtype != SOFT_FP64) return dtype == SOFT_MIXED_BF16X3 || dtype == SOFT_MIXED_TF32 ? SOFT_ERR_UNSUPPORTED
-                                                                                       : SOFT_ERR_INVALID_ARG;
+    if (dtype != SOFT_FP64 && dtype != SOFT_MIXED_BF16X3 && dtype != SOFT_MIXED_TF32) return SOFT_ERR_INVALID_ARG;
     soft_plan_s *p = new (std::nothrow) soft_plan_s();
     if (!p) return SOFT_ERR_OUT_OF_MEMORY;
     p->magic = kPlanMagic;
@@ -309,25 +355,45 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     alloc((void **)&p->clusters, sizeof(int2) * cl.size());
     alloc((void **)&p->runoff, sizeof(int64_t) * ro.size());
     alloc((void **)&p->err, sizeof(int));
-    alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
+    if (dtype == SOFT_FP64) {
+        alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
+    } else {
+        alloc((void **)&p->lw, sizeof(double) * n);
+        alloc((void **)&p->g32, sizeof(float2) * grid_elems(B));
+        alloc((void **)&p->S32, sizeof(float2) * grid_elems(B));
+    }
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
 
     e = cudaMemcpy(p->clusters, cl.data(), sizeof(int2) * cl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->runoff, ro.data(), sizeof(int64_t) * ro.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
     if (e == cudaSuccess) e = launch_tables(B, p->w, p->cosb, p->lcos, p->lsin, p->lfact, 0);
+    if (e == cudaSuccess && dtype != SOFT_FP64) e = launch_log_weights(B, p->w, p->lw, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
 
-    // One batched 2-D Z2Z plan over the 2B contiguous beta slices.
-    if (cufftCreate(&p->fft) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
-    p->fft_made = true;
     long long dims[2] = {n, n};
+    long long emb[2] = {n, n};
+    const long long slice = (long long)n * n;
     size_t work = 0;
-    if (cufftMakePlanMany64(p->fft, 2, dims, nullptr, 1, (long long)n * n, nullptr, 1, (long long)n * n,
-                            CUFFT_Z2Z, n, &work) != CUFFT_SUCCESS) {
-        free_plan(p);
-        return SOFT_ERR_CUDA;
+    cufftResult r;
+    if (dtype == SOFT_FP64) {
+        // One batched 2-D Z2Z plan over the 2B contiguous beta slices, S in layout [j][m][m'].
+        if (cufftCreate(&p->fft) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
+        p->fft_made = true;
+        r = cufftMakePlanMany64(p->fft, 2, dims, nullptr, 1, slice, nullptr, 1, slice, CUFFT_Z2Z, n, &work);
+        if (r != CUFFT_SUCCESS) { free_plan(p); return fail_cufft("cufftMakePlanMany64 (Z2Z)", r); }
+    } else {
+        // FP32 C2C plans; the beta index is the batch: contiguous slices on the grid
+        // side, stride 1 (beta fastest) with element stride 2B on the S side.
+        if (cufftCreate(&p->fft32f) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
+        p->fft32f_made = true;
+        r = cufftMakePlanMany64(p->fft32f, 2, dims, emb, 1, slice, emb, n, 1, CUFFT_C2C, n, &work);
+        if (r != CUFFT_SUCCESS) { free_plan(p); return fail_cufft("cufftMakePlanMany64 (C2C forward)", r); }
+        if (cufftCreate(&p->fft32i) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
+        p->fft32i_made = true;
+        r = cufftMakePlanMany64(p->fft32i, 2, dims, emb, n, 1, emb, 1, slice, CUFFT_C2C, n, &work);
+        if (r != CUFFT_SUCCESS) { free_plan(p); return fail_cufft("cufftMakePlanMany64 (C2C inverse)", r); }
     }
     *out = p;
     return SOFT_OK;
@@ -376,6 +442,7 @@ soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *st
 soft_status soft_dwt_forward(soft_plan p, const double *S, double *coef, void *stream) {
     soft_status st = check_plan_args(p, S, coef);
     if (st != SOFT_OK) return st;
+    if (p->dtype != SOFT_FP64) return SOFT_ERR_UNSUPPORTED;
     DeviceGuard g(p->device);
     return cuda_status(launch_dwt_forward_fp64(p->tables(), reinterpret_cast<const double2 *>(S),
                                                reinterpret_cast<double2 *>(coef), static_cast<cudaStream_t>(stream)));
@@ -384,6 +451,7 @@ soft_status soft_dwt_forward(soft_plan p, const double *S, double *coef, void *s
 soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *stream) {
     soft_status st = check_plan_args(p, coef, S);
     if (st != SOFT_OK) return st;
+    if (p->dtype != SOFT_FP64) return SOFT_ERR_UNSUPPORTED;
     DeviceGuard g(p->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_zero_nyquist(p->B, reinterpret_cast<double2 *>(S), s);

@@ -118,6 +118,31 @@ __device__ inline double seed_lognorm(const Tables &tb, int m, int mp) {
     return 0.5 * (tb.lfact[2 * m] - tb.lfact[m + mp] - tb.lfact[m - mp]);
 }
 
+// Per-CTA cluster prologue: the partner table and the partners' run offsets,
+// written by thread 0 into shared memory (the caller synchronises).
+struct ClusterSmem {
+    int np;
+    int pm[8], pmp[8], mir[8], lpar[8];
+    double sign[8];
+    int64_t off[8];
+};
+
+__device__ inline void load_cluster(const Tables &tb, int m, int mp, ClusterSmem &cs) {
+    if (threadIdx.x == 0) {
+        const Partners P = make_partners(m, mp);
+        cs.np = P.np;
+        for (int p = 0; p < 8; ++p) {
+            const bool on = p < P.np;
+            cs.pm[p] = on ? P.m[p] : 0;
+            cs.pmp[p] = on ? P.mp[p] : 0;
+            cs.mir[p] = on ? P.mirror[p] : 0;
+            cs.lpar[p] = on ? P.lpar[p] : 0;
+            cs.sign[p] = on ? P.sign[p] : 0.0;
+            cs.off[p] = on ? tb.runoff[runoff_index(tb.B, P.m[p], P.mp[p])] : 0;
+        }
+    }
+}
+
 // Records the detail returned by soft_last_error() on this host thread (soft_api.cu).
 void set_last_error_message(const char *where, const char *what);
 
@@ -127,5 +152,14 @@ cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, doubl
 cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s);
 cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *lsin, double *lfact,
                           cudaStream_t s);
+
+// Launchers (dwt_mixed.cu); mode is SOFT_MIXED_BF16X3 or SOFT_MIXED_TF32.
+cudaError_t launch_log_weights(int B, const double *w, double *lw, cudaStream_t s);
+cudaError_t launch_dwt_forward_mixed(int mode, const Tables &tb, const double *lw, const float2 *S, double *coef,
+                                     cudaStream_t s);
+cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s);
+cudaError_t launch_zero_nyquist32(int B, float2 *S, cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double2 *in, float2 *out, int64_t count, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float2 *in, double2 *out, int64_t count, cudaStream_t s);
 
 }  // namespace softgb
