@@ -54,8 +54,8 @@ typedef enum {
 
 typedef enum {
     SOFT_FP64 = 0,         /* every step in FP64 */
-    SOFT_MIXED_BF16X3 = 1, /* reserved: contraction on tensor cores, split BF16 x3 */
-    SOFT_MIXED_TF32 = 2    /* reserved: contraction on tensor cores, TF32 */
+    SOFT_MIXED_BF16X3 = 1, /* contraction on tcgen05 tensor cores, split BF16 x3 (rel-L2 <= 5e-5) */
+    SOFT_MIXED_TF32 = 2    /* contraction on tcgen05 tensor cores, TF32 (rel-L2 <= 2e-3) */
 } soft_dtype;
 
 /* Largest bandwidth B the kernels accept. */
@@ -108,12 +108,72 @@ soft_status soft_forward(soft_plan p, const double *grid, double *coef, void *st
  *   every beta slice (cuFFT, exp(-i...)).                               */
 soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *stream);
 
+/* Adjoints, for gradients of objectives through the transforms.  Adjoint is
+ * with respect to sum_k conj(a_k) b_k on both sides.  Writing the forward
+ * transform as f = V_B T_B W_B E x (Sec. 2.4; E the per-slice 2-D DFT with
+ * exp(+i...)) and the inverse as x = E^H T_B^T f:
+ *   soft_forward_adjoint:  coef -> grid,  E^H W_B T_B^T V_B  (iDWT with V on
+ *                          the coefficients and W on S, then the exp(-i) FFT)
+ *   soft_inverse_adjoint:  grid -> coef,  T_B E  (the exp(+i) FFT, then the
+ *                          DWT without V and W)
+ * Same pointer rules and precision mode as the plan's forward/inverse. */
+soft_status soft_forward_adjoint(soft_plan p, const double *coef, double *grid, void *stream);
+soft_status soft_inverse_adjoint(soft_plan p, const double *grid, double *coef, void *stream);
+
+/* Rotational correlation (fast rotational matching, which motivates the paper
+ * in Sec. 1; the paper gives no formula, the identity below is checked by
+ * brute force in the tests).  f_sh, g_sh: device, B^2 complex doubles each,
+ * the spherical-harmonic coefficients of two functions on the sphere (index
+ * l*l + m + l, l < B, orthonormal Y_lm with the Condon-Shortley phase).
+ *   soft_correlation_coeffs: coef(l,m,m') = g_lm conj(f_lm'), the SO(3)
+ *     Fourier coefficients of C(R) = int g(R^{-1} w) conj(f(w)) dw.
+ *   soft_correlate: the same, then the inverse transform into grid (device,
+ *     (2B)^3 complex): grid[j][i][k] = C(R_z(gamma_k) R_y(beta_j) R_z(alpha_i));
+ *     if best_index / best_value (device int64 / double) are non-NULL, also
+ *     the arg-max of Re C over the grid (linear index j*(2B)^2 + i*2B + k,
+ *     lowest index on ties, NaN never wins).  The first call allocates the
+ *     plan's coefficient workspace (B(4B^2-1)/3 complex doubles). */
+soft_status soft_correlation_coeffs(soft_plan p, const double *f_sh, const double *g_sh, double *coef, void *stream);
+soft_status soft_correlate(soft_plan p, const double *f_sh, const double *g_sh, double *grid, int64_t *best_index,
+                           double *best_value, void *stream);
+
+/* Batches: n transforms with n DISTINCT plans (any mix of bandwidths and
+ * modes; each plan lends its workspace), one pointer per entry in host arrays
+ * of device pointers.  The first call with a given (plans, pointers) captures
+ * the whole batch into a CUDA graph on a private stream (instantiated once,
+ * cached, most recent 16 kept; destroying a member plan drops it) and every
+ * call replays it on `stream`.  FP64 inverse transforms with B <= 128 share
+ * one persistent inverse-DWT launch that schedules all their (transform,
+ * symmetry cluster) work items, heaviest first, through an atomic counter;
+ * other entries run their per-plan kernels inside the same graph.
+ *   soft_batched_inverse:   coefs[i] -> grids[i]
+ *   soft_batched_forward:   grids[i] -> coefs[i]
+ *   soft_batched_correlate: (f_sh[i], g_sh[i]) -> grids[i] = C_i on the Euler
+ *                           grid, best_index[i] / best_value[i] (device arrays
+ *                           of n) = arg-max of Re C_i, as soft_correlate.
+ * Make the first call outside any stream capture of the caller's. */
+soft_status soft_batched_inverse(int n, const soft_plan *plans, const double *const *coefs, double *const *grids,
+                                 void *stream);
+soft_status soft_batched_forward(int n, const soft_plan *plans, const double *const *grids, double *const *coefs,
+                                 void *stream);
+soft_status soft_batched_correlate(int n, const soft_plan *plans, const double *const *f_sh,
+                                   const double *const *g_sh, double *const *grids, int64_t *best_index,
+                                   double *best_value, void *stream);
+
+/* Arg-max of the real parts of count complex doubles (device), lowest index on
+ * ties, NaN never wins: *index_out / *value_out (device).  scratch: device,
+ * soft_argmax_scratch_doubles() doubles, 16-byte aligned. */
+soft_status soft_argmax_real(const double *data, int64_t count, int64_t *index_out, double *value_out,
+                             double *scratch, void *stream);
+int soft_argmax_scratch_doubles(void);
+
 /* The DWT step alone (Sec. 2.4, matrix form V_B T_B W_B): S (device, layout
- * above) -> coef.  S is read only. */
+ * above) -> coef.  S is read only.  FP64 plans only (SOFT_ERR_UNSUPPORTED for
+ * mixed plans, whose S is FP32 in another layout). */
 soft_status soft_dwt_forward(soft_plan p, const double *S, double *coef, void *stream);
 
 /* The iDWT step alone (Sec. 2.4, T_B^T): coef -> S (device, layout above,
- * every entry written, the -B rows/columns set to 0). */
+ * every entry written, the -B rows/columns set to 0).  FP64 plans only. */
 soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *stream);
 
 /* The DWT step alone, without a plan and without allocating any memory

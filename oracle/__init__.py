@@ -22,6 +22,13 @@ the FFT on SO(3)" (arXiv:1808.00896):
                                  Eq. (fourier_representation) summed directly,
                                  O(B^6), small B only
 * ``forward_pairs`` / ``inverse_points`` -- sampled forms for large B
+* ``correlation_coeffs`` / ``correlation`` / ``argmax_real`` -- rotational
+                                 correlation of two spherical functions (the
+                                 rotational matching application of Sec. 1):
+                                 c(l,m,m') = g_lm conj(f_lm'), then ``inverse``
+* ``forward_adjoint`` / ``inverse_adjoint`` -- the adjoints of the two
+                                 transforms: E^H W T^T V and T E (E the
+                                 per-slice DFT with exp(+i))
 
 Every function is pinned by tests in ``tests/test_oracle_*.py`` to closed
 forms, a textbook routine (sympy's Wigner-d, scipy's Jacobi polynomials),
@@ -75,6 +82,9 @@ def _load():
             "oracle_direct_forward": (c_int, [c_int, dp, dp]),
             "oracle_direct_inverse": (c_int, [c_int, dp, dp]),
             "oracle_forward_pairs": (c_int, [c_int, dp, c_int, ip, dp]),
+            "oracle_forward_adjoint": (c_int, [c_int, dp, dp]),
+            "oracle_correlation_coeffs": (c_int, [c_int, dp, dp, dp]),
+            "oracle_inverse_adjoint": (c_int, [c_int, dp, dp]),
             "oracle_inverse_points": (c_int, [c_int, dp, c_int, ip, dp]),
         }
         for name, (res, args) in sig.items():
@@ -212,6 +222,52 @@ def direct_inverse(B: int, coef) -> np.ndarray:
     out = np.zeros((n, n, n), dtype=np.complex128)
     _load().oracle_direct_inverse(B, _dp(c.view(np.float64)), _dp(out.view(np.float64)))
     return out
+
+
+def forward_adjoint(B: int, coef) -> np.ndarray:
+    """Adjoint of ``forward``: coefficients -> grid, E^H W T^T V."""
+    c = _check_coef(B, coef)
+    n = 2 * B
+    out = np.zeros((n, n, n), dtype=np.complex128)
+    rc = _load().oracle_forward_adjoint(B, _dp(c.view(np.float64)), _dp(out.view(np.float64)))
+    if rc:
+        raise RuntimeError(f"oracle_forward_adjoint failed ({rc})")
+    return out
+
+
+def inverse_adjoint(B: int, grid) -> np.ndarray:
+    """Adjoint of ``inverse``: grid -> coefficients, T E."""
+    g = _check_grid(B, grid)
+    out = np.zeros(num_coeffs(B), dtype=np.complex128)
+    rc = _load().oracle_inverse_adjoint(B, _dp(g.view(np.float64)), _dp(out.view(np.float64)))
+    if rc:
+        raise RuntimeError(f"oracle_inverse_adjoint failed ({rc})")
+    return out
+
+
+def correlation_coeffs(B: int, f_sh, g_sh) -> np.ndarray:
+    """c(l,m,m') = g_lm conj(f_lm') for spherical-harmonic vectors of length B^2
+    (index l*l + m + l); the inverse transform of c is C(R) = <g(R^-1 .), f>."""
+    f = _as_c128(f_sh)
+    g = _as_c128(g_sh)
+    if f.size != B * B or g.size != B * B:
+        raise ValueError("spherical-harmonic vectors must hold B^2 values")
+    out = np.zeros(num_coeffs(B), dtype=np.complex128)
+    _load().oracle_correlation_coeffs(B, _dp(f.view(np.float64)), _dp(g.view(np.float64)),
+                                      _dp(out.view(np.float64)))
+    return out
+
+
+def correlation(B: int, f_sh, g_sh) -> np.ndarray:
+    """C(alpha_i, beta_j, gamma_k) on the (2B)^3 grid, layout [j][i][k]."""
+    return inverse(B, correlation_coeffs(B, f_sh, g_sh))
+
+
+def argmax_real(values) -> tuple[int, float]:
+    """Linear index and value of the largest real part (first index on ties)."""
+    v = np.asarray(values).reshape(-1).real
+    i = int(np.argmax(v))
+    return i, float(v[i])
 
 
 def forward_pairs(B: int, grid, pairs) -> list[np.ndarray]:

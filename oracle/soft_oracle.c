@@ -518,3 +518,104 @@ int oracle_inverse_points(int B, const double *coef, int npts, const int *pts, d
     free(dcol);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoints (with respect to sum_k conj(a_k) b_k on both sides).             */
+/* The forward transform is f = V T W E x (E: per-slice DFT with exp(+i)),    */
+/* so its adjoint is E^H W T^T V: the inverse's steps with V applied to the  */
+/* coefficients and W to S.  The inverse transform is E^H T^T, with adjoint  */
+/* T E: the forward's steps without V and W.                                 */
+/* ------------------------------------------------------------------------ */
+
+int oracle_forward_adjoint(int B, const double *coef, double *grid)
+{
+    if (B < 1) return 1;
+    int n = 2 * B;
+    size_t cnt = (size_t)2 * n * n * n;
+    double *dcol = (double *)malloc(sizeof(double) * B);
+    double *w = (double *)malloc(sizeof(double) * n);
+    if (!dcol || !w) { free(dcol); free(w); return 2; }
+    oracle_weights(B, w);
+    memset(grid, 0, sizeof(double) * cnt);
+    int64_t off = 0;
+    for (int m = 1 - B; m <= B - 1; ++m)
+        for (int mp = 1 - B; mp <= B - 1; ++mp) {
+            int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
+            int L = B - l0;
+            int mi = mod_n(m, n), mk = mod_n(mp, n);
+            for (int j = 0; j < n; ++j) {
+                oracle_wigner_d_column(B, m, mp, oracle_beta(B, j), dcol);
+                double re = 0.0, im = 0.0;
+                for (int t = 0; t < L; ++t) {
+                    double v = (2.0 * (l0 + t) + 1.0) / (8.0 * OR_PI * B);
+                    re += dcol[t] * v * coef[2 * (off + t)];
+                    im += dcol[t] * v * coef[2 * (off + t) + 1];
+                }
+                double *s = grid + 2 * (((size_t)j * n + mi) * n + mk);
+                s[0] = w[j] * re;
+                s[1] = w[j] * im;
+            }
+            off += L;
+        }
+    free(dcol); free(w);
+    oracle_dft2_slices(n, n, grid, -1);
+    return 0;
+}
+
+int oracle_inverse_adjoint(int B, const double *grid, double *coef)
+{
+    if (B < 1) return 1;
+    int n = 2 * B;
+    double *S = forward_separation(B, grid);
+    double *dcol = (double *)malloc(sizeof(double) * (size_t)n * B);
+    if (!S || !dcol) { free(S); free(dcol); return 2; }
+    int64_t off = 0;
+    for (int m = 1 - B; m <= B - 1; ++m)
+        for (int mp = 1 - B; mp <= B - 1; ++mp) {
+            int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
+            int L = B - l0;
+            int mi = mod_n(m, n), mk = mod_n(mp, n);
+            for (int j = 0; j < n; ++j) oracle_wigner_d_column(B, m, mp, oracle_beta(B, j), dcol + (size_t)j * B);
+            for (int t = 0; t < L; ++t) {
+                double re = 0.0, im = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    const double *s = S + 2 * (((size_t)j * n + mi) * n + mk);
+                    re += dcol[(size_t)j * B + t] * s[0];
+                    im += dcol[(size_t)j * B + t] * s[1];
+                }
+                coef[2 * (off + t)] = re;
+                coef[2 * (off + t) + 1] = im;
+            }
+            off += L;
+        }
+    free(S); free(dcol);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rotational correlation of two functions on the sphere (the fast            */
+/* rotational matching application of Sec. 1).  With spherical-harmonic     */
+/* coefficients f_lm, g_lm (index l*l + m + l, l < B), the correlation       */
+/*   C(R) = int_{S^2} g(R^{-1} w) conj(f(w)) dw                              */
+/* is the inverse transform of c(l,m,m') = g_lm conj(f_lm'), evaluated at    */
+/* R = R_z(gamma) R_y(beta) R_z(alpha) on the sampling grid.                 */
+/* ------------------------------------------------------------------------ */
+
+int oracle_correlation_coeffs(int B, const double *f_sh, const double *g_sh, double *coef)
+{
+    if (B < 1) return 1;
+    int64_t off = 0;
+    for (int m = 1 - B; m <= B - 1; ++m)
+        for (int mp = 1 - B; mp <= B - 1; ++mp) {
+            int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
+            for (int l = l0; l < B; ++l) {
+                const double *g = g_sh + 2 * ((int64_t)l * l + m + l);
+                const double *f = f_sh + 2 * ((int64_t)l * l + mp + l);
+                /* g * conj(f) */
+                coef[2 * (off + l - l0)] = g[0] * f[0] + g[1] * f[1];
+                coef[2 * (off + l - l0) + 1] = g[1] * f[0] - g[0] * f[1];
+            }
+            off += B - l0;
+        }
+    return 0;
+}

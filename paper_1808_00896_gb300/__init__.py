@@ -10,11 +10,12 @@ Importing this package does not load the CUDA library; the first plan does,
 and fails loudly if it has not been built.
 """
 
-__all__ = ["Plan", "num_coeffs"]
+__all__ = ["Plan", "num_coeffs", "soft_forward", "soft_inverse", "batched_inverse", "batched_forward",
+           "batched_correlate"]
 
 
 def __getattr__(name):
-    if name in ("Plan", "num_coeffs"):
+    if name in __all__:
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -108,6 +108,49 @@ class Plan:
                    "soft_inverse")
         return out
 
+    def forward_adjoint(self, coef: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Adjoint of ``forward``: coefficients -> grid (soft_forward_adjoint)."""
+        _check_tensor(coef, self.ncoef, self.device, "coef")
+        out = self.empty_grid() if out is None else out
+        _check_tensor(out, self.n ** 3, self.device, "out")
+        capi.check(capi.soft_forward_adjoint(self.handle, coef.data_ptr(), out.data_ptr(),
+                                             _stream_ptr(self.device, stream)), "soft_forward_adjoint")
+        return out
+
+    def inverse_adjoint(self, grid: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Adjoint of ``inverse``: grid -> coefficients (soft_inverse_adjoint)."""
+        _check_tensor(grid, self.n ** 3, self.device, "grid")
+        out = self.empty_coef() if out is None else out
+        _check_tensor(out, self.ncoef, self.device, "out")
+        capi.check(capi.soft_inverse_adjoint(self.handle, grid.data_ptr(), out.data_ptr(),
+                                             _stream_ptr(self.device, stream)), "soft_inverse_adjoint")
+        return out
+
+    def correlation_coeffs(self, f_sh: torch.Tensor, g_sh: torch.Tensor, out: torch.Tensor | None = None,
+                           stream=None) -> torch.Tensor:
+        """c(l,m,m') = g_lm conj(f_lm') (soft_correlation_coeffs); f_sh, g_sh: B^2 complex128."""
+        _check_tensor(f_sh, self.B * self.B, self.device, "f_sh")
+        _check_tensor(g_sh, self.B * self.B, self.device, "g_sh")
+        out = self.empty_coef() if out is None else out
+        _check_tensor(out, self.ncoef, self.device, "out")
+        capi.check(capi.load().soft_correlation_coeffs(self.handle, f_sh.data_ptr(), g_sh.data_ptr(), out.data_ptr(),
+                                                       _stream_ptr(self.device, stream)), "soft_correlation_coeffs")
+        return out
+
+    def correlate(self, f_sh: torch.Tensor, g_sh: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """C(R) on the Euler grid and the arg-max of Re C (soft_correlate).
+        Returns (grid, best_index tensor, best_value tensor), all on the device."""
+        _check_tensor(f_sh, self.B * self.B, self.device, "f_sh")
+        _check_tensor(g_sh, self.B * self.B, self.device, "g_sh")
+        out = self.empty_grid() if out is None else out
+        _check_tensor(out, self.n ** 3, self.device, "out")
+        idx = torch.empty(1, dtype=torch.int64, device=self.device)
+        val = torch.empty(1, dtype=torch.float64, device=self.device)
+        capi.check(capi.load().soft_correlate(self.handle, f_sh.data_ptr(), g_sh.data_ptr(), out.data_ptr(),
+                                              idx.data_ptr(), val.data_ptr(), _stream_ptr(self.device, stream)),
+                   "soft_correlate")
+        return out, idx, val
+
     def dwt_forward(self, S: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """DWT step only: S[j][m mod 2B][m' mod 2B] -> coefficients (soft_dwt_forward)."""
         _check_tensor(S, self.n ** 3, self.device, "S")
@@ -147,3 +190,100 @@ class Plan:
             capi.check(capi.soft_inverse_host(self.handle, c.ctypes.data, out.ctypes.data,
                                               _stream_ptr(self.device)), "soft_inverse_host")
         return out
+
+
+class _SoftForwardFn(torch.autograd.Function):
+    """grid -> coefficients; backward applies the adjoint E^H W T^T V."""
+
+    @staticmethod
+    def forward(ctx, grid, plan):
+        ctx.plan = plan
+        ctx.shape = grid.shape
+        return plan.forward(grid.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.forward_adjoint(g.contiguous()).reshape(ctx.shape), None
+
+
+class _SoftInverseFn(torch.autograd.Function):
+    """coefficients -> grid; backward applies the adjoint T E."""
+
+    @staticmethod
+    def forward(ctx, coef, plan):
+        ctx.plan = plan
+        ctx.shape = coef.shape
+        return plan.inverse(coef.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.inverse_adjoint(g.contiguous()).reshape(ctx.shape), None
+
+
+def soft_forward(grid: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable forward transform (complex128 grid of shape (2B,)*3)."""
+    return _SoftForwardFn.apply(grid, plan)
+
+
+def soft_inverse(coef: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable inverse transform (complex128 coefficient vector)."""
+    return _SoftInverseFn.apply(coef, plan)
+
+
+def _ptr_array(ts):
+    import ctypes
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def _plan_array(plans):
+    import ctypes
+    return (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+
+
+def _same_device(plans):
+    dev = plans[0].device
+    if any(p.device != dev for p in plans):
+        raise ValueError("all plans of a batch must be on one device")
+    return dev
+
+
+def batched_inverse(plans, coefs, grids=None, stream=None):
+    """Inverse transforms of a batch (soft_batched_inverse), one distinct plan per entry."""
+    dev = _same_device(plans)
+    grids = [p.empty_grid() for p in plans] if grids is None else grids
+    for p, c, g in zip(plans, coefs, grids):
+        _check_tensor(c, p.ncoef, dev, "coef")
+        _check_tensor(g, p.n ** 3, dev, "grid")
+    capi.check(capi.load().soft_batched_inverse(len(plans), _plan_array(plans), _ptr_array(coefs), _ptr_array(grids),
+                                                _stream_ptr(dev, stream)), "soft_batched_inverse")
+    return grids
+
+
+def batched_forward(plans, grids, coefs=None, stream=None):
+    """Forward transforms of a batch (soft_batched_forward)."""
+    dev = _same_device(plans)
+    coefs = [p.empty_coef() for p in plans] if coefs is None else coefs
+    for p, g, c in zip(plans, grids, coefs):
+        _check_tensor(g, p.n ** 3, dev, "grid")
+        _check_tensor(c, p.ncoef, dev, "coef")
+    capi.check(capi.load().soft_batched_forward(len(plans), _plan_array(plans), _ptr_array(grids), _ptr_array(coefs),
+                                                _stream_ptr(dev, stream)), "soft_batched_forward")
+    return coefs
+
+
+def batched_correlate(plans, f_shs, g_shs, grids=None, best_index=None, best_value=None, stream=None):
+    """Rotational correlations of a batch (soft_batched_correlate).
+    Returns (grids, best_index (n,) int64, best_value (n,) float64) on the device."""
+    dev = _same_device(plans)
+    n = len(plans)
+    grids = [p.empty_grid() for p in plans] if grids is None else grids
+    best_index = torch.empty(n, dtype=torch.int64, device=dev) if best_index is None else best_index
+    best_value = torch.empty(n, dtype=torch.float64, device=dev) if best_value is None else best_value
+    for p, f, g, gr in zip(plans, f_shs, g_shs, grids):
+        _check_tensor(f, p.B * p.B, dev, "f_sh")
+        _check_tensor(g, p.B * p.B, dev, "g_sh")
+        _check_tensor(gr, p.n ** 3, dev, "grid")
+    capi.check(capi.load().soft_batched_correlate(n, _plan_array(plans), _ptr_array(f_shs), _ptr_array(g_shs),
+                                                  _ptr_array(grids), best_index.data_ptr(), best_value.data_ptr(),
+                                                  _stream_ptr(dev, stream)), "soft_batched_correlate")
+    return grids, best_index, best_value

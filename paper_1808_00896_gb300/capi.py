@@ -37,6 +37,15 @@ SIGNATURES = {
     "soft_plan_sync": (_i, [_vp]),
     "soft_forward": (_i, [_vp, _vp, _vp, _vp]),
     "soft_inverse": (_i, [_vp, _vp, _vp, _vp]),
+    "soft_forward_adjoint": (_i, [_vp, _vp, _vp, _vp]),
+    "soft_inverse_adjoint": (_i, [_vp, _vp, _vp, _vp]),
+    "soft_batched_inverse": (_i, [_i, _vp, _vp, _vp, _vp]),
+    "soft_batched_forward": (_i, [_i, _vp, _vp, _vp, _vp]),
+    "soft_batched_correlate": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "soft_correlation_coeffs": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "soft_correlate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "soft_argmax_real": (_i, [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
+    "soft_argmax_scratch_doubles": (_i, []),
     "soft_dwt_forward": (_i, [_vp, _vp, _vp, _vp]),
     "soft_dwt_inverse": (_i, [_vp, _vp, _vp, _vp]),
     "soft_dwt_forward_noalloc": (_i, [_i, _vp, _vp, _vp]),
@@ -115,6 +124,14 @@ def soft_forward(plan: int, grid_ptr: int, coef_ptr: int, stream: int = 0) -> in
 
 def soft_inverse(plan: int, coef_ptr: int, grid_ptr: int, stream: int = 0) -> int:
     return load().soft_inverse(plan, coef_ptr, grid_ptr, stream)
+
+
+def soft_forward_adjoint(plan: int, coef_ptr: int, grid_ptr: int, stream: int = 0) -> int:
+    return load().soft_forward_adjoint(plan, coef_ptr, grid_ptr, stream)
+
+
+def soft_inverse_adjoint(plan: int, grid_ptr: int, coef_ptr: int, stream: int = 0) -> int:
+    return load().soft_inverse_adjoint(plan, grid_ptr, coef_ptr, stream)
 
 
 def soft_dwt_forward(plan: int, S_ptr: int, coef_ptr: int, stream: int = 0) -> int:

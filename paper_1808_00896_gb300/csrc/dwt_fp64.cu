@@ -74,7 +74,7 @@ __global__ void zero_nyquist_kernel(int B, double2 *S) {
 // ---------------------------------------------------------------------------
 template <int NT, int JPT>
 __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const double2 *__restrict__ S,
-                                                               double *__restrict__ coef) {
+                                                               double *__restrict__ coef, int flags) {
     constexpr int LT = NT / 16;
     extern __shared__ __align__(16) double smem[];
     __shared__ ClusterSmem cs;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
         double A, Ac, Bc;
         recurrence_coeffs(l, m, mp, A, Ac, Bc);
         rA[t] = A; rAc[t] = Ac; rBc[t] = Bc;
-        rV[t] = (2.0 * l + 1.0) / (8.0 * M_PI * B);
+        rV[t] = (flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0;
     }
     __syncthreads();
     const int np = cs.np;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
         if (p < np) {
             const int src = cs.mir[p] ? n - 1 - j : j;
             const double2 s = S[((int64_t)src * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)];
-            const double wj = tb.w[src];
+            const double wj = (flags & kApplyW) ? tb.w[src] : 1.0;
             v = make_double2(wj * s.x, wj * s.y);
         }
         *reinterpret_cast<double2 *>(&X[j * 16 + 2 * p]) = v;
@@ -201,14 +201,14 @@ __device__ __forceinline__ void idwt_walk(const double *F, const double *rA, con
     }
 }
 
+// One cluster of the inverse DWT; every thread of the CTA calls it.  smem holds
+// F[B][16] and the recurrence coefficients (3 x B doubles).
 template <int NT, int JPT>
-__global__ void __launch_bounds__(NT) dwt_inverse_fp64_kernel(Tables tb, const double *__restrict__ coef,
-                                                               double2 *__restrict__ S) {
-    extern __shared__ __align__(16) double smem[];
-    __shared__ ClusterSmem cs;
+__device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__restrict__ coef,
+                                             double2 *__restrict__ S, int flags, int m, int mp, double *smem,
+                                             ClusterSmem &cs) {
     const int B = tb.B, n = 2 * B, tid = threadIdx.x;
-    const int2 rep = tb.clusters[blockIdx.x];
-    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+    const int l0 = m, L = B - l0;
 
     double *F = smem;                  // [B][16]
     double *rA = F + (size_t)B * 16;
@@ -228,7 +228,8 @@ __global__ void __launch_bounds__(NT) dwt_inverse_fp64_kernel(Tables tb, const d
         double2 v = make_double2(0.0, 0.0);
         if (p < np) {
             const int l = l0 + t;
-            const double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
+            double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
+            if (flags & kApplyV) sg *= (2.0 * l + 1.0) / (8.0 * M_PI * B);
             const double2 c = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + t));
             v = make_double2(sg * c.x, sg * c.y);
         }
@@ -264,8 +265,9 @@ __global__ void __launch_bounds__(NT) dwt_inverse_fp64_kernel(Tables tb, const d
             for (int p = 0; p < 8; ++p) {
                 if (p < np) {
                     const int jj = cs.mir[p] ? n - 1 - j : j;
+                    const double wj = (flags & kApplyW) ? tb.w[jj] : 1.0;
                     S[((int64_t)jj * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)] =
-                        make_double2(acc[k][2 * p], acc[k][2 * p + 1]);
+                        make_double2(wj * acc[k][2 * p], wj * acc[k][2 * p + 1]);
                 }
             }
         }
@@ -273,24 +275,55 @@ __global__ void __launch_bounds__(NT) dwt_inverse_fp64_kernel(Tables tb, const d
 }
 
 template <int NT, int JPT>
-cudaError_t run_forward(const Tables &tb, const double2 *S, double *coef, cudaStream_t s) {
+__global__ void __launch_bounds__(NT) dwt_inverse_fp64_kernel(Tables tb, const double *__restrict__ coef,
+                                                               double2 *__restrict__ S, int flags) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ ClusterSmem cs;
+    const int2 rep = tb.clusters[blockIdx.x];
+    idwt_cluster<NT, JPT>(tb, coef, S, flags, rep.x, rep.y, smem, cs);
+}
+
+// Persistent inverse DWT over a batch of FP64 transforms of bandwidth <= 128:
+// one CTA per SM slot pulls (transform, cluster) items, heaviest first, from an
+// atomic counter until the list is exhausted.  No CTA waits on another.
+__global__ void __launch_bounds__(256) idwt_fp64_persistent_kernel(const BatchXform *__restrict__ xf,
+                                                                   const int2 *__restrict__ items, int nitems,
+                                                                   int *__restrict__ counter) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ ClusterSmem cs;
+    __shared__ int item;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = item;
+        if (it >= nitems) break;
+        const int2 w = items[it];
+        const BatchXform &X = xf[w.x];
+        const int2 rep = X.tb.clusters[w.y];
+        idwt_cluster<256, 1>(X.tb, X.coef, X.S, X.flags, rep.x, rep.y, smem, cs);
+        __syncthreads();  // smem and `item` are reused by the next item
+    }
+}
+
+template <int NT, int JPT>
+cudaError_t run_forward(const Tables &tb, const double2 *S, double *coef, cudaStream_t s, int flags) {
     const int B = tb.B, n = 2 * B;
     const size_t bytes = sizeof(double) * ((size_t)n * 16 + (size_t)(NT / 16) * n + 4 * (size_t)B);
     cudaError_t e = cudaFuncSetAttribute(dwt_forward_fp64_kernel<NT, JPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    dwt_forward_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, S, coef);
+    dwt_forward_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, S, coef, flags);
     return cudaGetLastError();
 }
 
 template <int NT, int JPT>
-cudaError_t run_inverse(const Tables &tb, const double *coef, double2 *S, cudaStream_t s) {
+cudaError_t run_inverse(const Tables &tb, const double *coef, double2 *S, cudaStream_t s, int flags) {
     const int B = tb.B;
     const size_t bytes = sizeof(double) * ((size_t)B * 16 + 3 * (size_t)B);
     cudaError_t e = cudaFuncSetAttribute(dwt_inverse_fp64_kernel<NT, JPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    dwt_inverse_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, coef, S);
+    dwt_inverse_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, coef, S, flags);
     return cudaGetLastError();
 }
 
@@ -313,22 +346,39 @@ cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s) {
 
 // Shape choice: the forward needs X (2B x 16) and a T tile (LT x 2B) in shared
 // memory; at 2B = 1024 only NT = 128 (LT = 8) fits the 227 KB of a CTA.
-cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s) {
+cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s, int flags) {
     const int n = 2 * tb.B;
     double *c = reinterpret_cast<double *>(coef);
-    if (n <= 256) return run_forward<256, 1>(tb, S, c, s);
-    if (n <= 512) return run_forward<256, 2>(tb, S, c, s);
-    return run_forward<128, 8>(tb, S, c, s);
+    if (n <= 256) return run_forward<256, 1>(tb, S, c, s, flags);
+    if (n <= 512) return run_forward<256, 2>(tb, S, c, s, flags);
+    return run_forward<128, 8>(tb, S, c, s, flags);
 }
 
-cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s) {
+cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
+                                        cudaStream_t s) {
+    const size_t bytes = sizeof(double) * ((size_t)maxB * 16 + 3 * (size_t)maxB);
+    cudaError_t e = cudaFuncSetAttribute(idwt_fp64_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, idwt_fp64_persistent_kernel, 256, bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
+    idwt_fp64_persistent_kernel<<<grid, 256, bytes, s>>>(xf, items, nitems, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s, int flags) {
     const int n = 2 * tb.B;
     const double *c = reinterpret_cast<const double *>(coef);
-    if (n <= 64) return run_inverse<64, 1>(tb, c, S, s);
-    if (n <= 128) return run_inverse<128, 1>(tb, c, S, s);
-    if (n <= 256) return run_inverse<256, 1>(tb, c, S, s);
-    if (n <= 512) return run_inverse<256, 2>(tb, c, S, s);
-    return run_inverse<256, 4>(tb, c, S, s);
+    if (n <= 64) return run_inverse<64, 1>(tb, c, S, s, flags);
+    if (n <= 128) return run_inverse<128, 1>(tb, c, S, s, flags);
+    if (n <= 256) return run_inverse<256, 1>(tb, c, S, s, flags);
+    if (n <= 512) return run_inverse<256, 2>(tb, c, S, s, flags);
+    return run_inverse<256, 4>(tb, c, S, s, flags);
 }
 
 }  // namespace softgb

@@ -65,18 +65,49 @@ __device__ __forceinline__ void put(unsigned char *plane0, int plane_bytes, int 
     }
 }
 
+// Store 16 bytes of consecutive K elements (8 BF16 or 4 TF32) of row r,
+// starting at k0 (a multiple of the per-16-byte count), into the A plane(s).
+template <int MODE>
+__device__ __forceinline__ void put_vec(unsigned char *plane0, int plane_bytes, int rows, int r, int k0,
+                                        const float (&v)[16 / Operands<MODE>::EB]) {
+    const uint32_t o = tc::kmajor_offset(r, k0, rows, Operands<MODE>::EB);
+    if (MODE == SOFT_MIXED_TF32) {
+        uint4 w;
+        w.x = __float_as_uint(tc::round_tf32(v[0]));
+        w.y = __float_as_uint(tc::round_tf32(v[1]));
+        w.z = __float_as_uint(tc::round_tf32(v[2]));
+        w.w = __float_as_uint(tc::round_tf32(v[3]));
+        *reinterpret_cast<uint4 *>(plane0 + o) = w;
+    } else {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            uint16_t h0, l0, h1, l1;
+            tc::split_bf16(v[2 * u], h0, l0);
+            tc::split_bf16(v[2 * u + 1], h1, l1);
+            h[u] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            l[u] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+        }
+        *reinterpret_cast<uint4 *>(plane0 + o) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(plane0 + plane_bytes + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// K elements per MMA (32 bytes of K).
+template <int MODE>
+constexpr int kstep_elems() { return 32 / Operands<MODE>::EB; }
+
 // Issue the MMAs of one K chunk (thread 0 only) and commit them to mbar.
 template <int MODE>
 __device__ __forceinline__ void issue_chunk(uint32_t tmem, const unsigned char *A, const unsigned char *Bop,
-                                            bool first, uint64_t *mbar) {
+                                            bool first, int ksteps, uint64_t *mbar) {
     using O = Operands<MODE>;
     tc::fence_after_sync();
     const uint32_t abase = tc::smem_u32(A), bbase = tc::smem_u32(Bop);
     constexpr uint32_t LBO_A = kTile * 16, LBO_B = kNCols * 16, SBO = 128;
-    constexpr int KSTEPS = kChunk * O::EB / 32;  // 32 bytes of K per MMA
     if (MODE == SOFT_MIXED_TF32) {
         constexpr uint32_t idesc = tc::instr_desc(2, kTile, kNCols);
-        for (int s = 0; s < KSTEPS; ++s) {
+        for (int s = 0; s < ksteps; ++s) {
             const uint64_t ad = tc::smem_desc(abase + s * 2 * LBO_A, LBO_A, SBO);
             const uint64_t bd = tc::smem_desc(bbase + s * 2 * LBO_B, LBO_B, SBO);
             tc::mma_tf32(tmem, ad, bd, idesc, (first && s == 0) ? 0u : 1u);
@@ -84,7 +115,7 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem, const unsigned char *
     } else {
         constexpr uint32_t idesc = tc::instr_desc(1, kTile, kNCols);
         const uint32_t alo = abase + O::A_BYTES, blo = bbase + O::B_BYTES;
-        for (int s = 0; s < KSTEPS; ++s) {
+        for (int s = 0; s < ksteps; ++s) {
             const uint32_t ao = s * 2 * LBO_A, bo = s * 2 * LBO_B;
             tc::mma_bf16(tmem, tc::smem_desc(abase + ao, LBO_A, SBO), tc::smem_desc(bbase + bo, LBO_B, SBO), idesc,
                          (first && s == 0) ? 0u : 1u);
@@ -106,7 +137,7 @@ struct MixedTables {
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, const float2 *__restrict__ S,
-                                                                 double *__restrict__ coef) {
+                                                                 double *__restrict__ coef, int flags) {
     using O = Operands<MODE>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
@@ -128,13 +159,13 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
         double a, ac, bc;
         recurrence_coeffs(l0 + t, m, mp, a, ac, bc);
         rA[t] = a; rAc[t] = ac; rBc[t] = bc;
-        rV[t] = (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B);
+        rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
     }
     {
         const double lognorm = seed_lognorm(tb, m, mp);
         for (int j = tid; j < n; j += kNT) {
             // w_B(j) d(l0,m,m';beta_j): the weight enters through the seed's logarithm
-            dcur[j] = seed_rep(m, mp, lognorm + mt.lw[j], tb.lcos[j], tb.lsin[j]);
+            dcur[j] = seed_rep(m, mp, (flags & kApplyW) ? lognorm + mt.lw[j] : lognorm, tb.lcos[j], tb.lsin[j]);
             dprev[j] = 0.0;
         }
     }
@@ -152,29 +183,51 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
     for (int lb = l0; lb < B && ok; lb += kTile) {
         const int rows = min(kTile, B - lb);
         for (int c = 0; c < nchunks && ok; ++c) {
-            // A: column tid of the tile = beta sample j; rows = degrees lb..lb+rows-1.
+            // K extent of this chunk, rounded up to whole MMA K steps (the padding is zero).
+            const int kvalid = min(kChunk, n - c * kChunk);
+            const int ksteps = (kvalid + kstep_elems<MODE>() - 1) / kstep_elems<MODE>();
+            const int kfill = ksteps * kstep_elems<MODE>();
+            // A: column tid = beta sample j, rows = degrees lb..lb+rows-1.  Rows past
+            // `rows` are left as they are: they only reach TMEM lanes that are never read.
             const int j = c * kChunk + tid;
-            if (j < n) {
+            constexpr int KPC = 16 / O::EB;
+            unsigned char *acol = A + (tid / KPC) * (kTile * 16) + (tid % KPC) * O::EB;  // row r at +16 r
+            if (tid < kvalid) {
                 const double x = tb.cosb[j];
                 double dc = dcur[j], dp = dprev[j];
                 for (int r = 0; r < rows; ++r) {
-                    put<MODE>(A, O::A_BYTES, kTile, r, tid, tc::f64_to_f32_trunc(dc));
+                    const float v = tc::f64_to_f32_trunc(dc);
+                    if (MODE == SOFT_MIXED_TF32) {
+                        *reinterpret_cast<float *>(acol + 16 * r) = tc::round_tf32(v);
+                    } else {
+                        uint16_t hi, lo;
+                        tc::split_bf16(v, hi, lo);
+                        *reinterpret_cast<uint16_t *>(acol + 16 * r) = hi;
+                        *reinterpret_cast<uint16_t *>(acol + O::A_BYTES + 16 * r) = lo;
+                    }
                     const int q = lb + r - l0;
                     const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -rBc[q] * dp);
                     dp = dc;
                     dc = nx;
                 }
-                for (int r = rows; r < kTile; ++r) put<MODE>(A, O::A_BYTES, kTile, r, tid, 0.0f);
                 dcur[j] = dc;
                 dprev[j] = dp;
-            } else {
-                for (int r = 0; r < kTile; ++r) put<MODE>(A, O::A_BYTES, kTile, r, tid, 0.0f);
+            } else if (tid < kfill) {
+                for (int r = 0; r < kTile; ++r) {
+                    if (MODE == SOFT_MIXED_TF32) {
+                        *reinterpret_cast<float *>(acol + 16 * r) = 0.f;
+                    } else {
+                        *reinterpret_cast<uint16_t *>(acol + 16 * r) = 0;
+                        *reinterpret_cast<uint16_t *>(acol + O::A_BYTES + 16 * r) = 0;
+                    }
+                }
             }
             // B: X chunk, row 2p / 2p+1 = re / im of partner p, k = beta sample in chunk.
             for (int e = tid; e < 8 * kChunk; e += kNT) {
                 const int p = e / kChunk, k = e % kChunk, jj = c * kChunk + k;
+                if (k >= kfill) continue;
                 float2 v = make_float2(0.f, 0.f);
-                if (p < np && jj < n) {
+                if (p < np && k < kvalid) {
                     const int src = cs.mir[p] ? n - 1 - jj : jj;
                     v = S[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + src];
                 }
@@ -183,7 +236,7 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
             }
             tc::fence_proxy_async();
             __syncthreads();
-            if (tid == 0) issue_chunk<MODE>(tmem, A, X, c == 0, &mbar);
+            if (tid == 0) issue_chunk<MODE>(tmem, A, X, c == 0, ksteps, &mbar);
             const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
             phase ^= 1u;
             ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
@@ -223,7 +276,7 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, const double *__restrict__ coef,
-                                                                 float2 *__restrict__ S) {
+                                                                 float2 *__restrict__ S, int flags) {
     using O = Operands<MODE>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
@@ -265,35 +318,47 @@ __global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, 
         }
         for (int lb = l0, c = 0; lb < B && ok; lb += kChunk, ++c) {
             const int cnt = min(kChunk, B - lb);
-            // A: row tid = beta sample j, K = degrees lb..lb+cnt-1.
-            for (int k = 0; k < kChunk; ++k) {
-                float v = 0.f;
-                if (active && k < cnt) {
-                    v = tc::f64_to_f32_trunc(dc);
-                    const int q = lb + k - l0;
-                    const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -rBc[q] * dp);
-                    dp = dc;
-                    dc = nx;
+            const int ksteps = (cnt + kstep_elems<MODE>() - 1) / kstep_elems<MODE>();
+            const int kfill = ksteps * kstep_elems<MODE>();
+            // A: row tid = beta sample j, K = degrees lb..lb+cnt-1 (zero up to kfill);
+            // 16-byte vector stores.  Rows of inactive samples are never read back.
+            constexpr int VEC = 16 / O::EB;
+            if (active) {
+                for (int k0 = 0; k0 < kfill; k0 += VEC) {
+                    float v[VEC];
+#pragma unroll
+                    for (int u = 0; u < VEC; ++u) {
+                        v[u] = 0.f;
+                        if (k0 + u < cnt) {
+                            v[u] = tc::f64_to_f32_trunc(dc);
+                            const int q = lb + k0 + u - l0;
+                            const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -rBc[q] * dp);
+                            dp = dc;
+                            dc = nx;
+                        }
+                    }
+                    put_vec<MODE>(A, O::A_BYTES, kTile, tid, k0, v);
                 }
-                put<MODE>(A, O::A_BYTES, kTile, tid, k, v);
             }
             // B: F chunk, row 2p / 2p+1 = sign-folded re / im of partner p at degree lb + k.
             for (int e = tid; e < 8 * kChunk; e += kNT) {
                 const int p = e / kChunk, k = e % kChunk;
+                if (k >= kfill) continue;
                 float re = 0.f, im = 0.f;
                 if (p < np && k < cnt) {
                     const int l = lb + k;
                     const double2 cv = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + (l - l0)));
                     const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
-                    re = tc::f64_to_f32_rn(neg ? -cv.x : cv.x);
-                    im = tc::f64_to_f32_rn(neg ? -cv.y : cv.y);
+                    const double v = (flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0;
+                    re = tc::f64_to_f32_rn(neg ? -v * cv.x : v * cv.x);
+                    im = tc::f64_to_f32_rn(neg ? -v * cv.y : v * cv.y);
                 }
                 put<MODE>(F, O::B_BYTES, kNCols, 2 * p, k, re);
                 put<MODE>(F, O::B_BYTES, kNCols, 2 * p + 1, k, im);
             }
             tc::fence_proxy_async();
             __syncthreads();
-            if (tid == 0) issue_chunk<MODE>(tmem, A, F, c == 0, &mbar);
+            if (tid == 0) issue_chunk<MODE>(tmem, A, F, c == 0, ksteps, &mbar);
             const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
             phase ^= 1u;
             ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
@@ -307,8 +372,9 @@ __global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, 
             for (int p = 0; p < 8; ++p) {
                 if (p >= np) break;
                 const int jj = cs.mir[p] ? n - 1 - j : j;
+                const float wj = (flags & kApplyW) ? tc::f64_to_f32_rn(tb.w[jj]) : 1.0f;
                 S[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + jj] =
-                    make_float2(__uint_as_float(d[2 * p]), __uint_as_float(d[2 * p + 1]));
+                    make_float2(wj * __uint_as_float(d[2 * p]), wj * __uint_as_float(d[2 * p + 1]));
             }
         }
         tc::fence_before_sync();
@@ -354,6 +420,26 @@ __global__ void f32_to_f64_kernel(const float2 *__restrict__ in, double2 *__rest
     }
 }
 
+// Y[q][j] = X[j][q] for a rows x cols complex64 matrix (rows = 2B beta
+// samples, cols = (2B)^2 order pairs): 32 x 32 tiles through shared memory,
+// coalesced on both sides.
+__global__ void transpose32_kernel(const float2 *__restrict__ X, float2 *__restrict__ Y, int rows, int64_t cols) {
+    __shared__ float2 tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int r0 = blockIdx.y * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int r = r0 + dy;
+        const int64_t c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[dy][threadIdx.x] = X[(int64_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t c = c0 + dy;
+        const int r = r0 + threadIdx.x;
+        if (r < rows && c < cols) Y[c * rows + r] = tile[threadIdx.x][dy];
+    }
+}
+
 int grid_for(int64_t count) { return (int)std::min<int64_t>((count + 255) / 256, 152 * 16); }
 
 }  // namespace
@@ -375,7 +461,7 @@ cudaError_t launch_log_weights(int B, const double *w, double *lw, cudaStream_t 
 }
 
 cudaError_t launch_dwt_forward_mixed(int mode, const Tables &tb, const double *lw, const float2 *S, double *coef,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, int flags) {
     MixedTables mt{tb, lw};
     const size_t bytes = mixed_forward_smem(mode, tb.B);
     cudaError_t e;
@@ -383,17 +469,18 @@ cudaError_t launch_dwt_forward_mixed(int mode, const Tables &tb, const double *l
         e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<SOFT_MIXED_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)bytes);
         if (e != cudaSuccess) return e;
-        dwt_forward_mixed_kernel<SOFT_MIXED_TF32><<<tb.ncl, kNT, bytes, s>>>(mt, S, coef);
+        dwt_forward_mixed_kernel<SOFT_MIXED_TF32><<<tb.ncl, kNT, bytes, s>>>(mt, S, coef, flags);
     } else {
         e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<SOFT_MIXED_BF16X3>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
-        dwt_forward_mixed_kernel<SOFT_MIXED_BF16X3><<<tb.ncl, kNT, bytes, s>>>(mt, S, coef);
+        dwt_forward_mixed_kernel<SOFT_MIXED_BF16X3><<<tb.ncl, kNT, bytes, s>>>(mt, S, coef, flags);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s) {
+cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s,
+                                     int flags) {
     MixedTables mt{tb, nullptr};
     const size_t bytes = mixed_inverse_smem(mode, tb.B);
     cudaError_t e;
@@ -401,12 +488,12 @@ cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *c
         e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<SOFT_MIXED_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)bytes);
         if (e != cudaSuccess) return e;
-        dwt_inverse_mixed_kernel<SOFT_MIXED_TF32><<<tb.ncl, kNT, bytes, s>>>(mt, coef, S);
+        dwt_inverse_mixed_kernel<SOFT_MIXED_TF32><<<tb.ncl, kNT, bytes, s>>>(mt, coef, S, flags);
     } else {
         e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<SOFT_MIXED_BF16X3>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
-        dwt_inverse_mixed_kernel<SOFT_MIXED_BF16X3><<<tb.ncl, kNT, bytes, s>>>(mt, coef, S);
+        dwt_inverse_mixed_kernel<SOFT_MIXED_BF16X3><<<tb.ncl, kNT, bytes, s>>>(mt, coef, S, flags);
     }
     return cudaGetLastError();
 }
@@ -414,6 +501,12 @@ cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *c
 cudaError_t launch_zero_nyquist32(int B, float2 *S, cudaStream_t s) {
     const int n = 2 * B;
     zero_nyquist32_kernel<<<grid_for((int64_t)(2 * n - 1) * n), 256, 0, s>>>(B, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose32(const float2 *X, float2 *Y, int rows, int64_t cols, cudaStream_t s) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    transpose32_kernel<<<grid, dim3(32, 8), 0, s>>>(X, Y, rows, cols);
     return cudaGetLastError();
 }
 

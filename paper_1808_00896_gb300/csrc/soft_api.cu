@@ -15,6 +15,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <list>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -32,6 +34,7 @@ struct soft_plan_s {
     double *w, *cosb, *lcos, *lsin, *lfact;
     int2 *clusters;
     int ncl;
+    std::vector<int2> h_clusters;  // host copy of the cluster work list
     int64_t *runoff;
     double2 *S;
     int *err;
@@ -43,6 +46,9 @@ struct soft_plan_s {
     cufftHandle fft32f, fft32i;
     bool fft32f_made, fft32i_made;
     double2 *stage_grid, *stage_coef;  // for the host-buffer entry points, allocated on first use
+    double2 *corr_coef;                // correlation coefficients, allocated on first use
+    double *amax_v;                    // arg-max partial results (argmax_parts() each)
+    int64_t *amax_i;
 
     // Per-phase timing (soft_plan_enable_timing): 3 events per timed call.
     static constexpr int kMaxRec = 4096;
@@ -186,39 +192,47 @@ void free_plan(soft_plan_s *p) {
     cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
     cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
     cudaFree(p->stage_grid); cudaFree(p->stage_coef);
+    cudaFree(p->corr_coef); cudaFree(p->amax_v); cudaFree(p->amax_i);
     p->magic = 0;
     delete p;
 }
 
-soft_status run_forward_mixed(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s) {
+soft_status run_forward_mixed(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s, int flags) {
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = launch_f64_to_f32(reinterpret_cast<const double2 *>(grid), p->g32, (int64_t)grid_elems(p->B), s);
     if (e != cudaSuccess) return fail_cuda("grid conversion kernel launch", e);
     cufftResult r = cufftSetStream(p->fft32f, s);
     if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
-    // S(m,m';j) with exp(+i...) = cuFFT INVERSE, written in layout [m][m'][j].
-    r = cufftExecC2C(p->fft32f, reinterpret_cast<cufftComplex *>(p->g32), reinterpret_cast<cufftComplex *>(p->S32),
+    // S(m,m';j) with exp(+i...) = cuFFT INVERSE, in place per contiguous slice,
+    // then transposed from [j][m][m'] to [m][m'][j].
+    r = cufftExecC2C(p->fft32f, reinterpret_cast<cufftComplex *>(p->g32), reinterpret_cast<cufftComplex *>(p->g32),
                      CUFFT_INVERSE);
     if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecC2C (forward slices)", r);
+    const int n = 2 * p->B;
+    e = launch_transpose32(p->g32, p->S32, n, (int64_t)n * n, s);
+    if (e != cudaSuccess) return fail_cuda("transpose kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
-    e = launch_dwt_forward_mixed(p->dtype, p->tables(), p->lw, p->S32, coef, s);
+    e = launch_dwt_forward_mixed(p->dtype, p->tables(), p->lw, p->S32, coef, s, flags);
     if (e != cudaSuccess) return fail_cuda("mixed DWT kernel launch", e);
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
 }
 
-soft_status run_inverse_mixed(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s) {
+soft_status run_inverse_mixed(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s, int flags) {
     cudaEvent_t *ev = timing_slot(p, 1);
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = launch_zero_nyquist32(p->B, p->S32, s);
     if (e != cudaSuccess) return fail_cuda("S clearing kernel launch", e);
-    e = launch_dwt_inverse_mixed(p->dtype, p->tables(), coef, p->S32, s);
+    e = launch_dwt_inverse_mixed(p->dtype, p->tables(), coef, p->S32, s, flags);
     if (e != cudaSuccess) return fail_cuda("mixed iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
-    cufftResult r = cufftSetStream(p->fft32i, s);
+    const int n = 2 * p->B;
+    e = launch_transpose32(p->S32, p->g32, n * n, (int64_t)n, s);
+    if (e != cudaSuccess) return fail_cuda("transpose kernel launch", e);
+    cufftResult r = cufftSetStream(p->fft32f, s);
     if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
-    r = cufftExecC2C(p->fft32i, reinterpret_cast<cufftComplex *>(p->S32), reinterpret_cast<cufftComplex *>(p->g32),
+    r = cufftExecC2C(p->fft32f, reinterpret_cast<cufftComplex *>(p->g32), reinterpret_cast<cufftComplex *>(p->g32),
                      CUFFT_FORWARD);
     if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecC2C (inverse slices)", r);
     e = launch_f32_to_f64(p->g32, reinterpret_cast<double2 *>(grid), (int64_t)grid_elems(p->B), s);
@@ -227,8 +241,10 @@ soft_status run_inverse_mixed(soft_plan_s *p, const double *coef, double *grid, 
     return SOFT_OK;
 }
 
-soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s) {
-    if (p->dtype != SOFT_FP64) return run_forward_mixed(p, grid, coef, s);
+// flags: kApplyW | kApplyV for the forward transform, 0 for the adjoint of the inverse.
+soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s,
+                        int flags = kApplyW | kApplyV) {
+    if (p->dtype != SOFT_FP64) return run_forward_mixed(p, grid, coef, s, flags);
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
     cufftResult r = cufftSetStream(p->fft, s);
@@ -238,19 +254,20 @@ soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaSt
     r = cufftExecZ2Z(p->fft, in, reinterpret_cast<cufftDoubleComplex *>(p->S), CUFFT_INVERSE);
     if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (forward slices)", r);
     if (ev) cudaEventRecord(ev[1], s);
-    cudaError_t e = launch_dwt_forward_fp64(p->tables(), p->S, reinterpret_cast<double2 *>(coef), s);
+    cudaError_t e = launch_dwt_forward_fp64(p->tables(), p->S, reinterpret_cast<double2 *>(coef), s, flags);
     if (e != cudaSuccess) return fail_cuda("DWT kernel launch", e);
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
 }
 
-soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s) {
-    if (p->dtype != SOFT_FP64) return run_inverse_mixed(p, coef, grid, s);
+// flags: 0 for the inverse transform, kApplyV | kApplyW for the adjoint of the forward.
+soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s, int flags = 0) {
+    if (p->dtype != SOFT_FP64) return run_inverse_mixed(p, coef, grid, s, flags);
     cudaEvent_t *ev = timing_slot(p, 1);
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = launch_zero_nyquist(p->B, p->S, s);
     if (e != cudaSuccess) return fail_cuda("S clearing kernel launch", e);
-    e = launch_dwt_inverse_fp64(p->tables(), reinterpret_cast<const double2 *>(coef), p->S, s);
+    e = launch_dwt_inverse_fp64(p->tables(), reinterpret_cast<const double2 *>(coef), p->S, s, flags);
     if (e != cudaSuccess) return fail_cuda("iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
     cufftResult r = cufftSetStream(p->fft, s);
@@ -277,6 +294,217 @@ soft_status ensure_staging(soft_plan_s *p) {
         }
     }
     return SOFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches: a list of transforms (any mix of bandwidths and modes, one plan per
+// entry) captured once into a CUDA graph and replayed on the caller's stream.
+// FP64 inverse transforms with B <= 128 share one persistent inverse-DWT
+// launch over all their clusters, heaviest first; everything else runs through
+// the per-plan path inside the same graph.
+// ---------------------------------------------------------------------------
+enum BatchKind { kBatchInverse = 0, kBatchForward = 1, kBatchCorrelate = 2 };
+
+struct BatchGraph {
+    int kind = 0;
+    std::vector<soft_plan_s *> plans;
+    std::vector<const void *> key;  // every pointer argument, in order
+    cudaGraphExec_t exec = nullptr;
+    BatchXform *d_xf = nullptr;
+    int2 *d_items = nullptr;
+    int *d_counter = nullptr;
+    ~BatchGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaFree(d_xf); cudaFree(d_items); cudaFree(d_counter);
+    }
+};
+
+std::mutex g_batch_mu;
+std::list<BatchGraph *> g_batches;  // most recently used first
+constexpr size_t kMaxCachedBatches = 16;
+
+void purge_batches_of(const soft_plan_s *p) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto it = g_batches.begin(); it != g_batches.end();) {
+        if (std::find((*it)->plans.begin(), (*it)->plans.end(), p) != (*it)->plans.end()) {
+            delete *it;
+            it = g_batches.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// Records the batch's work on stream cs (which is being captured).
+soft_status record_batch(BatchGraph *bg, int n, const void *const *a, const void *const *b, const void *const *c,
+                         const void *const *d, int64_t *best_index, double *best_value, cudaStream_t cs) {
+    std::vector<int> pers, rest;
+    int maxB = 1;
+    for (int i = 0; i < n; ++i) {
+        soft_plan_s *p = bg->plans[i];
+        if (bg->kind != kBatchForward && p->dtype == SOFT_FP64 && p->B <= kPersistentMaxB) {
+            pers.push_back(i);
+            maxB = std::max(maxB, p->B);
+        } else {
+            rest.push_back(i);
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (!pers.empty()) {
+        e = cudaMemsetAsync(bg->d_counter, 0, sizeof(int), cs);
+        for (int i : pers) {
+            soft_plan_s *p = bg->plans[i];
+            if (e == cudaSuccess && bg->kind == kBatchCorrelate)
+                e = launch_corr_coeffs(p->B, static_cast<const double2 *>(a[i]), static_cast<const double2 *>(b[i]),
+                                       p->runoff, p->corr_coef, cs);
+            if (e == cudaSuccess) e = launch_zero_nyquist(p->B, p->S, cs);
+        }
+        if (e == cudaSuccess) {
+            int nitems = 0;
+            for (int i : pers) nitems += bg->plans[i]->ncl;
+            e = launch_idwt_fp64_persistent(bg->d_xf, bg->d_items, nitems, bg->d_counter, maxB, cs);
+        }
+        if (e != cudaSuccess) return fail_cuda("batched inverse DWT", e);
+        for (int i : pers) {
+            soft_plan_s *p = bg->plans[i];
+            double *grid = bg->kind == kBatchCorrelate ? static_cast<double *>(const_cast<void *>(c[i]))
+                                                       : static_cast<double *>(const_cast<void *>(b[i]));
+            cufftResult r = cufftSetStream(p->fft, cs);
+            if (r == CUFFT_SUCCESS)
+                r = cufftExecZ2Z(p->fft, reinterpret_cast<cufftDoubleComplex *>(p->S),
+                                 reinterpret_cast<cufftDoubleComplex *>(grid), CUFFT_FORWARD);
+            if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (batched inverse slices)", r);
+            if (bg->kind == kBatchCorrelate) {
+                e = launch_argmax_real(reinterpret_cast<const double2 *>(grid), (int64_t)grid_elems(p->B), p->amax_v,
+                                       p->amax_i, best_index + i, best_value + i, cs);
+                if (e != cudaSuccess) return fail_cuda("batched arg-max", e);
+            }
+        }
+    }
+    for (int i : rest) {
+        soft_plan_s *p = bg->plans[i];
+        soft_status st = SOFT_OK;
+        if (bg->kind == kBatchForward) {
+            st = run_forward(p, static_cast<const double *>(a[i]), static_cast<double *>(const_cast<void *>(b[i])), cs);
+        } else if (bg->kind == kBatchInverse) {
+            st = run_inverse(p, static_cast<const double *>(a[i]), static_cast<double *>(const_cast<void *>(b[i])), cs);
+        } else {
+            double *grid = static_cast<double *>(const_cast<void *>(c[i]));
+            e = launch_corr_coeffs(p->B, static_cast<const double2 *>(a[i]), static_cast<const double2 *>(b[i]),
+                                   p->runoff, p->corr_coef, cs);
+            if (e != cudaSuccess) return fail_cuda("batched correlation coefficients", e);
+            st = run_inverse(p, reinterpret_cast<const double *>(p->corr_coef), grid, cs);
+            if (st == SOFT_OK) {
+                e = launch_argmax_real(reinterpret_cast<const double2 *>(grid), (int64_t)grid_elems(p->B), p->amax_v,
+                                       p->amax_i, best_index + i, best_value + i, cs);
+                if (e != cudaSuccess) return fail_cuda("batched arg-max", e);
+            }
+        }
+        if (st != SOFT_OK) return st;
+    }
+    (void)d;
+    return SOFT_OK;
+}
+
+// Validates a batch, finds or builds its graph, and launches it on `stream`.
+soft_status run_batch(int kind, int n, const soft_plan *plans, const void *const *a, const void *const *b,
+                      const void *const *c, int64_t *best_index, double *best_value, void *stream) {
+    if (n < 1 || !plans || !a || !b || (kind == kBatchCorrelate && (!c || !best_index || !best_value)))
+        return SOFT_ERR_INVALID_ARG;
+    std::vector<const void *> key;
+    std::vector<soft_plan_s *> ps(n);
+    int device = -1;
+    for (int i = 0; i < n; ++i) {
+        soft_plan_s *p = plans[i];
+        if (!valid(p)) return SOFT_ERR_INVALID_ARG;
+        if (device < 0) device = p->device;
+        if (p->device != device) return SOFT_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ps[j] == p) return SOFT_ERR_INVALID_ARG;  // each entry needs its own plan workspace
+        ps[i] = p;
+        if (!aligned16(a[i]) || !aligned16(b[i]) || (c && !aligned16(c[i]))) return SOFT_ERR_INVALID_ARG;
+        key.push_back(p); key.push_back(a[i]); key.push_back(b[i]); key.push_back(c ? c[i] : nullptr);
+    }
+    key.push_back(best_index); key.push_back(best_value);
+    DeviceGuard g(device);
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchGraph *bg = nullptr;
+    for (auto it = g_batches.begin(); it != g_batches.end(); ++it)
+        if ((*it)->kind == kind && (*it)->key == key) {
+            bg = *it;
+            g_batches.erase(it);
+            g_batches.push_front(bg);
+            break;
+        }
+    if (!bg) {
+        bg = new (std::nothrow) BatchGraph();
+        if (!bg) return SOFT_ERR_OUT_OF_MEMORY;
+        bg->kind = kind;
+        bg->plans = ps;
+        bg->key = key;
+        // Workspaces and the persistent kernel's tables, allocated before capture.
+        std::vector<BatchXform> xf(n);
+        std::vector<std::pair<int64_t, int2>> items;
+        for (int i = 0; i < n; ++i) {
+            soft_plan_s *p = ps[i];
+            if (kind == kBatchCorrelate && !p->corr_coef) {
+                cudaError_t e = cudaMalloc(&p->corr_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B));
+                if (e != cudaSuccess) { p->corr_coef = nullptr; delete bg; return fail_cuda("correlation workspace", e); }
+            }
+            xf[i].tb = p->tables();
+            xf[i].coef = kind == kBatchCorrelate ? reinterpret_cast<const double *>(p->corr_coef)
+                                                 : static_cast<const double *>(a[i]);
+            xf[i].S = p->S;
+            xf[i].flags = 0;
+            if (kind != kBatchForward && p->dtype == SOFT_FP64 && p->B <= kPersistentMaxB)
+                for (int cidx = 0; cidx < p->ncl; ++cidx) {
+                    const int2 cl = p->h_clusters[cidx];
+                    const int np = (cl.x == 0 && cl.y == 0) ? 1 : (cl.y == 0 || cl.x == cl.y) ? 4 : 8;
+                    items.push_back({(int64_t)(p->B - cl.x) * (2 * p->B) * np, make_int2(i, cidx)});
+                }
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const std::pair<int64_t, int2> &x, const std::pair<int64_t, int2> &y) { return x.first > y.first; });
+        std::vector<int2> hitems(items.size());
+        for (size_t t = 0; t < items.size(); ++t) hitems[t] = items[t].second;
+        cudaError_t e = cudaMalloc(&bg->d_xf, sizeof(BatchXform) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&bg->d_items, sizeof(int2) * std::max<size_t>(1, hitems.size()));
+        if (e == cudaSuccess) e = cudaMalloc(&bg->d_counter, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(bg->d_xf, xf.data(), sizeof(BatchXform) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !hitems.empty())
+            e = cudaMemcpy(bg->d_items, hitems.data(), sizeof(int2) * hitems.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { delete bg; return fail_cuda("batch set-up", e); }
+
+        // Capture on a private stream (per-phase timing is not recorded inside graphs).
+        cudaStream_t cs;
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete bg; return fail_cuda("batch capture stream", e); }
+        std::vector<bool> timing(n);
+        for (int i = 0; i < n; ++i) { timing[i] = ps[i]->timing; ps[i]->timing = false; }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        soft_status st = e == cudaSuccess ? record_batch(bg, n, a, b, c, nullptr, best_index, best_value, cs)
+                                          : fail_cuda("cudaStreamBeginCapture", e);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        for (int i = 0; i < n; ++i) ps[i]->timing = timing[i];
+        if (st == SOFT_OK && e2 != cudaSuccess) st = fail_cuda("cudaStreamEndCapture", e2);
+        if (st == SOFT_OK) {
+            e = cudaGraphInstantiate(&bg->exec, graph, 0);
+            if (e != cudaSuccess) st = fail_cuda("cudaGraphInstantiate", e);
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (st != SOFT_OK) { delete bg; return st; }
+        g_batches.push_front(bg);
+        while (g_batches.size() > kMaxCachedBatches) {
+            delete g_batches.back();
+            g_batches.pop_back();
+        }
+    }
+    cudaError_t e = cudaGraphLaunch(bg->exec, user);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("cudaGraphLaunch", e);
 }
 
 }  // namespace
@@ -339,6 +567,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     };
     std::stable_sort(cl.begin(), cl.end(), [&](const int2 &a, const int2 &b) { return weight(a) > weight(b); });
     p->ncl = (int)cl.size();
+    p->h_clusters = cl;
     std::vector<int64_t> ro((size_t)R * R);
     for (int m = 1 - B; m <= B - 1; ++m)
         for (int mp = 1 - B; mp <= B - 1; ++mp) ro[runoff_index(B, m, mp)] = run_start(B, m, mp);
@@ -355,6 +584,8 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     alloc((void **)&p->clusters, sizeof(int2) * cl.size());
     alloc((void **)&p->runoff, sizeof(int64_t) * ro.size());
     alloc((void **)&p->err, sizeof(int));
+    alloc((void **)&p->amax_v, sizeof(double) * argmax_parts());
+    alloc((void **)&p->amax_i, sizeof(int64_t) * argmax_parts());
     if (dtype == SOFT_FP64) {
         alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
     } else {
@@ -384,16 +615,14 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
         r = cufftMakePlanMany64(p->fft, 2, dims, nullptr, 1, slice, nullptr, 1, slice, CUFFT_Z2Z, n, &work);
         if (r != CUFFT_SUCCESS) { free_plan(p); return fail_cufft("cufftMakePlanMany64 (Z2Z)", r); }
     } else {
-        // FP32 C2C plans; the beta index is the batch: contiguous slices on the grid
-        // side, stride 1 (beta fastest) with element stride 2B on the S side.
+        // One FP32 C2C plan over the 2B contiguous slices, run in place on the
+        // staging buffer in both directions; a tiled transpose moves S between
+        // the FFT layout [j][m][m'] and the DWT layout [m][m'][j].
+        (void)emb;
         if (cufftCreate(&p->fft32f) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
         p->fft32f_made = true;
-        r = cufftMakePlanMany64(p->fft32f, 2, dims, emb, 1, slice, emb, n, 1, CUFFT_C2C, n, &work);
-        if (r != CUFFT_SUCCESS) { free_plan(p); return fail_cufft("cufftMakePlanMany64 (C2C forward)", r); }
-        if (cufftCreate(&p->fft32i) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
-        p->fft32i_made = true;
-        r = cufftMakePlanMany64(p->fft32i, 2, dims, emb, n, 1, emb, 1, slice, CUFFT_C2C, n, &work);
-        if (r != CUFFT_SUCCESS) { free_plan(p); return fail_cufft("cufftMakePlanMany64 (C2C inverse)", r); }
+        r = cufftMakePlanMany64(p->fft32f, 2, dims, nullptr, 1, slice, nullptr, 1, slice, CUFFT_C2C, n, &work);
+        if (r != CUFFT_SUCCESS) { free_plan(p); return fail_cufft("cufftMakePlanMany64 (C2C)", r); }
     }
     *out = p;
     return SOFT_OK;
@@ -404,6 +633,7 @@ soft_status soft_destroy(soft_plan p) {
     if (!valid(p)) return SOFT_ERR_INVALID_ARG;
     DeviceGuard g(p->device);
     cudaDeviceSynchronize();
+    purge_batches_of(p);
     free_plan(p);
     return SOFT_OK;
 }
@@ -438,6 +668,79 @@ soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *st
     DeviceGuard g(p->device);
     return run_inverse(p, coef, grid, static_cast<cudaStream_t>(stream));
 }
+
+soft_status soft_forward_adjoint(soft_plan p, const double *coef, double *grid, void *stream) {
+    soft_status st = check_plan_args(p, coef, grid);
+    if (st != SOFT_OK) return st;
+    DeviceGuard g(p->device);
+    return run_inverse(p, coef, grid, static_cast<cudaStream_t>(stream), kApplyV | kApplyW);
+}
+
+soft_status soft_inverse_adjoint(soft_plan p, const double *grid, double *coef, void *stream) {
+    soft_status st = check_plan_args(p, grid, coef);
+    if (st != SOFT_OK) return st;
+    DeviceGuard g(p->device);
+    return run_forward(p, grid, coef, static_cast<cudaStream_t>(stream), 0);
+}
+
+soft_status soft_batched_inverse(int n, const soft_plan *plans, const double *const *coefs, double *const *grids,
+                                 void *stream) {
+    return run_batch(kBatchInverse, n, plans, reinterpret_cast<const void *const *>(coefs),
+                     reinterpret_cast<const void *const *>(grids), nullptr, nullptr, nullptr, stream);
+}
+
+soft_status soft_batched_forward(int n, const soft_plan *plans, const double *const *grids, double *const *coefs,
+                                 void *stream) {
+    return run_batch(kBatchForward, n, plans, reinterpret_cast<const void *const *>(grids),
+                     reinterpret_cast<const void *const *>(coefs), nullptr, nullptr, nullptr, stream);
+}
+
+soft_status soft_batched_correlate(int n, const soft_plan *plans, const double *const *f_sh,
+                                   const double *const *g_sh, double *const *grids, int64_t *best_index,
+                                   double *best_value, void *stream) {
+    return run_batch(kBatchCorrelate, n, plans, reinterpret_cast<const void *const *>(f_sh),
+                     reinterpret_cast<const void *const *>(g_sh), reinterpret_cast<const void *const *>(grids),
+                     best_index, best_value, stream);
+}
+
+soft_status soft_correlation_coeffs(soft_plan p, const double *f_sh, const double *g_sh, double *coef, void *stream) {
+    if (!valid(p) || !aligned16(f_sh) || !aligned16(g_sh) || !aligned16(coef)) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    return cuda_status(launch_corr_coeffs(p->B, reinterpret_cast<const double2 *>(f_sh),
+                                          reinterpret_cast<const double2 *>(g_sh), p->runoff,
+                                          reinterpret_cast<double2 *>(coef), static_cast<cudaStream_t>(stream)));
+}
+
+soft_status soft_correlate(soft_plan p, const double *f_sh, const double *g_sh, double *grid, int64_t *best_index,
+                           double *best_value, void *stream) {
+    if (!valid(p) || !aligned16(f_sh) || !aligned16(g_sh) || !aligned16(grid)) return SOFT_ERR_INVALID_ARG;
+    if ((best_index == nullptr) != (best_value == nullptr)) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!p->corr_coef) {
+        cudaError_t e = cudaMalloc(&p->corr_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B));
+        if (e != cudaSuccess) { p->corr_coef = nullptr; return fail_cuda("correlation workspace", e); }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_corr_coeffs(p->B, reinterpret_cast<const double2 *>(f_sh),
+                                       reinterpret_cast<const double2 *>(g_sh), p->runoff, p->corr_coef, s);
+    if (e != cudaSuccess) return fail_cuda("correlation coefficient kernel launch", e);
+    soft_status st = run_inverse(p, reinterpret_cast<const double *>(p->corr_coef), grid, s);
+    if (st != SOFT_OK || !best_index) return st;
+    e = launch_argmax_real(reinterpret_cast<const double2 *>(grid), (int64_t)grid_elems(p->B), p->amax_v, p->amax_i,
+                           best_index, best_value, s);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("arg-max kernel launch", e);
+}
+
+soft_status soft_argmax_real(const double *data, int64_t count, int64_t *index_out, double *value_out,
+                             double *scratch, void *stream) {
+    if (!aligned16(data) || count < 1 || !index_out || !value_out || !aligned16(scratch)) return SOFT_ERR_INVALID_ARG;
+    double *sv = scratch;
+    int64_t *si = reinterpret_cast<int64_t *>(scratch + argmax_parts());
+    return cuda_status(launch_argmax_real(reinterpret_cast<const double2 *>(data), count, sv, si, index_out,
+                                          value_out, static_cast<cudaStream_t>(stream)));
+}
+
+int soft_argmax_scratch_doubles(void) { return 2 * argmax_parts(); }
 
 soft_status soft_dwt_forward(soft_plan p, const double *S, double *coef, void *stream) {
     soft_status st = check_plan_args(p, S, coef);

@@ -143,12 +143,40 @@ __device__ inline void load_cluster(const Tables &tb, int m, int mp, ClusterSmem
     }
 }
 
+// Scalings applied by the DWT kernels.  The transforms use
+//   forward  f = V T W E x       (DWT with kApplyW | kApplyV)
+//   inverse  x = E^H T^T f       (iDWT with no flag)
+// and their adjoints, with the same kernels,
+//   forward^H  = E^H W T^T V     (iDWT with kApplyV on the coefficients, kApplyW on S)
+//   inverse^H  = T E             (DWT with no flag).
+enum DwtFlags : int { kApplyW = 1, kApplyV = 2 };
+
+// One transform of a batch for the persistent inverse DWT (FP64, B <= 128).
+struct BatchXform {
+    Tables tb;
+    const double *coef;  // interleaved complex coefficients
+    double2 *S;          // the plan's S workspace, layout [j][m][m']
+    int flags;
+};
+constexpr int kPersistentMaxB = 128;
+cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
+                                        cudaStream_t s);
+
+// Launchers (correlate.cu).
+cudaError_t launch_corr_coeffs(int B, const double2 *f, const double2 *g, const int64_t *runoff, double2 *coef,
+                               cudaStream_t s);
+cudaError_t launch_argmax_real(const double2 *data, int64_t count, double *scratch_v, int64_t *scratch_i,
+                               int64_t *index_out, double *value_out, cudaStream_t s);
+int argmax_parts();
+
 // Records the detail returned by soft_last_error() on this host thread (soft_api.cu).
 void set_last_error_message(const char *where, const char *what);
 
 // Launchers (dwt_fp64.cu).
-cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s);
-cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s);
+cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s,
+                                    int flags = kApplyW | kApplyV);
+cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s,
+                                    int flags = 0);
 cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s);
 cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *lsin, double *lfact,
                           cudaStream_t s);
@@ -156,10 +184,12 @@ cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *
 // Launchers (dwt_mixed.cu); mode is SOFT_MIXED_BF16X3 or SOFT_MIXED_TF32.
 cudaError_t launch_log_weights(int B, const double *w, double *lw, cudaStream_t s);
 cudaError_t launch_dwt_forward_mixed(int mode, const Tables &tb, const double *lw, const float2 *S, double *coef,
-                                     cudaStream_t s);
-cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s);
+                                     cudaStream_t s, int flags = kApplyW | kApplyV);
+cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s,
+                                     int flags = 0);
 cudaError_t launch_zero_nyquist32(int B, float2 *S, cudaStream_t s);
 cudaError_t launch_f64_to_f32(const double2 *in, float2 *out, int64_t count, cudaStream_t s);
+cudaError_t launch_transpose32(const float2 *X, float2 *Y, int rows, int64_t cols, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float2 *in, double2 *out, int64_t count, cudaStream_t s);
 
 }  // namespace softgb

@@ -58,6 +58,26 @@ def coefficients(B: int, kind: str = "gauss_decay", seed: int = BASE_SEED) -> np
     raise ValueError(f"unknown coefficient kind {kind!r}")
 
 
+def sh_coefficients(B: int, seed: int = BASE_SEED) -> np.ndarray:
+    """Spherical-harmonic coefficients of a random band-limited function on the
+    sphere: f_lm (index l*l + m + l, l < B), iid complex Gaussian x 1/(l+1)."""
+    rng = np.random.default_rng(seed)
+    c = np.empty(B * B, dtype=np.complex128)
+    c.view(np.float64)[:] = rng.standard_normal(2 * B * B)
+    l = np.floor(np.sqrt(np.arange(B * B))).astype(np.float64)
+    return c / (l + 1.0)
+
+
+def correlation_requests(count: int = 64, bandwidths=(8, 16, 32, 64, 128), seed: int = BASE_SEED):
+    """Batched rotational-matching workload: `count` requests with bandwidths
+    drawn uniformly from `bandwidths`, each a pair (f_lm, g_lm) of random
+    band-limited spherical functions.  Returns a list of (B, f_sh, g_sh)."""
+    rng = np.random.default_rng(seed)
+    Bs = rng.choice(np.asarray(bandwidths), size=count)
+    return [(int(B), sh_coefficients(int(B), seed + 2 * i + 1), sh_coefficients(int(B), seed + 2 * i + 2))
+            for i, B in enumerate(Bs)]
+
+
 def random_grid(B: int, seed: int = BASE_SEED) -> np.ndarray:
     """iid U(-1,1) complex samples on the (2B)^3 grid, shape (2B, 2B, 2B) = [j][i][k]."""
     rng = np.random.default_rng(seed)

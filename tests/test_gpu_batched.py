@@ -1,0 +1,126 @@
+"""GPU: batched transforms (one persistent, graph-captured launch for the FP64
+inverse DWTs of B <= 128) against per-plan calls -- bit for bit in FP64 --
+and the rotational-correlation pipeline (coefficients, inverse transform,
+arg-max) against the oracle, on the batched rotational-matching workload."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1808_00896_gb300 import Plan, batched_correlate, batched_forward, batched_inverse, capi, synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1808_00896_gb300 import build
+    build.build()
+    oracle.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def _coef(B, seed):
+    return torch.from_numpy(synth.coefficients(B, "gauss_decay", seed=seed)).to(DEV)
+
+
+def test_batched_inverse_bitwise_equals_single_calls_and_replays():
+    specs = [(8, "fp64"), (16, "fp64"), (128, "fp64"), (33, "fp64"), (64, "fp64"), (256, "fp64"), (32, "bf16x3")]
+    plans = [Plan(B, m, device=DEV) for B, m in specs]
+    try:
+        for rnd in range(2):  # second round replays the cached graph on new data
+            coefs = [_coef(p.B, 100 * rnd + i) for i, p in enumerate(plans)]
+            grids = [p.empty_grid() for p in plans]
+            batched_inverse(plans, coefs, grids)
+            torch.cuda.synchronize(DEV)
+            for p, c, g in zip(plans, coefs, grids):
+                ref = p.inverse(c)
+                torch.cuda.synchronize(DEV)
+                if p.dtype == "fp64":
+                    assert torch.equal(g, ref), f"B={p.B} not bitwise equal"
+                else:
+                    assert synth.rel_l2(g.cpu().numpy(), ref.cpu().numpy()) < 1e-6
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_batched_forward_equals_single_calls():
+    specs = [(8, "fp64"), (64, "fp64"), (16, "tf32")]
+    plans = [Plan(B, m, device=DEV) for B, m in specs]
+    try:
+        grids = [torch.from_numpy(synth.random_grid(p.B, seed=7 + i)).to(DEV) for i, p in enumerate(plans)]
+        coefs = batched_forward(plans, grids)
+        torch.cuda.synchronize(DEV)
+        for p, g, c in zip(plans, grids, coefs):
+            assert torch.equal(c, p.forward(g))
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_batch_rejects_repeated_plan():
+    with Plan(8, device=DEV) as p:
+        c = _coef(8, 1)
+        g1, g2 = p.empty_grid(), p.empty_grid()
+        with pytest.raises(capi.SoftError):
+            batched_inverse([p, p], [c, c], [g1, g2])
+
+
+def test_single_correlation_vs_oracle():
+    B = 16
+    f = synth.sh_coefficients(B, seed=1)
+    g = synth.sh_coefficients(B, seed=2)
+    with Plan(B, device=DEV) as p:
+        grid, idx, val = p.correlate(torch.from_numpy(f).to(DEV), torch.from_numpy(g).to(DEV))
+        coef = p.correlation_coeffs(torch.from_numpy(f).to(DEV), torch.from_numpy(g).to(DEV))
+        torch.cuda.synchronize(DEV)
+    ref_c = oracle.correlation_coeffs(B, f, g)
+    # one complex product per entry; the GPU fuses multiply-adds, the oracle does not
+    assert synth.rel_l2(coef.cpu().numpy(), ref_c) < 1e-15
+    ref = oracle.correlation(B, f, g)
+    assert synth.rel_l2(grid.cpu().numpy(), ref) < 1e-10
+    oi, ov = oracle.argmax_real(ref)
+    gi, gv = int(idx.item()), float(val.item())
+    # the arg-max is unique unless two grid values tie within rounding
+    assert abs(gv - ov) < 1e-10 * abs(ov)
+    assert abs(ref.reshape(-1)[gi].real - ov) < 1e-10 * abs(ov)
+    assert gi == int(np.argmax(grid.cpu().numpy().reshape(-1).real))
+
+
+def test_batched_correlation_workload():
+    """64 requests, B uniform in {8,16,32,64,128}, one graph-captured batch:
+    per-request grids bitwise equal to single calls, arg-max equal to the
+    oracle's (B <= 32 checked against the full oracle, larger B against the
+    GPU grid and oracle values at the arg-max)."""
+    reqs = synth.correlation_requests(64, seed=synth.BASE_SEED + 4)
+    plans = [Plan(B, device=DEV) for B, _, _ in reqs]
+    try:
+        fs = [torch.from_numpy(f).to(DEV) for _, f, _ in reqs]
+        gs = [torch.from_numpy(g).to(DEV) for _, _, g in reqs]
+        grids, bi, bv = batched_correlate(plans, fs, gs)
+        grids2, bi2, bv2 = batched_correlate(plans, fs, gs, grids=grids)  # replay
+        torch.cuda.synchronize(DEV)
+        bi, bv = bi.cpu().numpy(), bv.cpu().numpy()
+        for t, ((B, f, g), p, gr) in enumerate(zip(reqs, plans, grids)):
+            single, si, sv = p.correlate(fs[t], gs[t])
+            torch.cuda.synchronize(DEV)
+            assert torch.equal(single, gr)
+            assert int(si.item()) == bi[t] and float(sv.item()) == bv[t]
+            if B <= 32:
+                ref = oracle.correlation(B, f, g)
+                assert synth.rel_l2(gr.cpu().numpy(), ref) < 1e-10
+                oi, ov = oracle.argmax_real(ref)
+                assert abs(bv[t] - ov) < 1e-10 * abs(ov)
+                assert abs(ref.reshape(-1)[bi[t]].real - ov) < 1e-10 * abs(ov)
+            elif t % 8 == 0:
+                n = 2 * B
+                j, rem = divmod(int(bi[t]), n * n)
+                i, k = divmod(rem, n)
+                val = oracle.inverse_points(B, oracle.correlation_coeffs(B, f, g), [(i, j, k)])[0]
+                assert abs(val.real - bv[t]) < 1e-10 * abs(bv[t])
+        assert np.array_equal(bi2.cpu().numpy(), bi)
+    finally:
+        for p in plans:
+            p.close()

@@ -135,3 +135,36 @@ def test_golden_forward_B4():
     assert np.array_equal(rows[:, :3].astype(np.int64), oracle.coef_lmm(B))
     ref = rows[:, 3] + 1j * rows[:, 4]
     assert synth.rel_l2(f, ref) < 1e-14
+
+
+@pytest.mark.parametrize("B", [1, 3, 6])
+def test_adjoints_dot_test(B):
+    """<F x, y> = <x, F^H y> and <G c, x> = <c, G^H x> with the pinned forward F
+    and inverse G: a wrong term, sign or index in an adjoint breaks the identity."""
+    rng = np.random.default_rng(B)
+    x = synth.random_grid(B, seed=50 + B)
+    y = synth.coefficients(B, "uniform", seed=60 + B)
+    lhs = np.vdot(oracle.forward(B, x), y)
+    rhs = np.vdot(x, oracle.forward_adjoint(B, y))
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+    lhs = np.vdot(oracle.inverse(B, y), x)
+    rhs = np.vdot(y, oracle.inverse_adjoint(B, x))
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+    assert rng is not None
+
+
+def test_adjoint_of_forward_is_dense_transpose():
+    """Brute force on B = 2: build the forward's matrix column by column and
+    compare its conjugate transpose with the adjoint applied to unit vectors."""
+    B = 2
+    n = 2 * B
+    N = n ** 3
+    M = np.zeros((oracle.num_coeffs(B), N), dtype=np.complex128)
+    for t in range(N):
+        e = np.zeros(N, dtype=np.complex128)
+        e[t] = 1.0
+        M[:, t] = oracle.forward(B, e.reshape(n, n, n))
+    for t in range(oracle.num_coeffs(B)):
+        e = np.zeros(oracle.num_coeffs(B), dtype=np.complex128)
+        e[t] = 1.0
+        assert np.allclose(oracle.forward_adjoint(B, e).reshape(-1), M.conj().T[:, t], atol=1e-14)
