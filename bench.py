@@ -47,6 +47,11 @@ for _B in (64, 128, 256, 512):
         WORKLOADS[f"b{_B}_{_m}"] = (_B, _m, "gauss_decay",
                                     f"mixed SOFT forward+inverse, B={_B}, {_d} contraction on tcgen05 tensor cores, "
                                     f"FP64 Wigner-d recurrence, FP32 2-D FFTs; complex128 in/out")
+# Batched rotational matching: 64 correlation requests, B uniform in {8,...,128}.
+CORR_WORKLOAD = ("corr64", "batched rotational matching: 64 correlation requests, B drawn uniformly from "
+                 "{8,16,32,64,128}, SH coefficients complex Gaussian x 1/(l+1); per request: correlation "
+                 "coefficients, FP64 inverse SOFT (one graph-captured persistent launch for all iDWTs), "
+                 "arg-max over the (2B)^3 grid")
 METRIC = "SOFT fwd+inv transforms/s"
 UNIT = "fwd+inv pairs/s"
 L2_BYTES = 129 * 2 ** 20
@@ -203,6 +208,99 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_corr(args) -> None:
+    """--workload corr64: batched correlations through soft_batched_correlate."""
+    import numpy as np
+    import torch
+
+    from paper_1808_00896_gb300 import Plan, batched_correlate, synth
+    from paper_1808_00896_gb300 import build as build_mod
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    build_mod.build()
+    reqs = synth.correlation_requests(64, seed=synth.BASE_SEED + 4 + 1000 * rank)
+    plans = [Plan(B, "fp64", device=dev) for B, _, _ in reqs]
+    fs = [torch.from_numpy(f).to(dev) for _, f, _ in reqs]
+    gs = [torch.from_numpy(g).to(dev) for _, _, g in reqs]
+    grids = [p.empty_grid() for p in plans]
+    bi = torch.empty(len(reqs), dtype=torch.int64, device=dev)
+    bv = torch.empty(len(reqs), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        batched_correlate(plans, fs, gs, grids, bi, bv)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(dev.index if world == 1 else local)
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        batched_correlate(plans, fs, gs, grids, bi, bv)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * len(reqs) * 1000.0 / ms
+    # e2e: SH coefficients host -> device, the batch, arg-max results device -> host.
+    fh = [torch.from_numpy(f).pin_memory() for _, f, _ in reqs]
+    gh = [torch.from_numpy(g).pin_memory() for _, _, g in reqs]
+    bih = torch.empty(len(reqs), dtype=torch.int64, pin_memory=True)
+    bvh = torch.empty(len(reqs), dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for a, b in zip(fs, fh):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(gs, gh):
+            a.copy_(b, non_blocking=True)
+        batched_correlate(plans, fs, gs, grids, bi, bv)
+        bih.copy_(bi, non_blocking=True)
+        bvh.copy_(bv, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_dt = time.perf_counter() - t0
+    h2d = sum(16 * B * B * 2 for B, _, _ in reqs)
+    # Roofline: the batch's inverse DWT flops over the whole step (FFT, coefficient
+    # build and arg-max included, so this understates the DWT kernel's own rate).
+    algo = sum(dwt_flops(B)["contraction"] + dwt_flops(B)["recurrence"] for B, _, _ in reqs)
+    peak_gflops = FP64_FLOPS_PER_SM_CLK * N_SM * SM_MAX_MHZ * 1e6 / 1e9
+    achieved = algo / (ms * 1e-3) / 1e9
+    if rank == 0:
+        Bs = [B for B, _, _ in reqs]
+        line = {
+            "metric": "batched rotational correlations/s", "value": value, "unit": "correlations/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CORR_WORKLOAD[1], "requests": len(reqs),
+                       "bandwidth_counts": {str(b): Bs.count(b) for b in sorted(set(Bs))},
+                       "parallelism": f"replicas x{world}", "l2": "per-step working set > 1 GB (> L2)"},
+            "e2e": {"value": world * len(reqs) * e2e_steps / e2e_dt, "unit": "correlations/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * len(reqs), "steps": e2e_steps},
+            "gpu_launches": None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s",
+                         "frac": achieved / peak_gflops, "traffic": None, "kernel": "idwt_fp64_persistent_kernel",
+                         "note": "whole-step time (FFTs, coefficient build and arg-max included)"},
+            "clocks": clocks, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -356,7 +454,7 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="b64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [CORR_WORKLOAD[0]], default="b64")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
@@ -364,6 +462,14 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
+    if args.workload == CORR_WORKLOAD[0]:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched correlation workload has no CPU "
+                              "reference arm; the oracle checks it in tests/test_gpu_batched.py"}))
+            return
+        args.steps = args.steps or 20
+        run_corr(args)
+        return
     if args.steps is None:
         B = WORKLOADS[args.workload][0]
         args.steps = {"ours": {16: 2000, 64: 400, 128: 60, 256: 10, 512: 3},

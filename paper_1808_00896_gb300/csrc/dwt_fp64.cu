@@ -64,18 +64,19 @@ __global__ void zero_nyquist_kernel(int B, double2 *S) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward DWT.  NT threads, LT = NT/16 degrees per tile, JPT beta samples per
-// thread in the recurrence phase.
+// Forward DWT.  NT threads, LT = NT/(16 TPI) degrees per tile, JPT beta samples
+// per thread in the recurrence phase, TPI threads per output (each sums a
+// contiguous 1/TPI of the beta range; TPI = 2 halves are combined by a shuffle).
 //   dynamic smem: X[2B][16] (w_B(j') S_p(j'), partner p in columns 2p, 2p+1),
 //                 T[LT][2B] (the current tile of T_B), rec[4][B] (A, Ac, Bc, V).
 // Phase A: every thread advances the recurrence of its beta samples LT steps,
 //          writing the tile of T.
 // Phase B: thread (t, c) forms sum_j T[t][j] X[j][c] for output column c.
 // ---------------------------------------------------------------------------
-template <int NT, int JPT>
+template <int NT, int JPT, int TPI>
 __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const double2 *__restrict__ S,
                                                                double *__restrict__ coef, int flags) {
-    constexpr int LT = NT / 16;
+    constexpr int LT = NT / (16 * TPI);
     extern __shared__ __align__(16) double smem[];
     __shared__ ClusterSmem cs;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x;
@@ -130,8 +131,10 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
     }
     __syncthreads();
 
-    const int pt = tid >> 4, pc = tid & 15;  // phase-B output (degree in tile, column)
+    const int half = tid % TPI, ot = tid / TPI;  // phase-B output (degree in tile, column) and beta part
+    const int pt = ot >> 4, pc = ot & 15;
     const int pp = pc >> 1;
+    const int jlen = n / TPI, jbeg = half * jlen;  // n = 2B is even
     for (int lb = l0; lb < B; lb += LT) {
         const int nt = min(LT, B - lb);
         // Phase A
@@ -150,21 +153,27 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
         }
         __syncthreads();
         // Phase B
-        if (pt < nt && pp < np) {
-            const double *Tr = T + pt * n;
-            const double *Xc = X + pc;
+        const bool active = pt < nt && pp < np;
+        double acc = 0.0;
+        if (active) {
+            const double *Tr = T + pt * n + jbeg;
+            const double *Xc = X + (size_t)jbeg * 16 + pc;
             double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
             int j = 0;
-            for (; j + 4 <= n; j += 4) {
+            for (; j + 4 <= jlen; j += 4) {
                 a0 = fma(Tr[j], Xc[j * 16], a0);
                 a1 = fma(Tr[j + 1], Xc[(j + 1) * 16], a1);
                 a2 = fma(Tr[j + 2], Xc[(j + 2) * 16], a2);
                 a3 = fma(Tr[j + 3], Xc[(j + 3) * 16], a3);
             }
-            for (; j < n; ++j) a0 = fma(Tr[j], Xc[j * 16], a0);
+            for (; j < jlen; ++j) a0 = fma(Tr[j], Xc[j * 16], a0);
+            acc = (a0 + a1) + (a2 + a3);
+        }
+        if (TPI == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (active && half == 0) {
             const int l = lb + pt;
             const double sg = (cs.lpar[pp] && (l & 1)) ? -cs.sign[pp] : cs.sign[pp];
-            coef[2 * (cs.off[pp] + (l - l0)) + (pc & 1)] = rV[l - l0] * sg * ((a0 + a1) + (a2 + a3));
+            coef[2 * (cs.off[pp] + (l - l0)) + (pc & 1)] = rV[l - l0] * sg * acc;
         }
         __syncthreads();
     }
@@ -305,14 +314,14 @@ __global__ void __launch_bounds__(256) idwt_fp64_persistent_kernel(const BatchXf
     }
 }
 
-template <int NT, int JPT>
+template <int NT, int JPT, int TPI>
 cudaError_t run_forward(const Tables &tb, const double2 *S, double *coef, cudaStream_t s, int flags) {
     const int B = tb.B, n = 2 * B;
-    const size_t bytes = sizeof(double) * ((size_t)n * 16 + (size_t)(NT / 16) * n + 4 * (size_t)B);
-    cudaError_t e = cudaFuncSetAttribute(dwt_forward_fp64_kernel<NT, JPT>,
+    const size_t bytes = sizeof(double) * ((size_t)n * 16 + (size_t)(NT / (16 * TPI)) * n + 4 * (size_t)B);
+    cudaError_t e = cudaFuncSetAttribute(dwt_forward_fp64_kernel<NT, JPT, TPI>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    dwt_forward_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, S, coef, flags);
+    dwt_forward_fp64_kernel<NT, JPT, TPI><<<tb.ncl, NT, bytes, s>>>(tb, S, coef, flags);
     return cudaGetLastError();
 }
 
@@ -345,13 +354,15 @@ cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s) {
 }
 
 // Shape choice: the forward needs X (2B x 16) and a T tile (LT x 2B) in shared
-// memory; at 2B = 1024 only NT = 128 (LT = 8) fits the 227 KB of a CTA.
+// memory.  Up to 2B = 256, 256 threads with LT = 16 (68 KB, 3 CTAs per SM);
+// beyond, LT = 8 with two threads per output, which keeps 256 threads per CTA
+// (2B = 512: 104 KB, 2 CTAs per SM; 2B = 1024: 208 KB, 1 CTA of 8 warps).
 cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s, int flags) {
     const int n = 2 * tb.B;
     double *c = reinterpret_cast<double *>(coef);
-    if (n <= 256) return run_forward<256, 1>(tb, S, c, s, flags);
-    if (n <= 512) return run_forward<256, 2>(tb, S, c, s, flags);
-    return run_forward<128, 8>(tb, S, c, s, flags);
+    if (n <= 256) return run_forward<256, 1, 1>(tb, S, c, s, flags);
+    if (n <= 512) return run_forward<256, 2, 2>(tb, S, c, s, flags);
+    return run_forward<256, 4, 2>(tb, S, c, s, flags);
 }
 
 cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,

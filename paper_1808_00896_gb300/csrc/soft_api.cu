@@ -604,7 +604,6 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
 
     long long dims[2] = {n, n};
-    long long emb[2] = {n, n};
     const long long slice = (long long)n * n;
     size_t work = 0;
     cufftResult r;
@@ -618,7 +617,6 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
         // One FP32 C2C plan over the 2B contiguous slices, run in place on the
         // staging buffer in both directions; a tiled transpose moves S between
         // the FFT layout [j][m][m'] and the DWT layout [m][m'][j].
-        (void)emb;
         if (cufftCreate(&p->fft32f) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
         p->fft32f_made = true;
         r = cufftMakePlanMany64(p->fft32f, 2, dims, nullptr, 1, slice, nullptr, 1, slice, CUFFT_C2C, n, &work);
