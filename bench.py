@@ -77,12 +77,12 @@ def kernel_source_sha() -> str:
 def dwt_flops(B: int) -> dict:
     """Algorithmic FP64 flops of one DWT (or iDWT) launch at bandwidth B:
     contraction 8B per coefficient (2B real FMAs on re and im), plus the
-    recurrence, 5 flops (2 FMA + 1 MUL) per generated T entry; one T column
-    block per symmetry cluster: sum over m = 0..B-1 of (m+1) clusters with
-    B-m degrees and 2B samples."""
+    rescaled three-term recurrence, 2 FMAs = 4 flops per generated T entry;
+    one T column block per symmetry cluster: sum over m = 0..B-1 of (m+1)
+    clusters with B-m degrees and 2B samples."""
     nc = B * (4 * B * B - 1) // 3
     t_entries = 2 * B * sum((m + 1) * (B - m) for m in range(B))
-    return {"contraction": 8 * B * nc, "recurrence": 5 * t_entries, "t_entries": t_entries}
+    return {"contraction": 8 * B * nc, "recurrence": 4 * t_entries, "t_entries": t_entries}
 
 
 class ClockSampler:
@@ -420,7 +420,7 @@ def run_ours(args) -> None:
     if dtype != "fp64":
         mult = 3 if dtype == "bf16x3" else 1
         roofline["tensor_tflops_achieved"] = mult * fl["contraction"] / (dom_ms * 1e-3) / 1e12
-        roofline["note"] = ("mixed mode: frac is the FP64 Wigner-d recurrence (5 flop per T entry) against the "
+        roofline["note"] = ("mixed mode: frac is the FP64 Wigner-d recurrence (2 FMA per T entry) against the "
                             "FP64 pipe; tensor_tflops_achieved counts the contraction's tensor-core flops")
 
     cpu = None

@@ -89,16 +89,11 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
     double *rAc = rA + B;
     double *rBc = rAc + B;
     double *rV = rBc + B;
+    double *rSig = rV + B;
 
     load_cluster(tb, m, mp, cs);
-    for (int t = tid; t < L; t += NT) {
-        const int l = l0 + t;
-        double A, Ac, Bc;
-        recurrence_coeffs(l, m, mp, A, Ac, Bc);
-        rA[t] = A; rAc[t] = Ac; rBc[t] = Bc;
-        rV[t] = (flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0;
-    }
-    __syncthreads();
+    for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
+    scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, rV);
     const int np = cs.np;
 
     // X: weighted S of every partner, beta index mirrored where the partner's
@@ -145,7 +140,7 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
                 for (int t = 0; t < nt; ++t) {
                     T[t * n + j] = dcur[k];
                     const int r = lb + t - l0;
-                    const double nx = fma(fma(rA[r], x[k], -rAc[r]), dcur[k], -rBc[r] * dprev[k]);
+                    const double nx = fma(fma(rA[r], x[k], -rAc[r]), dcur[k], -dprev[k]);
                     dprev[k] = dcur[k];
                     dcur[k] = nx;
                 }
@@ -186,12 +181,12 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
 //   dynamic smem: F[B][16], rec[3][B].
 // ---------------------------------------------------------------------------
 template <int NT, int JPT, int NC>
-__device__ __forceinline__ void idwt_walk(const double *F, const double *rA, const double *rAc, const double *rBc,
-                                          int L, double (&x)[JPT], double (&dcur)[JPT], double (&dprev)[JPT],
+__device__ __forceinline__ void idwt_walk(const double *F, const double *rA, const double *rAc, int L,
+                                          double (&x)[JPT], double (&dcur)[JPT], double (&dprev)[JPT],
                                           double (&acc)[JPT][16]) {
     for (int t = 0; t < L; ++t) {
         const double *Fr = F + t * 16;
-        const double A = rA[t], Ac = rAc[t], Bc = rBc[t];
+        const double A = rA[t], Ac = rAc[t];
 #pragma unroll
         for (int c = 0; c < NC; c += 2) {
             const double2 f = *reinterpret_cast<const double2 *>(Fr + c);
@@ -203,7 +198,7 @@ __device__ __forceinline__ void idwt_walk(const double *F, const double *rA, con
         }
 #pragma unroll
         for (int k = 0; k < JPT; ++k) {
-            const double nx = fma(fma(A, x[k], -Ac), dcur[k], -Bc * dprev[k]);
+            const double nx = fma(fma(A, x[k], -Ac), dcur[k], -dprev[k]);
             dprev[k] = dcur[k];
             dcur[k] = nx;
         }
@@ -223,14 +218,10 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
     double *rA = F + (size_t)B * 16;
     double *rAc = rA + B;
     double *rBc = rAc + B;
+    double *rSig = rBc + B;
 
     load_cluster(tb, m, mp, cs);
-    for (int t = tid; t < L; t += NT) {
-        double A, Ac, Bc;
-        recurrence_coeffs(l0 + t, m, mp, A, Ac, Bc);
-        rA[t] = A; rAc[t] = Ac; rBc[t] = Bc;
-    }
-    __syncthreads();
+    scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
     const int np = cs.np;
     for (int e = tid; e < L * 8; e += NT) {
         const int t = e >> 3, p = e & 7;
@@ -238,6 +229,7 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
         if (p < np) {
             const int l = l0 + t;
             double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
+            sg *= rSig[t];
             if (flags & kApplyV) sg *= (2.0 * l + 1.0) / (8.0 * M_PI * B);
             const double2 c = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + t));
             v = make_double2(sg * c.x, sg * c.y);
@@ -263,8 +255,8 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
     }
     __syncthreads();
 
-    if (np == 8) idwt_walk<NT, JPT, 16>(F, rA, rAc, rBc, L, x, dcur, dprev, acc);
-    else         idwt_walk<NT, JPT, 8>(F, rA, rAc, rBc, L, x, dcur, dprev, acc);
+    if (np == 8) idwt_walk<NT, JPT, 16>(F, rA, rAc, L, x, dcur, dprev, acc);
+    else         idwt_walk<NT, JPT, 8>(F, rA, rAc, L, x, dcur, dprev, acc);
 
 #pragma unroll
     for (int k = 0; k < JPT; ++k) {
@@ -317,7 +309,7 @@ __global__ void __launch_bounds__(256) idwt_fp64_persistent_kernel(const BatchXf
 template <int NT, int JPT, int TPI>
 cudaError_t run_forward(const Tables &tb, const double2 *S, double *coef, cudaStream_t s, int flags) {
     const int B = tb.B, n = 2 * B;
-    const size_t bytes = sizeof(double) * ((size_t)n * 16 + (size_t)(NT / (16 * TPI)) * n + 4 * (size_t)B);
+    const size_t bytes = sizeof(double) * ((size_t)n * 16 + (size_t)(NT / (16 * TPI)) * n + 5 * (size_t)B);
     cudaError_t e = cudaFuncSetAttribute(dwt_forward_fp64_kernel<NT, JPT, TPI>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -328,7 +320,7 @@ cudaError_t run_forward(const Tables &tb, const double2 *S, double *coef, cudaSt
 template <int NT, int JPT>
 cudaError_t run_inverse(const Tables &tb, const double *coef, double2 *S, cudaStream_t s, int flags) {
     const int B = tb.B;
-    const size_t bytes = sizeof(double) * ((size_t)B * 16 + 3 * (size_t)B);
+    const size_t bytes = sizeof(double) * ((size_t)B * 16 + 4 * (size_t)B);
     cudaError_t e = cudaFuncSetAttribute(dwt_inverse_fp64_kernel<NT, JPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -367,7 +359,7 @@ cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 
 
 cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
                                         cudaStream_t s) {
-    const size_t bytes = sizeof(double) * ((size_t)maxB * 16 + 3 * (size_t)maxB);
+    const size_t bytes = sizeof(double) * ((size_t)maxB * 16 + 4 * (size_t)maxB);
     cudaError_t e = cudaFuncSetAttribute(idwt_fp64_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e != cudaSuccess) return e;

@@ -32,21 +32,30 @@
 namespace softgb {
 namespace {
 
-constexpr int kNT = 128;       // threads per CTA: one warpgroup = the 128 TMEM lanes of the tile
-constexpr int kTile = 128;     // M rows per tensor-core tile
-constexpr int kChunk = 128;    // K elements staged per round
+// Inverse: M = 128 beta samples (one warpgroup = the 128 TMEM lanes), K chunks of
+// 64 degrees.  Forward: M = 64 degrees (tcgen05 M = 64 puts row 16w + i in TMEM
+// lane 32w + i), K chunks of NT beta samples, one per thread.  Both keep the A
+// operand at 256 bytes per recurrence chain so that more chains fit per SM.
+constexpr int kNT = 128;       // inverse: threads per CTA
+constexpr int kTile = 128;     // inverse: M rows per tile
+constexpr int kChunk = 64;     // inverse: K degrees staged per round
+constexpr int kFwdTile = 64;   // forward: M rows (degrees) per tile
 constexpr int kNCols = 16;     // N: 8 partners x (re, im)
 constexpr uint32_t kTmemCols = 32;
 constexpr uint32_t kWaitPolls = 1u << 22;
 
 __device__ __forceinline__ int mod_n(int a, int n) { return a < 0 ? a + n : a; }
 
-// Shared operand buffers for one K chunk.
-template <int MODE>
+// Shared operand buffers for one K chunk of an M x KC tile.
+template <int MODE, int M = kTile, int KC = kChunk>
 struct Operands {
     static constexpr int EB = MODE == SOFT_MIXED_TF32 ? 4 : 2;        // bytes per element
-    static constexpr int A_BYTES = kTile * kChunk * EB;              // one A plane
-    static constexpr int B_BYTES = kNCols * kChunk * EB;             // one B plane
+    static constexpr int KPC = 16 / EB;                              // K elements per 16 bytes
+    // A: K-direction stride between core matrices, padded by 16 bytes so that the
+    // 8-column groups written by one warp fall in different shared-memory banks.
+    static constexpr int A_LBO = M * 16 + 16;
+    static constexpr int A_BYTES = (KC / KPC) * A_LBO;                // one A plane
+    static constexpr int B_BYTES = kNCols * KC * EB;                 // one B plane
     static constexpr int PLANES = MODE == SOFT_MIXED_TF32 ? 1 : 2;   // (hi, lo) for BF16X3
     static constexpr int BYTES = PLANES * (A_BYTES + B_BYTES);
 };
@@ -68,9 +77,9 @@ __device__ __forceinline__ void put(unsigned char *plane0, int plane_bytes, int 
 // Store 16 bytes of consecutive K elements (8 BF16 or 4 TF32) of row r,
 // starting at k0 (a multiple of the per-16-byte count), into the A plane(s).
 template <int MODE>
-__device__ __forceinline__ void put_vec(unsigned char *plane0, int plane_bytes, int rows, int r, int k0,
+__device__ __forceinline__ void put_vec(unsigned char *plane0, int plane_bytes, int lbo, int r, int k0,
                                         const float (&v)[16 / Operands<MODE>::EB]) {
-    const uint32_t o = tc::kmajor_offset(r, k0, rows, Operands<MODE>::EB);
+    const uint32_t o = (uint32_t)((k0 / Operands<MODE>::KPC) * lbo + (r / 8) * 128 + (r % 8) * 16);
     if (MODE == SOFT_MIXED_TF32) {
         uint4 w;
         w.x = __float_as_uint(tc::round_tf32(v[0]));
@@ -98,22 +107,22 @@ template <int MODE>
 constexpr int kstep_elems() { return 32 / Operands<MODE>::EB; }
 
 // Issue the MMAs of one K chunk (thread 0 only) and commit them to mbar.
-template <int MODE>
+template <int MODE, int M, int KC>
 __device__ __forceinline__ void issue_chunk(uint32_t tmem, const unsigned char *A, const unsigned char *Bop,
                                             bool first, int ksteps, uint64_t *mbar) {
-    using O = Operands<MODE>;
+    using O = Operands<MODE, M, KC>;
     tc::fence_after_sync();
     const uint32_t abase = tc::smem_u32(A), bbase = tc::smem_u32(Bop);
-    constexpr uint32_t LBO_A = kTile * 16, LBO_B = kNCols * 16, SBO = 128;
+    constexpr uint32_t LBO_A = O::A_LBO, LBO_B = kNCols * 16, SBO = 128;
     if (MODE == SOFT_MIXED_TF32) {
-        constexpr uint32_t idesc = tc::instr_desc(2, kTile, kNCols);
+        constexpr uint32_t idesc = tc::instr_desc(2, M, kNCols);
         for (int s = 0; s < ksteps; ++s) {
             const uint64_t ad = tc::smem_desc(abase + s * 2 * LBO_A, LBO_A, SBO);
             const uint64_t bd = tc::smem_desc(bbase + s * 2 * LBO_B, LBO_B, SBO);
             tc::mma_tf32(tmem, ad, bd, idesc, (first && s == 0) ? 0u : 1u);
         }
     } else {
-        constexpr uint32_t idesc = tc::instr_desc(1, kTile, kNCols);
+        constexpr uint32_t idesc = tc::instr_desc(1, M, kNCols);
         const uint32_t alo = abase + O::A_BYTES, blo = bbase + O::B_BYTES;
         for (int s = 0; s < ksteps; ++s) {
             const uint32_t ao = s * 2 * LBO_A, bo = s * 2 * LBO_B;
@@ -126,25 +135,49 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem, const unsigned char *
     tc::mma_commit(mbar);
 }
 
+// Seed for the mixed modes: the FP64 log-seed y = log2(seed) is split into
+// k = floor(y) and f = y - k; 2^f comes from the FP32 special-function unit
+// and k goes straight into the FP64 exponent field.  Relative error ~3e-7 --
+// far below the ~1e-5 of the split-BF16 products -- at ~7 FP64 operations
+// instead of a full FP64 exp, with the FP64 exponent range kept (values
+// below ~1e-308 flush to 0, as in the FP64 path).
+__device__ __forceinline__ double seed_rep_mixed(int m, int mp, double lognorm, double lc, double ls) {
+    double lg = lognorm;
+    if (m + mp > 0) lg = fma((double)(m + mp), lc, lg);
+    if (m - mp > 0) lg = fma((double)(m - mp), ls, lg);
+    const double y = lg * 1.4426950408889634074;  // log2(e)
+    const double kf = floor(y);
+    const int k = (int)kf;
+    const float p = exp2f((float)(y - kf));       // [1, 2]
+    const unsigned long long b = (unsigned long long)__double_as_longlong(tc::f32_to_f64(p));
+    const int e = (int)((b >> 52) & 0x7FF) + k;   // biased exponent of the product
+    if (e <= 0) return 0.0;
+    return __longlong_as_double((long long)((b & ~(0x7FFull << 52)) | ((unsigned long long)e << 52)));
+}
+
 struct MixedTables {
     Tables tb;
     const double *lw;  // [2B] log w_B(j)
 };
 
 // ---------------------------------------------------------------------------
-// Forward DWT (mixed).  One CTA per cluster.
-//   dynamic smem: operands | dprev[2B] | dcur[2B] | rA,rAc,rBc,rV [B each]
+// Forward DWT (mixed).  One CTA per cluster, NT threads = NT beta samples per
+// K chunk (one recurrence chain per thread), M tiles of 64 degrees.
+//   dynamic smem: operands | dprev[2B] | dcur[2B] | rA,rAc,rV [B each]; the
+//   table-building scratch (Bc, sig) lives in the operand area, which is not
+//   yet in use then.
 // ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, const float2 *__restrict__ S,
-                                                                 double *__restrict__ coef, int flags) {
-    using O = Operands<MODE>;
+template <int MODE, int NT>
+__global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedTables mt, const float2 *__restrict__ S,
+                                                                double *__restrict__ coef, int flags) {
+    constexpr int TM = kFwdTile, KC = NT;
+    using O = Operands<MODE, TM, KC>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mbar;
     const Tables &tb = mt.tb;
-    const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5;
+    const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int2 rep = tb.clusters[blockIdx.x];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 
@@ -152,20 +185,17 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
     unsigned char *X = smem + O::PLANES * O::A_BYTES;
     double *dprev = reinterpret_cast<double *>(smem + O::BYTES);
     double *dcur = dprev + n;
-    double *rA = dcur + n, *rAc = rA + B, *rBc = rAc + B, *rV = rBc + B;
+    double *rA = dcur + n, *rAc = rA + B, *rV = rAc + B;
+    double *rBc = reinterpret_cast<double *>(smem), *rSig = rBc + B;  // scratch inside the operand area
 
     load_cluster(tb, m, mp, cs);
-    for (int t = tid; t < L; t += kNT) {
-        double a, ac, bc;
-        recurrence_coeffs(l0 + t, m, mp, a, ac, bc);
-        rA[t] = a; rAc[t] = ac; rBc[t] = bc;
-        rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
-    }
+    for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
+    scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, rV);
     {
         const double lognorm = seed_lognorm(tb, m, mp);
-        for (int j = tid; j < n; j += kNT) {
+        for (int j = tid; j < n; j += NT) {
             // w_B(j) d(l0,m,m';beta_j): the weight enters through the seed's logarithm
-            dcur[j] = seed_rep(m, mp, (flags & kApplyW) ? lognorm + mt.lw[j] : lognorm, tb.lcos[j], tb.lsin[j]);
+            dcur[j] = seed_rep_mixed(m, mp, (flags & kApplyW) ? lognorm + mt.lw[j] : lognorm, tb.lcos[j], tb.lsin[j]);
             dprev[j] = 0.0;
         }
     }
@@ -176,22 +206,21 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     const int np = cs.np;
-    const int nchunks = (n + kChunk - 1) / kChunk;
+    const int nchunks = (n + KC - 1) / KC;
     uint32_t phase = 0;
     bool ok = true;
+    unsigned char *acol = A + (tid / O::KPC) * O::A_LBO + (tid % O::KPC) * O::EB;  // this thread's column; row r at +16 r
 
-    for (int lb = l0; lb < B && ok; lb += kTile) {
-        const int rows = min(kTile, B - lb);
+    for (int lb = l0; lb < B && ok; lb += TM) {
+        const int rows = min(TM, B - lb);
         for (int c = 0; c < nchunks && ok; ++c) {
             // K extent of this chunk, rounded up to whole MMA K steps (the padding is zero).
-            const int kvalid = min(kChunk, n - c * kChunk);
+            const int kvalid = min(KC, n - c * KC);
             const int ksteps = (kvalid + kstep_elems<MODE>() - 1) / kstep_elems<MODE>();
             const int kfill = ksteps * kstep_elems<MODE>();
             // A: column tid = beta sample j, rows = degrees lb..lb+rows-1.  Rows past
             // `rows` are left as they are: they only reach TMEM lanes that are never read.
-            const int j = c * kChunk + tid;
-            constexpr int KPC = 16 / O::EB;
-            unsigned char *acol = A + (tid / KPC) * (kTile * 16) + (tid % KPC) * O::EB;  // row r at +16 r
+            const int j = c * KC + tid;
             if (tid < kvalid) {
                 const double x = tb.cosb[j];
                 double dc = dcur[j], dp = dprev[j];
@@ -206,14 +235,14 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
                         *reinterpret_cast<uint16_t *>(acol + O::A_BYTES + 16 * r) = lo;
                     }
                     const int q = lb + r - l0;
-                    const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -rBc[q] * dp);
+                    const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -dp);
                     dp = dc;
                     dc = nx;
                 }
                 dcur[j] = dc;
                 dprev[j] = dp;
             } else if (tid < kfill) {
-                for (int r = 0; r < kTile; ++r) {
+                for (int r = 0; r < TM; ++r) {
                     if (MODE == SOFT_MIXED_TF32) {
                         *reinterpret_cast<float *>(acol + 16 * r) = 0.f;
                     } else {
@@ -223,8 +252,8 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
                 }
             }
             // B: X chunk, row 2p / 2p+1 = re / im of partner p, k = beta sample in chunk.
-            for (int e = tid; e < 8 * kChunk; e += kNT) {
-                const int p = e / kChunk, k = e % kChunk, jj = c * kChunk + k;
+            for (int e = tid; e < 8 * KC; e += NT) {
+                const int p = e / KC, k = e % KC, jj = c * KC + k;
                 if (k >= kfill) continue;
                 float2 v = make_float2(0.f, 0.f);
                 if (p < np && k < kvalid) {
@@ -236,27 +265,30 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
             }
             tc::fence_proxy_async();
             __syncthreads();
-            if (tid == 0) issue_chunk<MODE>(tmem, A, X, c == 0, ksteps, &mbar);
+            if (tid == 0) issue_chunk<MODE, TM, KC>(tmem, A, X, c == 0, ksteps, &mbar);
             const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
             phase ^= 1u;
             ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
         }
         if (!ok) break;
-        // Epilogue: TMEM lane = row = degree lb + tid; 16 FP32 columns.
+        // Epilogue: degree lb + 16 w + i sits in TMEM lane 32 w + i (i < 16) of warp w < 4.
         tc::fence_after_sync();
-        uint32_t d[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), d);
-        if (tid < rows) {
-            const int l = lb + tid, q = l - l0;
+        if (warp < 4) {
+            uint32_t d[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), d);
+            const int r = 16 * warp + lane;
+            if (lane < 16 && r < rows) {
+                const int l = lb + r, q = l - l0;
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                if (p >= np) break;
-                const double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
-                const double v = rV[q] * sg;
-                double2 out;
-                out.x = v * tc::f32_to_f64(__uint_as_float(d[2 * p]));
-                out.y = v * tc::f32_to_f64(__uint_as_float(d[2 * p + 1]));
-                *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p] + q)) = out;
+                for (int p = 0; p < 8; ++p) {
+                    if (p >= np) break;
+                    const double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
+                    const double v = rV[q] * sg;
+                    double2 out;
+                    out.x = v * tc::f32_to_f64(__uint_as_float(d[2 * p]));
+                    out.y = v * tc::f32_to_f64(__uint_as_float(d[2 * p + 1]));
+                    *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p] + q)) = out;
+                }
             }
         }
         tc::fence_before_sync();
@@ -275,7 +307,7 @@ __global__ void __launch_bounds__(kNT) dwt_forward_mixed_kernel(MixedTables mt, 
 //   dynamic smem: operands | rA,rAc,rBc [B each]
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, const double *__restrict__ coef,
+__global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedTables mt, const double *__restrict__ coef,
                                                                  float2 *__restrict__ S, int flags) {
     using O = Operands<MODE>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -289,14 +321,10 @@ __global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, 
 
     unsigned char *A = smem;
     unsigned char *F = smem + O::PLANES * O::A_BYTES;
-    double *rA = reinterpret_cast<double *>(smem + O::BYTES), *rAc = rA + B, *rBc = rAc + B;
+    double *rA = reinterpret_cast<double *>(smem + O::BYTES), *rAc = rA + B, *rBc = rAc + B, *rSig = rBc + B;
 
     load_cluster(tb, m, mp, cs);
-    for (int t = tid; t < L; t += kNT) {
-        double a, ac, bc;
-        recurrence_coeffs(l0 + t, m, mp, a, ac, bc);
-        rA[t] = a; rAc[t] = ac; rBc[t] = bc;
-    }
+    scaled_recurrence_tables<kNT>(l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
     if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc::fence_before_sync();
@@ -314,7 +342,7 @@ __global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, 
         double x = 0.0, dc = 0.0, dp = 0.0;
         if (active) {
             x = tb.cosb[j];
-            dc = seed_rep(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
+            dc = seed_rep_mixed(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
         }
         for (int lb = l0, c = 0; lb < B && ok; lb += kChunk, ++c) {
             const int cnt = min(kChunk, B - lb);
@@ -332,12 +360,12 @@ __global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, 
                         if (k0 + u < cnt) {
                             v[u] = tc::f64_to_f32_trunc(dc);
                             const int q = lb + k0 + u - l0;
-                            const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -rBc[q] * dp);
+                            const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -dp);
                             dp = dc;
                             dc = nx;
                         }
                     }
-                    put_vec<MODE>(A, O::A_BYTES, kTile, tid, k0, v);
+                    put_vec<MODE>(A, O::A_BYTES, O::A_LBO, tid, k0, v);
                 }
             }
             // B: F chunk, row 2p / 2p+1 = sign-folded re / im of partner p at degree lb + k.
@@ -349,7 +377,7 @@ __global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, 
                     const int l = lb + k;
                     const double2 cv = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + (l - l0)));
                     const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
-                    const double v = (flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0;
+                    const double v = rSig[l - l0] * ((flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0);
                     re = tc::f64_to_f32_rn(neg ? -v * cv.x : v * cv.x);
                     im = tc::f64_to_f32_rn(neg ? -v * cv.y : v * cv.y);
                 }
@@ -358,7 +386,7 @@ __global__ void __launch_bounds__(kNT) dwt_inverse_mixed_kernel(MixedTables mt, 
             }
             tc::fence_proxy_async();
             __syncthreads();
-            if (tid == 0) issue_chunk<MODE>(tmem, A, F, c == 0, ksteps, &mbar);
+            if (tid == 0) issue_chunk<MODE, kTile, kChunk>(tmem, A, F, c == 0, ksteps, &mbar);
             const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
             phase ^= 1u;
             ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
@@ -444,14 +472,15 @@ int grid_for(int64_t count) { return (int)std::min<int64_t>((count + 255) / 256,
 
 }  // namespace
 
-size_t mixed_forward_smem(int mode, int B) {
-    const size_t ops = mode == SOFT_MIXED_TF32 ? Operands<SOFT_MIXED_TF32>::BYTES : Operands<SOFT_MIXED_BF16X3>::BYTES;
-    return ops + sizeof(double) * (2 * (size_t)(2 * B) + 4 * (size_t)B);
+template <int MODE, int NT>
+size_t mixed_forward_smem(int B) {
+    static_assert(Operands<MODE, kFwdTile, NT>::BYTES >= 2 * kMaxB * (int)sizeof(double), "scratch must fit");
+    return Operands<MODE, kFwdTile, NT>::BYTES + sizeof(double) * (2 * (size_t)(2 * B) + 3 * (size_t)B);
 }
 
 size_t mixed_inverse_smem(int mode, int B) {
     const size_t ops = mode == SOFT_MIXED_TF32 ? Operands<SOFT_MIXED_TF32>::BYTES : Operands<SOFT_MIXED_BF16X3>::BYTES;
-    return ops + sizeof(double) * 3 * (size_t)B;
+    return ops + sizeof(double) * 4 * (size_t)B;
 }
 
 cudaError_t launch_log_weights(int B, const double *w, double *lw, cudaStream_t s) {
@@ -460,23 +489,26 @@ cudaError_t launch_log_weights(int B, const double *w, double *lw, cudaStream_t 
     return cudaGetLastError();
 }
 
+template <int MODE, int NT>
+cudaError_t run_forward_mixed(const MixedTables &mt, const float2 *S, double *coef, cudaStream_t s, int flags) {
+    const size_t bytes = mixed_forward_smem<MODE, NT>(mt.tb.B);
+    cudaError_t e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<MODE, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    dwt_forward_mixed_kernel<MODE, NT><<<mt.tb.ncl, NT, bytes, s>>>(mt, S, coef, flags);
+    return cudaGetLastError();
+}
+
+// 128 beta samples per chunk up to 2B = 128 (44 KB, several CTAs per SM), 256 beyond.
 cudaError_t launch_dwt_forward_mixed(int mode, const Tables &tb, const double *lw, const float2 *S, double *coef,
                                      cudaStream_t s, int flags) {
     MixedTables mt{tb, lw};
-    const size_t bytes = mixed_forward_smem(mode, tb.B);
-    cudaError_t e;
-    if (mode == SOFT_MIXED_TF32) {
-        e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<SOFT_MIXED_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes);
-        if (e != cudaSuccess) return e;
-        dwt_forward_mixed_kernel<SOFT_MIXED_TF32><<<tb.ncl, kNT, bytes, s>>>(mt, S, coef, flags);
-    } else {
-        e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<SOFT_MIXED_BF16X3>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        dwt_forward_mixed_kernel<SOFT_MIXED_BF16X3><<<tb.ncl, kNT, bytes, s>>>(mt, S, coef, flags);
-    }
-    return cudaGetLastError();
+    const bool small = 2 * tb.B <= 128;
+    if (mode == SOFT_MIXED_TF32)
+        return small ? run_forward_mixed<SOFT_MIXED_TF32, 128>(mt, S, coef, s, flags)
+                     : run_forward_mixed<SOFT_MIXED_TF32, 256>(mt, S, coef, s, flags);
+    return small ? run_forward_mixed<SOFT_MIXED_BF16X3, 128>(mt, S, coef, s, flags)
+                 : run_forward_mixed<SOFT_MIXED_BF16X3, 256>(mt, S, coef, s, flags);
 }
 
 cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s,

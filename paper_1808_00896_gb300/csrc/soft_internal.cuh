@@ -102,6 +102,43 @@ __device__ inline void recurrence_coeffs(int l, int m, int mp, double &A, double
     Bc = L1 * sqrt((ll * ll - mm * mm) * (ll * ll - nn * nn)) / (ll * den);
 }
 
+// Rescaled recurrence.  With d(l0+t) = sig[t] e(t), sig[0] = sig[1] = 1 and
+// sig[t+1] = Bc_{l0+t} sig[t-1], the recurrence above becomes
+//   e(t+1) = (A'[t] x - Ac'[t]) e(t) - e(t-1),   A'[t] = A sig[t]/sig[t+1], Ac'[t] = Ac sig[t]/sig[t+1],
+// i.e. two FP64 operations per step instead of three; the factor sig[t] is
+// applied where d meets the data (V_l in the forward, the coefficients in the
+// inverse).  Builds rA = A', rAc = Ac', rSig = sig for t < L in shared memory
+// (rBc is scratch) and multiplies rV[t] by sig[t] if rV is given.  Called by
+// all NT threads; ends with a barrier.
+template <int NT>
+__device__ inline void scaled_recurrence_tables(int l0, int L, int m, int mp, double *rA, double *rAc, double *rBc,
+                                                double *rSig, double *rV) {
+    const int tid = threadIdx.x;
+    for (int t = tid; t < L; t += NT) {
+        double a, ac, bc;
+        recurrence_coeffs(l0 + t, m, mp, a, ac, bc);
+        rA[t] = a; rAc[t] = ac; rBc[t] = bc;
+    }
+    __syncthreads();
+    if (tid < 2) {  // the two parity chains of sig, one thread each
+        double sg = 1.0;
+        for (int t = tid; t < L; t += 2) {
+            if (t >= 2) sg *= rBc[t - 1];
+            rSig[t] = sg;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < L; t += NT) {
+        if (t + 1 < L) {
+            const double r = rSig[t] / rSig[t + 1];
+            rA[t] *= r;
+            rAc[t] *= r;
+        }
+        if (rV) rV[t] *= rSig[t];
+    }
+    __syncthreads();
+}
+
 // Seed d(l0, m, m'; beta_j), l0 = max(|m|,|m'|), for a representative m >= m' >= 0
 // (the "+" case of the paper's first initial condition):
 //   d(m, m, m') = sqrt((2m)! / ((m+m')!(m-m')!)) cos(b/2)^(m+m') sin(b/2)^(m-m'),
