@@ -65,8 +65,10 @@ SM_MAX_MHZ = 2070.0
 # DRAM traffic per launch of the dominant kernels from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel, bandwidth and
 # the SHA-256 of the kernel source it was taken on; reported as null when the
-# source has changed since.  Filled in from profiles/.
-TRAFFIC = {}
+# source has changed since.  From profiles/dwt_fp64_b64.md.
+TRAFFIC = {
+    ("dwt_forward_fp64_kernel", 64): (33_522_176 + 41_728, "0e927721a286684d"),
+}
 
 
 def kernel_source_sha() -> str:

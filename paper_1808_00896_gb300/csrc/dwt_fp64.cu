@@ -96,21 +96,21 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
     scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, rV);
     const int np = cs.np;
 
-    // X: weighted S of every partner, beta index mirrored where the partner's
-    // column is d(.; pi - beta).
+    // X: S of every partner, beta index mirrored where the partner's column is
+    // d(.; pi - beta).  The weight w_B(j) is not applied here: it enters T
+    // through the seeds below (T W, since the recurrence is linear in d;
+    // w_B is symmetric under j -> 2B-1-j, so mirrored partners see the same w).
     for (int e = tid; e < n * 8; e += NT) {
         const int j = e >> 3, p = e & 7;
         double2 v = make_double2(0.0, 0.0);
         if (p < np) {
             const int src = cs.mir[p] ? n - 1 - j : j;
-            const double2 s = S[((int64_t)src * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)];
-            const double wj = (flags & kApplyW) ? tb.w[src] : 1.0;
-            v = make_double2(wj * s.x, wj * s.y);
+            v = S[((int64_t)src * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)];
         }
         *reinterpret_cast<double2 *>(&X[j * 16 + 2 * p]) = v;
     }
 
-    // Recurrence state of this thread's beta samples.
+    // Recurrence state of this thread's beta samples: seeds w_B(j) d(l0,m,m';beta_j).
     double x[JPT], dcur[JPT], dprev[JPT];
     {
         const double lognorm = seed_lognorm(tb, m, mp);
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
             x[k] = 0.0; dcur[k] = 0.0; dprev[k] = 0.0;
             if (j < n) {
                 x[k] = tb.cosb[j];
-                dcur[k] = seed_rep(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
+                dcur[k] = seed_rep(m, mp, (flags & kApplyW) ? lognorm + tb.lw[j] : lognorm, tb.lcos[j], tb.lsin[j]);
             }
         }
     }
@@ -153,22 +153,22 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
         if (active) {
             const double *Tr = T + pt * n + jbeg;
             const double *Xc = X + (size_t)jbeg * 16 + pc;
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            // two chains: the FP64 pipe issues slowly enough that latency is hidden
+            double a0 = 0.0, a1 = 0.0;
             int j = 0;
-            for (; j + 4 <= jlen; j += 4) {
+            for (; j + 2 <= jlen; j += 2) {
                 a0 = fma(Tr[j], Xc[j * 16], a0);
                 a1 = fma(Tr[j + 1], Xc[(j + 1) * 16], a1);
-                a2 = fma(Tr[j + 2], Xc[(j + 2) * 16], a2);
-                a3 = fma(Tr[j + 3], Xc[(j + 3) * 16], a3);
             }
-            for (; j < jlen; ++j) a0 = fma(Tr[j], Xc[j * 16], a0);
-            acc = (a0 + a1) + (a2 + a3);
+            if (j < jlen) a0 = fma(Tr[j], Xc[j * 16], a0);
+            acc = a0 + a1;
         }
         if (TPI == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         if (active && half == 0) {
             const int l = lb + pt;
-            const double sg = (cs.lpar[pp] && (l & 1)) ? -cs.sign[pp] : cs.sign[pp];
-            coef[2 * (cs.off[pp] + (l - l0)) + (pc & 1)] = rV[l - l0] * sg * acc;
+            const double v = rV[l - l0];
+            const bool neg = (cs.sign[pp] < 0.0) != (cs.lpar[pp] && (l & 1));
+            coef[2 * (cs.off[pp] + (l - l0)) + (pc & 1)] = (neg ? -v : v) * acc;
         }
         __syncthreads();
     }

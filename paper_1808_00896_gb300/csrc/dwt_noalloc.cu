@@ -29,7 +29,7 @@ constexpr int kNoAllocMaxB = 256;
 
 // Byte layout of the array for bandwidth B (each part 256-byte aligned).
 struct NoAllocLayout {
-    size_t w, cosb, lcos, lsin, lfact, clusters, runoff, total;
+    size_t w, lw, cosb, lcos, lsin, lfact, clusters, runoff, total;
 };
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -39,6 +39,7 @@ __host__ __device__ constexpr NoAllocLayout noalloc_layout(int B) {
     const size_t n = 2 * (size_t)B;
     size_t o = 0;
     L.w = o;        o = align256(o + n * sizeof(double));
+    L.lw = o;       o = align256(o + n * sizeof(double));
     L.cosb = o;     o = align256(o + n * sizeof(double));
     L.lcos = o;     o = align256(o + n * sizeof(double));
     L.lsin = o;     o = align256(o + n * sizeof(double));
@@ -49,7 +50,7 @@ __host__ __device__ constexpr NoAllocLayout noalloc_layout(int B) {
     return L;
 }
 
-constexpr size_t kNoAllocBytes = noalloc_layout(kNoAllocMaxB).total;  // about 2.3 MiB
+constexpr size_t kNoAllocBytes = noalloc_layout(kNoAllocMaxB).total;  // about 2.3 MiB (2,377,472 bytes)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -130,17 +131,19 @@ extern "C" soft_status soft_dwt_forward_noalloc(int B, const double *S, double *
     tb.B = B;
     tb.ncl = B * (B + 1) / 2;
     double *w = reinterpret_cast<double *>(base + L.w);
+    double *lw = reinterpret_cast<double *>(base + L.lw);
     double *cosb = reinterpret_cast<double *>(base + L.cosb);
     double *lcos = reinterpret_cast<double *>(base + L.lcos);
     double *lsin = reinterpret_cast<double *>(base + L.lsin);
     double *lfact = reinterpret_cast<double *>(base + L.lfact);
     int2 *clusters = reinterpret_cast<int2 *>(base + L.clusters);
     int64_t *runoff = reinterpret_cast<int64_t *>(base + L.runoff);
-    tb.w = w; tb.cosb = cosb; tb.lcos = lcos; tb.lsin = lsin; tb.lfact = lfact;
+    tb.w = w; tb.lw = lw; tb.cosb = cosb; tb.lcos = lcos; tb.lsin = lsin; tb.lfact = lfact;
     tb.clusters = clusters; tb.runoff = runoff; tb.err = nullptr;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_tables(B, w, cosb, lcos, lsin, lfact, s);
+    if (e == cudaSuccess) e = launch_log_weights(B, w, lw, s);
     if (e == cudaSuccess) {
         noalloc_layout_kernel<<<64, 256, 0, s>>>(B, clusters, runoff);
         e = cudaGetLastError();

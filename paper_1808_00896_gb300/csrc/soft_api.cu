@@ -40,8 +40,8 @@ struct soft_plan_s {
     int *err;
     cufftHandle fft;
     bool fft_made;
+    double *lw;  // log w_B(j)
     // Mixed-precision plans: FP32 grid staging and S in layout [m][m'][j], FP32 cuFFT plans.
-    double *lw;
     float2 *g32, *S32;
     cufftHandle fft32f, fft32i;
     bool fft32f_made, fft32i_made;
@@ -61,7 +61,7 @@ struct soft_plan_s {
 
     Tables tables() const {
         Tables t;
-        t.B = B; t.ncl = ncl; t.w = w; t.cosb = cosb; t.lcos = lcos; t.lsin = lsin; t.lfact = lfact;
+        t.B = B; t.ncl = ncl; t.w = w; t.lw = lw; t.cosb = cosb; t.lcos = lcos; t.lsin = lsin; t.lfact = lfact;
         t.clusters = clusters; t.runoff = runoff; t.err = err;
         return t;
     }
@@ -586,10 +586,10 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     alloc((void **)&p->err, sizeof(int));
     alloc((void **)&p->amax_v, sizeof(double) * argmax_parts());
     alloc((void **)&p->amax_i, sizeof(int64_t) * argmax_parts());
+    alloc((void **)&p->lw, sizeof(double) * n);
     if (dtype == SOFT_FP64) {
         alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
     } else {
-        alloc((void **)&p->lw, sizeof(double) * n);
         alloc((void **)&p->g32, sizeof(float2) * grid_elems(B));
         alloc((void **)&p->S32, sizeof(float2) * grid_elems(B));
     }
@@ -599,7 +599,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     if (e == cudaSuccess) e = cudaMemcpy(p->runoff, ro.data(), sizeof(int64_t) * ro.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
     if (e == cudaSuccess) e = launch_tables(B, p->w, p->cosb, p->lcos, p->lsin, p->lfact, 0);
-    if (e == cudaSuccess && dtype != SOFT_FP64) e = launch_log_weights(B, p->w, p->lw, 0);
+    if (e == cudaSuccess) e = launch_log_weights(B, p->w, p->lw, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
 

@@ -18,6 +18,7 @@ struct Tables {
     int B;
     int ncl;                  // number of symmetry clusters, B(B+1)/2
     const double *w;          // [2B]  quadrature weights w_B(j), Eq. (weights)
+    const double *lw;         // [2B]  log w_B(j) (the forward folds W into its seeds)
     const double *cosb;       // [2B]  cos(beta_j)
     const double *lcos;       // [2B]  log cos(beta_j / 2)
     const double *lsin;       // [2B]  log sin(beta_j / 2)
