@@ -47,6 +47,16 @@ for _B in (64, 128, 256, 512):
         WORKLOADS[f"b{_B}_{_m}"] = (_B, _m, "gauss_decay",
                                     f"mixed SOFT forward+inverse, B={_B}, {_d} contraction on tcgen05 tensor cores, "
                                     f"FP64 Wigner-d recurrence, FP32 2-D FFTs; complex128 in/out")
+# Batches of same-B transforms through soft_batched_forward / soft_batched_inverse:
+# mixed plans share one DWT launch per group of 8 (N = 16 x 8 tensor-core columns).
+BATCHED = {}
+for _B, _nb in ((64, 8), (128, 8), (256, 8), (512, 4)):
+    for _m in ("bf16x3", "fp64"):
+        _name = f"b{_B}_{_m}_x{_nb}"
+        WORKLOADS[_name] = (_B, _m, "gauss_decay",
+                            f"{_nb} {'mixed BF16x3' if _m == 'bf16x3' else 'FP64'} SOFT forward+inverse transforms "
+                            f"at B={_B} per step through the batched, graph-captured API")
+        BATCHED[_name] = _nb
 # Batched rotational matching: 64 correlation requests, B uniform in {8,...,128}.
 CORR_WORKLOAD = ("corr64", "batched rotational matching: 64 correlation requests, B drawn uniformly from "
                  "{8,16,32,64,128}, SH coefficients complex Gaussian x 1/(l+1); per request: correlation "
@@ -303,6 +313,86 @@ def run_corr(args) -> None:
         p.close()
 
 
+def run_batched(args) -> None:
+    """Batched workloads: nb same-B transforms per step (forward + inverse)."""
+    import torch
+
+    from paper_1808_00896_gb300 import Plan, batched_forward, batched_inverse, synth
+    from paper_1808_00896_gb300 import build as build_mod
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    build_mod.build()
+    B, dtype, kind, desc = WORKLOADS[args.workload]
+    nb = BATCHED[args.workload]
+    plans = [Plan(B, dtype, device=dev) for _ in range(nb)]
+    coefs = [torch.from_numpy(synth.coefficients(B, kind, seed=synth.BASE_SEED + 100 * rank + i)).to(dev)
+             for i in range(nb)]
+    grids = batched_inverse(plans, coefs)
+    coef_out = [p.empty_coef() for p in plans]
+    grid_out = [p.empty_grid() for p in plans]
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        batched_forward(plans, grids, coef_out)
+        batched_inverse(plans, coefs, grid_out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(dev.index if world == 1 else local)
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nb * 1000.0 / ms
+    fl = dwt_flops(B)
+    peak_gflops = FP64_FLOPS_PER_SM_CLK * N_SM * SM_MAX_MHZ * 1e6 / 1e9
+    if dtype == "fp64":
+        algo = 2 * nb * (fl["contraction"] + fl["recurrence"])
+        note = "whole-step time (FFTs included): 2 nb DWT/iDWT launches of FP64 contraction + recurrence"
+    else:
+        algo = 2 * fl["recurrence"]  # one shared recurrence per batched DWT launch, 2 launches per step
+        note = ("whole-step time (FFTs included): the FP64 recurrence of the 2 batched (i)DWT launches, "
+                "shared by the nb transforms")
+    roofline = {"bound": "alu", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak_gflops, "unit": "GFLOP/s",
+                "frac": algo / (ms * 1e-3) / 1e9 / peak_gflops, "traffic": None,
+                "kernel": "dwt_forward_mixed_kernel" if dtype != "fp64" else "dwt_forward_fp64_kernel", "note": note}
+    if dtype != "fp64":
+        roofline["tensor_tflops_achieved"] = 2 * 3 * nb * fl["contraction"] / (ms * 1e-3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if dtype == "fp64" else dtype, "data": "synthetic",
+            "config": {"workload": desc, "B": B, "mode": dtype, "batch": nb, "coefficients": kind,
+                       "parallelism": f"replicas x{world}", "l2": "per-step working set > L2"},
+            "e2e": None, "gpu_launches": None, "roofline": roofline, "clocks": clocks, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -471,6 +561,13 @@ def main():
             return
         args.steps = args.steps or 20
         run_corr(args)
+        return
+    if args.workload in BATCHED:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "batched workloads have no CPU reference arm"}))
+            return
+        args.steps = args.steps or {64: 200, 128: 40, 256: 6, 512: 2}[WORKLOADS[args.workload][0]]
+        run_batched(args)
         return
     if args.steps is None:
         B = WORKLOADS[args.workload][0]

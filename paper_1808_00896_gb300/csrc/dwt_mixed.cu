@@ -41,13 +41,13 @@ constexpr int kTile = 128;     // inverse: M rows per tile
 constexpr int kChunk = 64;     // inverse: K degrees staged per round
 constexpr int kFwdTile = 64;   // forward: M rows (degrees) per tile
 constexpr int kNCols = 16;     // N: 8 partners x (re, im)
-constexpr uint32_t kTmemCols = 32;
 constexpr uint32_t kWaitPolls = 1u << 22;
 
 __device__ __forceinline__ int mod_n(int a, int n) { return a < 0 ? a + n : a; }
 
-// Shared operand buffers for one K chunk of an M x KC tile.
-template <int MODE, int M = kTile, int KC = kChunk>
+// Shared operand buffers for one K chunk of an M x KC tile with NC = 16 NB
+// columns (8 partners x (re, im) for each of NB transforms).
+template <int MODE, int M = kTile, int KC = kChunk, int NC = kNCols>
 struct Operands {
     static constexpr int EB = MODE == SOFT_MIXED_TF32 ? 4 : 2;        // bytes per element
     static constexpr int KPC = 16 / EB;                              // K elements per 16 bytes
@@ -55,10 +55,15 @@ struct Operands {
     // 8-column groups written by one warp fall in different shared-memory banks.
     static constexpr int A_LBO = M * 16 + 16;
     static constexpr int A_BYTES = (KC / KPC) * A_LBO;                // one A plane
-    static constexpr int B_BYTES = kNCols * KC * EB;                 // one B plane
+    static constexpr int B_LBO = NC * 16 + 16;                       // same padding for B
+    static constexpr int B_BYTES = (KC / KPC) * B_LBO;               // one B plane
     static constexpr int PLANES = MODE == SOFT_MIXED_TF32 ? 1 : 2;   // (hi, lo) for BF16X3
     static constexpr int BYTES = PLANES * (A_BYTES + B_BYTES);
 };
+
+// TMEM columns for an N-column FP32 accumulator (power of two, >= 32).
+template <int NC>
+constexpr uint32_t tmem_cols() { return NC <= 32 ? 32u : NC <= 64 ? 64u : NC <= 128 ? 128u : 256u; }
 
 // Store one value into plane(s) of an operand tile at (r, k).
 template <int MODE>
@@ -102,27 +107,40 @@ __device__ __forceinline__ void put_vec(unsigned char *plane0, int plane_bytes, 
     }
 }
 
+// Store 8 consecutive K elements (k0 a multiple of 8) of B-operand row r.
+template <int MODE>
+__device__ __forceinline__ void put_b8(unsigned char *plane0, int plane_bytes, int lbo, int r, int k0,
+                                       const float (&v)[8]) {
+    if constexpr (MODE == SOFT_MIXED_TF32) {
+        const float a[4] = {v[0], v[1], v[2], v[3]}, b[4] = {v[4], v[5], v[6], v[7]};
+        put_vec<MODE>(plane0, plane_bytes, lbo, r, k0, a);
+        put_vec<MODE>(plane0, plane_bytes, lbo, r, k0 + 4, b);
+    } else {
+        put_vec<MODE>(plane0, plane_bytes, lbo, r, k0, v);
+    }
+}
+
 // K elements per MMA (32 bytes of K).
 template <int MODE>
 constexpr int kstep_elems() { return 32 / Operands<MODE>::EB; }
 
 // Issue the MMAs of one K chunk (thread 0 only) and commit them to mbar.
-template <int MODE, int M, int KC>
+template <int MODE, int M, int KC, int NC>
 __device__ __forceinline__ void issue_chunk(uint32_t tmem, const unsigned char *A, const unsigned char *Bop,
                                             bool first, int ksteps, uint64_t *mbar) {
-    using O = Operands<MODE, M, KC>;
+    using O = Operands<MODE, M, KC, NC>;
     tc::fence_after_sync();
     const uint32_t abase = tc::smem_u32(A), bbase = tc::smem_u32(Bop);
-    constexpr uint32_t LBO_A = O::A_LBO, LBO_B = kNCols * 16, SBO = 128;
+    constexpr uint32_t LBO_A = O::A_LBO, LBO_B = O::B_LBO, SBO = 128;
     if (MODE == SOFT_MIXED_TF32) {
-        constexpr uint32_t idesc = tc::instr_desc(2, M, kNCols);
+        constexpr uint32_t idesc = tc::instr_desc(2, M, NC);
         for (int s = 0; s < ksteps; ++s) {
             const uint64_t ad = tc::smem_desc(abase + s * 2 * LBO_A, LBO_A, SBO);
             const uint64_t bd = tc::smem_desc(bbase + s * 2 * LBO_B, LBO_B, SBO);
             tc::mma_tf32(tmem, ad, bd, idesc, (first && s == 0) ? 0u : 1u);
         }
     } else {
-        constexpr uint32_t idesc = tc::instr_desc(1, M, kNCols);
+        constexpr uint32_t idesc = tc::instr_desc(1, M, NC);
         const uint32_t alo = abase + O::A_BYTES, blo = bbase + O::B_BYTES;
         for (int s = 0; s < ksteps; ++s) {
             const uint32_t ao = s * 2 * LBO_A, bo = s * 2 * LBO_B;
@@ -155,28 +173,30 @@ __device__ __forceinline__ double seed_rep_mixed(int m, int mp, double lognorm, 
     return __longlong_as_double((long long)((b & ~(0x7FFull << 52)) | ((unsigned long long)e << 52)));
 }
 
-struct MixedTables {
+// The transforms of one launch: same bandwidth (shared tables), own data.
+struct MixedBatch {
     Tables tb;
-    const double *lw;  // [2B] log w_B(j)
+    const float2 *S[kMaxMixedBatch];  // FP32 S workspaces, layout [m][m'][j]
+    double *coef[kMaxMixedBatch];     // interleaved complex coefficients
 };
 
 // ---------------------------------------------------------------------------
 // Forward DWT (mixed).  One CTA per cluster, NT threads = NT beta samples per
-// K chunk (one recurrence chain per thread), M tiles of 64 degrees.
+// K chunk (one recurrence chain per thread), M tiles of 64 degrees, N = 16 NB
+// columns: the T tile produced once serves the NB transforms of the batch.
 //   dynamic smem: operands | dprev[2B] | dcur[2B] | rA,rAc,rV [B each]; the
 //   table-building scratch (Bc, sig) lives in the operand area, which is not
 //   yet in use then.
 // ---------------------------------------------------------------------------
-template <int MODE, int NT>
-__global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedTables mt, const float2 *__restrict__ S,
-                                                                double *__restrict__ coef, int flags) {
-    constexpr int TM = kFwdTile, KC = NT;
-    using O = Operands<MODE, TM, KC>;
+template <int MODE, int NT, int NB>
+__global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedBatch mb, int flags) {
+    constexpr int TM = kFwdTile, KC = NT, NC = 16 * NB;
+    using O = Operands<MODE, TM, KC, NC>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mbar;
-    const Tables &tb = mt.tb;
+    const Tables &tb = mb.tb;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int2 rep = tb.clusters[blockIdx.x];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
@@ -195,11 +215,11 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedTables mt
         const double lognorm = seed_lognorm(tb, m, mp);
         for (int j = tid; j < n; j += NT) {
             // w_B(j) d(l0,m,m';beta_j): the weight enters through the seed's logarithm
-            dcur[j] = seed_rep_mixed(m, mp, (flags & kApplyW) ? lognorm + mt.lw[j] : lognorm, tb.lcos[j], tb.lsin[j]);
+            dcur[j] = seed_rep_mixed(m, mp, (flags & kApplyW) ? lognorm + tb.lw[j] : lognorm, tb.lcos[j], tb.lsin[j]);
             dprev[j] = 0.0;
         }
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, tmem_cols<NC>());
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc::fence_before_sync();
     __syncthreads();
@@ -251,43 +271,78 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedTables mt
                     }
                 }
             }
-            // B: X chunk, row 2p / 2p+1 = re / im of partner p, k = beta sample in chunk.
-            for (int e = tid; e < 8 * KC; e += NT) {
-                const int p = e / KC, k = e % KC, jj = c * KC + k;
-                if (k >= kfill) continue;
-                float2 v = make_float2(0.f, 0.f);
-                if (p < np && k < kvalid) {
-                    const int src = cs.mir[p] ? n - 1 - jj : jj;
-                    v = S[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + src];
+            // B: X chunk, row 16 b + 2p (+1) = re (im) of partner p of transform b, k = beta sample;
+            // each thread moves 8 consecutive samples (two 16-byte loads per 4, one 16-byte store per row).
+            for (int e = tid; e < 8 * NB * (KC / 8); e += NT) {
+                const int bp = e / (KC / 8), k0 = 8 * (e % (KC / 8));
+                const int b = bp >> 3, p = bp & 7;
+                if (k0 >= kfill) continue;
+                float re[8], im[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) { re[u] = 0.f; im[u] = 0.f; }
+                if (p < np) {
+                    const float2 *run = mb.S[b] + ((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n;
+                    const int j0 = c * KC + k0;
+                    if (k0 + 8 <= kvalid) {
+                        // samples j0..j0+7, or n-8-j0..n-1-j0 read in reverse for mirrored partners
+                        const float4 *q = reinterpret_cast<const float4 *>(run + (cs.mir[p] ? n - 8 - j0 : j0));
+                        float2 w[8];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const float4 t = q[h];
+                            w[2 * h] = make_float2(t.x, t.y);
+                            w[2 * h + 1] = make_float2(t.z, t.w);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float2 t = cs.mir[p] ? w[7 - u] : w[u];
+                            re[u] = t.x;
+                            im[u] = t.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (k0 + u < kvalid) {
+                                const int jj = j0 + u;
+                                const float2 t = run[cs.mir[p] ? n - 1 - jj : jj];
+                                re[u] = t.x;
+                                im[u] = t.y;
+                            }
+                    }
                 }
-                put<MODE>(X, O::B_BYTES, kNCols, 2 * p, k, v.x);
-                put<MODE>(X, O::B_BYTES, kNCols, 2 * p + 1, k, v.y);
+                put_b8<MODE>(X, O::B_BYTES, O::B_LBO, 16 * b + 2 * p, k0, re);
+                put_b8<MODE>(X, O::B_BYTES, O::B_LBO, 16 * b + 2 * p + 1, k0, im);
             }
             tc::fence_proxy_async();
             __syncthreads();
-            if (tid == 0) issue_chunk<MODE, TM, KC>(tmem, A, X, c == 0, ksteps, &mbar);
+            if (tid == 0) issue_chunk<MODE, TM, KC, NC>(tmem, A, X, c == 0, ksteps, &mbar);
             const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
             phase ^= 1u;
             ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
         }
         if (!ok) break;
-        // Epilogue: degree lb + 16 w + i sits in TMEM lane 32 w + i (i < 16) of warp w < 4.
+        // Epilogue: degree lb + 16 w + i sits in TMEM lane 32 w + i (i < 16) of warp w < 4;
+        // transform b's 16 columns start at column 16 b.
         tc::fence_after_sync();
         if (warp < 4) {
-            uint32_t d[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), d);
             const int r = 16 * warp + lane;
-            if (lane < 16 && r < rows) {
-                const int l = lb + r, q = l - l0;
+            const int l = lb + r, q = l - l0;
+            const bool live = lane < 16 && r < rows;
+#pragma unroll 1
+            for (int b = 0; b < NB; ++b) {
+                uint32_t d[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * b, d);
+                if (live) {
 #pragma unroll
-                for (int p = 0; p < 8; ++p) {
-                    if (p >= np) break;
-                    const double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
-                    const double v = rV[q] * sg;
-                    double2 out;
-                    out.x = v * tc::f32_to_f64(__uint_as_float(d[2 * p]));
-                    out.y = v * tc::f32_to_f64(__uint_as_float(d[2 * p + 1]));
-                    *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p] + q)) = out;
+                    for (int p = 0; p < 8; ++p) {
+                        if (p >= np) break;
+                        const double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
+                        const double v = rV[q] * sg;
+                        double2 out;
+                        out.x = v * tc::f32_to_f64(__uint_as_float(d[2 * p]));
+                        out.y = v * tc::f32_to_f64(__uint_as_float(d[2 * p + 1]));
+                        *reinterpret_cast<double2 *>(mb.coef[b] + 2 * (cs.off[p] + q)) = out;
+                    }
                 }
             }
         }
@@ -298,23 +353,24 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedTables mt
     if (!ok && tid == 0 && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols<NC>());
 }
 
 // ---------------------------------------------------------------------------
 // Inverse DWT (mixed).  One CTA per cluster, looping over tiles of 128 beta
-// samples; K = degrees in chunks of 128.
-//   dynamic smem: operands | rA,rAc,rBc [B each]
+// samples; K = degrees in chunks of 64; N = 16 NB columns (the sign-folded
+// coefficients of the NB transforms), so each generated T tile serves the batch.
+//   dynamic smem: operands | rA,rAc,rBc,rSig [B each]
 // ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedTables mt, const double *__restrict__ coef,
-                                                                 float2 *__restrict__ S, int flags) {
-    using O = Operands<MODE>;
+template <int MODE, int NB>
+__global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedBatch mb, int flags) {
+    constexpr int NC = 16 * NB;
+    using O = Operands<MODE, kTile, kChunk, NC>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mbar;
-    const Tables &tb = mt.tb;
+    const Tables &tb = mb.tb;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5;
     const int2 rep = tb.clusters[blockIdx.x];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
@@ -325,7 +381,7 @@ __global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedTables m
 
     load_cluster(tb, m, mp, cs);
     scaled_recurrence_tables<kNT>(l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, tmem_cols<NC>());
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc::fence_before_sync();
     __syncthreads();
@@ -368,41 +424,57 @@ __global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedTables m
                     put_vec<MODE>(A, O::A_BYTES, O::A_LBO, tid, k0, v);
                 }
             }
-            // B: F chunk, row 2p / 2p+1 = sign-folded re / im of partner p at degree lb + k.
-            for (int e = tid; e < 8 * kChunk; e += kNT) {
-                const int p = e / kChunk, k = e % kChunk;
-                if (k >= kfill) continue;
-                float re = 0.f, im = 0.f;
-                if (p < np && k < cnt) {
-                    const int l = lb + k;
-                    const double2 cv = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + (l - l0)));
-                    const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
-                    const double v = rSig[l - l0] * ((flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0);
-                    re = tc::f64_to_f32_rn(neg ? -v * cv.x : v * cv.x);
-                    im = tc::f64_to_f32_rn(neg ? -v * cv.y : v * cv.y);
+            // B: F chunk, row 16 b + 2p (+1) = sign- and sig-folded re (im) of partner p of
+            // transform b at degrees lb + k0 .. lb + k0 + 7 (8 per thread, 16-byte stores).
+            for (int e = tid; e < 8 * NB * (kChunk / 8); e += kNT) {
+                const int bp = e / (kChunk / 8), k0 = 8 * (e % (kChunk / 8));
+                const int b = bp >> 3, p = bp & 7;
+                if (k0 >= kfill) continue;
+                float re[8], im[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) { re[u] = 0.f; im[u] = 0.f; }
+                if (p < np) {
+                    const double2 *run = reinterpret_cast<const double2 *>(mb.coef[b]) + cs.off[p] + (lb - l0);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int k = k0 + u;
+                        if (k < cnt) {
+                            const int l = lb + k;
+                            const double2 cv = run[k];
+                            const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
+                            const double v =
+                                rSig[l - l0] * ((flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0);
+                            re[u] = tc::f64_to_f32_rn(neg ? -v * cv.x : v * cv.x);
+                            im[u] = tc::f64_to_f32_rn(neg ? -v * cv.y : v * cv.y);
+                        }
+                    }
                 }
-                put<MODE>(F, O::B_BYTES, kNCols, 2 * p, k, re);
-                put<MODE>(F, O::B_BYTES, kNCols, 2 * p + 1, k, im);
+                put_b8<MODE>(F, O::B_BYTES, O::B_LBO, 16 * b + 2 * p, k0, re);
+                put_b8<MODE>(F, O::B_BYTES, O::B_LBO, 16 * b + 2 * p + 1, k0, im);
             }
             tc::fence_proxy_async();
             __syncthreads();
-            if (tid == 0) issue_chunk<MODE, kTile, kChunk>(tmem, A, F, c == 0, ksteps, &mbar);
+            if (tid == 0) issue_chunk<MODE, kTile, kChunk, NC>(tmem, A, F, c == 0, ksteps, &mbar);
             const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
             phase ^= 1u;
             ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
         }
         if (!ok) break;
         tc::fence_after_sync();
-        uint32_t d[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), d);
-        if (active) {
+#pragma unroll 1
+        for (int b = 0; b < NB; ++b) {
+            uint32_t d[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * b, d);
+            if (active) {
+                float2 *Sb = const_cast<float2 *>(mb.S[b]);
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                if (p >= np) break;
-                const int jj = cs.mir[p] ? n - 1 - j : j;
-                const float wj = (flags & kApplyW) ? tc::f64_to_f32_rn(tb.w[jj]) : 1.0f;
-                S[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + jj] =
-                    make_float2(wj * __uint_as_float(d[2 * p]), wj * __uint_as_float(d[2 * p + 1]));
+                for (int p = 0; p < 8; ++p) {
+                    if (p >= np) break;
+                    const int jj = cs.mir[p] ? n - 1 - j : j;
+                    const float wj = (flags & kApplyW) ? tc::f64_to_f32_rn(tb.w[jj]) : 1.0f;
+                    Sb[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + jj] =
+                        make_float2(wj * __uint_as_float(d[2 * p]), wj * __uint_as_float(d[2 * p + 1]));
+                }
             }
         }
         tc::fence_before_sync();
@@ -412,7 +484,7 @@ __global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedTables m
     if (!ok && tid == 0 && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols<NC>());
 }
 
 // log w_B(j) for the forward's weighted seeds.
@@ -470,18 +542,64 @@ __global__ void transpose32_kernel(const float2 *__restrict__ X, float2 *__restr
 
 int grid_for(int64_t count) { return (int)std::min<int64_t>((count + 255) / 256, 152 * 16); }
 
-}  // namespace
-
-template <int MODE, int NT>
+template <int MODE, int NT, int NB>
 size_t mixed_forward_smem(int B) {
-    static_assert(Operands<MODE, kFwdTile, NT>::BYTES >= 2 * kMaxB * (int)sizeof(double), "scratch must fit");
-    return Operands<MODE, kFwdTile, NT>::BYTES + sizeof(double) * (2 * (size_t)(2 * B) + 3 * (size_t)B);
+    static_assert(Operands<MODE, kFwdTile, NT, 16 * NB>::BYTES >= 2 * kMaxB * (int)sizeof(double), "scratch must fit");
+    return Operands<MODE, kFwdTile, NT, 16 * NB>::BYTES + sizeof(double) * (2 * (size_t)(2 * B) + 3 * (size_t)B);
 }
 
-size_t mixed_inverse_smem(int mode, int B) {
-    const size_t ops = mode == SOFT_MIXED_TF32 ? Operands<SOFT_MIXED_TF32>::BYTES : Operands<SOFT_MIXED_BF16X3>::BYTES;
-    return ops + sizeof(double) * 4 * (size_t)B;
+template <int MODE, int NB>
+size_t mixed_inverse_smem(int B) {
+    return Operands<MODE, kTile, kChunk, 16 * NB>::BYTES + sizeof(double) * 4 * (size_t)B;
 }
+
+template <int MODE, int NT, int NB>
+cudaError_t run_forward_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
+    const size_t bytes = mixed_forward_smem<MODE, NT, NB>(mb.tb.B);
+    cudaError_t e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<MODE, NT, NB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    dwt_forward_mixed_kernel<MODE, NT, NB><<<mb.tb.ncl, NT, bytes, s>>>(mb, flags);
+    return cudaGetLastError();
+}
+
+template <int MODE, int NB>
+cudaError_t run_inverse_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
+    const size_t bytes = mixed_inverse_smem<MODE, NB>(mb.tb.B);
+    cudaError_t e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<MODE, NB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    dwt_inverse_mixed_kernel<MODE, NB><<<mb.tb.ncl, kNT, bytes, s>>>(mb, flags);
+    return cudaGetLastError();
+}
+
+// Forward shapes: one transform uses 128 beta samples per chunk up to 2B = 128
+// and 256 beyond (two CTAs per SM at 2B = 1024); batches use 128 per chunk so
+// that the N = 16 NB column operand stays small.
+template <int MODE>
+cudaError_t forward_mixed_nb(const MixedBatch &mb, int nb, cudaStream_t s, int flags) {
+    switch (nb) {
+        case 1: return 2 * mb.tb.B <= 128 ? run_forward_mixed<MODE, 128, 1>(mb, s, flags)
+                                          : run_forward_mixed<MODE, 256, 1>(mb, s, flags);
+        case 2: return run_forward_mixed<MODE, 128, 2>(mb, s, flags);
+        case 4: return run_forward_mixed<MODE, 128, 4>(mb, s, flags);
+        case 8: return run_forward_mixed<MODE, 128, 8>(mb, s, flags);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int MODE>
+cudaError_t inverse_mixed_nb(const MixedBatch &mb, int nb, cudaStream_t s, int flags) {
+    switch (nb) {
+        case 1: return run_inverse_mixed<MODE, 1>(mb, s, flags);
+        case 2: return run_inverse_mixed<MODE, 2>(mb, s, flags);
+        case 4: return run_inverse_mixed<MODE, 4>(mb, s, flags);
+        case 8: return run_inverse_mixed<MODE, 8>(mb, s, flags);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
 
 cudaError_t launch_log_weights(int B, const double *w, double *lw, cudaStream_t s) {
     const int n = 2 * B;
@@ -489,45 +607,37 @@ cudaError_t launch_log_weights(int B, const double *w, double *lw, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <int MODE, int NT>
-cudaError_t run_forward_mixed(const MixedTables &mt, const float2 *S, double *coef, cudaStream_t s, int flags) {
-    const size_t bytes = mixed_forward_smem<MODE, NT>(mt.tb.B);
-    cudaError_t e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<MODE, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    dwt_forward_mixed_kernel<MODE, NT><<<mt.tb.ncl, NT, bytes, s>>>(mt, S, coef, flags);
-    return cudaGetLastError();
+// nb transforms of one bandwidth; nb in {1, 2, 4, 8} (a batch of other sizes
+// is split by the caller).
+cudaError_t launch_dwt_forward_mixed_batch(int mode, const Tables &tb, int nb, const float2 *const *S,
+                                           double *const *coef, cudaStream_t s, int flags) {
+    if (nb < 1 || nb > kMaxMixedBatch) return cudaErrorInvalidValue;
+    MixedBatch mb{};
+    mb.tb = tb;
+    for (int b = 0; b < nb; ++b) { mb.S[b] = S[b]; mb.coef[b] = coef[b]; }
+    return mode == SOFT_MIXED_TF32 ? forward_mixed_nb<SOFT_MIXED_TF32>(mb, nb, s, flags)
+                                   : forward_mixed_nb<SOFT_MIXED_BF16X3>(mb, nb, s, flags);
 }
 
-// 128 beta samples per chunk up to 2B = 128 (44 KB, several CTAs per SM), 256 beyond.
+cudaError_t launch_dwt_inverse_mixed_batch(int mode, const Tables &tb, int nb, const double *const *coef,
+                                           float2 *const *S, cudaStream_t s, int flags) {
+    if (nb < 1 || nb > kMaxMixedBatch) return cudaErrorInvalidValue;
+    MixedBatch mb{};
+    mb.tb = tb;
+    for (int b = 0; b < nb; ++b) { mb.S[b] = S[b]; mb.coef[b] = const_cast<double *>(coef[b]); }
+    return mode == SOFT_MIXED_TF32 ? inverse_mixed_nb<SOFT_MIXED_TF32>(mb, nb, s, flags)
+                                   : inverse_mixed_nb<SOFT_MIXED_BF16X3>(mb, nb, s, flags);
+}
+
 cudaError_t launch_dwt_forward_mixed(int mode, const Tables &tb, const double *lw, const float2 *S, double *coef,
                                      cudaStream_t s, int flags) {
-    MixedTables mt{tb, lw};
-    const bool small = 2 * tb.B <= 128;
-    if (mode == SOFT_MIXED_TF32)
-        return small ? run_forward_mixed<SOFT_MIXED_TF32, 128>(mt, S, coef, s, flags)
-                     : run_forward_mixed<SOFT_MIXED_TF32, 256>(mt, S, coef, s, flags);
-    return small ? run_forward_mixed<SOFT_MIXED_BF16X3, 128>(mt, S, coef, s, flags)
-                 : run_forward_mixed<SOFT_MIXED_BF16X3, 256>(mt, S, coef, s, flags);
+    (void)lw;  // tb.lw
+    return launch_dwt_forward_mixed_batch(mode, tb, 1, &S, &coef, s, flags);
 }
 
 cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s,
                                      int flags) {
-    MixedTables mt{tb, nullptr};
-    const size_t bytes = mixed_inverse_smem(mode, tb.B);
-    cudaError_t e;
-    if (mode == SOFT_MIXED_TF32) {
-        e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<SOFT_MIXED_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes);
-        if (e != cudaSuccess) return e;
-        dwt_inverse_mixed_kernel<SOFT_MIXED_TF32><<<tb.ncl, kNT, bytes, s>>>(mt, coef, S, flags);
-    } else {
-        e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<SOFT_MIXED_BF16X3>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        dwt_inverse_mixed_kernel<SOFT_MIXED_BF16X3><<<tb.ncl, kNT, bytes, s>>>(mt, coef, S, flags);
-    }
-    return cudaGetLastError();
+    return launch_dwt_inverse_mixed_batch(mode, tb, 1, &coef, &S, s, flags);
 }
 
 cudaError_t launch_zero_nyquist32(int B, float2 *S, cudaStream_t s) {

@@ -197,9 +197,8 @@ void free_plan(soft_plan_s *p) {
     delete p;
 }
 
-soft_status run_forward_mixed(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s, int flags) {
-    cudaEvent_t *ev = timing_slot(p, 0);
-    if (ev) cudaEventRecord(ev[0], s);
+// Mixed plans, the steps around the DWT: grid (FP64) -> S32 [m][m'][j] ...
+soft_status mixed_grid_to_S(soft_plan_s *p, const double *grid, cudaStream_t s) {
     cudaError_t e = launch_f64_to_f32(reinterpret_cast<const double2 *>(grid), p->g32, (int64_t)grid_elems(p->B), s);
     if (e != cudaSuccess) return fail_cuda("grid conversion kernel launch", e);
     cufftResult r = cufftSetStream(p->fft32f, s);
@@ -211,9 +210,30 @@ soft_status run_forward_mixed(soft_plan_s *p, const double *grid, double *coef, 
     if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecC2C (forward slices)", r);
     const int n = 2 * p->B;
     e = launch_transpose32(p->g32, p->S32, n, (int64_t)n * n, s);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("transpose kernel launch", e);
+}
+
+// ... and S32 -> grid (FP64): transpose, FFT with exp(-i...), conversion.
+soft_status mixed_S_to_grid(soft_plan_s *p, double *grid, cudaStream_t s) {
+    const int n = 2 * p->B;
+    cudaError_t e = launch_transpose32(p->S32, p->g32, n * n, (int64_t)n, s);
     if (e != cudaSuccess) return fail_cuda("transpose kernel launch", e);
+    cufftResult r = cufftSetStream(p->fft32f, s);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
+    r = cufftExecC2C(p->fft32f, reinterpret_cast<cufftComplex *>(p->g32), reinterpret_cast<cufftComplex *>(p->g32),
+                     CUFFT_FORWARD);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecC2C (inverse slices)", r);
+    e = launch_f32_to_f64(p->g32, reinterpret_cast<double2 *>(grid), (int64_t)grid_elems(p->B), s);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("grid conversion kernel launch", e);
+}
+
+soft_status run_forward_mixed(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s, int flags) {
+    cudaEvent_t *ev = timing_slot(p, 0);
+    if (ev) cudaEventRecord(ev[0], s);
+    soft_status st = mixed_grid_to_S(p, grid, s);
+    if (st != SOFT_OK) return st;
     if (ev) cudaEventRecord(ev[1], s);
-    e = launch_dwt_forward_mixed(p->dtype, p->tables(), p->lw, p->S32, coef, s, flags);
+    cudaError_t e = launch_dwt_forward_mixed(p->dtype, p->tables(), p->lw, p->S32, coef, s, flags);
     if (e != cudaSuccess) return fail_cuda("mixed DWT kernel launch", e);
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
@@ -227,16 +247,8 @@ soft_status run_inverse_mixed(soft_plan_s *p, const double *coef, double *grid, 
     e = launch_dwt_inverse_mixed(p->dtype, p->tables(), coef, p->S32, s, flags);
     if (e != cudaSuccess) return fail_cuda("mixed iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
-    const int n = 2 * p->B;
-    e = launch_transpose32(p->S32, p->g32, n * n, (int64_t)n, s);
-    if (e != cudaSuccess) return fail_cuda("transpose kernel launch", e);
-    cufftResult r = cufftSetStream(p->fft32f, s);
-    if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
-    r = cufftExecC2C(p->fft32f, reinterpret_cast<cufftComplex *>(p->g32), reinterpret_cast<cufftComplex *>(p->g32),
-                     CUFFT_FORWARD);
-    if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecC2C (inverse slices)", r);
-    e = launch_f32_to_f64(p->g32, reinterpret_cast<double2 *>(grid), (int64_t)grid_elems(p->B), s);
-    if (e != cudaSuccess) return fail_cuda("grid conversion kernel launch", e);
+    soft_status st = mixed_S_to_grid(p, grid, s);
+    if (st != SOFT_OK) return st;
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
 }
@@ -381,7 +393,62 @@ soft_status record_batch(BatchGraph *bg, int n, const void *const *a, const void
             }
         }
     }
-    for (int i : rest) {
+    // Mixed-precision transforms of one (mode, B): groups of 8, 4, 2, 1 share one
+    // DWT launch, so each Wigner-d tile feeds 16 x group tensor-core columns.
+    std::vector<int> single;
+    if (bg->kind != kBatchCorrelate) {
+        std::vector<bool> taken(n, false);
+        for (int i : rest) {
+            soft_plan_s *p = bg->plans[i];
+            if (p->dtype == SOFT_FP64 || taken[i]) continue;
+            std::vector<int> grp;
+            for (int j : rest)
+                if (!taken[j] && bg->plans[j]->dtype == p->dtype && bg->plans[j]->B == p->B) grp.push_back(j);
+            for (size_t g0 = 0; g0 < grp.size();) {
+                const size_t left = grp.size() - g0;
+                const int nb = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+                const float2 *Sv[kMaxMixedBatch];
+                float2 *Sw[kMaxMixedBatch];
+                double *cw[kMaxMixedBatch];
+                const double *cr[kMaxMixedBatch];
+                for (int t = 0; t < nb; ++t) {
+                    const int idx = grp[g0 + t];
+                    soft_plan_s *q = bg->plans[idx];
+                    taken[idx] = true;
+                    Sv[t] = q->S32;
+                    Sw[t] = q->S32;
+                    cw[t] = static_cast<double *>(const_cast<void *>(b[idx]));
+                    cr[t] = static_cast<const double *>(a[idx]);
+                    soft_status st = SOFT_OK;
+                    if (bg->kind == kBatchForward) {
+                        st = mixed_grid_to_S(q, static_cast<const double *>(a[idx]), cs);
+                    } else {
+                        cudaError_t e0 = launch_zero_nyquist32(q->B, q->S32, cs);
+                        if (e0 != cudaSuccess) st = fail_cuda("S clearing kernel launch", e0);
+                    }
+                    if (st != SOFT_OK) return st;
+                }
+                const Tables tb = p->tables();
+                e = bg->kind == kBatchForward
+                        ? launch_dwt_forward_mixed_batch(p->dtype, tb, nb, Sv, cw, cs)
+                        : launch_dwt_inverse_mixed_batch(p->dtype, tb, nb, cr, Sw, cs);
+                if (e != cudaSuccess) return fail_cuda("batched mixed DWT", e);
+                if (bg->kind == kBatchInverse)
+                    for (int t = 0; t < nb; ++t) {
+                        const int idx = grp[g0 + t];
+                        soft_status st =
+                            mixed_S_to_grid(bg->plans[idx], static_cast<double *>(const_cast<void *>(b[idx])), cs);
+                        if (st != SOFT_OK) return st;
+                    }
+                g0 += nb;
+            }
+        }
+        for (int i : rest)
+            if (!taken[i]) single.push_back(i);
+    } else {
+        single = rest;
+    }
+    for (int i : single) {
         soft_plan_s *p = bg->plans[i];
         soft_status st = SOFT_OK;
         if (bg->kind == kBatchForward) {

@@ -12,6 +12,7 @@
 namespace softgb {
 
 constexpr int kMaxB = 512;
+constexpr int kMaxMixedBatch = 8;  // transforms sharing one mixed-precision DWT launch
 
 // Per-plan device tables (all FP64 unless stated).
 struct Tables {
@@ -225,6 +226,12 @@ cudaError_t launch_dwt_forward_mixed(int mode, const Tables &tb, const double *l
                                      cudaStream_t s, int flags = kApplyW | kApplyV);
 cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s,
                                      int flags = 0);
+// nb (1, 2, 4 or 8) transforms of one bandwidth in one launch: the generated
+// Wigner-d tile feeds N = 16 nb tensor-core columns.
+cudaError_t launch_dwt_forward_mixed_batch(int mode, const Tables &tb, int nb, const float2 *const *S,
+                                           double *const *coef, cudaStream_t s, int flags = kApplyW | kApplyV);
+cudaError_t launch_dwt_inverse_mixed_batch(int mode, const Tables &tb, int nb, const double *const *coef,
+                                           float2 *const *S, cudaStream_t s, int flags = 0);
 cudaError_t launch_zero_nyquist32(int B, float2 *S, cudaStream_t s);
 cudaError_t launch_f64_to_f32(const double2 *in, float2 *out, int64_t count, cudaStream_t s);
 cudaError_t launch_transpose32(const float2 *X, float2 *Y, int rows, int64_t cols, cudaStream_t s);

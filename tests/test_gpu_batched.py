@@ -124,3 +124,30 @@ def test_batched_correlation_workload():
     finally:
         for p in plans:
             p.close()
+
+
+def test_batched_mixed_groups_equal_single_calls():
+    """Same-(mode, B) mixed plans are grouped 8/4/2/1 into shared DWT launches
+    (N = 16 x group tensor-core columns); results must match single calls."""
+    specs = [(32, "bf16x3")] * 8 + [(16, "tf32")] * 4 + [(64, "bf16x3")] * 3 + [(8, "fp64")]
+    plans = [Plan(B, m, device=DEV) for B, m in specs]
+    try:
+        coefs = [_coef(p.B, 500 + i) for i, p in enumerate(plans)]
+        grids = batched_inverse(plans, coefs)
+        back = batched_forward(plans, grids)
+        torch.cuda.synchronize(DEV)
+        for i, p in enumerate(plans):
+            g1 = p.inverse(coefs[i])
+            c1 = p.forward(grids[i])
+            torch.cuda.synchronize(DEV)
+            assert synth.rel_l2(grids[i].cpu().numpy(), g1.cpu().numpy()) < 1e-12, (i, p.B, p.dtype)
+            assert synth.rel_l2(back[i].cpu().numpy(), c1.cpu().numpy()) < 1e-12, (i, p.B, p.dtype)
+        # and against the oracle for one member of each group
+        for i in (0, 8, 12):
+            B = plans[i].B
+            ref = oracle.inverse(B, coefs[i].cpu().numpy())
+            bound = 5e-5 if plans[i].dtype == "bf16x3" else 2e-3
+            assert synth.rel_l2(grids[i].cpu().numpy(), ref) < bound
+    finally:
+        for p in plans:
+            p.close()
