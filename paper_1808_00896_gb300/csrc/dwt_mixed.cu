@@ -188,9 +188,12 @@ struct MixedBatch {
 //   table-building scratch (Bc, sig) lives in the operand area, which is not
 //   yet in use then.
 // ---------------------------------------------------------------------------
-template <int MODE, int NT, int NB>
-__global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedBatch mb, int flags) {
-    constexpr int TM = kFwdTile, KC = NT, NC = 16 * NB;
+template <int MODE, int KC, int NB, bool LD>
+__global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(MixedBatch mb, int flags) {
+    // KC producer threads (one beta sample each per chunk); with LD, a second
+    // group of KC threads loads the B operand while the producers run the recurrence.
+    constexpr int NT = LD ? 2 * KC : KC;
+    constexpr int TM = kFwdTile, NC = 16 * NB;
     using O = Operands<MODE, TM, KC, NC>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
@@ -241,7 +244,9 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedBatch mb,
             // A: column tid = beta sample j, rows = degrees lb..lb+rows-1.  Rows past
             // `rows` are left as they are: they only reach TMEM lanes that are never read.
             const int j = c * KC + tid;
-            if (tid < kvalid) {
+            if (tid >= KC) {
+                // loader threads: no column of A
+            } else if (tid < kvalid) {
                 const double x = tb.cosb[j];
                 double dc = dcur[j], dp = dprev[j];
                 for (int r = 0; r < rows; ++r) {
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedBatch mb,
             }
             // B: X chunk, row 16 b + 2p (+1) = re (im) of partner p of transform b, k = beta sample;
             // each thread moves 8 consecutive samples (two 16-byte loads per 4, one 16-byte store per row).
-            for (int e = tid; e < 8 * NB * (KC / 8); e += NT) {
+            for (int e = LD ? tid - KC : tid; e >= 0 && e < 8 * NB * (KC / 8); e += LD ? KC : NT) {
                 const int bp = e / (KC / 8), k0 = 8 * (e % (KC / 8));
                 const int b = bp >> 3, p = bp & 7;
                 if (k0 >= kfill) continue;
@@ -333,14 +338,15 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedBatch mb,
                 uint32_t d[16];
                 tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * b, d);
                 if (live) {
+                    // V_l sig_l and the partner sign applied in FP32 (the accumulator's precision)
+                    const float v = tc::f64_to_f32_rn(rV[q]);
 #pragma unroll
                     for (int p = 0; p < 8; ++p) {
                         if (p >= np) break;
-                        const double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
-                        const double v = rV[q] * sg;
+                        const float vs = ((cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1))) ? -v : v;
                         double2 out;
-                        out.x = v * tc::f32_to_f64(__uint_as_float(d[2 * p]));
-                        out.y = v * tc::f32_to_f64(__uint_as_float(d[2 * p + 1]));
+                        out.x = tc::f32_to_f64(vs * __uint_as_float(d[2 * p]));
+                        out.y = tc::f32_to_f64(vs * __uint_as_float(d[2 * p + 1]));
                         *reinterpret_cast<double2 *>(mb.coef[b] + 2 * (cs.off[p] + q)) = out;
                     }
                 }
@@ -362,8 +368,10 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_mixed_kernel(MixedBatch mb,
 // coefficients of the NB transforms), so each generated T tile serves the batch.
 //   dynamic smem: operands | rA,rAc,rBc,rSig [B each]
 // ---------------------------------------------------------------------------
-template <int MODE, int NB>
-__global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedBatch mb, int flags) {
+template <int MODE, int NB, bool LD>
+__global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kernel(MixedBatch mb, int flags) {
+    // kNT producer threads (one beta sample each); with LD, kNT more threads load the B operand.
+    constexpr int NT = LD ? 2 * kNT : kNT;
     constexpr int NC = 16 * NB;
     using O = Operands<MODE, kTile, kChunk, NC>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -378,9 +386,12 @@ __global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedBatch mb
     unsigned char *A = smem;
     unsigned char *F = smem + O::PLANES * O::A_BYTES;
     double *rA = reinterpret_cast<double *>(smem + O::BYTES), *rAc = rA + B, *rBc = rAc + B, *rSig = rBc + B;
+    float *fsc = reinterpret_cast<float *>(rSig + B);  // [B] sig_l (V_l) in FP32, the B operand's scale
 
     load_cluster(tb, m, mp, cs);
-    scaled_recurrence_tables<kNT>(l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
+    scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
+    for (int t = tid; t < L; t += NT)
+        fsc[t] = tc::f64_to_f32_rn(rSig[t] * ((flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0));
     if (warp == 0) tc::tmem_alloc(&tmem_slot, tmem_cols<NC>());
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc::fence_before_sync();
@@ -394,7 +405,7 @@ __global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedBatch mb
 
     for (int jb = 0; jb < n && ok; jb += kTile) {
         const int j = jb + tid;
-        const bool active = j < n;
+        const bool active = tid < kNT && j < n;
         double x = 0.0, dc = 0.0, dp = 0.0;
         if (active) {
             x = tb.cosb[j];
@@ -426,7 +437,7 @@ __global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedBatch mb
             }
             // B: F chunk, row 16 b + 2p (+1) = sign- and sig-folded re (im) of partner p of
             // transform b at degrees lb + k0 .. lb + k0 + 7 (8 per thread, 16-byte stores).
-            for (int e = tid; e < 8 * NB * (kChunk / 8); e += kNT) {
+            for (int e = LD ? tid - kNT : tid; e >= 0 && e < 8 * NB * (kChunk / 8); e += LD ? kNT : NT) {
                 const int bp = e / (kChunk / 8), k0 = 8 * (e % (kChunk / 8));
                 const int b = bp >> 3, p = bp & 7;
                 if (k0 >= kfill) continue;
@@ -442,10 +453,9 @@ __global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedBatch mb
                             const int l = lb + k;
                             const double2 cv = run[k];
                             const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
-                            const double v =
-                                rSig[l - l0] * ((flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0);
-                            re[u] = tc::f64_to_f32_rn(neg ? -v * cv.x : v * cv.x);
-                            im[u] = tc::f64_to_f32_rn(neg ? -v * cv.y : v * cv.y);
+                            const float v = neg ? -fsc[l - l0] : fsc[l - l0];  // FP32 scale: no FP64 work here
+                            re[u] = v * tc::f64_to_f32_rn(cv.x);
+                            im[u] = v * tc::f64_to_f32_rn(cv.y);
                         }
                     }
                 }
@@ -462,7 +472,7 @@ __global__ void __launch_bounds__(kNT, 1) dwt_inverse_mixed_kernel(MixedBatch mb
         if (!ok) break;
         tc::fence_after_sync();
 #pragma unroll 1
-        for (int b = 0; b < NB; ++b) {
+        for (int b = 0; b < NB && warp < 4; ++b) {
             uint32_t d[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * b, d);
             if (active) {
@@ -542,48 +552,50 @@ __global__ void transpose32_kernel(const float2 *__restrict__ X, float2 *__restr
 
 int grid_for(int64_t count) { return (int)std::min<int64_t>((count + 255) / 256, 152 * 16); }
 
-template <int MODE, int NT, int NB>
+template <int MODE, int KC, int NB>
 size_t mixed_forward_smem(int B) {
-    static_assert(Operands<MODE, kFwdTile, NT, 16 * NB>::BYTES >= 2 * kMaxB * (int)sizeof(double), "scratch must fit");
-    return Operands<MODE, kFwdTile, NT, 16 * NB>::BYTES + sizeof(double) * (2 * (size_t)(2 * B) + 3 * (size_t)B);
+    static_assert(Operands<MODE, kFwdTile, KC, 16 * NB>::BYTES >= 2 * kMaxB * (int)sizeof(double), "scratch must fit");
+    return Operands<MODE, kFwdTile, KC, 16 * NB>::BYTES + sizeof(double) * (2 * (size_t)(2 * B) + 3 * (size_t)B);
 }
 
 template <int MODE, int NB>
 size_t mixed_inverse_smem(int B) {
-    return Operands<MODE, kTile, kChunk, 16 * NB>::BYTES + sizeof(double) * 4 * (size_t)B;
+    return Operands<MODE, kTile, kChunk, 16 * NB>::BYTES + sizeof(double) * 4 * (size_t)B + sizeof(float) * (size_t)B;
 }
 
-template <int MODE, int NT, int NB>
+template <int MODE, int KC, int NB, bool LD>
 cudaError_t run_forward_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
-    const size_t bytes = mixed_forward_smem<MODE, NT, NB>(mb.tb.B);
-    cudaError_t e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<MODE, NT, NB>,
+    const size_t bytes = mixed_forward_smem<MODE, KC, NB>(mb.tb.B);
+    cudaError_t e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<MODE, KC, NB, LD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    dwt_forward_mixed_kernel<MODE, NT, NB><<<mb.tb.ncl, NT, bytes, s>>>(mb, flags);
+    dwt_forward_mixed_kernel<MODE, KC, NB, LD><<<mb.tb.ncl, LD ? 2 * KC : KC, bytes, s>>>(mb, flags);
     return cudaGetLastError();
 }
 
-template <int MODE, int NB>
+template <int MODE, int NB, bool LD>
 cudaError_t run_inverse_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
     const size_t bytes = mixed_inverse_smem<MODE, NB>(mb.tb.B);
-    cudaError_t e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<MODE, NB>,
+    cudaError_t e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<MODE, NB, LD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    dwt_inverse_mixed_kernel<MODE, NB><<<mb.tb.ncl, kNT, bytes, s>>>(mb, flags);
+    dwt_inverse_mixed_kernel<MODE, NB, LD><<<mb.tb.ncl, LD ? 2 * kNT : kNT, bytes, s>>>(mb, flags);
     return cudaGetLastError();
 }
 
 // Forward shapes: one transform uses 128 beta samples per chunk up to 2B = 128
 // and 256 beyond (two CTAs per SM at 2B = 1024); batches use 128 per chunk so
 // that the N = 16 NB column operand stays small.
+// Batches (NB >= 2) add a loader warpgroup: the B operand is NB times larger
+// than for one transform, and its loads then overlap the recurrence.
 template <int MODE>
 cudaError_t forward_mixed_nb(const MixedBatch &mb, int nb, cudaStream_t s, int flags) {
     switch (nb) {
-        case 1: return 2 * mb.tb.B <= 128 ? run_forward_mixed<MODE, 128, 1>(mb, s, flags)
-                                          : run_forward_mixed<MODE, 256, 1>(mb, s, flags);
-        case 2: return run_forward_mixed<MODE, 128, 2>(mb, s, flags);
-        case 4: return run_forward_mixed<MODE, 128, 4>(mb, s, flags);
-        case 8: return run_forward_mixed<MODE, 128, 8>(mb, s, flags);
+        case 1: return 2 * mb.tb.B <= 128 ? run_forward_mixed<MODE, 128, 1, false>(mb, s, flags)
+                                          : run_forward_mixed<MODE, 256, 1, false>(mb, s, flags);
+        case 2: return run_forward_mixed<MODE, 128, 2, true>(mb, s, flags);
+        case 4: return run_forward_mixed<MODE, 128, 4, true>(mb, s, flags);
+        case 8: return run_forward_mixed<MODE, 128, 8, true>(mb, s, flags);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -591,10 +603,10 @@ cudaError_t forward_mixed_nb(const MixedBatch &mb, int nb, cudaStream_t s, int f
 template <int MODE>
 cudaError_t inverse_mixed_nb(const MixedBatch &mb, int nb, cudaStream_t s, int flags) {
     switch (nb) {
-        case 1: return run_inverse_mixed<MODE, 1>(mb, s, flags);
-        case 2: return run_inverse_mixed<MODE, 2>(mb, s, flags);
-        case 4: return run_inverse_mixed<MODE, 4>(mb, s, flags);
-        case 8: return run_inverse_mixed<MODE, 8>(mb, s, flags);
+        case 1: return run_inverse_mixed<MODE, 1, false>(mb, s, flags);
+        case 2: return run_inverse_mixed<MODE, 2, true>(mb, s, flags);
+        case 4: return run_inverse_mixed<MODE, 4, true>(mb, s, flags);
+        case 8: return run_inverse_mixed<MODE, 8, true>(mb, s, flags);
         default: return cudaErrorInvalidValue;
     }
 }
