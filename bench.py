@@ -155,6 +155,19 @@ class ClockSampler:
                 "power_w_median": statistics.median(power) if power else None}
 
 
+def max_over_ranks(x: float) -> float:
+    """Max of a per-rank number over all ranks (identity without a process
+    group).  CPU tensor on gloo, the current CUDA device otherwise."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = torch.device("cpu") if dist.get_backend() == "gloo" else torch.device("cuda", torch.cuda.current_device())
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -262,10 +275,7 @@ def run_corr(args) -> None:
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     value = world * len(reqs) * 1000.0 / ms
     # e2e: SH coefficients host -> device, the batch, arg-max results device -> host.
     fh = [torch.from_numpy(f).pin_memory() for _, f, _ in reqs]
@@ -360,10 +370,7 @@ def run_batched(args) -> None:
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     value = world * nb * 1000.0 / ms
     fl = dwt_flops(B)
     peak_gflops = FP64_FLOPS_PER_SM_CLK * N_SM * SM_MAX_MHZ * 1e6 / 1e9
@@ -418,6 +425,7 @@ def run_ours(args) -> None:
         R = 1  # one input already exceeds L2 several times over
 
     plan = Plan(B, dtype, device=dev)
+    tuned = plan.tune() if args.tune else None
     coefs = [torch.from_numpy(synth.coefficients(B, kind, seed=synth.BASE_SEED + 100 * rank + r)).to(dev)
              for r in range(R)]
     grids = [plan.inverse(c) for c in coefs]
@@ -451,10 +459,7 @@ def run_ours(args) -> None:
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total)
     plan.sync()
     phase_ms, phase_cnt = capi.soft_plan_read_timing(plan.handle)
     capi.soft_plan_enable_timing(plan.handle, False)
@@ -480,10 +485,7 @@ def run_ours(args) -> None:
         plan.forward_host(gh, cr)
         plan.inverse_host(ch, gr)
     e2e_dt = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_dt = float(t.item())
+    e2e_dt = max_over_ranks(e2e_dt)
     e2e = {"value": world * e2e_steps / e2e_dt, "unit": UNIT,
            "h2d_bytes_per_step": grid_bytes + coef_bytes, "d2h_bytes_per_step": coef_bytes + grid_bytes,
            "steps": e2e_steps}
@@ -528,6 +530,7 @@ def run_ours(args) -> None:
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if dtype == "fp64" else dtype, "data": "synthetic",
             "config": {"workload": desc, "B": B, "mode": dtype, "coefficients": kind, "inputs_rotated": R,
+                       "tile_variants": None if tuned is None else {"dwt": tuned["dwt"], "idwt": tuned["idwt"]},
                        "l2": f"{R} rotating input sets of {(grid_bytes + coef_bytes) / 2**20:.1f} MiB "
                              f"(> 129 MB L2 per pass)" if R > 1 else "single input larger than L2",
                        "parallelism": f"replicas x{world}"},
@@ -551,6 +554,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="autotune the DWT tile shapes before timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

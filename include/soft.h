@@ -203,6 +203,24 @@ soft_status soft_dwt_forward_noalloc(int B, const double *S, double *coef, void 
 soft_status soft_forward_host(soft_plan p, const double *grid_host, double *coef_host, void *stream);
 soft_status soft_inverse_host(soft_plan p, const double *coef_host, double *grid_host, void *stream);
 
+/* Tile-shape variants, for autotuning (not from the paper).  kernel 0 is the
+ * DWT, 1 the iDWT.  soft_plan_num_variants returns how many shapes exist for
+ * the plan's bandwidth and mode (-1 for a bad plan or kernel); variant 0 is
+ * the built-in default.  soft_plan_set_variant selects one for all later
+ * calls on the plan (SOFT_ERR_INVALID_ARG if out of range).  Results do not
+ * depend on the variant beyond rounding order. */
+int soft_plan_num_variants(soft_plan p, int kernel);
+soft_status soft_plan_set_variant(soft_plan p, int kernel, int variant);
+
+/* Failure-detection self-test (not from the paper).  Every wait inside the
+ * tensor-core kernels is a bounded poll of an mbarrier; when it runs out the
+ * kernel stops its work, records a timeout in the plan's device error word and
+ * returns, so the CUDA context stays usable and soft_plan_sync() reports
+ * SOFT_ERR_TIMEOUT.  This entry point runs that same bounded wait on an
+ * mbarrier that nothing arrives on, limited to `polls` polls (1..2^20), so the
+ * path can be exercised without a real failure.  Asynchronous on `stream`. */
+soft_status soft_selftest_bounded_wait(soft_plan p, int polls, void *stream);
+
 /* Per-phase timing.  When enabled, every soft_forward / soft_inverse records
  * CUDA events (on the call's stream) around its 2-D FFT and its (i)DWT
  * kernel(s); soft_plan_read_timing() waits for them, adds up the elapsed

@@ -82,6 +82,18 @@ class Plan:
     def sync(self) -> None:
         capi.soft_plan_sync(self.handle)
 
+    def tune(self, reps: int = 3, use_cache: bool = True) -> dict:
+        """Pick the fastest DWT / iDWT tile shapes for this plan (cached per GPU, B, mode)."""
+        from . import autotune
+        return autotune.tune(self, reps=reps, use_cache=use_cache)
+
+    def set_variant(self, kernel: int, variant: int) -> None:
+        """Select tile-shape variant `variant` of kernel 0 (DWT) or 1 (iDWT)."""
+        capi.check(capi.load().soft_plan_set_variant(self.handle, kernel, variant), "soft_plan_set_variant")
+
+    def num_variants(self, kernel: int) -> int:
+        return capi.load().soft_plan_num_variants(self.handle, kernel)
+
     # -- allocation helpers ---------------------------------------------------
     def empty_grid(self) -> torch.Tensor:
         return torch.empty((self.n,) * 3, dtype=torch.complex128, device=self.device)

@@ -51,6 +51,9 @@ SIGNATURES = {
     "soft_dwt_forward_noalloc": (_i, [_i, _vp, _vp, _vp]),
     "soft_forward_host": (_i, [_vp, _vp, _vp, _vp]),
     "soft_inverse_host": (_i, [_vp, _vp, _vp, _vp]),
+    "soft_selftest_bounded_wait": (_i, [_vp, _i, _vp]),
+    "soft_plan_num_variants": (_i, [_vp, _i]),
+    "soft_plan_set_variant": (_i, [_vp, _i, _i]),
     "soft_plan_enable_timing": (_i, [_vp, _i]),
     "soft_plan_read_timing": (_i, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }

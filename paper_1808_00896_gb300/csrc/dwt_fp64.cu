@@ -66,7 +66,7 @@ __global__ void zero_nyquist_kernel(int B, double2 *S) {
 // ---------------------------------------------------------------------------
 // Forward DWT.  NT threads, LT = NT/(16 TPI) degrees per tile, JPT beta samples
 // per thread in the recurrence phase, TPI threads per output (each sums a
-// contiguous 1/TPI of the beta range; TPI = 2 halves are combined by a shuffle).
+// contiguous 1/TPI of the beta range; the TPI partial sums are combined by shuffles).
 //   dynamic smem: X[2B][16] (w_B(j') S_p(j'), partner p in columns 2p, 2p+1),
 //                 T[LT][2B] (the current tile of T_B), rec[4][B] (A, Ac, Bc, V).
 // Phase A: every thread advances the recurrence of its beta samples LT steps,
@@ -74,7 +74,7 @@ __global__ void zero_nyquist_kernel(int B, double2 *S) {
 // Phase B: thread (t, c) forms sum_j T[t][j] X[j][c] for output column c.
 // ---------------------------------------------------------------------------
 template <int NT, int JPT, int TPI>
-__global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const double2 *__restrict__ S,
+__global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, const double2 *__restrict__ S,
                                                                double *__restrict__ coef, int flags) {
     constexpr int LT = NT / (16 * TPI);
     extern __shared__ __align__(16) double smem[];
@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
     __syncthreads();
 
     const int half = tid % TPI, ot = tid / TPI;  // phase-B output (degree in tile, column) and beta part
+    static_assert(TPI == 1 || TPI == 2 || TPI == 4, "TPI");
     const int pt = ot >> 4, pc = ot & 15;
     const int pp = pc >> 1;
     const int jlen = n / TPI, jbeg = half * jlen;  // n = 2B is even
@@ -163,7 +164,8 @@ __global__ void __launch_bounds__(NT) dwt_forward_fp64_kernel(Tables tb, const d
             if (j < jlen) a0 = fma(Tr[j], Xc[j * 16], a0);
             acc = a0 + a1;
         }
-        if (TPI == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (TPI >= 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (TPI >= 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (active && half == 0) {
             const int l = lb + pt;
             const double v = rV[l - l0];
@@ -276,7 +278,7 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
 }
 
 template <int NT, int JPT>
-__global__ void __launch_bounds__(NT) dwt_inverse_fp64_kernel(Tables tb, const double *__restrict__ coef,
+__global__ void __launch_bounds__(NT, 1) dwt_inverse_fp64_kernel(Tables tb, const double *__restrict__ coef,
                                                                double2 *__restrict__ S, int flags) {
     extern __shared__ __align__(16) double smem[];
     __shared__ ClusterSmem cs;
@@ -349,11 +351,25 @@ cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s) {
 // memory.  Up to 2B = 256, 256 threads with LT = 16 (68 KB, 3 CTAs per SM);
 // beyond, LT = 8 with two threads per output, which keeps 256 threads per CTA
 // (2B = 512: 104 KB, 2 CTAs per SM; 2B = 1024: 208 KB, 1 CTA of 8 warps).
+// Tile-shape variants (NT, JPT, TPI) per bandwidth range; variant 0 is the
+// default, the others are what the autotuner compares it against.
+int dwt_forward_fp64_variants(int B) { return 2 * B <= 256 ? 3 : 2 * B <= 512 ? 3 : 2; }
+
 cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s, int flags) {
     const int n = 2 * tb.B;
     double *c = reinterpret_cast<double *>(coef);
-    if (n <= 256) return run_forward<256, 1, 1>(tb, S, c, s, flags);
-    if (n <= 512) return run_forward<256, 2, 2>(tb, S, c, s, flags);
+    const int v = tb.fwd_variant;
+    if (n <= 256) {
+        if (v == 1) return run_forward<256, 1, 2>(tb, S, c, s, flags);
+        if (v == 2) return run_forward<128, 2, 1>(tb, S, c, s, flags);
+        return run_forward<256, 1, 1>(tb, S, c, s, flags);
+    }
+    if (n <= 512) {
+        if (v == 1) return run_forward<256, 2, 1>(tb, S, c, s, flags);
+        if (v == 2) return run_forward<512, 1, 4>(tb, S, c, s, flags);
+        return run_forward<256, 2, 2>(tb, S, c, s, flags);
+    }
+    if (v == 1) return run_forward<512, 2, 4>(tb, S, c, s, flags);
     return run_forward<256, 4, 2>(tb, S, c, s, flags);
 }
 
@@ -374,14 +390,21 @@ cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items,
     return cudaGetLastError();
 }
 
+int dwt_inverse_fp64_variants(int B) { return 2 * B <= 256 ? 2 : 2 * B <= 512 ? 3 : 2; }
+
 cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s, int flags) {
     const int n = 2 * tb.B;
     const double *c = reinterpret_cast<const double *>(coef);
-    if (n <= 64) return run_inverse<64, 1>(tb, c, S, s, flags);
-    if (n <= 128) return run_inverse<128, 1>(tb, c, S, s, flags);
-    if (n <= 256) return run_inverse<256, 1>(tb, c, S, s, flags);
-    if (n <= 512) return run_inverse<256, 2>(tb, c, S, s, flags);
-    return run_inverse<256, 4>(tb, c, S, s, flags);
+    const int v = tb.inv_variant;
+    if (n <= 64) return v == 1 ? run_inverse<32, 2>(tb, c, S, s, flags) : run_inverse<64, 1>(tb, c, S, s, flags);
+    if (n <= 128) return v == 1 ? run_inverse<64, 2>(tb, c, S, s, flags) : run_inverse<128, 1>(tb, c, S, s, flags);
+    if (n <= 256) return v == 1 ? run_inverse<128, 2>(tb, c, S, s, flags) : run_inverse<256, 1>(tb, c, S, s, flags);
+    if (n <= 512) {
+        if (v == 1) return run_inverse<512, 1>(tb, c, S, s, flags);
+        if (v == 2) return run_inverse<128, 4>(tb, c, S, s, flags);
+        return run_inverse<256, 2>(tb, c, S, s, flags);
+    }
+    return v == 1 ? run_inverse<512, 2>(tb, c, S, s, flags) : run_inverse<256, 4>(tb, c, S, s, flags);
 }
 
 }  // namespace softgb

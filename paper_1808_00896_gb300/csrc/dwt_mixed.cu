@@ -497,6 +497,17 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols<NC>());
 }
 
+// Self-test of the bounded wait used by the mixed kernels: one CTA polls an
+// mbarrier that nothing arrives on, gives up after `polls` polls and records
+// SOFT_ERR_TIMEOUT's code (2) in the error word, exactly as a DWT kernel would.
+__global__ void bounded_wait_selftest_kernel(uint32_t polls, int *err) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
+    __syncthreads();
+    const bool done = tc::mbar_wait(&mbar, 0u, polls);
+    if (!__syncthreads_and(done) && threadIdx.x == 0 && err) atomicExch(err, 2);
+}
+
 // log w_B(j) for the forward's weighted seeds.
 __global__ void log_weights_kernel(int n, const double *w, double *lw) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -591,8 +602,12 @@ cudaError_t run_inverse_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
 template <int MODE>
 cudaError_t forward_mixed_nb(const MixedBatch &mb, int nb, cudaStream_t s, int flags) {
     switch (nb) {
-        case 1: return 2 * mb.tb.B <= 128 ? run_forward_mixed<MODE, 128, 1, false>(mb, s, flags)
-                                          : run_forward_mixed<MODE, 256, 1, false>(mb, s, flags);
+        case 1: {
+            // variant 0: 128 samples per chunk up to 2B = 128, 256 beyond; variant 1: the other
+            const bool k128 = (2 * mb.tb.B <= 128) != (mb.tb.fwd_variant == 1);
+            return k128 ? run_forward_mixed<MODE, 128, 1, false>(mb, s, flags)
+                        : run_forward_mixed<MODE, 256, 1, false>(mb, s, flags);
+        }
         case 2: return run_forward_mixed<MODE, 128, 2, true>(mb, s, flags);
         case 4: return run_forward_mixed<MODE, 128, 4, true>(mb, s, flags);
         case 8: return run_forward_mixed<MODE, 128, 8, true>(mb, s, flags);
@@ -650,6 +665,11 @@ cudaError_t launch_dwt_forward_mixed(int mode, const Tables &tb, const double *l
 cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *coef, float2 *S, cudaStream_t s,
                                      int flags) {
     return launch_dwt_inverse_mixed_batch(mode, tb, 1, &coef, &S, s, flags);
+}
+
+cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t s) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(polls, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_zero_nyquist32(int B, float2 *S, cudaStream_t s) {

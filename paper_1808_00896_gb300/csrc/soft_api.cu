@@ -53,6 +53,7 @@ struct soft_plan_s {
     // Per-phase timing (soft_plan_enable_timing): 3 events per timed call.
     static constexpr int kMaxRec = 4096;
     bool timing;
+    int fwd_variant, inv_variant;  // tile-shape variants chosen by soft_plan_set_variant
     int nrec;
     int rec_kind[kMaxRec];             // 0 = forward, 1 = inverse
     std::vector<cudaEvent_t> events;   // 3 * kMaxRec, created on first use
@@ -63,6 +64,7 @@ struct soft_plan_s {
         Tables t;
         t.B = B; t.ncl = ncl; t.w = w; t.lw = lw; t.cosb = cosb; t.lcos = lcos; t.lsin = lsin; t.lfact = lfact;
         t.clusters = clusters; t.runoff = runoff; t.err = err;
+        t.fwd_variant = fwd_variant; t.inv_variant = inv_variant;
         return t;
     }
 };
@@ -860,6 +862,26 @@ soft_status soft_inverse_host(soft_plan p, const double *coef_host, double *grid
     e = cudaMemcpyAsync(grid_host, p->stage_grid, sizeof(double2) * grid_elems(p->B), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return cuda_status(e);
+}
+
+soft_status soft_selftest_bounded_wait(soft_plan p, int polls, void *stream) {
+    if (!valid(p) || polls < 1 || polls > (1 << 20)) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    return cuda_status(launch_bounded_wait_selftest((uint32_t)polls, p->err, static_cast<cudaStream_t>(stream)));
+}
+
+int soft_plan_num_variants(soft_plan p, int kernel) {
+    if (!valid(p) || (kernel != 0 && kernel != 1)) return -1;
+    if (p->dtype == SOFT_FP64) return kernel == 0 ? dwt_forward_fp64_variants(p->B) : dwt_inverse_fp64_variants(p->B);
+    return kernel == 0 ? 2 : 1;
+}
+
+soft_status soft_plan_set_variant(soft_plan p, int kernel, int variant) {
+    const int nv = soft_plan_num_variants(p, kernel);
+    if (nv < 0 || variant < 0 || variant >= nv) return SOFT_ERR_INVALID_ARG;
+    if (kernel == 0) p->fwd_variant = variant;
+    else p->inv_variant = variant;
+    return SOFT_OK;
 }
 
 soft_status soft_plan_enable_timing(soft_plan p, int on) {

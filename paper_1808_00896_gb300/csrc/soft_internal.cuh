@@ -28,6 +28,8 @@ struct Tables {
     const int64_t *runoff;    // [(2B-1)^2] start of the l-run of (m,m') in the coefficient array,
                               //   index (m + B - 1) * (2B - 1) + (m' + B - 1)
     int *err;                 // device error word (0 = fine)
+    int fwd_variant = 0;      // tile-shape variant of the DWT kernel (0 = default)
+    int inv_variant = 0;      // tile-shape variant of the iDWT kernel
 };
 
 __host__ __device__ inline int64_t runoff_index(int B, int m, int mp) {
@@ -217,6 +219,8 @@ cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 
 cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s,
                                     int flags = 0);
 cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s);
+int dwt_forward_fp64_variants(int B);
+int dwt_inverse_fp64_variants(int B);
 cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *lsin, double *lfact,
                           cudaStream_t s);
 
@@ -233,6 +237,7 @@ cudaError_t launch_dwt_forward_mixed_batch(int mode, const Tables &tb, int nb, c
 cudaError_t launch_dwt_inverse_mixed_batch(int mode, const Tables &tb, int nb, const double *const *coef,
                                            float2 *const *S, cudaStream_t s, int flags = 0);
 cudaError_t launch_zero_nyquist32(int B, float2 *S, cudaStream_t s);
+cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t s);
 cudaError_t launch_f64_to_f32(const double2 *in, float2 *out, int64_t count, cudaStream_t s);
 cudaError_t launch_transpose32(const float2 *X, float2 *Y, int rows, int64_t cols, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float2 *in, double2 *out, int64_t count, cudaStream_t s);

@@ -188,3 +188,20 @@ def test_argument_errors_on_gpu():
         with pytest.raises(ValueError):
             p.forward(c)
         assert lib.soft_plan_bandwidth(h) == B
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A wait that nothing satisfies gives up after its poll limit, the kernel
+    records a timeout, soft_plan_sync reports it, and the next transform on the
+    same context is still correct."""
+    B = 8
+    with Plan(B, "bf16x3", device=DEV) as p:
+        lib = capi.load()
+        assert lib.soft_selftest_bounded_wait(p.handle, 2000, None) == capi.SOFT_OK
+        assert lib.soft_plan_sync(p.handle) == capi.SOFT_ERR_TIMEOUT
+        assert lib.soft_plan_sync(p.handle) == capi.SOFT_OK  # the error word is cleared once read
+        coef = synth.coefficients(B, "uniform", seed=77)
+        g = p.inverse(torch.from_numpy(coef).to(DEV))
+        p.sync()
+        assert synth.rel_l2(g.cpu().numpy(), oracle.inverse(B, coef)) < 5e-5
+        assert lib.soft_selftest_bounded_wait(p.handle, 0, None) == capi.SOFT_ERR_INVALID_ARG
