@@ -155,6 +155,19 @@ class ClockSampler:
                 "power_w_median": statistics.median(power) if power else None}
 
 
+def busy_warmup(step, warmup: int, sync, min_seconds: float = 0.3) -> None:
+    """Untimed steps: at least `warmup` of them, and more until `min_seconds`
+    have passed, so the clock sampler is attached and the GPU is under load
+    (not idling) when the timed region opens."""
+    t0 = time.perf_counter()
+    i = 0
+    while i < warmup or time.perf_counter() - t0 < min_seconds:
+        step(i)
+        i += 1
+        if i >= warmup:
+            sync()
+
+
 def max_over_ranks(x: float) -> float:
     """Max of a per-rank number over all ranks (identity without a process
     group).  CPU tensor on gloo, the current CUDA device otherwise."""
@@ -264,7 +277,7 @@ def run_corr(args) -> None:
     if world > 1:
         torch.distributed.barrier()
     sampler.start()
-    time.sleep(0.3)
+    busy_warmup(lambda i: batched_correlate(plans, fs, gs, grids, bi, bv), 0, lambda: torch.cuda.synchronize(dev))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
@@ -359,7 +372,7 @@ def run_batched(args) -> None:
     if world > 1:
         torch.distributed.barrier()
     sampler.start()
-    time.sleep(0.3)
+    busy_warmup(lambda i: step(), 0, lambda: torch.cuda.synchronize(dev))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
@@ -448,7 +461,9 @@ def run_ours(args) -> None:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     sampler.start()
-    time.sleep(0.3)  # let the sampler attach before the timed region
+    capi.soft_plan_enable_timing(plan.handle, False)
+    busy_warmup(lambda i: step(i % R), 0, lambda: torch.cuda.synchronize(dev))
+    capi.soft_plan_enable_timing(plan.handle, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for s in range(args.steps):

@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
     extern __shared__ __align__(16) double smem[];
     __shared__ ClusterSmem cs;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x;
-    const int2 rep = tb.clusters[blockIdx.x];
+    const int cidx = blockIdx.x;
+    const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 
     double *X = smem;              // [n][16]
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
 
     load_cluster(tb, m, mp, cs);
     for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
-    scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, rV);
+    cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, rV);
     const int np = cs.np;
 
     // X: S of every partner, beta index mirrored where the partner's column is
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
             x[k] = 0.0; dcur[k] = 0.0; dprev[k] = 0.0;
             if (j < n) {
                 x[k] = tb.cosb[j];
-                dcur[k] = seed_rep(m, mp, (flags & kApplyW) ? lognorm + tb.lw[j] : lognorm, tb.lcos[j], tb.lsin[j]);
+                dcur[k] = cluster_seed(tb, cidx, j, m, mp, lognorm, (flags & kApplyW) != 0);
             }
         }
     }
@@ -211,8 +212,8 @@ __device__ __forceinline__ void idwt_walk(const double *F, const double *rA, con
 // F[B][16] and the recurrence coefficients (3 x B doubles).
 template <int NT, int JPT>
 __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__restrict__ coef,
-                                             double2 *__restrict__ S, int flags, int m, int mp, double *smem,
-                                             ClusterSmem &cs) {
+                                             double2 *__restrict__ S, int flags, int cidx, int m, int mp,
+                                             double *smem, ClusterSmem &cs) {
     const int B = tb.B, n = 2 * B, tid = threadIdx.x;
     const int l0 = m, L = B - l0;
 
@@ -223,7 +224,7 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
     double *rSig = rBc + B;
 
     load_cluster(tb, m, mp, cs);
-    scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
+    cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
     const int np = cs.np;
     for (int e = tid; e < L * 8; e += NT) {
         const int t = e >> 3, p = e & 7;
@@ -249,7 +250,7 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
             x[k] = 0.0; dcur[k] = 0.0; dprev[k] = 0.0;
             if (j < n) {
                 x[k] = tb.cosb[j];
-                dcur[k] = seed_rep(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
+                dcur[k] = cluster_seed(tb, cidx, j, m, mp, lognorm, false);
             }
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc[k][c] = 0.0;
@@ -283,7 +284,28 @@ __global__ void __launch_bounds__(NT, 1) dwt_inverse_fp64_kernel(Tables tb, cons
     extern __shared__ __align__(16) double smem[];
     __shared__ ClusterSmem cs;
     const int2 rep = tb.clusters[blockIdx.x];
-    idwt_cluster<NT, JPT>(tb, coef, S, flags, rep.x, rep.y, smem, cs);
+    idwt_cluster<NT, JPT>(tb, coef, S, flags, blockIdx.x, rep.x, rep.y, smem, cs);
+}
+
+// One CTA per cluster: the rescaled recurrence coefficients and the seeds of
+// the cluster, written once per plan for every later DWT launch to load.
+__global__ void __launch_bounds__(256) cluster_tables_kernel(Tables tb, double *__restrict__ seedtab,
+                                                             double *__restrict__ rectab) {
+    extern __shared__ __align__(16) double smem[];
+    const int B = tb.B, n = 2 * B, c = blockIdx.x;
+    const int2 rep = tb.clusters[c];
+    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+    double *rA = smem, *rAc = rA + B, *rBc = rAc + B, *rSig = rBc + B;
+    scaled_recurrence_tables<256>(l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
+    double *dst = rectab + (size_t)c * B * 3;
+    for (int t = threadIdx.x; t < L; t += 256) {
+        dst[3 * t] = rA[t];
+        dst[3 * t + 1] = rAc[t];
+        dst[3 * t + 2] = rSig[t];
+    }
+    const double lognorm = seed_lognorm(tb, m, mp);
+    for (int j = threadIdx.x; j < n; j += 256)
+        seedtab[(size_t)c * n + j] = seed_rep(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
 }
 
 // Persistent inverse DWT over a batch of FP64 transforms of bandwidth <= 128:
@@ -303,7 +325,7 @@ __global__ void __launch_bounds__(256) idwt_fp64_persistent_kernel(const BatchXf
         const int2 w = items[it];
         const BatchXform &X = xf[w.x];
         const int2 rep = X.tb.clusters[w.y];
-        idwt_cluster<256, 1>(X.tb, X.coef, X.S, X.flags, rep.x, rep.y, smem, cs);
+        idwt_cluster<256, 1>(X.tb, X.coef, X.S, X.flags, w.y, rep.x, rep.y, smem, cs);
         __syncthreads();  // smem and `item` are reused by the next item
     }
 }
@@ -336,6 +358,15 @@ cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *
                           cudaStream_t s) {
     const int n = 2 * B;
     tables_kernel<<<(n + 1 + 127) / 128, 128, 0, s>>>(B, w, cosb, lcos, lsin, lfact);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_tables(const Tables &tb, double *seedtab, double *rectab, cudaStream_t s) {
+    Tables t = tb;
+    t.seedtab = nullptr;
+    t.rectab = nullptr;
+    const size_t bytes = sizeof(double) * 4 * (size_t)tb.B;
+    cluster_tables_kernel<<<tb.ncl, 256, bytes, s>>>(t, seedtab, rectab);
     return cudaGetLastError();
 }
 

@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
     __shared__ __align__(8) uint64_t mbar;
     const Tables &tb = mb.tb;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int2 rep = tb.clusters[blockIdx.x];
+    const int cidx = blockIdx.x;
+    const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 
     unsigned char *A = smem;                    // A planes (T tile), then B planes (X chunk)
@@ -213,12 +214,18 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
 
     load_cluster(tb, m, mp, cs);
     for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
-    scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, rV);
+    cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, rV);
     {
         const double lognorm = seed_lognorm(tb, m, mp);
         for (int j = tid; j < n; j += NT) {
-            // w_B(j) d(l0,m,m';beta_j): the weight enters through the seed's logarithm
-            dcur[j] = seed_rep_mixed(m, mp, (flags & kApplyW) ? lognorm + tb.lw[j] : lognorm, tb.lcos[j], tb.lsin[j]);
+            // w_B(j) d(l0,m,m';beta_j): from the plan's seed table, or exp2f of the log-seed
+            if (tb.seedtab) {
+                const double sd = tb.seedtab[(size_t)cidx * n + j];
+                dcur[j] = (flags & kApplyW) ? sd * tb.w[j] : sd;
+            } else {
+                dcur[j] = seed_rep_mixed(m, mp, (flags & kApplyW) ? lognorm + tb.lw[j] : lognorm, tb.lcos[j],
+                                         tb.lsin[j]);
+            }
             dprev[j] = 0.0;
         }
     }
@@ -380,7 +387,8 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     __shared__ __align__(8) uint64_t mbar;
     const Tables &tb = mb.tb;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5;
-    const int2 rep = tb.clusters[blockIdx.x];
+    const int cidx = blockIdx.x;
+    const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 
     unsigned char *A = smem;
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     float *fsc = reinterpret_cast<float *>(rSig + B);  // [B] sig_l (V_l) in FP32, the B operand's scale
 
     load_cluster(tb, m, mp, cs);
-    scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
+    cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
     for (int t = tid; t < L; t += NT)
         fsc[t] = tc::f64_to_f32_rn(rSig[t] * ((flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0));
     if (warp == 0) tc::tmem_alloc(&tmem_slot, tmem_cols<NC>());
@@ -409,7 +417,7 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
         double x = 0.0, dc = 0.0, dp = 0.0;
         if (active) {
             x = tb.cosb[j];
-            dc = seed_rep_mixed(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
+            dc = tb.seedtab ? tb.seedtab[(size_t)cidx * n + j] : seed_rep_mixed(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
         }
         for (int lb = l0, c = 0; lb < B && ok; lb += kChunk, ++c) {
             const int cnt = min(kChunk, B - lb);

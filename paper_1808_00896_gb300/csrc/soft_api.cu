@@ -41,6 +41,7 @@ struct soft_plan_s {
     cufftHandle fft;
     bool fft_made;
     double *lw;  // log w_B(j)
+    double *seedtab, *rectab;  // per-cluster seeds and recurrence coefficients, built at creation
     // Mixed-precision plans: FP32 grid staging and S in layout [m][m'][j], FP32 cuFFT plans.
     float2 *g32, *S32;
     cufftHandle fft32f, fft32i;
@@ -65,6 +66,7 @@ struct soft_plan_s {
         t.B = B; t.ncl = ncl; t.w = w; t.lw = lw; t.cosb = cosb; t.lcos = lcos; t.lsin = lsin; t.lfact = lfact;
         t.clusters = clusters; t.runoff = runoff; t.err = err;
         t.fwd_variant = fwd_variant; t.inv_variant = inv_variant;
+        t.seedtab = seedtab; t.rectab = rectab;
         return t;
     }
 };
@@ -191,6 +193,7 @@ void free_plan(soft_plan_s *p) {
     if (p->fft32f_made) cufftDestroy(p->fft32f);
     if (p->fft32i_made) cufftDestroy(p->fft32i);
     cudaFree(p->lw); cudaFree(p->g32); cudaFree(p->S32);
+    cudaFree(p->seedtab); cudaFree(p->rectab);
     cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
     cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
     cudaFree(p->stage_grid); cudaFree(p->stage_coef);
@@ -656,6 +659,8 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     alloc((void **)&p->amax_v, sizeof(double) * argmax_parts());
     alloc((void **)&p->amax_i, sizeof(int64_t) * argmax_parts());
     alloc((void **)&p->lw, sizeof(double) * n);
+    alloc((void **)&p->seedtab, sizeof(double) * (size_t)n * cl.size());
+    alloc((void **)&p->rectab, sizeof(double) * 3 * (size_t)B * cl.size());
     if (dtype == SOFT_FP64) {
         alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
     } else {
@@ -669,6 +674,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
     if (e == cudaSuccess) e = launch_tables(B, p->w, p->cosb, p->lcos, p->lsin, p->lfact, 0);
     if (e == cudaSuccess) e = launch_log_weights(B, p->w, p->lw, 0);
+    if (e == cudaSuccess) e = launch_cluster_tables(p->tables(), p->seedtab, p->rectab, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
 

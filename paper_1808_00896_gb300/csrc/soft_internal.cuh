@@ -28,6 +28,9 @@ struct Tables {
     const int64_t *runoff;    // [(2B-1)^2] start of the l-run of (m,m') in the coefficient array,
                               //   index (m + B - 1) * (2B - 1) + (m' + B - 1)
     int *err;                 // device error word (0 = fine)
+    // Per-cluster tables built once per plan (null: computed on the fly in each CTA).
+    const double *seedtab = nullptr;  // [ncl][2B]  d(l0,m,m';beta_j) of each cluster, unweighted
+    const double *rectab = nullptr;   // [ncl][B][3] (A', Ac', sig) of the rescaled recurrence, l = l0 + t
     int fwd_variant = 0;      // tile-shape variant of the DWT kernel (0 = default)
     int inv_variant = 0;      // tile-shape variant of the iDWT kernel
 };
@@ -143,6 +146,27 @@ __device__ inline void scaled_recurrence_tables(int l0, int L, int m, int mp, do
     __syncthreads();
 }
 
+// Per-cluster recurrence tables in shared memory for cluster cidx: copied from
+// the plan's precomputed table when there is one, computed otherwise.  Same
+// contract as scaled_recurrence_tables (rBc is scratch; ends with a barrier).
+template <int NT>
+__device__ inline void cluster_recurrence(const Tables &tb, int cidx, int l0, int L, int m, int mp, double *rA,
+                                          double *rAc, double *rBc, double *rSig, double *rV) {
+    if (tb.rectab) {
+        const double *src = tb.rectab + (size_t)cidx * tb.B * 3;
+        for (int t = threadIdx.x; t < L; t += NT) {
+            rA[t] = src[3 * t];
+            rAc[t] = src[3 * t + 1];
+            const double sg = src[3 * t + 2];
+            rSig[t] = sg;
+            if (rV) rV[t] *= sg;
+        }
+        __syncthreads();
+    } else {
+        scaled_recurrence_tables<NT>(l0, L, m, mp, rA, rAc, rBc, rSig, rV);
+    }
+}
+
 // Seed d(l0, m, m'; beta_j), l0 = max(|m|,|m'|), for a representative m >= m' >= 0
 // (the "+" case of the paper's first initial condition):
 //   d(m, m, m') = sqrt((2m)! / ((m+m')!(m-m')!)) cos(b/2)^(m+m') sin(b/2)^(m-m'),
@@ -157,6 +181,16 @@ __device__ inline double seed_rep(int m, int mp, double lognorm, double lc, doub
 
 __device__ inline double seed_lognorm(const Tables &tb, int m, int mp) {
     return 0.5 * (tb.lfact[2 * m] - tb.lfact[m + mp] - tb.lfact[m - mp]);
+}
+
+// Seed of cluster cidx at beta_j, times w_B(j) when `weighted` (the forward's
+// T W): from the plan's table, or exp of the log-domain seed.
+__device__ inline double cluster_seed(const Tables &tb, int cidx, int j, int m, int mp, double lognorm, bool weighted) {
+    if (tb.seedtab) {
+        const double sd = tb.seedtab[(size_t)cidx * 2 * tb.B + j];
+        return weighted ? sd * tb.w[j] : sd;
+    }
+    return seed_rep(m, mp, weighted ? lognorm + tb.lw[j] : lognorm, tb.lcos[j], tb.lsin[j]);
 }
 
 // Per-CTA cluster prologue: the partner table and the partners' run offsets,
@@ -219,6 +253,8 @@ cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 
 cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s,
                                     int flags = 0);
 cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s);
+// Builds tb's per-cluster seed and recurrence tables into seedtab / rectab.
+cudaError_t launch_cluster_tables(const Tables &tb, double *seedtab, double *rectab, cudaStream_t s);
 int dwt_forward_fp64_variants(int B);
 int dwt_inverse_fp64_variants(int B);
 cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *lsin, double *lfact,
