@@ -47,6 +47,10 @@ for _B in (64, 128, 256, 512):
         WORKLOADS[f"b{_B}_{_m}"] = (_B, _m, "gauss_decay",
                                     f"mixed SOFT forward+inverse, B={_B}, {_d} contraction on tcgen05 tensor cores, "
                                     f"FP64 Wigner-d recurrence, FP32 2-D FFTs; complex128 in/out")
+    WORKLOADS[f"b{_B}_fp64tc"] = (_B, "fp64_tc", "gauss_decay",
+                                  f"FP64-accurate SOFT forward+inverse, B={_B}: FP64 Wigner-d recurrence, S and "
+                                  f"2-D FFTs, contraction on tcgen05 tensor cores as exact base-128 BF16 digit "
+                                  f"products (7 digits per operand)")
 # Batches of same-B transforms through soft_batched_forward / soft_batched_inverse:
 # mixed plans share one DWT launch per group of 8 (N = 16 x 8 tensor-core columns).
 BATCHED = {}
@@ -509,7 +513,7 @@ def run_ours(args) -> None:
     fl = dwt_flops(B)
     fwd_ms = phase_ms[1] / max(1, phase_cnt[1])
     inv_ms = phase_ms[2] / max(1, phase_cnt[2])
-    kname = "fp64" if dtype == "fp64" else "mixed"
+    kname = {"fp64": "fp64", "fp64_tc": "tc"}.get(dtype, "mixed")
     dom, dom_ms = (f"dwt_forward_{kname}_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else \
         (f"dwt_inverse_{kname}_kernel", inv_ms)
     peak_gflops = FP64_FLOPS_PER_SM_CLK * N_SM * SM_MAX_MHZ * 1e6 / 1e9
@@ -527,10 +531,12 @@ def run_ours(args) -> None:
                                         "dwt_forward": fwd_ms, "dwt_inverse": inv_ms,
                                         "fft_inverse": phase_ms[3] / max(1, phase_cnt[3])}}
     if dtype != "fp64":
-        mult = 3 if dtype == "bf16x3" else 1
+        # tensor-core products per real multiply-add of the contraction: 3 split-BF16
+        # pairs, 1 TF32, or the 28 digit pairs (levels 0..6) of the FP64-accurate mode
+        mult = {"bf16x3": 3, "fp64_tc": 28}.get(dtype, 1)
         roofline["tensor_tflops_achieved"] = mult * fl["contraction"] / (dom_ms * 1e-3) / 1e12
-        roofline["note"] = ("mixed mode: frac is the FP64 Wigner-d recurrence (2 FMA per T entry) against the "
-                            "FP64 pipe; tensor_tflops_achieved counts the contraction's tensor-core flops")
+        roofline["note"] = ("tensor-core contraction: frac is the FP64 Wigner-d recurrence (2 FMA per T entry) "
+                            "against the FP64 pipe; tensor_tflops_achieved counts the contraction's tensor-core flops")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

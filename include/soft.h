@@ -55,7 +55,10 @@ typedef enum {
 typedef enum {
     SOFT_FP64 = 0,         /* every step in FP64 */
     SOFT_MIXED_BF16X3 = 1, /* contraction on tcgen05 tensor cores, split BF16 x3 (rel-L2 <= 5e-5) */
-    SOFT_MIXED_TF32 = 2    /* contraction on tcgen05 tensor cores, TF32 (rel-L2 <= 2e-3) */
+    SOFT_MIXED_TF32 = 2,   /* contraction on tcgen05 tensor cores, TF32 (rel-L2 <= 2e-3) */
+    SOFT_FP64_TC = 3       /* FP64 recurrence, S and FFTs; contraction on tcgen05 tensor cores as exact
+                            * fixed-point BF16 digit products (7 base-128 digits per operand, FP32 TMEM
+                            * sums exact for the leading levels), FP64 accuracy (rel-L2 <= 1e-10) */
 } soft_dtype;
 
 /* Largest bandwidth B the kernels accept. */
@@ -168,12 +171,13 @@ soft_status soft_argmax_real(const double *data, int64_t count, int64_t *index_o
 int soft_argmax_scratch_doubles(void);
 
 /* The DWT step alone (Sec. 2.4, matrix form V_B T_B W_B): S (device, layout
- * above) -> coef.  S is read only.  FP64 plans only (SOFT_ERR_UNSUPPORTED for
- * mixed plans, whose S is FP32 in another layout). */
+ * above) -> coef.  S is read only.  SOFT_FP64 and SOFT_FP64_TC plans only
+ * (SOFT_ERR_UNSUPPORTED for mixed plans, whose S is FP32 in another layout). */
 soft_status soft_dwt_forward(soft_plan p, const double *S, double *coef, void *stream);
 
 /* The iDWT step alone (Sec. 2.4, T_B^T): coef -> S (device, layout above,
- * every entry written, the -B rows/columns set to 0).  FP64 plans only. */
+ * every entry written, the -B rows/columns set to 0).  SOFT_FP64 and
+ * SOFT_FP64_TC plans only. */
 soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *stream);
 
 /* The DWT step alone, without a plan and without allocating any memory

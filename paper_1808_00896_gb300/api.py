@@ -12,7 +12,8 @@ import torch
 
 from . import capi
 
-_DTYPES = {"fp64": capi.SOFT_FP64, "bf16x3": capi.SOFT_MIXED_BF16X3, "tf32": capi.SOFT_MIXED_TF32}
+_DTYPES = {"fp64": capi.SOFT_FP64, "bf16x3": capi.SOFT_MIXED_BF16X3, "tf32": capi.SOFT_MIXED_TF32,
+           "fp64_tc": capi.SOFT_FP64_TC}
 
 
 def num_coeffs(B: int) -> int:

@@ -22,6 +22,7 @@ SOFT_ERR_DEVICE = 6
 SOFT_FP64 = 0
 SOFT_MIXED_BF16X3 = 1
 SOFT_MIXED_TF32 = 2
+SOFT_FP64_TC = 3
 
 # name -> (restype, argtypes); mirrors include/soft.h
 _vp, _i, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64

@@ -1,0 +1,758 @@
+// dwt_fp64tc.cu -- FP64-accurate DWT / iDWT with the contraction on the
+// tcgen05 tensor cores (mode SOFT_FP64_TC).
+//
+// Same mathematics as dwt_fp64.cu (Sec. 2.4: f = V_B T_B W_B S per order pair,
+// S = T_B^T f), the same FP64 Wigner-d recurrence (Eq. (Wigner_d_recurrence),
+// rescaled, from the plan's per-cluster tables), FP64 S and FP64 FFTs.  Only
+// the contraction moves, from 16 FP64 FMAs per Wigner-d entry to the tensor
+// cores, by the error-free splitting idea of Ozaki, Ogita, Oishi and Rump
+// ("Error-free transformations of matrix multiplication by using fast routines
+// of matrix multiplication and its applications", Numer. Algorithms 59, 2012):
+//
+//   * every operand entry is read as a fixed-point number against a
+//     power-of-two scale and cut into kDig = 7 balanced base-128 digits
+//     (|q| <= 64), each an exact BF16:  v 2^alpha ~= sum_i q_i 2^(-6-7i),
+//     error <= 2^-49 of the scale;
+//   * digit products are integers of magnitude <= 2^12, so an FP32 TMEM
+//     accumulator summing all digit pairs (i, k) of one level i + k over a
+//     contraction of K <= 1024 terms stays exact for levels 0..3
+//     ((level + 1) 2^22 <= 2^24); levels 4..6 carry a relative weight
+//     <= 2^-28, where FP32 rounding is immaterial, and pairs of level >= 7
+//     (weight <= 2^-49) are dropped;
+//   * per K step, the MMA of A digit i runs against B digits 0..6-i stacked as
+//     the N = 16 (7 - i) rows of one operand and accumulates into TMEM columns
+//     16 i .. 16 i + N - 1, so level k of output column c always lands in
+//     column 16 k + c: 7 MMAs per K step, 112 accumulator columns;
+//   * the epilogue recombines the levels -- the four exact leading ones in
+//     64-bit integers, so that no FP32 rounding touches them -- and builds the
+//     FP64 result by integer operations with the scales folded into its
+//     exponent.
+//
+// Scales.  The rescaled recurrence yields e(t) = d(l0+t)/sig_t.  With
+// sig_t = 2^E_t mu_t, mu_t in [1, 2), e(t) 2^E_t = d/mu_t is in [-1, 1]
+// because |d| <= 1.  The forward also carries w_B(j) (folded into the seeds),
+// bounded by 2^-ew.  Data columns (S in the forward, the sign-, V- and
+// mu-folded coefficients in the inverse) are scaled by 2^-F_c, F_c the
+// exponent just above the column's largest magnitude over the contraction.
+//
+// The forward contracts K = 2B <= 1024 beta samples and the inverse K = L <= B
+// degrees, both within the exactness bound for B <= 512.
+#include "soft.h"
+#include "soft_internal.cuh"
+#include "tcgen05.cuh"
+
+#include <algorithm>
+
+namespace softgb {
+namespace {
+
+constexpr int kDig = 7;              // digits per operand entry (and levels kept)
+constexpr int kCols = 16;            // 8 partners x (re, im)
+constexpr int kNB = kDig * kCols;    // 112 B-operand rows: digit k of column c at row 16 k + c
+constexpr uint32_t kTmemCols = 128;  // >= 112 accumulator columns
+constexpr uint32_t kWaitPolls = 1u << 22;
+
+__device__ __forceinline__ int mod_n(int a, int n) { return a < 0 ? a + n : a; }
+
+// FP32 bit pattern of a small integer (|q| < 2^22), exactly; its upper half is
+// the BF16 of q when |q| <= 256.  One integer add and one FP32 add.
+__device__ __forceinline__ uint32_t small_int_bits(int q) {
+    return __float_as_uint(__int_as_float(0x4B400000 + q) - 12582912.0f);
+}
+
+// Balanced base-128 digits of N = round(v 2^(alpha + 48)) for |v 2^alpha| <= 1:
+// N = sum_i q_i 128^(6 - i), so v 2^alpha ~= sum_i q_i 2^(-6-7i), |q_i| <= 64.
+// Returned as FP32 bit patterns (BF16 in the upper halves).  Integer operations
+// only; magnitudes below 2^-49 of the scale give 0.
+__device__ __forceinline__ void digits7(double v, int alpha, uint32_t (&q)[kDig]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const uint32_t bh = (uint32_t)(b >> 32);
+    const int e = (int)((bh >> 20) & 0x7FF);
+    // floor(|v| 2^(alpha + 49)) = significand >> s, s >= 3 within the bound; zero
+    // (and subnormal) inputs shift everything out.
+    const int s = e == 0 ? 63 : min(max(1026 - alpha - e, 0), 63);
+    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    long long N = (long long)(((M >> s) + 1) >> 1);  // round half away from zero
+    if (bh >> 31) N = -N;
+    // N = hi 2^21 + lo, lo in [0, 2^21): three digits from lo, the carry into hi,
+    // then three more digits and the leading one from hi, all in 32-bit arithmetic.
+    int lo = (int)(N & 0x1FFFFF);
+    int hi = (int)(N >> 21);
+#pragma unroll
+    for (int i = kDig - 1; i >= 4; --i) {
+        const int t = lo + 64;
+        q[i] = small_int_bits((t & 127) - 64);
+        lo = t >> 7;
+    }
+    hi += lo;
+#pragma unroll
+    for (int i = 3; i >= 1; --i) {
+        const int t = hi + 64;
+        q[i] = small_int_bits((t & 127) - 64);
+        hi = t >> 7;
+    }
+    q[0] = small_int_bits(hi);
+}
+
+// Unbiased exponent of a positive normal double.
+__device__ __forceinline__ int exponent_of(double v) {
+    return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF) - 1023;
+}
+
+// Magnitude bits of |v| (orders like |v| for finite values).
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Column exponent F with |x| < 2^F for every |x| <= the double whose magnitude bits are mb.
+__device__ __forceinline__ int column_exponent(unsigned long long mb) {
+    return mb == 0 ? 0 : (int)(mb >> 52) - 1023 + 1;
+}
+
+// v 2^k by an exponent-field add (v normal or 0; results below the normal range flush to 0).
+__device__ __forceinline__ double ldexp_bits(double v, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0 || e == 0x7FF) return v;
+    const int e2 = e + k;
+    if (e2 <= 0) return __longlong_as_double((long long)(b & (1ull << 63)));
+    if (e2 >= 0x7FF) return __longlong_as_double((long long)((b & (1ull << 63)) | (0x7FFull << 52)));
+    return __longlong_as_double((long long)((b & ~(0x7FFull << 52)) | ((unsigned long long)e2 << 52)));
+}
+
+// FP32 pattern of an exact integer |v| <= 2^24 -> int (integer operations).
+__device__ __forceinline__ int exact_f32_int(uint32_t b) {
+    const int e = (int)((b >> 23) & 0xFF);
+    const uint32_t m2 = ((b & 0x7FFFFFu) | 0x800000u) << 1;
+    const int v = (int)(m2 >> min(151 - e, 31));
+    return (b >> 31) ? -v : v;
+}
+
+// X 2^k as a double for |X| < 2^63 (integer operations; low bits beyond 53
+// truncated, results below the normal range flush to 0).
+__device__ __forceinline__ double int64_ldexp(long long X, int k) {
+    if (X == 0) return 0.0;
+    const unsigned long long s = (unsigned long long)X & (1ull << 63);
+    const unsigned long long a = X < 0 ? 0ull - (unsigned long long)X : (unsigned long long)X;
+    const int lz = __clzll((long long)a);
+    const int e = 1023 + 63 - lz + k;  // biased exponent of the leading bit
+    if (e <= 0) return __longlong_as_double((long long)s);
+    const unsigned long long mant = (lz >= 11 ? a << (lz - 11) : a >> (11 - lz)) & 0xFFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(s | ((unsigned long long)e << 52) | mant));
+}
+
+// Epilogue for one warp's 32 TMEM lanes: the 16 outputs of this lane's row,
+//   out_c = 2^(F_c - 12) T_c,  T = L0 + 2^-7 L1 + 2^-14 L2 + 2^-21 L3 + 2^-28 R',
+// R' = L4 + 2^-7 L5 + 2^-14 L6 in FP32 (weight <= 2^-28: its rounding is
+// immaterial).  Levels 0..3 are exact integers and are combined exactly in
+// 64-bit integers, X = 2^39 T:
+//   X = (((L0 128 + L1) 128 + L2) 128 + L3) 2^18 + round(2^11 R'),
+// so most of the result's bits -- which sit in levels 1..3 whenever entries
+// are small against their scales -- never pass through FP32 rounding.  No
+// FP64 arithmetic.  Warp-collective (tcgen05.ld).
+__device__ __forceinline__ void epilogue_levels(uint32_t tbase, const int *colexp, double (&out)[kCols]) {
+    uint32_t d[16];
+    float rp[16];
+    tc::tmem_ld16(tbase + kCols * 6, d);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) rp[c] = __uint_as_float(d[c]);
+#pragma unroll 1
+    for (int k = 5; k >= 4; --k) {
+        tc::tmem_ld16(tbase + kCols * k, d);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) rp[c] = fmaf(rp[c], 0x1p-7f, __uint_as_float(d[c]));
+    }
+    int y[16];
+    tc::tmem_ld16(tbase, d);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) y[c] = exact_f32_int(d[c]);
+    tc::tmem_ld16(tbase + kCols, d);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) y[c] = y[c] * 128 + exact_f32_int(d[c]);  // <= 2^30
+    long long X[16];
+    tc::tmem_ld16(tbase + 2 * kCols, d);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) X[c] = (long long)y[c] * 128 + exact_f32_int(d[c]);
+    tc::tmem_ld16(tbase + 3 * kCols, d);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        X[c] = X[c] * 128 + exact_f32_int(d[c]);
+        X[c] = X[c] * (1ll << 18) + __float2ll_rn(rp[c] * 0x1p11f);
+        out[c] = int64_ldexp(X[c], colexp[c] - 12 - 39);
+    }
+}
+
+// Store the digits of 4 consecutive K entries (k0 a multiple of 4) of operand
+// row `row` into the 7 digit planes: 8 bytes per plane at plane0 + i * plane
+// (+ the row and K-group offsets of the no-swizzle K-major layout).
+__device__ __forceinline__ void put_digits4(unsigned char *plane0, int plane, int lbo, int row, int k0,
+                                            const double (&v)[4], const int (&alpha)[4]) {
+    uint32_t d[4][kDig];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) digits7(v[u], alpha[u], d[u]);
+    unsigned char *dst = plane0 + (k0 / 8) * lbo + 16 * row + 2 * (k0 % 8);
+#pragma unroll
+    for (int i = 0; i < kDig; ++i) {
+        uint2 w;
+        w.x = __byte_perm(d[0][i], d[1][i], 0x7632);
+        w.y = __byte_perm(d[2][i], d[3][i], 0x7632);
+        *reinterpret_cast<uint2 *>(dst + i * plane) = w;
+    }
+}
+
+// One K chunk of MMAs (thread 0): for each K step of 16, A digit i (plane i)
+// against B digits 0..6-i into TMEM columns 16 i ..; committed to mbar.
+template <int M>
+__device__ __forceinline__ void issue_levels(uint32_t tmem, const unsigned char *A, int a_plane, uint32_t a_lbo,
+                                             const unsigned char *Bop, uint32_t b_lbo, bool first, int ksteps,
+                                             uint64_t *mbar) {
+    tc::fence_after_sync();
+    const uint32_t abase = tc::smem_u32(A), bbase = tc::smem_u32(Bop);
+    for (int s = 0; s < ksteps; ++s) {
+        const uint64_t bd = tc::smem_desc(bbase + s * 2 * b_lbo, b_lbo, 128);
+#pragma unroll
+        for (int i = 0; i < kDig; ++i) {
+            const uint32_t idesc = tc::instr_desc(1, M, kCols * (kDig - i));
+            const uint64_t ad = tc::smem_desc(abase + i * a_plane + s * 2 * a_lbo, a_lbo, 128);
+            tc::mma_bf16(tmem + kCols * i, ad, bd, idesc, (first && s == 0 && i == 0) ? 0u : 1u);
+        }
+    }
+    tc::mma_commit(mbar);
+}
+
+// Largest magnitude (as bits) per column over the threads that share `tid & 7`:
+// every thread holds the maxima of columns 2 (tid & 7) and 2 (tid & 7) + 1.
+// Leaves F_c in colexp[16].  All NT threads call it.
+template <int NT>
+__device__ __forceinline__ void reduce_column_exponents(unsigned long long m0, unsigned long long m1,
+                                                        unsigned long long (*part)[kCols], int *colexp) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int off = 8; off < 32; off <<= 1) {
+        m0 = max(m0, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)m0, off));
+        m1 = max(m1, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)m1, off));
+    }
+    if (lane < 8) {
+        part[warp][2 * lane] = m0;
+        part[warp][2 * lane + 1] = m1;
+    }
+    __syncthreads();
+    if (tid < kCols) {
+        unsigned long long mb = 0;
+        for (int w = 0; w < NT / 32; ++w) mb = max(mb, part[w][tid]);
+        colexp[tid] = column_exponent(mb);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Both kernels split the CTA into two warp-specialised groups:
+//   producers  (128 threads, warps 0-3) run the FP64 recurrence -- two FMAs
+//              per Wigner-d entry and nothing else -- and write the raw FP64
+//              values into a double-buffered staging area, 8 rows (forward)
+//              or 8 degrees (inverse) per buffer;
+//   converters (256 threads, warps 4-11) cut staged values and the data
+//              operand into digits (4 values per thread and task), issue the
+//              chunk's MMAs from one thread, and run the epilogue (warps 4-7,
+//              one per TMEM lane quarter).  Two converter warps per scheduler
+//              hide the latency of the integer digit chains.
+// So the FP64 pipe (producers) and the integer pipes (converters) work in
+// parallel instead of in one warp's instruction stream.  Hand-off through
+// mbarriers (full: 128 producer arrivals, empty: 256 converter arrivals);
+// every wait is bounded, and each group takes its verdict with an AND-reducing
+// named barrier so that a timeout makes the whole group leave together.
+// ---------------------------------------------------------------------------
+constexpr int kProd = 128;    // producer threads (warps 0-3)
+constexpr int kConv = 256;    // converter threads (warps 4-11)
+constexpr int kThreads = kProd + kConv;
+constexpr int kBarConv = 1;   // named barrier of the converters
+constexpr int kBarProd = 2;   // named barrier of the producers
+
+constexpr int kStages = 4;    // staging ring depth (groups of 8 rows / degrees)
+
+struct PipeBars {
+    uint64_t full[kStages], empty[kStages], mma;
+};
+
+__device__ __forceinline__ void init_pipe(PipeBars &pb) {
+#pragma unroll
+    for (int b = 0; b < kStages; ++b) {
+        tc::mbar_init(&pb.full[b], kProd);
+        tc::mbar_init(&pb.empty[b], kConv);
+    }
+    tc::mbar_init(&pb.mma, 1);
+}
+
+// Producer: wait until staging buffer gi % kStages is free (its previous group consumed).
+__device__ __forceinline__ bool producer_acquire(PipeBars &pb, uint32_t gi) {
+    const bool done = tc::mbar_wait(&pb.empty[gi % kStages], ((gi / kStages) & 1) ^ 1u, kWaitPolls);
+    return tc::group_and(kBarProd, kProd, done);
+}
+
+// Converter: wait until staging buffer gi % kStages holds group gi.
+__device__ __forceinline__ bool converter_acquire(PipeBars &pb, uint32_t gi) {
+    const bool done = tc::mbar_wait(&pb.full[gi % kStages], (gi / kStages) & 1, kWaitPolls);
+    return tc::group_and(kBarConv, kConv, done);
+}
+
+// Converter: wait for the chunk MMAs committed last.
+__device__ __forceinline__ bool converter_wait_mma(PipeBars &pb, uint32_t &mph) {
+    const bool done = tc::mbar_wait(&pb.mma, mph, kWaitPolls);
+    mph ^= 1u;
+    return tc::group_and(kBarConv, kConv, done);
+}
+
+// ---------------------------------------------------------------------------
+// Forward DWT.  One CTA per cluster; tiles of TM = 64 degrees (M), K chunks of
+// KC = 128 beta samples, one producer per sample; the producers keep the
+// recurrence state of their (up to 8) samples in registers.
+// Converter schedule per chunk c: B operand of c into buffer c % 2 (while the
+// MMAs of c - 1 run), wait for those MMAs (then the epilogue when c - 1 closed
+// a tile), A digits of the staged groups, MMAs of c.
+//   dynamic smem: A planes [7] | B operand [2] | staging [kStages][8 rows][KC] |
+//                 rA, rAc, rV [B] | alpha [B] (int)
+//   (the table-building scratch rBc, rSig lives in the operand area)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, const double2 *__restrict__ S,
+                                                                     double *__restrict__ coef, int flags) {
+    constexpr int NT = kThreads, KC = kProd, TM = 64, G = 8, NG = TM / G, MAXC = 2 * kMaxB / KC;
+    constexpr int A_LBO = TM * 16 + 16, A_PLANE = (KC / 8) * A_LBO;
+    constexpr int B_LBO = kNB * 16 + 16, B_BYTES = (KC / 8) * B_LBO;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ ClusterSmem cs;
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) PipeBars pb;
+    __shared__ unsigned long long part[NT / 32][kCols];
+    __shared__ int colexp[kCols];
+    __shared__ int wshift;
+    const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int cidx = blockIdx.x;
+    const int2 rep = tb.clusters[cidx];
+    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+
+    unsigned char *A = smem;
+    unsigned char *X = smem + kDig * A_PLANE;  // [2][B_BYTES]
+    double *stage = reinterpret_cast<double *>(X + 2 * B_BYTES);  // [kStages][G][KC]
+    double *rA = stage + kStages * G * KC, *rAc = rA + B, *rV = rAc + B;
+    int *ralpha = reinterpret_cast<int *>(rV + B);
+    double *rBc = reinterpret_cast<double *>(smem), *rSig = rBc + B;
+
+    load_cluster(tb, m, mp, cs);
+    for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
+    if (warp == 0) {
+        // 2^ew max_j w_B(j) < 1 for the weighted seeds
+        unsigned long long mb = 0;
+        if (flags & kApplyW)
+            for (int j = lane; j < n; j += 32) mb = max(mb, abs_bits(tb.w[j]));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb, off));
+        if (lane == 0) wshift = (flags & kApplyW) ? -column_exponent(mb) : 0;
+    }
+    cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, rV);  // rV *= sig; ends with a barrier
+    const int np = cs.np;
+    for (int t = tid; t < L; t += NT) {
+        const int a = exponent_of(rSig[t]) + wshift;
+        ralpha[t] = a;
+        rV[t] = ldexp_bits(rV[t], -a);  // V_l sig_t 2^-alpha_t
+    }
+    // Column scales: max over all beta samples of |S_p| (re and im separately).
+    {
+        unsigned long long m0 = 0, m1 = 0;
+        const int p = tid & 7;
+        if (p < np) {
+            const int64_t col = (int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n);
+#pragma unroll 4
+            for (int j = tid >> 3; j < n; j += NT / 8) {
+                const double2 v = S[(int64_t)j * n * n + col];  // all j: the mirror does not change the maximum
+                m0 = max(m0, abs_bits(v.x));
+                m1 = max(m1, abs_bits(v.y));
+            }
+        }
+        reduce_column_exponents<NT>(m0, m1, part, colexp);
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
+    if (tid == 0) init_pipe(pb);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const int nchunks = (n + KC - 1) / KC;
+    bool ok = true;
+
+    if (tid < kProd) {
+        // ---- producers: sample j = c KC + t of every chunk c, rows in groups of G ----
+        const int t = tid;
+        double xr[MAXC], dc[MAXC], dp[MAXC];
+#pragma unroll
+        for (int c = 0; c < MAXC; ++c) {
+            const int j = c * KC + t;
+            xr[c] = 0.0; dc[c] = 0.0; dp[c] = 0.0;
+            if (j < n) {
+                xr[c] = tb.cosb[j];
+                const double sd = tb.seedtab[(size_t)cidx * n + j];
+                dc[c] = (flags & kApplyW) ? sd * tb.w[j] : sd;
+            }
+        }
+        uint32_t gi = 0;
+        for (int lb = l0; lb < B && ok; lb += TM) {
+            const int rows = min(TM, B - lb);
+#pragma unroll
+            for (int c = 0; c < MAXC; ++c) {
+                if (c >= nchunks || !ok) break;
+                const bool col = c * KC + t < n;
+                for (int g = 0; g < NG; ++g, ++gi) {
+                    ok = producer_acquire(pb, gi);
+                    if (!ok) break;
+                    double *st = stage + (gi % kStages) * G * KC + t;
+#pragma unroll
+                    for (int rr = 0; rr < G; ++rr) {
+                        const int r = g * G + rr;
+                        double v = 0.0;
+                        if (col && r < rows) {
+                            v = dc[c];
+                            const int q = lb + r - l0;
+                            const double nx = fma(fma(rA[q], xr[c], -rAc[q]), dc[c], -dp[c]);
+                            dp[c] = dc[c];
+                            dc[c] = nx;
+                        }
+                        st[rr * KC] = v;
+                    }
+                    tc::mbar_arrive(&pb.full[gi % kStages]);
+                }
+            }
+        }
+    } else {
+        // ---- converters ----
+        const int t = tid - kProd;
+        const int wq = warp & 3;  // TMEM lane quarter of this warp
+        uint32_t gi = 0, mph = 0, cc = 0;
+        bool pending = false;     // MMAs committed and not yet waited for
+        int plb = 0, prows = 0;   // the tile those MMAs close (prows > 0), for the deferred epilogue
+        auto epilogue = [&](int tlb, int trows) {
+            // Degree tlb + 16 w + i sits in TMEM lane 32 w + i (i < 16), w = lane quarter (warps 4-7).
+            tc::fence_after_sync();
+            if (t < 128) {
+                const int r = 16 * wq + lane;
+                const int l = tlb + r, q = l - l0;
+                double v16[kCols];
+                epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), colexp, v16);
+                if (lane < 16 && r < trows) {
+                    const double v = rV[q];
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) {
+                        if (p >= np) break;
+                        const double vs = ((cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1))) ? -v : v;
+                        *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p] + q)) =
+                            make_double2(vs * v16[2 * p], vs * v16[2 * p + 1]);
+                    }
+                }
+            }
+            tc::fence_before_sync();
+        };
+        for (int lb = l0; lb < B && ok; lb += TM) {
+            const int rows = min(TM, B - lb);
+            for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+                const int kvalid = min(KC, n - c * KC);
+                const int ksteps = (kvalid + 15) / 16;
+                const int kfill = ksteps * 16;
+                unsigned char *Xc = X + (cc & 1) * B_BYTES;
+                {
+                    // B operand: partner p, re (h = 0) or im (h = 1), beta samples k0..k0+7
+                    const int p = t & 7, h = (t >> 3) & 1, k0 = 8 * (t >> 4);
+                    if (k0 < kfill) {
+                        double v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) v[u] = 0.0;
+                        if (p < np) {
+                            const int64_t colp = (int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n);
+                            const double *Sd = reinterpret_cast<const double *>(S) + h;
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (k0 + u < kvalid) {
+                                    const int jj = c * KC + k0 + u;
+                                    v[u] = Sd[2 * ((int64_t)(cs.mir[p] ? n - 1 - jj : jj) * n * n + colp)];
+                                }
+                        }
+                        const int a = -colexp[2 * p + h];
+                        const int al[4] = {a, a, a, a};
+                        const double v0[4] = {v[0], v[1], v[2], v[3]}, v1[4] = {v[4], v[5], v[6], v[7]};
+                        put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h, k0, v0, al);
+                        put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h, k0 + 4, v1, al);
+                    }
+                }
+                if (pending) {
+                    ok = converter_wait_mma(pb, mph);
+                    pending = false;
+                    if (!ok) break;
+                    if (prows > 0) epilogue(plb, prows);
+                }
+                // A operand: staged row 8 g + t / 32, samples 4 (t % 32) .. + 3
+                const int rr = t >> 5, k4 = 4 * (t & 31);
+                for (int g = 0; g < NG; ++g, ++gi) {
+                    ok = converter_acquire(pb, gi);
+                    if (!ok) break;
+                    const int r = g * G + rr;
+                    if (r < rows && k4 < kfill) {
+                        const double2 *src =
+                            reinterpret_cast<const double2 *>(stage + (gi % kStages) * G * KC + rr * KC + k4);
+                        const double2 w0 = src[0], w1 = src[1];
+                        const double v[4] = {w0.x, w0.y, w1.x, w1.y};
+                        const int a = ralpha[lb + r - l0];
+                        const int al[4] = {a, a, a, a};
+                        put_digits4(A, A_PLANE, A_LBO, r, k4, v, al);
+                    }
+                    tc::mbar_arrive(&pb.empty[gi % kStages]);
+                }
+                if (!ok) break;
+                tc::fence_proxy_async();
+                tc::group_sync(kBarConv, kConv);
+                if (t == 0) issue_levels<TM>(tmem, A, A_PLANE, A_LBO, Xc, B_LBO, c == 0, ksteps, &pb.mma);
+                pending = true;
+                plb = lb;
+                prows = c == nchunks - 1 ? rows : 0;
+            }
+        }
+        if (pending) {
+            // the last tile's MMAs (or, after a timeout, MMAs still in flight)
+            const bool done = converter_wait_mma(pb, mph);
+            if (ok && done && prows > 0) epilogue(plb, prows);
+            ok = ok && done;
+        }
+    }
+    if (!ok && tb.err) atomicExch(tb.err, 2);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// Inverse DWT.  One CTA per cluster; tiles of 128 beta samples (the TMEM
+// lanes, one producer each), K chunks of 64 degrees, staged 8 degrees at a
+// time: staging [kStages][128 rows][SR] with SR = 10 doubles per row (8 used;
+// the pad spreads the rows over the shared-memory banks).  Same converter
+// schedule as the forward.
+//   dynamic smem: A planes [7] | B operand [2] | staging | rA, rAc, rG, rSig [B] | alpha [B] (int)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, const double *__restrict__ coef,
+                                                                     double2 *__restrict__ S, int flags) {
+    constexpr int NT = kThreads, TM = kProd, KC = 64, SR = 10;
+    constexpr int A_LBO = TM * 16 + 16, A_PLANE = (KC / 8) * A_LBO;
+    constexpr int B_LBO = kNB * 16 + 16, B_BYTES = (KC / 8) * B_LBO;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ ClusterSmem cs;
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) PipeBars pb;
+    __shared__ unsigned long long part[NT / 32][kCols];
+    __shared__ int colexp[kCols];
+    const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5;
+    const int cidx = blockIdx.x;
+    const int2 rep = tb.clusters[cidx];
+    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+
+    unsigned char *A = smem;
+    unsigned char *X = smem + kDig * A_PLANE;  // [2][B_BYTES]
+    double *stage = reinterpret_cast<double *>(X + 2 * B_BYTES);  // [kStages][TM][SR]
+    double *rA = stage + kStages * TM * SR, *rAc = rA + B, *rG = rAc + B, *rSig = rG + B;
+    int *ralpha = reinterpret_cast<int *>(rSig + B);
+
+    load_cluster(tb, m, mp, cs);
+    cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rG, rSig, nullptr);  // rG: scratch until here
+    const int np = cs.np;
+    for (int t = tid; t < L; t += NT) {
+        const int a = exponent_of(rSig[t]);
+        ralpha[t] = a;
+        const double v = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
+        rG[t] = v * ldexp_bits(rSig[t], -a);  // V_l mu_t
+    }
+    __syncthreads();
+    // Column maxima of F[t][2p (+1)] = sign_p(l) V_l mu_t f(l, m_p, m'_p).
+    {
+        unsigned long long m0 = 0, m1 = 0;
+        const int p = tid & 7;
+        if (p < np)
+            for (int t = tid >> 3; t < L; t += NT / 8) {
+                const double2 c = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + t));
+                m0 = max(m0, abs_bits(rG[t] * c.x));
+                m1 = max(m1, abs_bits(rG[t] * c.y));
+            }
+        reduce_column_exponents<NT>(m0, m1, part, colexp);
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
+    if (tid == 0) init_pipe(pb);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    bool ok = true;
+
+    if (tid < kProd) {
+        // ---- producers: beta sample j = jb + t walks the degrees ----
+        const int t = tid;
+        uint32_t gi = 0;
+        for (int jb = 0; jb < n && ok; jb += TM) {
+            const int j = jb + t;
+            const bool active = j < n;
+            double x = 0.0, dc = 0.0, dp = 0.0;
+            if (active) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
+            for (int lb = l0; lb < B && ok; lb += KC) {
+                const int cnt = min(KC, B - lb);
+                const int ngroups = 2 * ((cnt + 15) / 16);  // K padded to whole MMA steps
+                for (int g = 0; g < ngroups; ++g, ++gi) {
+                    ok = producer_acquire(pb, gi);
+                    if (!ok) break;
+                    double v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int k = 8 * g + u;
+                        v[u] = 0.0;
+                        if (active && k < cnt) {
+                            v[u] = dc;
+                            const int q = lb + k - l0;
+                            const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -dp);
+                            dp = dc;
+                            dc = nx;
+                        }
+                    }
+                    double2 *st = reinterpret_cast<double2 *>(stage + ((gi % kStages) * TM + t) * SR);
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) st[h] = make_double2(v[2 * h], v[2 * h + 1]);
+                    tc::mbar_arrive(&pb.full[gi % kStages]);
+                }
+            }
+        }
+    } else {
+        // ---- converters ----
+        const int t = tid - kProd;
+        const int wq = warp & 3;
+        const int row = t & 127, half = t >> 7;  // A operand: 4 of the 8 staged degrees of one row
+        uint32_t gi = 0, mph = 0, cc = 0;
+        bool pending = false;
+        int pjb = -1;  // the tile whose last MMAs are pending (>= 0), for the deferred epilogue
+        auto epilogue = [&](int tjb) {
+            // Beta sample tjb + t sits in TMEM lane t (warps 4-7).
+            tc::fence_after_sync();
+            if (t < 128) {
+                const int jt = tjb + t;
+                double v16[kCols];
+                epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), colexp, v16);
+                if (jt < n) {
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) {
+                        if (p >= np) break;
+                        const int jj = cs.mir[p] ? n - 1 - jt : jt;
+                        double re = v16[2 * p], im = v16[2 * p + 1];
+                        if (flags & kApplyW) {
+                            const double wj = tb.w[jj];
+                            re *= wj;
+                            im *= wj;
+                        }
+                        S[((int64_t)jj * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)] = make_double2(re, im);
+                    }
+                }
+            }
+            tc::fence_before_sync();
+        };
+        for (int jb = 0; jb < n && ok; jb += TM) {
+            const bool active = jb + row < n;
+            for (int lb = l0, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
+                const int cnt = min(KC, B - lb);
+                const int ksteps = (cnt + 15) / 16;
+                const int kfill = ksteps * 16;
+                unsigned char *Xc = X + (cc & 1) * B_BYTES;
+                {
+                    // B operand: column q2, degrees lb + k0 .. + 3 of F (FP64, formed here)
+                    const int q2 = t & 15, k0 = 4 * (t >> 4);
+                    if (k0 < kfill) {
+                        double v[4];
+                        int al[4];
+                        const int p = q2 >> 1;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            v[u] = 0.0;
+                            al[u] = -colexp[q2];
+                            const int k = k0 + u;
+                            if (p < np && k < cnt) {
+                                const int q = lb + k - l0, l = lb + k;
+                                const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
+                                const double cv = coef[2 * (cs.off[p] + q) + (q2 & 1)];
+                                v[u] = (neg ? -rG[q] : rG[q]) * cv;
+                            }
+                        }
+                        put_digits4(Xc, 16 * kCols, B_LBO, q2, k0, v, al);
+                    }
+                }
+                if (pending) {
+                    ok = converter_wait_mma(pb, mph);
+                    pending = false;
+                    if (!ok) break;
+                    if (pjb >= 0) epilogue(pjb);
+                }
+                for (int g = 0; g < 2 * ksteps; ++g, ++gi) {
+                    ok = converter_acquire(pb, gi);
+                    if (!ok) break;
+                    if (active) {
+                        const double2 *src =
+                            reinterpret_cast<const double2 *>(stage + ((gi % kStages) * TM + row) * SR + 4 * half);
+                        const double2 w0 = src[0], w1 = src[1];
+                        const double v[4] = {w0.x, w0.y, w1.x, w1.y};
+                        int al[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = 8 * g + 4 * half + u;
+                            al[u] = k < cnt ? ralpha[lb + k - l0] : 0;
+                        }
+                        put_digits4(A, A_PLANE, A_LBO, row, 8 * g + 4 * half, v, al);
+                    }
+                    tc::mbar_arrive(&pb.empty[gi % kStages]);
+                }
+                if (!ok) break;
+                tc::fence_proxy_async();
+                tc::group_sync(kBarConv, kConv);
+                if (t == 0) issue_levels<TM>(tmem, A, A_PLANE, A_LBO, Xc, B_LBO, c == 0, ksteps, &pb.mma);
+                pending = true;
+                pjb = lb + KC >= B ? jb : -1;
+            }
+        }
+        if (pending) {
+            const bool done = converter_wait_mma(pb, mph);
+            if (ok && done && pjb >= 0) epilogue(pjb);
+            ok = ok && done;
+        }
+    }
+    if (!ok && tb.err) atomicExch(tb.err, 2);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s, int flags) {
+    if (!tb.seedtab || !tb.rectab) return cudaErrorInvalidValue;
+    constexpr int KC = kProd, A_PLANE = (KC / 8) * (64 * 16 + 16), B_BYTES = (KC / 8) * (kNB * 16 + 16);
+    const int B = tb.B;
+    const size_t bytes = (size_t)kDig * A_PLANE + 2 * (size_t)B_BYTES +
+                         sizeof(double) * (kStages * 8 * (size_t)KC + 3 * (size_t)B) + sizeof(int) * (size_t)B;
+    cudaError_t e =
+        cudaFuncSetAttribute(dwt_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    dwt_forward_tc_kernel<<<tb.ncl, kThreads, bytes, s>>>(tb, S, reinterpret_cast<double *>(coef), flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dwt_inverse_tc(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s, int flags) {
+    if (!tb.seedtab || !tb.rectab) return cudaErrorInvalidValue;
+    constexpr int TM = kProd, KC = 64, SR = 10;
+    constexpr int A_PLANE = (KC / 8) * (TM * 16 + 16), B_BYTES = (KC / 8) * (kNB * 16 + 16);
+    const int B = tb.B;
+    const size_t bytes = (size_t)kDig * A_PLANE + 2 * (size_t)B_BYTES +
+                         sizeof(double) * (kStages * (size_t)TM * SR + 4 * (size_t)B) + sizeof(int) * (size_t)B;
+    cudaError_t e =
+        cudaFuncSetAttribute(dwt_inverse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    dwt_inverse_tc_kernel<<<tb.ncl, kThreads, bytes, s>>>(tb, reinterpret_cast<const double *>(coef), S, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace softgb

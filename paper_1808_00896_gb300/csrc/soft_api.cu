@@ -147,6 +147,21 @@ int64_t run_start(int B, int m, int mp) {
     return row + in;
 }
 
+// Plans whose S is FP64 in layout [j][m][m'] with Z2Z FFTs (plain FP64 and FP64 on tensor cores).
+bool fp64_layout(int dtype) { return dtype == SOFT_FP64 || dtype == SOFT_FP64_TC; }
+
+cudaError_t launch_dwt_forward_plan(const soft_plan_s *p, const double2 *S, double2 *coef, cudaStream_t s,
+                                    int flags) {
+    return p->dtype == SOFT_FP64_TC ? launch_dwt_forward_tc(p->tables(), S, coef, s, flags)
+                                    : launch_dwt_forward_fp64(p->tables(), S, coef, s, flags);
+}
+
+cudaError_t launch_dwt_inverse_plan(const soft_plan_s *p, const double2 *coef, double2 *S, cudaStream_t s,
+                                    int flags) {
+    return p->dtype == SOFT_FP64_TC ? launch_dwt_inverse_tc(p->tables(), coef, S, s, flags)
+                                    : launch_dwt_inverse_fp64(p->tables(), coef, S, s, flags);
+}
+
 soft_status check_plan_args(const soft_plan_s *p, const void *a, const void *b) {
     if (!valid(p)) return SOFT_ERR_INVALID_ARG;
     if (!aligned16(a) || !aligned16(b) || a == b) return SOFT_ERR_INVALID_ARG;
@@ -261,7 +276,7 @@ soft_status run_inverse_mixed(soft_plan_s *p, const double *coef, double *grid, 
 // flags: kApplyW | kApplyV for the forward transform, 0 for the adjoint of the inverse.
 soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s,
                         int flags = kApplyW | kApplyV) {
-    if (p->dtype != SOFT_FP64) return run_forward_mixed(p, grid, coef, s, flags);
+    if (!fp64_layout(p->dtype)) return run_forward_mixed(p, grid, coef, s, flags);
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
     cufftResult r = cufftSetStream(p->fft, s);
@@ -271,7 +286,7 @@ soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaSt
     r = cufftExecZ2Z(p->fft, in, reinterpret_cast<cufftDoubleComplex *>(p->S), CUFFT_INVERSE);
     if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (forward slices)", r);
     if (ev) cudaEventRecord(ev[1], s);
-    cudaError_t e = launch_dwt_forward_fp64(p->tables(), p->S, reinterpret_cast<double2 *>(coef), s, flags);
+    cudaError_t e = launch_dwt_forward_plan(p, p->S, reinterpret_cast<double2 *>(coef), s, flags);
     if (e != cudaSuccess) return fail_cuda("DWT kernel launch", e);
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
@@ -279,12 +294,12 @@ soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaSt
 
 // flags: 0 for the inverse transform, kApplyV | kApplyW for the adjoint of the forward.
 soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s, int flags = 0) {
-    if (p->dtype != SOFT_FP64) return run_inverse_mixed(p, coef, grid, s, flags);
+    if (!fp64_layout(p->dtype)) return run_inverse_mixed(p, coef, grid, s, flags);
     cudaEvent_t *ev = timing_slot(p, 1);
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = launch_zero_nyquist(p->B, p->S, s);
     if (e != cudaSuccess) return fail_cuda("S clearing kernel launch", e);
-    e = launch_dwt_inverse_fp64(p->tables(), reinterpret_cast<const double2 *>(coef), p->S, s, flags);
+    e = launch_dwt_inverse_plan(p, reinterpret_cast<const double2 *>(coef), p->S, s, flags);
     if (e != cudaSuccess) return fail_cuda("iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
     cufftResult r = cufftSetStream(p->fft, s);
@@ -405,7 +420,7 @@ soft_status record_batch(BatchGraph *bg, int n, const void *const *a, const void
         std::vector<bool> taken(n, false);
         for (int i : rest) {
             soft_plan_s *p = bg->plans[i];
-            if (p->dtype == SOFT_FP64 || taken[i]) continue;
+            if (fp64_layout(p->dtype) || taken[i]) continue;
             std::vector<int> grp;
             for (int j : rest)
                 if (!taken[j] && bg->plans[j]->dtype == p->dtype && bg->plans[j]->B == p->B) grp.push_back(j);
@@ -618,7 +633,8 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     *out = nullptr;
     if (B < 1) return SOFT_ERR_INVALID_ARG;
     if (B > kMaxB) return SOFT_ERR_UNSUPPORTED;
-    if (dtype != SOFT_FP64 && dtype != SOFT_MIXED_BF16X3 && dtype != SOFT_MIXED_TF32) return SOFT_ERR_INVALID_ARG;
+    if (dtype != SOFT_FP64 && dtype != SOFT_MIXED_BF16X3 && dtype != SOFT_MIXED_TF32 && dtype != SOFT_FP64_TC)
+        return SOFT_ERR_INVALID_ARG;
     soft_plan_s *p = new (std::nothrow) soft_plan_s();
     if (!p) return SOFT_ERR_OUT_OF_MEMORY;
     p->magic = kPlanMagic;
@@ -661,7 +677,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     alloc((void **)&p->lw, sizeof(double) * n);
     alloc((void **)&p->seedtab, sizeof(double) * (size_t)n * cl.size());
     alloc((void **)&p->rectab, sizeof(double) * 3 * (size_t)B * cl.size());
-    if (dtype == SOFT_FP64) {
+    if (fp64_layout(dtype)) {
         alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
     } else {
         alloc((void **)&p->g32, sizeof(float2) * grid_elems(B));
@@ -682,7 +698,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     const long long slice = (long long)n * n;
     size_t work = 0;
     cufftResult r;
-    if (dtype == SOFT_FP64) {
+    if (fp64_layout(dtype)) {
         // One batched 2-D Z2Z plan over the 2B contiguous beta slices, S in layout [j][m][m'].
         if (cufftCreate(&p->fft) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
         p->fft_made = true;
@@ -818,22 +834,22 @@ int soft_argmax_scratch_doubles(void) { return 2 * argmax_parts(); }
 soft_status soft_dwt_forward(soft_plan p, const double *S, double *coef, void *stream) {
     soft_status st = check_plan_args(p, S, coef);
     if (st != SOFT_OK) return st;
-    if (p->dtype != SOFT_FP64) return SOFT_ERR_UNSUPPORTED;
+    if (!fp64_layout(p->dtype)) return SOFT_ERR_UNSUPPORTED;
     DeviceGuard g(p->device);
-    return cuda_status(launch_dwt_forward_fp64(p->tables(), reinterpret_cast<const double2 *>(S),
-                                               reinterpret_cast<double2 *>(coef), static_cast<cudaStream_t>(stream)));
+    return cuda_status(launch_dwt_forward_plan(p, reinterpret_cast<const double2 *>(S),
+                                               reinterpret_cast<double2 *>(coef), static_cast<cudaStream_t>(stream),
+                                               kApplyW | kApplyV));
 }
 
 soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *stream) {
     soft_status st = check_plan_args(p, coef, S);
     if (st != SOFT_OK) return st;
-    if (p->dtype != SOFT_FP64) return SOFT_ERR_UNSUPPORTED;
+    if (!fp64_layout(p->dtype)) return SOFT_ERR_UNSUPPORTED;
     DeviceGuard g(p->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_zero_nyquist(p->B, reinterpret_cast<double2 *>(S), s);
     if (e == cudaSuccess)
-        e = launch_dwt_inverse_fp64(p->tables(), reinterpret_cast<const double2 *>(coef),
-                                    reinterpret_cast<double2 *>(S), s);
+        e = launch_dwt_inverse_plan(p, reinterpret_cast<const double2 *>(coef), reinterpret_cast<double2 *>(S), s, 0);
     return cuda_status(e);
 }
 
@@ -879,6 +895,7 @@ soft_status soft_selftest_bounded_wait(soft_plan p, int polls, void *stream) {
 int soft_plan_num_variants(soft_plan p, int kernel) {
     if (!valid(p) || (kernel != 0 && kernel != 1)) return -1;
     if (p->dtype == SOFT_FP64) return kernel == 0 ? dwt_forward_fp64_variants(p->B) : dwt_inverse_fp64_variants(p->B);
+    if (p->dtype == SOFT_FP64_TC) return 1;
     return kernel == 0 ? 2 : 1;
 }
 

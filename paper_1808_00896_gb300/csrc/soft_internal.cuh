@@ -257,6 +257,12 @@ cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s);
 cudaError_t launch_cluster_tables(const Tables &tb, double *seedtab, double *rectab, cudaStream_t s);
 int dwt_forward_fp64_variants(int B);
 int dwt_inverse_fp64_variants(int B);
+// FP64-accurate tensor-core DWT / iDWT (dwt_fp64tc.cu); same S layout and
+// flags as the FP64 launchers; need the plan's per-cluster tables.
+cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s,
+                                  int flags = kApplyW | kApplyV);
+cudaError_t launch_dwt_inverse_tc(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s,
+                                  int flags = 0);
 cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *lsin, double *lfact,
                           cudaStream_t s);
 
