@@ -77,16 +77,17 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 
 # DRAM traffic per launch of the dominant kernels from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel, bandwidth and
-# the SHA-256 of the kernel source it was taken on; reported as null when the
-# source has changed since.  From profiles/dwt_fp64_b64.md.
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel and bandwidth,
+# with the source file and the SHA-256 prefix of it that the capture was taken
+# on; reported as null once that file has changed.
 TRAFFIC = {
-    ("dwt_forward_fp64_kernel", 64): (33_522_176 + 41_728, "0e927721a286684d"),
+    ("dwt_forward_fp64_kernel", 64): (36_875_264 + 82_944, "dwt_fp64.cu", "5ee75560c49fbeab"),
+    ("dwt_forward_tc_kernel", 128): (311_866_368 + 46_717_696, "dwt_fp64tc.cu", "cd54b8cc14f33cf8"),
 }
 
 
-def kernel_source_sha() -> str:
-    path = os.path.join(ROOT, "paper_1808_00896_gb300", "csrc", "dwt_fp64.cu")
+def kernel_source_sha(name: str = "dwt_fp64.cu") -> str:
+    path = os.path.join(ROOT, "paper_1808_00896_gb300", "csrc", name)
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
@@ -522,7 +523,7 @@ def run_ours(args) -> None:
     algo = fl["contraction"] + fl["recurrence"] if dtype == "fp64" else fl["recurrence"]
     achieved = algo / (dom_ms * 1e-3) / 1e9
     tr = TRAFFIC.get((dom, B))
-    traffic = tr[0] if (tr and tr[1] == kernel_source_sha()) else None
+    traffic = tr[0] if (tr and tr[2] == kernel_source_sha(tr[1])) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s",
                 "frac": achieved / peak_gflops, "traffic": traffic, "kernel": dom,
                 "peak_source": "derived: nominal FP64 1.25 TFLOP/s = 4 flop/clk/SM x 152 SM x 2070 MHz",
