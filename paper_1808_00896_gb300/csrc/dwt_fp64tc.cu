@@ -252,26 +252,34 @@ __device__ __forceinline__ void reduce_column_exponents(unsigned long long m0, u
 //              values into a double-buffered staging area, 8 rows (forward)
 //              or 8 degrees (inverse) per buffer;
 //   converters (256 threads, warps 4-11) cut staged values and the data
-//              operand into digits (4 values per thread and task), issue the
-//              chunk's MMAs from one thread, and run the epilogue (warps 4-7,
-//              one per TMEM lane quarter).  Two converter warps per scheduler
-//              hide the latency of the integer digit chains.
+//              operand into digits (4 values per thread and task) and run the
+//              epilogue (warps 4-7, one per TMEM lane quarter).  Two converter
+//              warps per scheduler hide the latency of the integer digit chains;
+//   issuer     (lane 0 of warp 12) issues each chunk's MMAs once the
+//              converters signal the operands ready.  A tcgen05.mma of these
+//              shapes occupies its issuing thread for ~45 cycles, so issuing
+//              from a converter would stall that whole group; from its own
+//              warp the issue overlaps the converters' next B operand.
 // So the FP64 pipe (producers) and the integer pipes (converters) work in
 // parallel instead of in one warp's instruction stream.  Hand-off through
-// mbarriers (full: 128 producer arrivals, empty: 256 converter arrivals);
-// every wait is bounded, and each group takes its verdict with an AND-reducing
-// named barrier so that a timeout makes the whole group leave together.
+// mbarriers (full: 128 producer arrivals, empty: 256 converter arrivals,
+// ready: one converter arrival per chunk, mma: the tcgen05 commit);
+// every wait is bounded.  Converters, which synchronise among themselves to
+// agree on when the operands are complete, take each verdict with an
+// AND-reducing named barrier so that a timeout makes the whole group leave
+// together; producers and the issuer synchronise with nobody but the mbarriers
+// and leave individually.
 // ---------------------------------------------------------------------------
 constexpr int kProd = 128;    // producer threads (warps 0-3)
 constexpr int kConv = 256;    // converter threads (warps 4-11)
-constexpr int kThreads = kProd + kConv;
+constexpr int kIssuer = kProd + kConv;  // lane 0 of warp 12 issues the MMAs
+constexpr int kThreads = kIssuer + 32;
 constexpr int kBarConv = 1;   // named barrier of the converters
-constexpr int kBarProd = 2;   // named barrier of the producers
 
 constexpr int kStages = 4;    // staging ring depth (groups of 8 rows / degrees)
 
 struct PipeBars {
-    uint64_t full[kStages], empty[kStages], mma;
+    uint64_t full[kStages], empty[kStages], ready, mma;
 };
 
 __device__ __forceinline__ void init_pipe(PipeBars &pb) {
@@ -280,13 +288,22 @@ __device__ __forceinline__ void init_pipe(PipeBars &pb) {
         tc::mbar_init(&pb.full[b], kProd);
         tc::mbar_init(&pb.empty[b], kConv);
     }
+    tc::mbar_init(&pb.ready, 1);
     tc::mbar_init(&pb.mma, 1);
 }
 
-// Producer: wait until staging buffer gi % kStages is free (its previous group consumed).
+// Issuer: wait until the converters have written the operands of the next chunk.
+__device__ __forceinline__ bool issuer_acquire(PipeBars &pb, uint32_t &rph) {
+    const bool done = tc::mbar_wait(&pb.ready, rph, kWaitPolls);
+    rph ^= 1u;
+    return done;
+}
+
+// Producer: wait until staging buffer gi % kStages is free (its previous group
+// consumed).  Producers take no named barrier anywhere, so each decides alone:
+// one that gives up stops arriving, and the converters' own bounded waits end.
 __device__ __forceinline__ bool producer_acquire(PipeBars &pb, uint32_t gi) {
-    const bool done = tc::mbar_wait(&pb.empty[gi % kStages], ((gi / kStages) & 1) ^ 1u, kWaitPolls);
-    return tc::group_and(kBarProd, kProd, done);
+    return tc::mbar_wait(&pb.empty[gi % kStages], ((gi / kStages) & 1) ^ 1u, kWaitPolls);
 }
 
 // Converter: wait until staging buffer gi % kStages holds group gi.
@@ -422,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
                 }
             }
         }
-    } else {
+    } else if (tid < kIssuer) {
         // ---- converters ----
         const int t = tid - kProd;
         const int wq = warp & 3;  // TMEM lane quarter of this warp
@@ -507,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
                 if (!ok) break;
                 tc::fence_proxy_async();
                 tc::group_sync(kBarConv, kConv);
-                if (t == 0) issue_levels<TM>(tmem, A, A_PLANE, A_LBO, Xc, B_LBO, c == 0, ksteps, &pb.mma);
+                if (t == 0) tc::mbar_arrive(&pb.ready);
                 pending = true;
                 plb = lb;
                 prows = c == nchunks - 1 ? rows : 0;
@@ -519,6 +536,16 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
             if (ok && done && prows > 0) epilogue(plb, prows);
             ok = ok && done;
         }
+    } else if (tid == kIssuer) {
+        // ---- issuer: the MMAs of every chunk, in the converters' order ----
+        uint32_t rph = 0, cc = 0;
+        for (int lb = l0; lb < B && ok; lb += TM)
+            for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+                ok = issuer_acquire(pb, rph);
+                if (!ok) break;
+                const int ksteps = (min(KC, n - c * KC) + 15) / 16;
+                issue_levels<TM>(tmem, A, A_PLANE, A_LBO, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps, &pb.mma);
+            }
     }
     if (!ok && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
@@ -621,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
                 }
             }
         }
-    } else {
+    } else if (tid < kIssuer) {
         // ---- converters ----
         const int t = tid - kProd;
         const int wq = warp & 3;
@@ -709,7 +736,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
                 if (!ok) break;
                 tc::fence_proxy_async();
                 tc::group_sync(kBarConv, kConv);
-                if (t == 0) issue_levels<TM>(tmem, A, A_PLANE, A_LBO, Xc, B_LBO, c == 0, ksteps, &pb.mma);
+                if (t == 0) tc::mbar_arrive(&pb.ready);
                 pending = true;
                 pjb = lb + KC >= B ? jb : -1;
             }
@@ -719,6 +746,15 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
             if (ok && done && pjb >= 0) epilogue(pjb);
             ok = ok && done;
         }
+    } else if (tid == kIssuer) {
+        uint32_t rph = 0, cc = 0;
+        for (int jb = 0; jb < n && ok; jb += TM)
+            for (int lb = l0, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
+                ok = issuer_acquire(pb, rph);
+                if (!ok) break;
+                const int ksteps = (min(KC, B - lb) + 15) / 16;
+                issue_levels<TM>(tmem, A, A_PLANE, A_LBO, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps, &pb.mma);
+            }
     }
     if (!ok && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();

@@ -1,0 +1,324 @@
+// fft_df.cu -- batched 2-D FFT of the beta slices in double-float arithmetic
+// on the FP32 pipe, for the FP64-accurate tensor-core mode (SOFT_FP64_TC).
+//
+// Step 1 of Sec. 2.4 (and its inverse): for every beta sample j the 2-D DFT
+//   S(m, m'; j) = sum_{i,k} f(alpha_i, beta_j, gamma_k) exp(s i (m alpha_i + m' gamma_k)),
+// unnormalised, s = +1 for the forward transform and -1 for the inverse, on
+// the n x n slice, n = 2B.  The GB300's FP32 pipe is ~58x wider than its FP64
+// pipe, so the butterflies run on unevaluated pairs of floats ("double-float",
+// hi + lo with |lo| <= ulp(hi)/2, ~48 significant bits) built from the
+// error-free sum of Knuth (two-sum) and the FMA-based error-free product;
+// every row is scaled by the power of two of its largest magnitude (so the
+// pairs stay inside the FP32 exponent range for any data) and split from FP64;
+// results are recombined into FP64 and scaled back.  Power-of-two n only (the
+// plan falls back to cuFFT otherwise).
+//
+// Two passes, no extra memory:
+//   rows:    length-n DFT along the contiguous index of every row (n^2 rows),
+//            FP64 or double-float in, double-float out;
+//   columns: length-n DFT along the middle index for every (slice, column),
+//            in place on the double-float data, FP64 out.
+// Each DFT is an in-place radix-2 decimation-in-time transform in shared
+// memory: bit-reversed load, log2(n) butterfly stages, natural-order store.
+#include "soft_internal.cuh"
+#include "tcgen05.cuh"
+
+#include <algorithm>
+
+namespace softgb {
+namespace {
+
+struct dfloat {
+    float hi, lo;
+};
+
+// s + e = a + b exactly (Knuth's two-sum, no ordering assumption).
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+// s + e = a + b exactly when |a| >= |b| (or a == 0).
+__device__ __forceinline__ dfloat fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+// a + b with the error of the leading sum recovered; the trailing parts are
+// added plainly.  The error is ~2^-47 of |a| + |b|, which is the norm-wise
+// bound a DFT needs (a butterfly's output error relative to its inputs).
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+    dfloat s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ dfloat df_neg(dfloat a) { return {-a.hi, -a.lo}; }
+
+struct dcomplex {
+    dfloat re, im;
+};
+
+__device__ __forceinline__ dcomplex load_df(const float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 store_df(const dcomplex v) { return make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo); }
+
+// FP64 -> double-float: hi = fl32(x), lo = fl32(x - hi) (x - hi is exact in FP64).
+__device__ __forceinline__ dfloat split_f64(double x) {
+    const float hi = tc::f64_to_f32_rn(x);
+    return {hi, tc::f64_to_f32_rn(x - tc::f32_to_f64(hi))};
+}
+
+__device__ __forceinline__ double join_f64(dfloat v) { return tc::f32_to_f64(v.hi) + tc::f32_to_f64(v.lo); }
+
+// v 2^k by an exponent-field add (v normal or 0; results below the normal
+// range flush to signed 0).
+__device__ __forceinline__ double scale2(double v, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0 || e == 0x7FF || k == 0) return e == 0 ? 0.0 * v : v;
+    const int e2 = e + k;
+    if (e2 <= 0) return __longlong_as_double((long long)(b & (1ull << 63)));
+    if (e2 >= 0x7FF) return __longlong_as_double((long long)((b & (1ull << 63)) | (0x7FFull << 52)));
+    return __longlong_as_double((long long)((b & ~(0x7FFull << 52)) | ((unsigned long long)e2 << 52)));
+}
+
+// 2^k as a float for the power-of-two scalings of the double-float values
+// (0 below the FP32 normal range, where the scaled values are negligible).
+__device__ __forceinline__ float pow2f(int k) { return k < -126 ? 0.f : __int_as_float((min(k, 127) + 127) << 23); }
+
+// Row scales: every row of the first pass is scaled by the power of two of
+// its own largest magnitude, s_r = (its largest biased exponent) - 1023, so
+// the double-float values stay inside the FP32 exponent range whatever the
+// data's scale; the column pass brings the rows of a slice to their common
+// largest scale by exact power-of-two products before its DFTs, and scales
+// the results back.  All-zero rows get kZeroRow.
+constexpr int kZeroRow = -100000;
+
+// a b + sg c d in double-float: the two leading products with their exact
+// errors (FMA), their error-free sum, and the cross terms folded in by FMAs
+// (lo * lo terms, <= 2^-48 relative, dropped).
+__device__ __forceinline__ dfloat df_dot2(dfloat a, dfloat b, dfloat c, dfloat d, float sg) {
+    const float p1 = a.hi * b.hi, p2 = sg * (c.hi * d.hi);
+    const float e1 = fmaf(a.hi, b.hi, -p1), e2 = sg * fmaf(c.hi, d.hi, -sg * p2);
+    const dfloat s = two_sum(p1, p2);
+    float t = s.lo + (e1 + e2);
+    t = fmaf(a.hi, b.lo, t);
+    t = fmaf(a.lo, b.hi, t);
+    t = fmaf(sg * c.hi, d.lo, t);
+    t = fmaf(sg * c.lo, d.hi, t);
+    return fast_two_sum(s.hi, t);
+}
+
+// w * x (w conjugated when conj).
+__device__ __forceinline__ dcomplex cmul(dcomplex w, dcomplex x, bool conj) {
+    if (conj) w.im = df_neg(w.im);
+    return {df_dot2(w.re, x.re, w.im, x.im, -1.f), df_dot2(w.re, x.im, w.im, x.re, 1.f)};
+}
+
+__device__ __forceinline__ dcomplex cadd(dcomplex a, dcomplex b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dcomplex csub(dcomplex a, dcomplex b) {
+    return {df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))};
+}
+// x * (+i) when pos, x * (-i) otherwise.
+__device__ __forceinline__ dcomplex mul_i(dcomplex x, bool pos) {
+    return pos ? dcomplex{df_neg(x.im), x.re} : dcomplex{x.im, df_neg(x.re)};
+}
+
+__device__ __forceinline__ int bitrev(int t, int logn) { return (int)(__brev((unsigned)t) >> (32 - logn)); }
+
+// The log2(n) butterfly stages of `cnt` independent length-n DFTs stored
+// contiguously in s (each bit-reversed on entry), by all threads of the block:
+// pairs of radix-2 decimation-in-time stages fused into one radix-4 pass over
+// shared memory (sizes 2h and 4h), plus a last radix-2 stage when log2(n) is
+// odd.  tw[t] = exp(+2 pi i t / n), t < n/2; conj selects the - sign.
+__device__ void dft_stages(float4 *s, int cnt, int n, int logn, const float4 *tw, bool conj) {
+    int h = 1, lh = 0;  // first sub-stage has size 2h
+    for (; 4 * h <= n; h *= 4, lh += 2) {
+        const int nq = cnt * (n >> 2);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+            const int row = q >> (logn - 2), qq = q & ((n >> 2) - 1);
+            const int k = qq & (h - 1), g = qq >> lh;
+            const int i0 = row * n + g * 4 * h + k;
+            const dcomplex w1 = load_df(tw[k << (logn - 1 - lh)]);  // exp(+- 2 pi i k / (2h))
+            const dcomplex w2 = load_df(tw[k << (logn - 2 - lh)]);  // exp(+- 2 pi i k / (4h))
+            const dcomplex x0 = load_df(s[i0]), x1 = load_df(s[i0 + h]);
+            const dcomplex x2 = load_df(s[i0 + 2 * h]), x3 = load_df(s[i0 + 3 * h]);
+            const dcomplex t1 = cmul(w1, x1, conj), t3 = cmul(w1, x3, conj);
+            const dcomplex a0 = cadd(x0, t1), a1 = csub(x0, t1), a2 = cadd(x2, t3), a3 = csub(x2, t3);
+            const dcomplex u2 = cmul(w2, a2, conj);
+            const dcomplex u3 = mul_i(cmul(w2, a3, conj), !conj);  // exp(+- 2 pi i (k + h) / (4h)) = w2 (+-i)
+            s[i0] = store_df(cadd(a0, u2));
+            s[i0 + 2 * h] = store_df(csub(a0, u2));
+            s[i0 + h] = store_df(cadd(a1, u3));
+            s[i0 + 3 * h] = store_df(csub(a1, u3));
+        }
+    }
+    if (2 * h == n) {  // odd log2(n): one radix-2 stage of size n
+        const int nb = cnt * (n >> 1);
+        __syncthreads();
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const int row = b >> (logn - 1), k = b & (h - 1);
+            const int i = row * n + k, j = i + h;
+            const dcomplex t = cmul(load_df(tw[k]), load_df(s[j]), conj);
+            const dcomplex a = load_df(s[i]);
+            s[i] = store_df(cadd(a, t));
+            s[j] = store_df(csub(a, t));
+        }
+    }
+    __syncthreads();
+}
+
+constexpr int kFftThreads = 256;
+
+// Rows pass: nrows rows of n (contiguous).  FP64 (double2) or double-float
+// (float4) in, double-float out, possibly to the same memory (each block reads
+// its rows before writing them).  `rpb` rows per block.
+__global__ void __launch_bounds__(kFftThreads) fft_rows_kernel(const double2 *in, float4 *out, int64_t nrows, int n,
+                                                                int logn, int rpb, const float4 *__restrict__ twg,
+                                                                int conj, int *__restrict__ rexp) {
+    extern __shared__ __align__(16) float4 sm[];
+    float4 *tw = sm;              // [n/2]
+    float4 *s = sm + (n >> 1);    // [rpb][n]
+    for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) tw[t] = twg[t];
+    __shared__ int rmax[256];  // largest biased exponent of each row; rpb <= 256
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    for (int t = threadIdx.x; t < rpb; t += blockDim.x) rmax[t] = 0;
+    // each thread holds at most kPer of the block's rpb * n <= 1024 elements
+    constexpr int kPer = 4;
+    double2 v[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) v[u] = make_double2(0.0, 0.0);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = threadIdx.x + u * kFftThreads;
+        if (e < rpb * n && r0 + (e >> logn) < nrows) {
+            v[u] = in[(r0 + (e >> logn)) * n + (e & (n - 1))];
+            const int ex = (int)max(((unsigned long long)__double_as_longlong(v[u].x) >> 52) & 0x7FF,
+                                    ((unsigned long long)__double_as_longlong(v[u].y) >> 52) & 0x7FF);
+            if (ex) atomicMax(&rmax[e >> logn], ex);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = threadIdx.x + u * kFftThreads;
+        if (e < rpb * n) {
+            const int rl = e >> logn, sh = rmax[rl] ? 1023 - rmax[rl] : 0;
+            const dfloat re = split_f64(scale2(v[u].x, sh)), im = split_f64(scale2(v[u].y, sh));
+            s[rl * n + bitrev(e & (n - 1), logn)] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+    }
+    for (int t = threadIdx.x; t < rpb; t += blockDim.x)
+        if (r0 + t < nrows) rexp[r0 + t] = rmax[t] ? rmax[t] - 1023 : kZeroRow;
+    dft_stages(s, rpb, n, logn, tw, conj != 0);
+    for (int e = threadIdx.x; e < rpb * n; e += blockDim.x) {
+        const int64_t r = r0 + (e >> logn);
+        if (r < nrows) out[r * n + (e & (n - 1))] = s[e];
+    }
+}
+
+// Columns pass: for every slice and column, the length-n DFT along the middle
+// index (stride n), `kb` adjacent columns per block; double-float in, FP64
+// (double2) out, possibly to the same memory (each block reads its whole
+// tile before writing it).
+__global__ void __launch_bounds__(kFftThreads) fft_cols_kernel(const float4 *in, double2 *out, int n, int logn, int kb,
+                                                                const float4 *__restrict__ twg, int conj,
+                                                                const int *__restrict__ rexp) {
+    extern __shared__ __align__(16) float4 sm[];
+    float4 *tw = sm;              // [n/2]
+    float4 *s = sm + (n >> 1);    // [kb][n], column-major: column c at s + c n
+    for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) tw[t] = twg[t];
+    const int tiles = n / kb;
+    const int64_t js = blockIdx.x / tiles;
+    const int k0 = (blockIdx.x % tiles) * kb;
+    const int64_t base = js * n * n + k0;
+    // the slice's common scale: the largest of its rows' scales
+    __shared__ int smax;
+    __shared__ int sexp[2 * kMaxB];
+    if (threadIdx.x == 0) smax = kZeroRow;
+    __syncthreads();
+    int lm = kZeroRow;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int x = rexp[js * n + i];
+        sexp[i] = x;
+        lm = max(lm, x);
+    }
+    atomicMax(&smax, lm);
+    __syncthreads();
+    const int sref = smax;
+    for (int e = threadIdx.x; e < n * kb; e += blockDim.x) {
+        const int i = e / kb, c = e % kb;
+        const float f = pow2f(sexp[i] - sref);
+        const float4 x = in[base + (int64_t)i * n + c];
+        s[c * n + bitrev(i, logn)] = make_float4(x.x * f, x.y * f, x.z * f, x.w * f);
+    }
+    dft_stages(s, kb, n, logn, tw, conj != 0);
+    const int sh = sref == kZeroRow ? 0 : sref;
+    for (int e = threadIdx.x; e < n * kb; e += blockDim.x) {
+        const int i = e / kb, c = e % kb;
+        const dcomplex v = load_df(s[c * n + i]);
+        out[base + (int64_t)i * n + c] = make_double2(scale2(join_f64(v.re), sh), scale2(join_f64(v.im), sh));
+    }
+}
+
+// tw[t] = exp(+2 pi i t / n) in double-float, t < n/2.
+__global__ void twiddle_kernel(int n, float4 *tw) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n / 2) {
+        const double a = 2.0 * t / n;
+        const dfloat c = split_f64(cospi(a)), s = split_f64(sinpi(a));
+        tw[t] = make_float4(c.hi, c.lo, s.hi, s.lo);
+    }
+}
+
+int ilog2_exact(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return (1 << l) == n ? l : -1;
+}
+
+}  // namespace
+
+bool df_fft_supported(int B) {
+    const int n = 2 * B;
+    return n >= 2 && n <= 2 * kMaxB && ilog2_exact(n) >= 0;
+}
+
+cudaError_t launch_df_twiddles(int B, float4 *tw, cudaStream_t s) {
+    const int n = 2 * B;
+    twiddle_kernel<<<(n / 2 + 127) / 128, 128, 0, s>>>(n, tw);
+    return cudaGetLastError();
+}
+
+// 2-D DFT of the 2B slices of n x n: `in` (FP64, layout [j][i][k]) -> `out`
+// (FP64, [j][m][m']), exp(sign i ...), unnormalised.  `work` is a
+// double-float buffer of n^3 float4 (16 bytes each); it may be `in` or `out`.
+// `rexp` is n^2 ints of scratch (the row scales).
+cudaError_t launch_df_fft2(int B, const double2 *in, double2 *out, float4 *work, const float4 *tw, int sign,
+                           int *rexp, cudaStream_t s) {
+    const int n = 2 * B, logn = ilog2_exact(n);
+    if (logn < 1) return cudaErrorInvalidValue;
+    const int conj = sign < 0 ? 1 : 0;
+    const int64_t nrows = (int64_t)n * n;
+    const int rpb = std::max(1, 512 / n);
+    const size_t rbytes = sizeof(float4) * ((size_t)n / 2 + (size_t)rpb * n);
+    cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rbytes);
+    if (e != cudaSuccess) return e;
+    fft_rows_kernel<<<(unsigned)((nrows + rpb - 1) / rpb), kFftThreads, rbytes, s>>>(in, work, nrows, n, logn, rpb,
+                                                                                     tw, conj, rexp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int kb = std::min(n, std::max(4, 4096 / n));
+    const size_t cbytes = sizeof(float4) * ((size_t)n / 2 + (size_t)kb * n);
+    e = cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
+    if (e != cudaSuccess) return e;
+    fft_cols_kernel<<<(unsigned)((int64_t)n * (n / kb)), kFftThreads, cbytes, s>>>(work, out, n, logn, kb, tw, conj,
+                                                                                    rexp);
+    return cudaGetLastError();
+}
+
+}  // namespace softgb

@@ -42,6 +42,8 @@ struct soft_plan_s {
     bool fft_made;
     double *lw;  // log w_B(j)
     double *seedtab, *rectab;  // per-cluster seeds and recurrence coefficients, built at creation
+    float4 *dftw;              // FP64-TC plans with power-of-two 2B: double-float FFT twiddles (else null)
+    int *dfexp;                // and its row scales (n^2 ints)
     // Mixed-precision plans: FP32 grid staging and S in layout [m][m'][j], FP32 cuFFT plans.
     float2 *g32, *S32;
     cufftHandle fft32f, fft32i;
@@ -208,7 +210,7 @@ void free_plan(soft_plan_s *p) {
     if (p->fft32f_made) cufftDestroy(p->fft32f);
     if (p->fft32i_made) cufftDestroy(p->fft32i);
     cudaFree(p->lw); cudaFree(p->g32); cudaFree(p->S32);
-    cudaFree(p->seedtab); cudaFree(p->rectab);
+    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->dftw); cudaFree(p->dfexp);
     cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
     cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
     cudaFree(p->stage_grid); cudaFree(p->stage_coef);
@@ -279,12 +281,19 @@ soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaSt
     if (!fp64_layout(p->dtype)) return run_forward_mixed(p, grid, coef, s, flags);
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
-    cufftResult r = cufftSetStream(p->fft, s);
-    if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
-    // S(m,m';j) = sum_{i,k} f exp(+i(m alpha_i + m' gamma_k)): cuFFT's INVERSE direction, unnormalised.
-    cufftDoubleComplex *in = reinterpret_cast<cufftDoubleComplex *>(const_cast<double *>(grid));
-    r = cufftExecZ2Z(p->fft, in, reinterpret_cast<cufftDoubleComplex *>(p->S), CUFFT_INVERSE);
-    if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (forward slices)", r);
+    // S(m,m';j) = sum_{i,k} f exp(+i(m alpha_i + m' gamma_k)), unnormalised.
+    if (p->dftw) {
+        cudaError_t e0 = launch_df_fft2(p->B, reinterpret_cast<const double2 *>(grid), p->S,
+                                        reinterpret_cast<float4 *>(p->S), p->dftw, +1, p->dfexp, s);
+        if (e0 != cudaSuccess) return fail_cuda("double-float FFT launch", e0);
+    } else {
+        cufftResult r = cufftSetStream(p->fft, s);
+        if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
+        // cuFFT's INVERSE direction is exp(+i ...)
+        cufftDoubleComplex *in = reinterpret_cast<cufftDoubleComplex *>(const_cast<double *>(grid));
+        r = cufftExecZ2Z(p->fft, in, reinterpret_cast<cufftDoubleComplex *>(p->S), CUFFT_INVERSE);
+        if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (forward slices)", r);
+    }
     if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = launch_dwt_forward_plan(p, p->S, reinterpret_cast<double2 *>(coef), s, flags);
     if (e != cudaSuccess) return fail_cuda("DWT kernel launch", e);
@@ -302,12 +311,19 @@ soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaSt
     e = launch_dwt_inverse_plan(p, reinterpret_cast<const double2 *>(coef), p->S, s, flags);
     if (e != cudaSuccess) return fail_cuda("iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
-    cufftResult r = cufftSetStream(p->fft, s);
-    if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
-    // f = sum_{m,m'} S exp(-i(m alpha_i + m' gamma_k)): cuFFT's FORWARD direction, unnormalised.
-    r = cufftExecZ2Z(p->fft, reinterpret_cast<cufftDoubleComplex *>(p->S),
-                     reinterpret_cast<cufftDoubleComplex *>(grid), CUFFT_FORWARD);
-    if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (inverse slices)", r);
+    // f = sum_{m,m'} S exp(-i(m alpha_i + m' gamma_k)), unnormalised.
+    if (p->dftw) {
+        e = launch_df_fft2(p->B, p->S, reinterpret_cast<double2 *>(grid), reinterpret_cast<float4 *>(p->S), p->dftw,
+                           -1, p->dfexp, s);
+        if (e != cudaSuccess) return fail_cuda("double-float FFT launch", e);
+    } else {
+        cufftResult r = cufftSetStream(p->fft, s);
+        if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
+        // cuFFT's FORWARD direction is exp(-i ...)
+        r = cufftExecZ2Z(p->fft, reinterpret_cast<cufftDoubleComplex *>(p->S),
+                         reinterpret_cast<cufftDoubleComplex *>(grid), CUFFT_FORWARD);
+        if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (inverse slices)", r);
+    }
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
 }
@@ -677,6 +693,10 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     alloc((void **)&p->lw, sizeof(double) * n);
     alloc((void **)&p->seedtab, sizeof(double) * (size_t)n * cl.size());
     alloc((void **)&p->rectab, sizeof(double) * 3 * (size_t)B * cl.size());
+    if (dtype == SOFT_FP64_TC && df_fft_supported(B)) {
+        alloc((void **)&p->dftw, sizeof(float4) * (size_t)(n / 2));
+        alloc((void **)&p->dfexp, sizeof(int) * (size_t)n * n);
+    }
     if (fp64_layout(dtype)) {
         alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
     } else {
@@ -691,6 +711,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     if (e == cudaSuccess) e = launch_tables(B, p->w, p->cosb, p->lcos, p->lsin, p->lfact, 0);
     if (e == cudaSuccess) e = launch_log_weights(B, p->w, p->lw, 0);
     if (e == cudaSuccess) e = launch_cluster_tables(p->tables(), p->seedtab, p->rectab, 0);
+    if (e == cudaSuccess && p->dftw) e = launch_df_twiddles(B, p->dftw, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
 
@@ -698,7 +719,9 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     const long long slice = (long long)n * n;
     size_t work = 0;
     cufftResult r;
-    if (fp64_layout(dtype)) {
+    if (p->dftw) {
+        // FP64-TC with power-of-two 2B: the double-float FFT needs no cuFFT plan.
+    } else if (fp64_layout(dtype)) {
         // One batched 2-D Z2Z plan over the 2B contiguous beta slices, S in layout [j][m][m'].
         if (cufftCreate(&p->fft) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
         p->fft_made = true;

@@ -257,6 +257,13 @@ cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s);
 cudaError_t launch_cluster_tables(const Tables &tb, double *seedtab, double *rectab, cudaStream_t s);
 int dwt_forward_fp64_variants(int B);
 int dwt_inverse_fp64_variants(int B);
+// Double-float 2-D FFT of the beta slices (fft_df.cu), for power-of-two 2B:
+// `in` [j][i][k] FP64 -> `out` [j][m][m'] FP64, exp(sign i ...), unnormalised;
+// `work` (n^3 x 16 bytes) may alias `in` or `out`; `rexp`: n^2 ints of scratch.
+bool df_fft_supported(int B);
+cudaError_t launch_df_twiddles(int B, float4 *tw, cudaStream_t s);
+cudaError_t launch_df_fft2(int B, const double2 *in, double2 *out, float4 *work, const float4 *tw, int sign,
+                           int *rexp, cudaStream_t s);
 // FP64-accurate tensor-core DWT / iDWT (dwt_fp64tc.cu); same S layout and
 // flags as the FP64 launchers; need the plan's per-cluster tables.
 cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s,

@@ -196,3 +196,29 @@ def test_one_hot_coefficient_gives_wigner_D():
             back = p.forward(torch.from_numpy(g).to(DEV)).cpu().numpy()
         assert synth.rel_l2(g, oracle.inverse(B, c)) < TOL
         assert synth.rel_l2(back, c) < TOL
+
+
+@pytest.mark.parametrize("scale", [1e-150, 1e150])
+def test_inputs_far_outside_the_fp32_range(scale):
+    """The double-float FFT of power-of-two bandwidths works on the data scaled
+    by the power of two of its largest magnitude, and the digit scales of the
+    contraction come from the data too, so accuracy holds at any FP64 scale."""
+    B = 16
+    grid = synth.random_grid(B, seed=31000) * scale
+    coef = synth.coefficients(B, "gauss_decay", seed=31001) * scale
+    with Plan(B, MODE, device=DEV) as p:
+        f = p.forward(torch.from_numpy(grid).to(DEV), out=nan_coef(B)).cpu().numpy()
+        g = p.inverse(torch.from_numpy(coef).to(DEV), out=nan_grid(B)).cpu().numpy()
+        p.sync()
+    assert synth.rel_l2(f, oracle.forward(B, grid)) < TOL
+    assert synth.rel_l2(g, oracle.inverse(B, coef)) < TOL
+
+
+def test_all_zero_input():
+    B = 8
+    with Plan(B, MODE, device=DEV) as p:
+        f = p.forward(torch.zeros((2 * B,) * 3, dtype=torch.complex128, device=DEV), out=nan_coef(B)).cpu().numpy()
+        g = p.inverse(torch.zeros(synth.num_coeffs(B), dtype=torch.complex128, device=DEV), out=nan_grid(B))
+        p.sync()
+    assert np.all(f == 0)
+    assert torch.all(g == 0)
