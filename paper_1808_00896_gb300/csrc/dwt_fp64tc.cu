@@ -418,7 +418,8 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
             for (int c = 0; c < MAXC; ++c) {
                 if (c >= nchunks || !ok) break;
                 const bool col = c * KC + t < n;
-                for (int g = 0; g < NG; ++g, ++gi) {
+#pragma unroll 1
+                for (int g = 0; g < NG; ++g, ++gi) {  // rolled: the chunk loop around it is unrolled
                     ok = producer_acquire(pb, gi);
                     if (!ok) break;
                     double *st = stage + (gi % kStages) * G * KC + t;
