@@ -339,9 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
     __shared__ ClusterSmem cs;
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) PipeBars pb;
-    __shared__ unsigned long long part[NT / 32][kCols];
     __shared__ int colexp[kCols];
-    __shared__ int wshift;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cidx = blockIdx.x;
     const int2 rep = tb.clusters[cidx];
@@ -356,16 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
 
     load_cluster(tb, m, mp, cs);
     for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
-    if (warp == 0) {
-        // 2^ew max_j w_B(j) < 1 for the weighted seeds
-        unsigned long long mb = 0;
-        if (flags & kApplyW)
-            for (int j = lane; j < n; j += 32) mb = max(mb, abs_bits(tb.w[j]));
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-            mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb, off));
-        if (lane == 0) wshift = (flags & kApplyW) ? -column_exponent(mb) : 0;
-    }
+    const int wshift = (flags & kApplyW) ? -tb.wexp : 0;  // 2^wshift max_j w_B(j) < 1 for the weighted seeds
     cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, rV);  // rV *= sig; ends with a barrier
     const int np = cs.np;
     for (int t = tid; t < L; t += NT) {
@@ -373,20 +362,13 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
         ralpha[t] = a;
         rV[t] = ldexp_bits(rV[t], -a);  // V_l sig_t 2^-alpha_t
     }
-    // Column scales: max over all beta samples of |S_p| (re and im separately).
-    {
-        unsigned long long m0 = 0, m1 = 0;
-        const int p = tid & 7;
-        if (p < np) {
-            const int64_t col = (int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n);
-#pragma unroll 4
-            for (int j = tid >> 3; j < n; j += NT / 8) {
-                const double2 v = S[(int64_t)j * n * n + col];  // all j: the mirror does not change the maximum
-                m0 = max(m0, abs_bits(v.x));
-                m1 = max(m1, abs_bits(v.y));
-            }
-        }
-        reduce_column_exponents<NT>(m0, m1, part, colexp);
+    // Column scales of S_p (re and im), from the per-(m, m') exponents written
+    // by colexp_kernel before this launch (the mirror does not change a maximum).
+    if (tid < kCols) {
+        const int p = tid >> 1;
+        int e = 0;
+        if (p < np) e = tb.colexp[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * 2 + (tid & 1)];
+        colexp[tid] = e == 0 ? 0 : e - 1023 + 1;
     }
     if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
     if (tid == 0) init_pipe(pb);
@@ -599,6 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
         unsigned long long m0 = 0, m1 = 0;
         const int p = tid & 7;
         if (p < np)
+#pragma unroll 4
             for (int t = tid >> 3; t < L; t += NT / 8) {
                 const double2 c = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + t));
                 m0 = max(m0, abs_bits(rG[t] * c.x));
@@ -763,10 +746,34 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+// colexp[(m n + m') 2 + h] = the largest biased FP64 exponent of the real
+// (h = 0) or imaginary (h = 1) part of S[j][m][m'] over j: one thread per
+// (m, m'), loads coalesced across threads, one pass over S.
+__global__ void __launch_bounds__(256) colexp_kernel(const double2 *__restrict__ S, int n, int *__restrict__ colexp) {
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nn; q += (int64_t)gridDim.x * blockDim.x) {
+        int e0 = 0, e1 = 0;
+#pragma unroll 8
+        for (int j = 0; j < n; ++j) {
+            const double2 v = S[j * nn + q];
+            e0 = max(e0, (int)((abs_bits(v.x) >> 52) & 0x7FF));
+            e1 = max(e1, (int)((abs_bits(v.y) >> 52) & 0x7FF));
+        }
+        colexp[2 * q] = e0;
+        colexp[2 * q + 1] = e1;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s, int flags) {
-    if (!tb.seedtab || !tb.rectab) return cudaErrorInvalidValue;
+    if (!tb.seedtab || !tb.rectab || !tb.colexp) return cudaErrorInvalidValue;
+    {
+        const int64_t nn = 4LL * tb.B * tb.B;
+        colexp_kernel<<<(unsigned)std::min<int64_t>((nn + 255) / 256, 152 * 16), 256, 0, s>>>(S, 2 * tb.B, tb.colexp);
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
     constexpr int KC = kProd, A_PLANE = (KC / 8) * (64 * 16 + 16), B_BYTES = (KC / 8) * (kNB * 16 + 16);
     const int B = tb.B;
     const size_t bytes = (size_t)kDig * A_PLANE + 2 * (size_t)B_BYTES +

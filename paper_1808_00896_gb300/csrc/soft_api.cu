@@ -12,6 +12,7 @@
 #include <cufft.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -44,6 +45,8 @@ struct soft_plan_s {
     double *seedtab, *rectab;  // per-cluster seeds and recurrence coefficients, built at creation
     float4 *dftw;              // FP64-TC plans with power-of-two 2B: double-float FFT twiddles (else null)
     int *dfexp;                // and its row scales (n^2 ints)
+    int *colexp;               // FP64-TC plans: per-(m, m') exponents of S for the DWT's column scales
+    int wexp;                  // 2^wexp > max_j w_B(j)
     // Mixed-precision plans: FP32 grid staging and S in layout [m][m'][j], FP32 cuFFT plans.
     float2 *g32, *S32;
     cufftHandle fft32f, fft32i;
@@ -69,6 +72,7 @@ struct soft_plan_s {
         t.clusters = clusters; t.runoff = runoff; t.err = err;
         t.fwd_variant = fwd_variant; t.inv_variant = inv_variant;
         t.seedtab = seedtab; t.rectab = rectab;
+        t.wexp = wexp; t.colexp = colexp;
         return t;
     }
 };
@@ -210,7 +214,7 @@ void free_plan(soft_plan_s *p) {
     if (p->fft32f_made) cufftDestroy(p->fft32f);
     if (p->fft32i_made) cufftDestroy(p->fft32i);
     cudaFree(p->lw); cudaFree(p->g32); cudaFree(p->S32);
-    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->dftw); cudaFree(p->dfexp);
+    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->dftw); cudaFree(p->dfexp); cudaFree(p->colexp);
     cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
     cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
     cudaFree(p->stage_grid); cudaFree(p->stage_coef);
@@ -693,6 +697,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     alloc((void **)&p->lw, sizeof(double) * n);
     alloc((void **)&p->seedtab, sizeof(double) * (size_t)n * cl.size());
     alloc((void **)&p->rectab, sizeof(double) * 3 * (size_t)B * cl.size());
+    if (dtype == SOFT_FP64_TC) alloc((void **)&p->colexp, sizeof(int) * 2 * (size_t)n * n);
     if (dtype == SOFT_FP64_TC && df_fft_supported(B)) {
         alloc((void **)&p->dftw, sizeof(float4) * (size_t)(n / 2));
         alloc((void **)&p->dfexp, sizeof(int) * (size_t)n * n);
@@ -714,6 +719,17 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     if (e == cudaSuccess && p->dftw) e = launch_df_twiddles(B, p->dftw, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+    {
+        // weight scale: the power of two just above the largest quadrature weight
+        std::vector<double> hw((size_t)n);
+        e = cudaMemcpy(hw.data(), p->w, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+        double wmax = 0.0;
+        for (double v : hw) wmax = std::max(wmax, std::fabs(v));
+        int ex = 0;
+        std::frexp(wmax, &ex);  // wmax = f 2^ex, f in [0.5, 1)
+        p->wexp = wmax > 0.0 ? ex : 0;
+    }
 
     long long dims[2] = {n, n};
     const long long slice = (long long)n * n;

@@ -31,6 +31,10 @@ struct Tables {
     // Per-cluster tables built once per plan (null: computed on the fly in each CTA).
     const double *seedtab = nullptr;  // [ncl][2B]  d(l0,m,m';beta_j) of each cluster, unweighted
     const double *rectab = nullptr;   // [ncl][B][3] (A', Ac', sig) of the rescaled recurrence, l = l0 + t
+    int wexp = 0;             // 2^wexp > max_j w_B(j) (the FP64-TC forward's weight scale)
+    int *colexp = nullptr;    // FP64-TC plans: [2B][2B][2] largest biased FP64 exponent of |Re|, |Im| of
+                              //   S(m, m'; .) over the beta samples, index (m mod 2B, m' mod 2B); written
+                              //   before each forward DWT
     int fwd_variant = 0;      // tile-shape variant of the DWT kernel (0 = default)
     int inv_variant = 0;      // tile-shape variant of the iDWT kernel
 };
