@@ -92,3 +92,14 @@ def test_null_plan_handling(lib):
     assert lib.soft_plan_sync(None) == capi.SOFT_ERR_INVALID_ARG
     assert capi.status_string(capi.SOFT_ERR_TIMEOUT) == "SOFT_ERR_TIMEOUT"
     assert capi.status_string(99) == "SOFT_ERR_UNKNOWN"
+
+
+def test_header_enums_match_the_binding():
+    """Every SOFT_* enumerator of include/soft.h has the same value in capi."""
+    import re
+    header = open(os.path.join(os.path.dirname(__file__), "..", "include", "soft.h")).read()
+    found = dict(re.findall(r"\b(SOFT_[A-Z0-9_]+)\s*=\s*(\d+)", header))
+    assert {"SOFT_OK", "SOFT_FP64", "SOFT_MIXED_BF16X3", "SOFT_MIXED_TF32", "SOFT_FP64_TC",
+            "SOFT_ERR_TIMEOUT", "SOFT_ERR_DEVICE"} <= set(found)
+    for name, value in found.items():
+        assert getattr(capi, name) == int(value), name

@@ -222,3 +222,27 @@ def test_all_zero_input():
         p.sync()
     assert np.all(f == 0)
     assert torch.all(g == 0)
+
+
+def test_full_size_B512_against_the_fp64_path():
+    """Every coefficient and every grid value at B = 512 (1024^3 grid) against
+    the plain FP64 GPU path, whose own agreement with the oracle the sampled
+    tests establish at this size.  Norms are taken on the device."""
+    B = 512
+    grid = torch.from_numpy(synth.random_grid(B, seed=32512)).to(DEV)
+    coef = torch.from_numpy(synth.coefficients(B, "gauss_decay", seed=32513)).to(DEV)
+
+    def rel(x, ref):
+        return (torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref)).item()
+
+    with Plan(B, "fp64", device=DEV) as a:
+        fa = a.forward(grid)
+        ga = a.inverse(coef)
+        a.sync()
+    with Plan(B, MODE, device=DEV) as b:
+        fb = b.forward(grid)
+        gb = b.inverse(coef)
+        b.sync()
+    del grid
+    assert rel(fb, fa) < TOL
+    assert rel(gb, ga) < TOL
