@@ -3,9 +3,10 @@
 //
 // Same mathematics as dwt_fp64.cu (Sec. 2.4: f = V_B T_B W_B S per order pair,
 // S = T_B^T f), the same FP64 Wigner-d recurrence (Eq. (Wigner_d_recurrence),
-// rescaled, from the plan's per-cluster tables), FP64 S and FP64 FFTs.  Only
-// the contraction moves, from 16 FP64 FMAs per Wigner-d entry to the tensor
-// cores, by the error-free splitting idea of Ozaki, Ogita, Oishi and Rump
+// rescaled, from the plan's per-cluster tables) and FP64 S (the 2-D FFTs of
+// this mode are in fft_df.cu).  Only the contraction moves, from 16 FP64 FMAs
+// per Wigner-d entry to the tensor cores, by the error-free splitting idea of
+// Ozaki, Ogita, Oishi and Rump
 // ("Error-free transformations of matrix multiplication by using fast routines
 // of matrix multiplication and its applications", Numer. Algorithms 59, 2012):
 //
@@ -31,9 +32,10 @@
 // Scales.  The rescaled recurrence yields e(t) = d(l0+t)/sig_t.  With
 // sig_t = 2^E_t mu_t, mu_t in [1, 2), e(t) 2^E_t = d/mu_t is in [-1, 1]
 // because |d| <= 1.  The forward also carries w_B(j) (folded into the seeds),
-// bounded by 2^-ew.  Data columns (S in the forward, the sign-, V- and
-// mu-folded coefficients in the inverse) are scaled by 2^-F_c, F_c the
-// exponent just above the column's largest magnitude over the contraction.
+// bounded by 2^-ew (ew fixed per plan).  Data columns (S in the forward, the
+// sign-, V- and mu-folded coefficients in the inverse) are scaled by 2^-F_c,
+// F_c the exponent just above the column's largest magnitude over the
+// contraction (for S from one coalesced pass, colexp_kernel, before the DWT).
 //
 // The forward contracts K = 2B <= 1024 beta samples and the inverse K = L <= B
 // degrees, both within the exactness bound for B <= 512.
@@ -200,8 +202,8 @@ __device__ __forceinline__ void put_digits4(unsigned char *plane0, int plane, in
     }
 }
 
-// One K chunk of MMAs (thread 0): for each K step of 16, A digit i (plane i)
-// against B digits 0..6-i into TMEM columns 16 i ..; committed to mbar.
+// One K chunk of MMAs (issued by one thread): for each K step of 16, A digit
+// i (plane i) against B digits 0..6-i into TMEM columns 16 i ..; committed to mbar.
 template <int M>
 __device__ __forceinline__ void issue_levels(uint32_t tmem, const unsigned char *A, int a_plane, uint32_t a_lbo,
                                              const unsigned char *Bop, uint32_t b_lbo, bool first, int ksteps,
@@ -249,8 +251,8 @@ __device__ __forceinline__ void reduce_column_exponents(unsigned long long m0, u
 // Both kernels split the CTA into two warp-specialised groups:
 //   producers  (128 threads, warps 0-3) run the FP64 recurrence -- two FMAs
 //              per Wigner-d entry and nothing else -- and write the raw FP64
-//              values into a double-buffered staging area, 8 rows (forward)
-//              or 8 degrees (inverse) per buffer;
+//              values into a staging ring of kStages groups, 8 rows (forward)
+//              or 8 degrees (inverse) per group;
 //   converters (256 threads, warps 4-11) cut staged values and the data
 //              operand into digits (4 values per thread and task) and run the
 //              epilogue (warps 4-7, one per TMEM lane quarter).  Two converter

@@ -15,7 +15,7 @@
 //
 // Two passes, no extra memory:
 //   rows:    length-n DFT along the contiguous index of every row (n^2 rows),
-//            FP64 or double-float in, double-float out;
+//            FP64 in, double-float out;
 //   columns: length-n DFT along the middle index for every (slice, column),
 //            in place on the double-float data, FP64 out.
 // Each DFT is an in-place radix-2 decimation-in-time transform in shared
@@ -173,9 +173,10 @@ __device__ void dft_stages(float4 *s, int cnt, int n, int logn, const float4 *tw
 
 constexpr int kFftThreads = 256;
 
-// Rows pass: nrows rows of n (contiguous).  FP64 (double2) or double-float
-// (float4) in, double-float out, possibly to the same memory (each block reads
-// its rows before writing them).  `rpb` rows per block.
+// Rows pass: nrows rows of n (contiguous), FP64 in, double-float out,
+// possibly to the same memory (each block reads its rows before writing
+// them); every row scaled by its own power of two, recorded in rexp.  `rpb`
+// rows per block.
 __global__ void __launch_bounds__(kFftThreads) fft_rows_kernel(const double2 *in, float4 *out, int64_t nrows, int n,
                                                                 int logn, int rpb, const float4 *__restrict__ twg,
                                                                 int conj, int *__restrict__ rexp) {
