@@ -82,7 +82,8 @@ const char *soft_last_error(void);
 
 /* Create a plan for bandwidth B on the current CUDA device.  Allocates the
  * plan's device workspace ((2B)^3 complex doubles for S plus small tables),
- * builds the cuFFT plan and computes the quadrature weights of Eq. (weights)
+ * builds the slice-FFT tables (the library's own FFT when 2B is a power of
+ * two, else a cuFFT plan) and computes the quadrature weights of Eq. (weights)
  * and the other beta tables on the device.  *out receives the handle, or NULL
  * on failure.  Returns SOFT_ERR_INVALID_ARG for B < 1 or out == NULL,
  * SOFT_ERR_UNSUPPORTED for B > soft_max_bandwidth() or an unbuilt dtype. */
@@ -101,14 +102,14 @@ soft_status soft_plan_sync(soft_plan p);
 
 /* Forward transform (FSOFT, Sec. 2.4): grid (device, (2B)^3 complex) ->
  * coef (device, B(4B^2-1)/3 complex), f(l,m,m') of Eq. (quadrature):
- *   2-D FFT of every beta slice (cuFFT, exp(+i...)) into the plan's S,
+ *   2-D FFT of every beta slice (exp(+i...)) into the plan's S,
  *   then the DWT f = V_B T_B W_B S for every order pair (m,m').       */
 soft_status soft_forward(soft_plan p, const double *grid, double *coef, void *stream);
 
 /* Inverse transform (iFSOFT, Sec. 2.4): coef -> grid, the function values of
  * Eq. (fourier_representation) on the sampling grid:
  *   iDWT S = T_B^T f for every (m,m') into the plan's S, then 2-D FFT of
- *   every beta slice (cuFFT, exp(-i...)).                               */
+ *   every beta slice (exp(-i...)).                                      */
 soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *stream);
 
 /* Adjoints, for gradients of objectives through the transforms.  Adjoint is

@@ -1,0 +1,246 @@
+// fft_fp64.cu -- batched 2-D FFT of the beta slices in FP64, for the FP64
+// plans (SOFT_FP64) with power-of-two n = 2B (other n keep cuFFT Z2Z).
+//
+// Step 1 of Sec. 2.4 (and its inverse): for every beta sample j the 2-D DFT
+//   S(m, m'; j) = sum_{i,k} f(alpha_i, beta_j, gamma_k) exp(s i (m alpha_i + m' gamma_k)),
+// unnormalised, s = +1 for the forward transform and -1 for the inverse, on
+// the n x n slice.
+//
+// On GB300 the FP64 pipe retires 2 FMA per clock per SM and every other
+// instruction class is far wider, so the cost of an FP64 FFT is its count of
+// FP64 operations.  The butterflies therefore use the FMA factorisation of
+// Goedecker (SIAM J. Sci. Comput. 18, 1997): with the twiddle written as
+// w = mu (1 + i tau), |tau| <= 1, the pair a +- w b costs 6 FMAs instead of a
+// complex product and two complex sums (8 operations).  The first two radix-2
+// stages, whose twiddles are 1 and +-i, are fused into the load as one
+// twiddle-free radix-4 step (16 additions per 4 points).  A length-n DFT thus
+// takes 4 + 3 (log2 n - 2) FP64 operations per point.
+//
+// Two passes:
+//   rows:    length-n DFT along the contiguous index of every row (n^2 rows);
+//   columns: length-n DFT along the middle index for every (slice, column),
+//            in place.
+// Each DFT is an in-place radix-2 decimation-in-time transform in shared
+// memory over bit-reversed input, its stages taken in pairs (radix 4) with a
+// last radix-2 stage when log2 n is odd.
+#include "soft_internal.cuh"
+
+#include <algorithm>
+
+namespace softgb {
+namespace {
+
+// a <- a + w b, b <- a - w b for w in factored form (FftTw64):
+//   swap = 0: w = m (1 + i tau), m1 = m2 = m;
+//   swap = 1: w = i m (1 + i tau), m1 = -m, m2 = m;
+// z = (1 + i tau) b, then a + w b = (a.re + m1 p, a.im + m2 q) with
+// (p, q) = (z.re, z.im), or (z.im, z.re) when swap.
+__device__ __forceinline__ void bfly(double2 &a, double2 &b, const FftTw64 &w) {
+    const double zr = fma(-w.tau, b.y, b.x), zi = fma(w.tau, b.x, b.y);
+    const double p = w.swap ? zi : zr, q = w.swap ? zr : zi;
+    const double ar = a.x, ai = a.y;
+    a = make_double2(fma(w.m1, p, ar), fma(w.m2, q, ai));
+    b = make_double2(fma(-w.m1, p, ar), fma(-w.m2, q, ai));
+}
+
+// The first two radix-2 stages of the decimation in time on
+// x0..x3 = x[t], x[t + n/2], x[t + n/4], x[t + 3n/4] (the contents of
+// bit-reversed positions 4 rev(t) + 0..3): twiddles 1, 1 and exp(+- i pi/2).
+__device__ __forceinline__ void first_radix4(const double2 x0, const double2 x1, const double2 x2, const double2 x3,
+                                             bool conj, double2 *dst) {
+    const double2 a0 = make_double2(x0.x + x1.x, x0.y + x1.y), a1 = make_double2(x0.x - x1.x, x0.y - x1.y);
+    const double2 a2 = make_double2(x2.x + x3.x, x2.y + x3.y), a3 = make_double2(x2.x - x3.x, x2.y - x3.y);
+    dst[0] = make_double2(a0.x + a2.x, a0.y + a2.y);
+    dst[2] = make_double2(a0.x - a2.x, a0.y - a2.y);
+    const double2 u = make_double2(a1.x - a3.y, a1.y + a3.x);  // a1 + i a3
+    const double2 v = make_double2(a1.x + a3.y, a1.y - a3.x);  // a1 - i a3
+    dst[1] = conj ? v : u;
+    dst[3] = conj ? u : v;
+}
+
+// Bit reversal of t within `bits` bits (0 for bits == 0).
+__device__ __forceinline__ int bitrev_n(int t, int bits) {
+    return bits ? (int)(__brev((unsigned)t) >> (32 - bits)) : 0;
+}
+
+// Stages from sub-DFT half-size h = 2^lh on, for `cnt` DFTs of length n held
+// at s + r ld (r < cnt), by all threads of the block: radix-4 passes (stages
+// of sizes 2h and 4h), then one radix-2 stage when one is left.  tw[t] is the
+// factored exp(+- 2 pi i t / n), t < n/2.
+__device__ void stages(double2 *s, int cnt, int ld, int n, int logn, int h, int lh, const FftTw64 *tw) {
+    for (; 4 * h <= n; h *= 4, lh += 2) {
+        const int nq = cnt * (n >> 2);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+            const int row = q >> (logn - 2), qq = q & ((n >> 2) - 1);
+            const int k = qq & (h - 1), g = qq >> lh;
+            double2 *p = s + row * ld + g * 4 * h + k;
+            double2 x0 = p[0], x1 = p[h], x2 = p[2 * h], x3 = p[3 * h];
+            const FftTw64 w1 = tw[k << (logn - 1 - lh)];  // exp(+- 2 pi i k / (2h))
+            bfly(x0, x1, w1);
+            bfly(x2, x3, w1);
+            bfly(x0, x2, tw[k << (logn - 2 - lh)]);        // exp(+- 2 pi i k / (4h))
+            bfly(x1, x3, tw[(k + h) << (logn - 2 - lh)]);  // exp(+- 2 pi i (k + h) / (4h))
+            p[0] = x0;
+            p[h] = x1;
+            p[2 * h] = x2;
+            p[3 * h] = x3;
+        }
+    }
+    if (2 * h == n) {  // one radix-2 stage of size n is left
+        const int nb = cnt * h;
+        __syncthreads();
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const int row = b >> lh, k = b & (h - 1);
+            double2 *p = s + row * ld + k;
+            double2 x0 = p[0], x1 = p[h];
+            bfly(x0, x1, tw[k]);
+            p[0] = x0;
+            p[h] = x1;
+        }
+    }
+    __syncthreads();
+}
+
+constexpr int kThreads = 256;
+constexpr int kTile = 1024;  // elements per block and pass (at least one row or column)
+
+__device__ void load_twiddles(FftTw64 *tw, const FftTw64 *__restrict__ twg, int n) {
+    for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) tw[t] = twg[t];
+}
+
+// Rows pass: nrows rows of n contiguous elements, `rpb` rows per block,
+// in -> out (the same memory is allowed: a block reads its rows before it
+// writes them).
+__global__ void __launch_bounds__(kThreads) fft64_rows_kernel(const double2 *in, double2 *out, int64_t nrows, int n,
+                                                               int logn, int rpb, const FftTw64 *__restrict__ twg,
+                                                               int conj) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    FftTw64 *tw = reinterpret_cast<FftTw64 *>(smraw);                              // [n/2]
+    double2 *s = reinterpret_cast<double2 *>(smraw + sizeof(FftTw64) * (n >> 1));  // [rpb][n]
+    load_twiddles(tw, twg, n);
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int rows = (int)std::min<int64_t>(rpb, nrows - r0);
+    if (logn >= 2) {
+        const int n4 = n >> 2;
+        for (int q = threadIdx.x; q < rows * n4; q += blockDim.x) {
+            const int rl = q / n4, t = q - rl * n4;
+            const double2 *x = in + (r0 + rl) * n + t;
+            first_radix4(x[0], x[n >> 1], x[n4], x[3 * n4], conj != 0, s + rl * n + 4 * bitrev_n(t, logn - 2));
+        }
+        stages(s, rows, n, n, logn, 4, 2, tw);
+    } else {
+        for (int e = threadIdx.x; e < rows * n; e += blockDim.x) s[e] = in[r0 * n + e];  // n = 2: identity order
+        stages(s, rows, n, n, logn, 1, 0, tw);
+    }
+    for (int e = threadIdx.x; e < rows * n; e += blockDim.x) out[r0 * n + e] = s[e];
+}
+
+// Columns pass: for every slice and column, the length-n DFT along the middle
+// index (stride n), `kb` adjacent columns per block, in place.  Shared memory
+// holds column c at s + c (n + 1) (the pad spreads the columns over the banks).
+__global__ void __launch_bounds__(kThreads) fft64_cols_kernel(double2 *data, int n, int logn, int kb,
+                                                               const FftTw64 *__restrict__ twg, int conj) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    FftTw64 *tw = reinterpret_cast<FftTw64 *>(smraw);
+    double2 *s = reinterpret_cast<double2 *>(smraw + sizeof(FftTw64) * (n >> 1));
+    load_twiddles(tw, twg, n);
+    const int ld = n + 1;
+    const int tiles = n / kb;
+    const int64_t js = blockIdx.x / tiles;
+    const int k0 = (blockIdx.x % tiles) * kb;
+    double2 *base = data + js * n * n + k0;
+    if (logn >= 2) {
+        const int n4 = n >> 2;
+        for (int q = threadIdx.x; q < kb * n4; q += blockDim.x) {
+            const int t = q / kb, c = q - t * kb;
+            const double2 *x = base + (int64_t)t * n + c;
+            first_radix4(x[(int64_t)0], x[(int64_t)(n >> 1) * n], x[(int64_t)n4 * n], x[(int64_t)3 * n4 * n],
+                         conj != 0, s + c * ld + 4 * bitrev_n(t, logn - 2));
+        }
+        stages(s, kb, ld, n, logn, 4, 2, tw);
+    } else {
+        for (int e = threadIdx.x; e < kb * n; e += blockDim.x) {
+            const int i = e / kb, c = e - i * kb;
+            s[c * ld + i] = base[(int64_t)i * n + c];
+        }
+        stages(s, kb, ld, n, logn, 1, 0, tw);
+    }
+    for (int e = threadIdx.x; e < kb * n; e += blockDim.x) {
+        const int i = e / kb, c = e - i * kb;
+        base[(int64_t)i * n + c] = s[c * ld + i];
+    }
+}
+
+// tw[t] for t < n/2: exp(sign 2 pi i t / n) in the factored form of bfly().
+__global__ void twiddle64_kernel(int n, int sign, FftTw64 *tw) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n / 2) return;
+    const double a = 2.0 * t / n;
+    const double c = cospi(a), s = sign * sinpi(a);
+    FftTw64 w;
+    w.pad = 0;
+    if (fabs(c) >= fabs(s)) {  // w = c (1 + i s/c)
+        w.swap = 0;
+        w.tau = s / c;
+        w.m1 = c;
+        w.m2 = c;
+    } else {  // w = i s (1 - i c/s)
+        w.swap = 1;
+        w.tau = -c / s;
+        w.m1 = -s;
+        w.m2 = s;
+    }
+    tw[t] = w;
+}
+
+int ilog2_pow2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return (1 << l) == n ? l : -1;
+}
+
+}  // namespace
+
+bool fft64_supported(int B) {
+    const int n = 2 * B;
+    return n >= 2 && n <= 2 * kMaxB && ilog2_pow2(n) >= 0;
+}
+
+size_t fft64_twiddle_count(int B) { return (size_t)2 * (size_t)B; }
+
+cudaError_t launch_fft64_twiddles(int B, FftTw64 *tw, cudaStream_t s) {
+    const int n = 2 * B, half = n / 2;
+    twiddle64_kernel<<<(half + 127) / 128, 128, 0, s>>>(n, +1, tw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    twiddle64_kernel<<<(half + 127) / 128, 128, 0, s>>>(n, -1, tw + half);
+    return cudaGetLastError();
+}
+
+// 2-D DFT of the n slices of n x n: `in` (layout [j][i][k]) -> `out`
+// ([j][m][m']), exp(sign i ...), unnormalised; `out` may be `in`.
+cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw64 *tw, int sign, cudaStream_t s) {
+    const int n = 2 * B, logn = ilog2_pow2(n);
+    if (logn < 1) return cudaErrorInvalidValue;
+    const FftTw64 *t = sign < 0 ? tw + n / 2 : tw;
+    const int conj = sign < 0 ? 1 : 0;
+    const int64_t nrows = (int64_t)n * n;
+    const int rpb = std::max(1, kTile / n);
+    const size_t twb = sizeof(FftTw64) * (size_t)(n / 2);
+    const size_t rbytes = twb + sizeof(double2) * (size_t)rpb * n;
+    cudaError_t e = cudaFuncSetAttribute(fft64_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rbytes);
+    if (e != cudaSuccess) return e;
+    fft64_rows_kernel<<<(unsigned)((nrows + rpb - 1) / rpb), kThreads, rbytes, s>>>(in, out, nrows, n, logn, rpb, t,
+                                                                                      conj);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int kb = std::min(n, std::max(2, kTile / n));
+    const size_t cbytes = twb + sizeof(double2) * (size_t)kb * (n + 1);
+    e = cudaFuncSetAttribute(fft64_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
+    if (e != cudaSuccess) return e;
+    fft64_cols_kernel<<<(unsigned)((int64_t)n * (n / kb)), kThreads, cbytes, s>>>(out, n, logn, kb, t, conj);
+    return cudaGetLastError();
+}
+
+}  // namespace softgb

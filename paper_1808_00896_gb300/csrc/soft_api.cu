@@ -45,6 +45,7 @@ struct soft_plan_s {
     double *seedtab, *rectab;  // per-cluster seeds and recurrence coefficients, built at creation
     float4 *dftw;              // FP64-TC plans with power-of-two 2B: double-float FFT twiddles (else null)
     int *dfexp;                // and its row scales (n^2 ints)
+    FftTw64 *tw64;             // FP64 plans with power-of-two 2B: FP64 FFT twiddles (else null: cuFFT Z2Z)
     int *colexp;               // FP64-TC plans: per-(m, m') exponents of S for the DWT's column scales
     int wexp;                  // 2^wexp > max_j w_B(j)
     // Mixed-precision plans: FP32 grid staging and S in layout [m][m'][j], FP32 cuFFT plans.
@@ -214,7 +215,7 @@ void free_plan(soft_plan_s *p) {
     if (p->fft32f_made) cufftDestroy(p->fft32f);
     if (p->fft32i_made) cufftDestroy(p->fft32i);
     cudaFree(p->lw); cudaFree(p->g32); cudaFree(p->S32);
-    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->dftw); cudaFree(p->dfexp); cudaFree(p->colexp);
+    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->dftw); cudaFree(p->dfexp); cudaFree(p->tw64); cudaFree(p->colexp);
     cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
     cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
     cudaFree(p->stage_grid); cudaFree(p->stage_coef);
@@ -279,6 +280,29 @@ soft_status run_inverse_mixed(soft_plan_s *p, const double *coef, double *grid, 
     return SOFT_OK;
 }
 
+// The 2-D DFTs of the beta slices in the FP64 layouts, in -> out
+// ([j][i][k] <-> [j][m][m']), exp(sign i ...), unnormalised: the library's
+// double-float (FP64-TC plans) or FP64 (FP64 plans) FFT for power-of-two 2B,
+// cuFFT Z2Z otherwise.  For sign < 0 `in` is the plan's S and may be
+// overwritten.
+soft_status slice_fft(soft_plan_s *p, const double2 *in, double2 *out, int sign, cudaStream_t s) {
+    if (p->dftw) {
+        cudaError_t e = launch_df_fft2(p->B, in, out, reinterpret_cast<float4 *>(p->S), p->dftw, sign, p->dfexp, s);
+        return e == cudaSuccess ? SOFT_OK : fail_cuda("double-float FFT launch", e);
+    }
+    if (p->tw64) {
+        cudaError_t e = launch_fft64_2d(p->B, in, out, p->tw64, sign, s);
+        return e == cudaSuccess ? SOFT_OK : fail_cuda("FP64 FFT launch", e);
+    }
+    cufftResult r = cufftSetStream(p->fft, s);
+    if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
+    // cuFFT's INVERSE direction is exp(+i ...), its FORWARD direction exp(-i ...)
+    r = cufftExecZ2Z(p->fft, reinterpret_cast<cufftDoubleComplex *>(const_cast<double2 *>(in)),
+                     reinterpret_cast<cufftDoubleComplex *>(out), sign > 0 ? CUFFT_INVERSE : CUFFT_FORWARD);
+    return r == CUFFT_SUCCESS ? SOFT_OK : fail_cufft(sign > 0 ? "cufftExecZ2Z (forward slices)"
+                                                              : "cufftExecZ2Z (inverse slices)", r);
+}
+
 // flags: kApplyW | kApplyV for the forward transform, 0 for the adjoint of the inverse.
 soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s,
                         int flags = kApplyW | kApplyV) {
@@ -286,18 +310,8 @@ soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaSt
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
     // S(m,m';j) = sum_{i,k} f exp(+i(m alpha_i + m' gamma_k)), unnormalised.
-    if (p->dftw) {
-        cudaError_t e0 = launch_df_fft2(p->B, reinterpret_cast<const double2 *>(grid), p->S,
-                                        reinterpret_cast<float4 *>(p->S), p->dftw, +1, p->dfexp, s);
-        if (e0 != cudaSuccess) return fail_cuda("double-float FFT launch", e0);
-    } else {
-        cufftResult r = cufftSetStream(p->fft, s);
-        if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
-        // cuFFT's INVERSE direction is exp(+i ...)
-        cufftDoubleComplex *in = reinterpret_cast<cufftDoubleComplex *>(const_cast<double *>(grid));
-        r = cufftExecZ2Z(p->fft, in, reinterpret_cast<cufftDoubleComplex *>(p->S), CUFFT_INVERSE);
-        if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (forward slices)", r);
-    }
+    soft_status st = slice_fft(p, reinterpret_cast<const double2 *>(grid), p->S, +1, s);
+    if (st != SOFT_OK) return st;
     if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = launch_dwt_forward_plan(p, p->S, reinterpret_cast<double2 *>(coef), s, flags);
     if (e != cudaSuccess) return fail_cuda("DWT kernel launch", e);
@@ -316,18 +330,8 @@ soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaSt
     if (e != cudaSuccess) return fail_cuda("iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
     // f = sum_{m,m'} S exp(-i(m alpha_i + m' gamma_k)), unnormalised.
-    if (p->dftw) {
-        e = launch_df_fft2(p->B, p->S, reinterpret_cast<double2 *>(grid), reinterpret_cast<float4 *>(p->S), p->dftw,
-                           -1, p->dfexp, s);
-        if (e != cudaSuccess) return fail_cuda("double-float FFT launch", e);
-    } else {
-        cufftResult r = cufftSetStream(p->fft, s);
-        if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
-        // cuFFT's FORWARD direction is exp(-i ...)
-        r = cufftExecZ2Z(p->fft, reinterpret_cast<cufftDoubleComplex *>(p->S),
-                         reinterpret_cast<cufftDoubleComplex *>(grid), CUFFT_FORWARD);
-        if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (inverse slices)", r);
-    }
+    soft_status st = slice_fft(p, p->S, reinterpret_cast<double2 *>(grid), -1, s);
+    if (st != SOFT_OK) return st;
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
 }
@@ -421,11 +425,8 @@ soft_status record_batch(BatchGraph *bg, int n, const void *const *a, const void
             soft_plan_s *p = bg->plans[i];
             double *grid = bg->kind == kBatchCorrelate ? static_cast<double *>(const_cast<void *>(c[i]))
                                                        : static_cast<double *>(const_cast<void *>(b[i]));
-            cufftResult r = cufftSetStream(p->fft, cs);
-            if (r == CUFFT_SUCCESS)
-                r = cufftExecZ2Z(p->fft, reinterpret_cast<cufftDoubleComplex *>(p->S),
-                                 reinterpret_cast<cufftDoubleComplex *>(grid), CUFFT_FORWARD);
-            if (r != CUFFT_SUCCESS) return fail_cufft("cufftExecZ2Z (batched inverse slices)", r);
+            soft_status st = slice_fft(p, p->S, reinterpret_cast<double2 *>(grid), -1, cs);
+            if (st != SOFT_OK) return st;
             if (bg->kind == kBatchCorrelate) {
                 e = launch_argmax_real(reinterpret_cast<const double2 *>(grid), (int64_t)grid_elems(p->B), p->amax_v,
                                        p->amax_i, best_index + i, best_value + i, cs);
@@ -702,6 +703,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
         alloc((void **)&p->dftw, sizeof(float4) * (size_t)(n / 2));
         alloc((void **)&p->dfexp, sizeof(int) * (size_t)n * n);
     }
+    if (dtype == SOFT_FP64 && fft64_supported(B)) alloc((void **)&p->tw64, sizeof(FftTw64) * fft64_twiddle_count(B));
     if (fp64_layout(dtype)) {
         alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
     } else {
@@ -717,6 +719,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     if (e == cudaSuccess) e = launch_log_weights(B, p->w, p->lw, 0);
     if (e == cudaSuccess) e = launch_cluster_tables(p->tables(), p->seedtab, p->rectab, 0);
     if (e == cudaSuccess && p->dftw) e = launch_df_twiddles(B, p->dftw, 0);
+    if (e == cudaSuccess && p->tw64) e = launch_fft64_twiddles(B, p->tw64, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
     {
@@ -735,8 +738,8 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     const long long slice = (long long)n * n;
     size_t work = 0;
     cufftResult r;
-    if (p->dftw) {
-        // FP64-TC with power-of-two 2B: the double-float FFT needs no cuFFT plan.
+    if (p->dftw || p->tw64) {
+        // Power-of-two 2B in the FP64 layouts: the library's own FFTs need no cuFFT plan.
     } else if (fp64_layout(dtype)) {
         // One batched 2-D Z2Z plan over the 2B contiguous beta slices, S in layout [j][m][m'].
         if (cufftCreate(&p->fft) != CUFFT_SUCCESS) { free_plan(p); return SOFT_ERR_CUDA; }
