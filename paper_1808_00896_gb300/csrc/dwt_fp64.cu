@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
     extern __shared__ __align__(16) double smem[];
     __shared__ ClusterSmem cs;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x;
-    const int cidx = blockIdx.x;
+    const int cidx = tb.fwd_order ? tb.fwd_order[blockIdx.x] : (int)blockIdx.x;
     const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 
@@ -129,9 +129,18 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
 
     const int half = tid % TPI, ot = tid / TPI;  // phase-B output (degree in tile, column) and beta part
     static_assert(TPI == 1 || TPI == 2 || TPI == 4, "TPI");
-    const int pt = ot >> 4, pc = ot & 15;
+    // The 16 lanes (x TPI) of a degree cover its 16 real output columns (8
+    // partners x re/im).  With at most 4 partners the upper 8 columns have no
+    // work, and for TPI <= 2 they would be half-warps that still occupy the
+    // FP64 pipe, so there the lanes take 8 columns x 2 halves of the beta range
+    // (combined by one more shuffle) instead.
+    const bool fold = TPI <= 2 && np <= 4;
+    const int pt = ot >> 4, pc = fold ? (ot & 7) : (ot & 15);
     const int pp = pc >> 1;
-    const int jlen = n / TPI, jbeg = half * jlen;  // n = 2B is even
+    const int upper = fold ? (ot >> 3) & 1 : 0;  // second half of the beta range
+    const int parts = fold ? 2 * TPI : TPI, part = half + TPI * upper;
+    const int jlen = (n + parts - 1) / parts, jbeg = min(n, part * jlen);
+    const int jcnt = min(jlen, n - jbeg);
     for (int lb = l0; lb < B; lb += LT) {
         const int nt = min(LT, B - lb);
         // Phase A
@@ -158,16 +167,17 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
             // two chains: the FP64 pipe issues slowly enough that latency is hidden
             double a0 = 0.0, a1 = 0.0;
             int j = 0;
-            for (; j + 2 <= jlen; j += 2) {
+            for (; j + 2 <= jcnt; j += 2) {
                 a0 = fma(Tr[j], Xc[j * 16], a0);
                 a1 = fma(Tr[j + 1], Xc[(j + 1) * 16], a1);
             }
-            if (j < jlen) a0 = fma(Tr[j], Xc[j * 16], a0);
+            if (j < jcnt) a0 = fma(Tr[j], Xc[j * 16], a0);
             acc = a0 + a1;
         }
         if (TPI >= 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         if (TPI >= 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (active && half == 0) {
+        if (fold) acc += __shfl_xor_sync(0xffffffffu, acc, 8 * TPI);  // the two beta halves (fold is CTA-uniform)
+        if (active && half == 0 && upper == 0) {
             const int l = lb + pt;
             const double v = rV[l - l0];
             const bool neg = (cs.sign[pp] < 0.0) != (cs.lpar[pp] && (l & 1));
@@ -283,8 +293,9 @@ __global__ void __launch_bounds__(NT, 1) dwt_inverse_fp64_kernel(Tables tb, cons
                                                                double2 *__restrict__ S, int flags) {
     extern __shared__ __align__(16) double smem[];
     __shared__ ClusterSmem cs;
-    const int2 rep = tb.clusters[blockIdx.x];
-    idwt_cluster<NT, JPT>(tb, coef, S, flags, blockIdx.x, rep.x, rep.y, smem, cs);
+    const int cidx = tb.inv_order ? tb.inv_order[blockIdx.x] : (int)blockIdx.x;
+    const int2 rep = tb.clusters[cidx];
+    idwt_cluster<NT, JPT>(tb, coef, S, flags, cidx, rep.x, rep.y, smem, cs);
 }
 
 // One CTA per cluster: the rescaled recurrence coefficients and the seeds of
@@ -310,10 +321,13 @@ __global__ void __launch_bounds__(256) cluster_tables_kernel(Tables tb, double *
 
 // Persistent inverse DWT over a batch of FP64 transforms of bandwidth <= 128:
 // one CTA per SM slot pulls (transform, cluster) items, heaviest first, from an
-// atomic counter until the list is exhausted.  No CTA waits on another.
-__global__ void __launch_bounds__(256) idwt_fp64_persistent_kernel(const BatchXform *__restrict__ xf,
-                                                                   const int2 *__restrict__ items, int nitems,
-                                                                   int *__restrict__ counter) {
+// atomic counter until the list is exhausted.  No CTA waits on another.  The
+// tile shape (NT threads x JPT beta samples) is the single-transform iDWT's
+// for the batch's largest bandwidth, so NT * JPT covers its 2B samples.
+template <int NT, int JPT>
+__global__ void __launch_bounds__(NT) idwt_fp64_persistent_kernel(const BatchXform *__restrict__ xf,
+                                                                  const int2 *__restrict__ items, int nitems,
+                                                                  int *__restrict__ counter) {
     extern __shared__ __align__(16) double smem[];
     __shared__ ClusterSmem cs;
     __shared__ int item;
@@ -325,7 +339,7 @@ __global__ void __launch_bounds__(256) idwt_fp64_persistent_kernel(const BatchXf
         const int2 w = items[it];
         const BatchXform &X = xf[w.x];
         const int2 rep = X.tb.clusters[w.y];
-        idwt_cluster<256, 1>(X.tb, X.coef, X.S, X.flags, w.y, rep.x, rep.y, smem, cs);
+        idwt_cluster<NT, JPT>(X.tb, X.coef, X.S, X.flags, w.y, rep.x, rep.y, smem, cs);
         __syncthreads();  // smem and `item` are reused by the next item
     }
 }
@@ -404,21 +418,31 @@ cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 
     return run_forward<256, 4, 2>(tb, S, c, s, flags);
 }
 
-cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
-                                        cudaStream_t s) {
+template <int NT, int JPT>
+cudaError_t run_idwt_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
+                                cudaStream_t s) {
     const size_t bytes = sizeof(double) * ((size_t)maxB * 16 + 4 * (size_t)maxB);
-    cudaError_t e = cudaFuncSetAttribute(idwt_fp64_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(idwt_fp64_persistent_kernel<NT, JPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, idwt_fp64_persistent_kernel, 256, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, idwt_fp64_persistent_kernel<NT, JPT>, NT, bytes);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
-    idwt_fp64_persistent_kernel<<<grid, 256, bytes, s>>>(xf, items, nitems, counter);
+    idwt_fp64_persistent_kernel<NT, JPT><<<grid, NT, bytes, s>>>(xf, items, nitems, counter);
     return cudaGetLastError();
+}
+
+cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
+                                        cudaStream_t s) {
+    const int n = 2 * maxB;
+    if (n <= 64) return run_idwt_persistent<32, 2>(xf, items, nitems, counter, maxB, s);
+    if (n <= 128) return run_idwt_persistent<64, 2>(xf, items, nitems, counter, maxB, s);
+    if (n <= 256) return run_idwt_persistent<256, 1>(xf, items, nitems, counter, maxB, s);
+    return cudaErrorInvalidValue;
 }
 
 int dwt_inverse_fp64_variants(int B) { return 2 * B <= 256 ? 2 : 2 * B <= 512 ? 3 : 2; }

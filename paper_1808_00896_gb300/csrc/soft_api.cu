@@ -43,6 +43,7 @@ struct soft_plan_s {
     bool fft_made;
     double *lw;  // log w_B(j)
     double *seedtab, *rectab;  // per-cluster seeds and recurrence coefficients, built at creation
+    int *fwd_order, *inv_order;  // FP64 plans: the DWT and iDWT dispatch orders (Tables)
     float4 *dftw;              // FP64-TC plans with power-of-two 2B: double-float FFT twiddles (else null)
     int *dfexp;                // and its row scales (n^2 ints)
     FftTw64 *tw64;             // FP64 plans with power-of-two 2B: FP64 FFT twiddles (else null: cuFFT Z2Z)
@@ -72,7 +73,7 @@ struct soft_plan_s {
         t.B = B; t.ncl = ncl; t.w = w; t.lw = lw; t.cosb = cosb; t.lcos = lcos; t.lsin = lsin; t.lfact = lfact;
         t.clusters = clusters; t.runoff = runoff; t.err = err;
         t.fwd_variant = fwd_variant; t.inv_variant = inv_variant;
-        t.seedtab = seedtab; t.rectab = rectab;
+        t.seedtab = seedtab; t.rectab = rectab; t.fwd_order = fwd_order; t.inv_order = inv_order;
         t.wexp = wexp; t.colexp = colexp;
         return t;
     }
@@ -215,7 +216,7 @@ void free_plan(soft_plan_s *p) {
     if (p->fft32f_made) cufftDestroy(p->fft32f);
     if (p->fft32i_made) cufftDestroy(p->fft32i);
     cudaFree(p->lw); cudaFree(p->g32); cudaFree(p->S32);
-    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->dftw); cudaFree(p->dfexp); cudaFree(p->tw64); cudaFree(p->colexp);
+    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->fwd_order); cudaFree(p->inv_order); cudaFree(p->dftw); cudaFree(p->dfexp); cudaFree(p->tw64); cudaFree(p->colexp);
     cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
     cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
     cudaFree(p->stage_grid); cudaFree(p->stage_coef);
@@ -570,7 +571,8 @@ soft_status run_batch(int kind, int n, const soft_plan *plans, const void *const
                 for (int cidx = 0; cidx < p->ncl; ++cidx) {
                     const int2 cl = p->h_clusters[cidx];
                     const int np = (cl.x == 0 && cl.y == 0) ? 1 : (cl.y == 0 || cl.x == cl.y) ? 4 : 8;
-                    items.push_back({(int64_t)(p->B - cl.x) * (2 * p->B) * np, make_int2(i, cidx)});
+                    // FP64 work of the item: 2B samples x (B - m) degrees x (real columns + 2)
+                    items.push_back({(int64_t)(p->B - cl.x) * (2 * p->B) * (np == 8 ? 18 : 10), make_int2(i, cidx)});
                 }
         }
         std::stable_sort(items.begin(), items.end(),
@@ -698,6 +700,8 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     alloc((void **)&p->lw, sizeof(double) * n);
     alloc((void **)&p->seedtab, sizeof(double) * (size_t)n * cl.size());
     alloc((void **)&p->rectab, sizeof(double) * 3 * (size_t)B * cl.size());
+    if (dtype == SOFT_FP64) alloc((void **)&p->fwd_order, sizeof(int) * cl.size());
+    if (dtype == SOFT_FP64) alloc((void **)&p->inv_order, sizeof(int) * cl.size());
     if (dtype == SOFT_FP64_TC) alloc((void **)&p->colexp, sizeof(int) * 2 * (size_t)n * n);
     if (dtype == SOFT_FP64_TC && df_fft_supported(B)) {
         alloc((void **)&p->dftw, sizeof(float4) * (size_t)(n / 2));
@@ -713,6 +717,28 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
 
     e = cudaMemcpy(p->clusters, cl.data(), sizeof(int2) * cl.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && p->fwd_order && p->inv_order) {
+        // Longest first by each FP64 kernel's FP64 time per cluster.  The
+        // forward DWT spends the same time per degree on 4 partners as on 8 (its
+        // idle half-warps still occupy the FP64 pipe): order by degree count,
+        // 8 partners first at equal count.  The iDWT walks 16 real columns for
+        // 8 partners and 8 otherwise, plus 2 FMAs of recurrence per degree.
+        auto partners = [](const int2 &c) { return (c.x == 0 && c.y == 0) ? 1 : (c.y == 0 || c.x == c.y) ? 4 : 8; };
+        auto longest_first = [&](auto cost) {
+            std::vector<int> ord(cl.size());
+            for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost(cl[a]) > cost(cl[b]); });
+            return ord;
+        };
+        const std::vector<int> fo = longest_first([&](const int2 &c) {
+            return (int64_t)(B - c.x) * 16 + partners(c);
+        });
+        const std::vector<int> io = longest_first([&](const int2 &c) {
+            return (int64_t)(B - c.x) * (partners(c) == 8 ? 18 : 10);
+        });
+        e = cudaMemcpy(p->fwd_order, fo.data(), sizeof(int) * fo.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->inv_order, io.data(), sizeof(int) * io.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemcpy(p->runoff, ro.data(), sizeof(int64_t) * ro.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
     if (e == cudaSuccess) e = launch_tables(B, p->w, p->cosb, p->lcos, p->lsin, p->lfact, 0);

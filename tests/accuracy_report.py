@@ -21,7 +21,7 @@ def main(bandwidths):
         coef = synth.coefficients(B, "gauss_decay", seed=123 + B)
         g_ref = oracle.inverse(B, coef)
         f_ref = oracle.forward(B, g_ref)
-        for mode in ("fp64", "bf16x3", "tf32"):
+        for mode in ("fp64", "fp64_tc", "bf16x3", "tf32"):
             with Plan(B, mode, device=dev) as p:
                 f = p.forward(torch.from_numpy(g_ref).to(dev)).cpu().numpy()
                 g = p.inverse(torch.from_numpy(coef).to(dev)).cpu().numpy()

@@ -18,8 +18,9 @@ def _built():
     assert torch.cuda.is_available(), "GPU tests need CUDA"
 
 
-@pytest.mark.parametrize("B,mode", [(16, "fp64"), (100, "fp64"), (200, "fp64"), (400, "fp64"), (30, "bf16x3"),
-                                    (200, "tf32")])
+# Odd B (129, 257) give 2B samples that 4 threads per output cannot split evenly.
+@pytest.mark.parametrize("B,mode", [(16, "fp64"), (100, "fp64"), (129, "fp64"), (200, "fp64"), (257, "fp64"),
+                                    (400, "fp64"), (30, "bf16x3"), (200, "tf32")])
 def test_variants_agree(B, mode):
     grid = torch.from_numpy(synth.random_grid(B, seed=B)).to(DEV)
     coef = torch.from_numpy(synth.coefficients(B, "gauss_decay", seed=B + 1)).to(DEV)
