@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
     __shared__ __align__(8) PipeBars pb;
     __shared__ int colexp[kCols];
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int cidx = blockIdx.x;
+    const int cidx = tb.fwd_order ? tb.fwd_order[blockIdx.x] : (int)blockIdx.x;
     const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 
@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
     __shared__ unsigned long long part[NT / 32][kCols];
     __shared__ int colexp[kCols];
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5;
-    const int cidx = blockIdx.x;
+    const int cidx = tb.inv_order ? tb.inv_order[blockIdx.x] : (int)blockIdx.x;
     const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 

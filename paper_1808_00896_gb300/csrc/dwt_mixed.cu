@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
     __shared__ __align__(8) uint64_t mbar;
     const Tables &tb = mb.tb;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int cidx = blockIdx.x;
+    const int cidx = tb.fwd_order ? tb.fwd_order[blockIdx.x] : (int)blockIdx.x;
     const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     __shared__ __align__(8) uint64_t mbar;
     const Tables &tb = mb.tb;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5;
-    const int cidx = blockIdx.x;
+    const int cidx = tb.inv_order ? tb.inv_order[blockIdx.x] : (int)blockIdx.x;
     const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 

@@ -43,7 +43,7 @@ struct soft_plan_s {
     bool fft_made;
     double *lw;  // log w_B(j)
     double *seedtab, *rectab;  // per-cluster seeds and recurrence coefficients, built at creation
-    int *fwd_order, *inv_order;  // FP64 plans: the DWT and iDWT dispatch orders (Tables)
+    int *fwd_order, *inv_order;  // FP64 and FP64-TC plans: the DWT and iDWT dispatch orders (Tables)
     float4 *dftw;              // FP64-TC plans with power-of-two 2B: double-float FFT twiddles (else null)
     int *dfexp;                // and its row scales (n^2 ints)
     FftTw64 *tw64;             // FP64 plans with power-of-two 2B: FP64 FFT twiddles (else null: cuFFT Z2Z)
@@ -700,8 +700,10 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     alloc((void **)&p->lw, sizeof(double) * n);
     alloc((void **)&p->seedtab, sizeof(double) * (size_t)n * cl.size());
     alloc((void **)&p->rectab, sizeof(double) * 3 * (size_t)B * cl.size());
-    if (dtype == SOFT_FP64) alloc((void **)&p->fwd_order, sizeof(int) * cl.size());
-    if (dtype == SOFT_FP64) alloc((void **)&p->inv_order, sizeof(int) * cl.size());
+    // Mixed plans keep the shared order: their forward tile spans every degree
+    // of a cluster up to B = 128, so their cost hardly depends on the degree count.
+    if (fp64_layout(dtype)) alloc((void **)&p->fwd_order, sizeof(int) * cl.size());
+    if (fp64_layout(dtype)) alloc((void **)&p->inv_order, sizeof(int) * cl.size());
     if (dtype == SOFT_FP64_TC) alloc((void **)&p->colexp, sizeof(int) * 2 * (size_t)n * n);
     if (dtype == SOFT_FP64_TC && df_fft_supported(B)) {
         alloc((void **)&p->dftw, sizeof(float4) * (size_t)(n / 2));
@@ -718,11 +720,13 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
 
     e = cudaMemcpy(p->clusters, cl.data(), sizeof(int2) * cl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && p->fwd_order && p->inv_order) {
-        // Longest first by each FP64 kernel's FP64 time per cluster.  The
-        // forward DWT spends the same time per degree on 4 partners as on 8 (its
-        // idle half-warps still occupy the FP64 pipe): order by degree count,
-        // 8 partners first at equal count.  The iDWT walks 16 real columns for
-        // 8 partners and 8 otherwise, plus 2 FMAs of recurrence per degree.
+        // Longest first by each kernel's time per cluster.  The FP64 forward DWT
+        // spends the same time per degree on 4 partners as on 8 (its idle
+        // half-warps would still occupy the FP64 pipe, and it folds them away),
+        // and the FP64-TC kernels always compute 16 columns: order by degree
+        // count, 8 partners first at equal count.  The FP64 iDWT walks 16 real
+        // columns for 8 partners and 8 otherwise, plus 2 FMAs of recurrence per
+        // degree.
         auto partners = [](const int2 &c) { return (c.x == 0 && c.y == 0) ? 1 : (c.y == 0 || c.x == c.y) ? 4 : 8; };
         auto longest_first = [&](auto cost) {
             std::vector<int> ord(cl.size());
@@ -733,9 +737,9 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
         const std::vector<int> fo = longest_first([&](const int2 &c) {
             return (int64_t)(B - c.x) * 16 + partners(c);
         });
-        const std::vector<int> io = longest_first([&](const int2 &c) {
+        const std::vector<int> io = dtype == SOFT_FP64 ? longest_first([&](const int2 &c) {
             return (int64_t)(B - c.x) * (partners(c) == 8 ? 18 : 10);
-        });
+        }) : fo;
         e = cudaMemcpy(p->fwd_order, fo.data(), sizeof(int) * fo.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->inv_order, io.data(), sizeof(int) * io.size(), cudaMemcpyHostToDevice);
     }

@@ -36,7 +36,7 @@ struct Tables {
                               //   S(m, m'; .) over the beta samples, index (m mod 2B, m' mod 2B); written
                               //   before each forward DWT
     int fwd_variant = 0;      // tile-shape variant of the DWT kernel (0 = default)
-    // [ncl] dispatch orders of the FP64 DWT and iDWT kernels (CTA b handles
+    // [ncl] dispatch orders of the DWT and iDWT kernels (CTA b handles
     // cluster fwd_order[b] / inv_order[b]; null: cluster b), longest first by
     // each kernel's own cost per cluster.
     const int *fwd_order = nullptr;
