@@ -204,7 +204,13 @@ soft_status soft_dwt_forward_noalloc(int B, const double *S, double *coef, void 
 /* Host-buffer forms: grid_host / coef_host are HOST pointers (pageable or
  * pinned).  The call copies the input to plan-owned device staging buffers
  * (allocated on first use), runs the transform on `stream`, copies the
- * result back and synchronises the stream before returning. */
+ * result back and synchronises the stream before returning.  For SOFT_FP64
+ * and SOFT_FP64_TC plans with power-of-two 2B the grid's copies overlap the
+ * 2-D FFTs, in chunks of beta slices, on a second stream that the plan owns
+ * (created on first use); the call then synchronises both streams before it
+ * returns, also after an error, so no copy into the caller's buffers is left
+ * in flight.  Results are identical to soft_forward / soft_inverse on the
+ * same data.  Overlapping the copies needs pinned host memory. */
 soft_status soft_forward_host(soft_plan p, const double *grid_host, double *coef_host, void *stream);
 soft_status soft_inverse_host(soft_plan p, const double *coef_host, double *grid_host, void *stream);
 

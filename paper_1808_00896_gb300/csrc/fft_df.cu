@@ -295,16 +295,17 @@ cudaError_t launch_df_twiddles(int B, float4 *tw, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// 2-D DFT of the 2B slices of n x n: `in` (FP64, layout [j][i][k]) -> `out`
-// (FP64, [j][m][m']), exp(sign i ...), unnormalised.  `work` is a
-// double-float buffer of n^3 float4 (16 bytes each); it may be `in` or `out`.
-// `rexp` is n^2 ints of scratch (the row scales).
+// 2-D DFT of `nslices` consecutive n x n slices (n = 2B): `in` (FP64, layout
+// [j][i][k]) -> `out` (FP64, [j][m][m']), exp(sign i ...), unnormalised.
+// `work` is a double-float buffer of nslices n^2 float4 (16 bytes each); it
+// may be `in` or `out`.  `rexp` is nslices n ints of scratch (the row
+// scales).  All four point at the first slice of the range.
 cudaError_t launch_df_fft2(int B, const double2 *in, double2 *out, float4 *work, const float4 *tw, int sign,
-                           int *rexp, cudaStream_t s) {
+                           int *rexp, cudaStream_t s, int nslices) {
     const int n = 2 * B, logn = ilog2_exact(n);
-    if (logn < 1) return cudaErrorInvalidValue;
+    if (logn < 1 || nslices < 1 || nslices > n) return cudaErrorInvalidValue;
     const int conj = sign < 0 ? 1 : 0;
-    const int64_t nrows = (int64_t)n * n;
+    const int64_t nrows = (int64_t)nslices * n;
     const int rpb = std::max(1, 512 / n);
     const size_t rbytes = sizeof(float4) * ((size_t)n / 2 + (size_t)rpb * n);
     cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rbytes);
@@ -317,8 +318,8 @@ cudaError_t launch_df_fft2(int B, const double2 *in, double2 *out, float4 *work,
     const size_t cbytes = sizeof(float4) * ((size_t)n / 2 + (size_t)kb * n);
     e = cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
     if (e != cudaSuccess) return e;
-    fft_cols_kernel<<<(unsigned)((int64_t)n * (n / kb)), kFftThreads, cbytes, s>>>(work, out, n, logn, kb, tw, conj,
-                                                                                    rexp);
+    fft_cols_kernel<<<(unsigned)((int64_t)nslices * (n / kb)), kFftThreads, cbytes, s>>>(work, out, n, logn, kb, tw,
+                                                                                          conj, rexp);
     return cudaGetLastError();
 }
 

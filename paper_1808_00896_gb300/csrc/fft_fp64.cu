@@ -218,14 +218,16 @@ cudaError_t launch_fft64_twiddles(int B, FftTw64 *tw, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// 2-D DFT of the n slices of n x n: `in` (layout [j][i][k]) -> `out`
-// ([j][m][m']), exp(sign i ...), unnormalised; `out` may be `in`.
-cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw64 *tw, int sign, cudaStream_t s) {
+// 2-D DFT of `nslices` consecutive n x n slices (n = 2B): `in` (layout
+// [j][i][k]) -> `out` ([j][m][m']), exp(sign i ...), unnormalised; `out` may
+// be `in`.  Both point at the first slice of the range.
+cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw64 *tw, int sign, cudaStream_t s,
+                            int nslices) {
     const int n = 2 * B, logn = ilog2_pow2(n);
-    if (logn < 1) return cudaErrorInvalidValue;
+    if (logn < 1 || nslices < 1 || nslices > n) return cudaErrorInvalidValue;
     const FftTw64 *t = sign < 0 ? tw + n / 2 : tw;
     const int conj = sign < 0 ? 1 : 0;
-    const int64_t nrows = (int64_t)n * n;
+    const int64_t nrows = (int64_t)nslices * n;
     const int rpb = std::max(1, kTile / n);
     const size_t twb = sizeof(FftTw64) * (size_t)(n / 2);
     const size_t rbytes = twb + sizeof(double2) * (size_t)rpb * n;
@@ -239,7 +241,7 @@ cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw6
     const size_t cbytes = twb + sizeof(double2) * (size_t)kb * (n + 1);
     e = cudaFuncSetAttribute(fft64_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
     if (e != cudaSuccess) return e;
-    fft64_cols_kernel<<<(unsigned)((int64_t)n * (n / kb)), kThreads, cbytes, s>>>(out, n, logn, kb, t, conj);
+    fft64_cols_kernel<<<(unsigned)((int64_t)nslices * (n / kb)), kThreads, cbytes, s>>>(out, n, logn, kb, t, conj);
     return cudaGetLastError();
 }
 

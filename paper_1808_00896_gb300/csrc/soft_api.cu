@@ -54,6 +54,13 @@ struct soft_plan_s {
     cufftHandle fft32f, fft32i;
     bool fft32f_made, fft32i_made;
     double2 *stage_grid, *stage_coef;  // for the host-buffer entry points, allocated on first use
+    // Host-buffer entry points with the library's own slice FFT: a copy stream and
+    // events that pipeline the grid's host copies with the FFTs, slice chunk by
+    // slice chunk (created on first use).
+    static constexpr int kHostChunks = 8;
+    cudaStream_t copy_stream;
+    bool copy_made;
+    cudaEvent_t hev[kHostChunks + 1];
     double2 *corr_coef;                // correlation coefficients, allocated on first use
     double *amax_v;                    // arg-max partial results (argmax_parts() each)
     int64_t *amax_i;
@@ -212,6 +219,9 @@ void free_plan(soft_plan_s *p) {
     if (!p) return;
     for (auto &e : p->events)
         if (e) cudaEventDestroy(e);
+    for (auto &e : p->hev)
+        if (e) cudaEventDestroy(e);
+    if (p->copy_made) cudaStreamDestroy(p->copy_stream);
     if (p->fft_made) cufftDestroy(p->fft);
     if (p->fft32f_made) cufftDestroy(p->fft32f);
     if (p->fft32i_made) cufftDestroy(p->fft32i);
@@ -285,16 +295,25 @@ soft_status run_inverse_mixed(soft_plan_s *p, const double *coef, double *grid, 
 // ([j][i][k] <-> [j][m][m']), exp(sign i ...), unnormalised: the library's
 // double-float (FP64-TC plans) or FP64 (FP64 plans) FFT for power-of-two 2B,
 // cuFFT Z2Z otherwise.  For sign < 0 `in` is the plan's S and may be
-// overwritten.
-soft_status slice_fft(soft_plan_s *p, const double2 *in, double2 *out, int sign, cudaStream_t s) {
+// overwritten.  Slices j0 .. j0 + nsl - 1 only (`in` and `out` point at slice
+// 0); a partial range needs the library's own FFT (own_slice_fft()).
+bool own_slice_fft(const soft_plan_s *p) { return p->dftw || p->tw64; }
+
+soft_status slice_fft(soft_plan_s *p, const double2 *in, double2 *out, int sign, cudaStream_t s, int j0 = 0,
+                      int nsl = -1) {
+    const int n = 2 * p->B;
+    if (nsl < 0) nsl = n;
+    const size_t off = (size_t)j0 * n * n;
     if (p->dftw) {
-        cudaError_t e = launch_df_fft2(p->B, in, out, reinterpret_cast<float4 *>(p->S), p->dftw, sign, p->dfexp, s);
+        cudaError_t e = launch_df_fft2(p->B, in + off, out + off, reinterpret_cast<float4 *>(p->S) + off, p->dftw, sign,
+                                       p->dfexp + (size_t)j0 * n, s, nsl);
         return e == cudaSuccess ? SOFT_OK : fail_cuda("double-float FFT launch", e);
     }
     if (p->tw64) {
-        cudaError_t e = launch_fft64_2d(p->B, in, out, p->tw64, sign, s);
+        cudaError_t e = launch_fft64_2d(p->B, in + off, out + off, p->tw64, sign, s, nsl);
         return e == cudaSuccess ? SOFT_OK : fail_cuda("FP64 FFT launch", e);
     }
+    if (j0 != 0 || nsl != n) return SOFT_ERR_INVALID_ARG;
     cufftResult r = cufftSetStream(p->fft, s);
     if (r != CUFFT_SUCCESS) return fail_cufft("cufftSetStream", r);
     // cuFFT's INVERSE direction is exp(+i ...), its FORWARD direction exp(-i ...)
@@ -304,14 +323,94 @@ soft_status slice_fft(soft_plan_s *p, const double2 *in, double2 *out, int sign,
                                                               : "cufftExecZ2Z (inverse slices)", r);
 }
 
+soft_status ensure_copy_stream(soft_plan_s *p) {
+    if (!p->copy_made) {
+        const cudaError_t e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail_cuda("copy stream", e);
+        p->copy_made = true;
+    }
+    for (auto &ev : p->hev) {
+        if (ev) continue;
+        const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) { ev = nullptr; return fail_cuda("copy events", e); }
+    }
+    return SOFT_OK;
+}
+
+// Slice chunk c of K: slices [c n / K, (c + 1) n / K).
+int chunk_begin(int n, int K, int c) { return (int)((int64_t)c * n / K); }
+
+// Number of slice chunks of the host pipeline: chunks of at least 8 MiB for
+// the FP64 FFT and 32 MiB for the double-float FFT (whose columns pass takes
+// up to 32 columns per block, so smaller chunks leave SMs idle), at most
+// kHostChunks.  Smaller chunks measured slower: each one costs launches and
+// event round trips.
+int host_chunks(const soft_plan_s *p) {
+    const int n = 2 * p->B;
+    const double bytes = 16.0 * (double)n * n * n;
+    const double per = (p->dftw ? 32.0 : 8.0) * 1024 * 1024;
+    return std::max(1, std::min(std::min(soft_plan_s::kHostChunks, n), (int)(bytes / per)));
+}
+
+// Forward FFT stage fed from host memory: chunk c of the grid is copied to
+// the device buffer `grid` on the plan's copy stream, and its slices'
+// FFTs run on `s` as soon as that copy lands, while the next chunk copies.
+soft_status forward_fft_from_host(soft_plan_s *p, const double *grid_host, double2 *grid, cudaStream_t s) {
+    const int n = 2 * p->B, K = host_chunks(p);
+    const size_t slice = (size_t)n * n;
+    cudaStream_t cs = p->copy_stream;
+    // the copies overwrite `grid`: they wait for the work already queued on s
+    cudaError_t e = cudaEventRecord(p->hev[K], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->hev[K], 0);
+    if (e != cudaSuccess) return fail_cuda("copy stream ordering", e);
+    for (int c = 0; c < K; ++c) {
+        const int j0 = chunk_begin(n, K, c), j1 = chunk_begin(n, K, c + 1);
+        e = cudaMemcpyAsync(grid + j0 * slice, reinterpret_cast<const double2 *>(grid_host) + j0 * slice,
+                            sizeof(double2) * slice * (j1 - j0), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(p->hev[c], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->hev[c], 0);
+        if (e != cudaSuccess) return fail_cuda("grid chunk copy", e);
+        soft_status st = slice_fft(p, grid, p->S, +1, s, j0, j1 - j0);
+        if (st != SOFT_OK) return st;
+    }
+    return SOFT_OK;
+}
+
+// Inverse FFT stage drained to host memory: the FFTs of chunk c's slices
+// run on `s` into the device buffer `grid`, and the chunk is copied to the
+// host on the copy stream while the next chunk's FFTs run; `s` then waits
+// for the last copy.
+soft_status inverse_fft_to_host(soft_plan_s *p, double2 *grid, double *grid_host, cudaStream_t s) {
+    const int n = 2 * p->B, K = host_chunks(p);
+    const size_t slice = (size_t)n * n;
+    cudaStream_t cs = p->copy_stream;
+    for (int c = 0; c < K; ++c) {
+        const int j0 = chunk_begin(n, K, c), j1 = chunk_begin(n, K, c + 1);
+        soft_status st = slice_fft(p, p->S, grid, -1, s, j0, j1 - j0);
+        if (st != SOFT_OK) return st;
+        cudaError_t e = cudaEventRecord(p->hev[c], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->hev[c], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(reinterpret_cast<double2 *>(grid_host) + j0 * slice, grid + j0 * slice,
+                                sizeof(double2) * slice * (j1 - j0), cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return fail_cuda("grid chunk copy", e);
+    }
+    cudaError_t e = cudaEventRecord(p->hev[K], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->hev[K], 0);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("copy stream ordering", e);
+}
+
 // flags: kApplyW | kApplyV for the forward transform, 0 for the adjoint of the inverse.
+// grid_host: when set, `grid` is a device staging buffer that the FFT stage
+// fills from this host copy of the grid, chunk by chunk.
 soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaStream_t s,
-                        int flags = kApplyW | kApplyV) {
+                        int flags = kApplyW | kApplyV, const double *grid_host = nullptr) {
     if (!fp64_layout(p->dtype)) return run_forward_mixed(p, grid, coef, s, flags);
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
     // S(m,m';j) = sum_{i,k} f exp(+i(m alpha_i + m' gamma_k)), unnormalised.
-    soft_status st = slice_fft(p, reinterpret_cast<const double2 *>(grid), p->S, +1, s);
+    soft_status st = grid_host ? forward_fft_from_host(p, grid_host, reinterpret_cast<double2 *>(const_cast<double *>(grid)), s)
+                               : slice_fft(p, reinterpret_cast<const double2 *>(grid), p->S, +1, s);
     if (st != SOFT_OK) return st;
     if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = launch_dwt_forward_plan(p, p->S, reinterpret_cast<double2 *>(coef), s, flags);
@@ -321,7 +420,10 @@ soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaSt
 }
 
 // flags: 0 for the inverse transform, kApplyV | kApplyW for the adjoint of the forward.
-soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s, int flags = 0) {
+// grid_host: when set, the FFT stage also copies `grid` (a device staging
+// buffer) to this host buffer, chunk by chunk.
+soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaStream_t s, int flags = 0,
+                        double *grid_host = nullptr) {
     if (!fp64_layout(p->dtype)) return run_inverse_mixed(p, coef, grid, s, flags);
     cudaEvent_t *ev = timing_slot(p, 1);
     if (ev) cudaEventRecord(ev[0], s);
@@ -331,7 +433,8 @@ soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaSt
     if (e != cudaSuccess) return fail_cuda("iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
     // f = sum_{m,m'} S exp(-i(m alpha_i + m' gamma_k)), unnormalised.
-    soft_status st = slice_fft(p, p->S, reinterpret_cast<double2 *>(grid), -1, s);
+    soft_status st = grid_host ? inverse_fft_to_host(p, reinterpret_cast<double2 *>(grid), grid_host, s)
+                               : slice_fft(p, p->S, reinterpret_cast<double2 *>(grid), -1, s);
     if (st != SOFT_OK) return st;
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
@@ -925,21 +1028,47 @@ soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *s
     return cuda_status(e);
 }
 
+// With the library's own slice FFT (FP64 and FP64-TC plans, power-of-two 2B)
+// the grid's host copy is pipelined with the FFTs in slice chunks on the
+// plan's copy stream; otherwise the copy, the transform and the copy back run
+// in sequence on `stream`.  Both synchronise `stream` (and the copy stream)
+// before returning, also after an error, so no copy into the caller's host
+// buffers is left in flight.
+soft_status finish_host_call(soft_plan_s *p, cudaStream_t s, soft_status st) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (p->copy_made) {
+        const cudaError_t e2 = cudaStreamSynchronize(p->copy_stream);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (st != SOFT_OK) return st;
+    return cuda_status(e);
+}
+
 soft_status soft_forward_host(soft_plan p, const double *grid_host, double *coef_host, void *stream) {
     if (!valid(p) || !grid_host || !coef_host) return SOFT_ERR_INVALID_ARG;
     DeviceGuard g(p->device);
     soft_status st = ensure_staging(p);
     if (st != SOFT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(p->stage_grid, grid_host, sizeof(double2) * grid_elems(p->B),
-                                    cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    st = run_forward(p, reinterpret_cast<const double *>(p->stage_grid), reinterpret_cast<double *>(p->stage_coef), s);
-    if (st != SOFT_OK) return st;
-    e = cudaMemcpyAsync(coef_host, p->stage_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B),
-                        cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return cuda_status(e);
+    const bool pipelined = fp64_layout(p->dtype) && own_slice_fft(p);
+    if (pipelined) {
+        st = ensure_copy_stream(p);
+        if (st != SOFT_OK) return st;
+        st = run_forward(p, reinterpret_cast<const double *>(p->stage_grid), reinterpret_cast<double *>(p->stage_coef),
+                         s, kApplyW | kApplyV, grid_host);
+    } else {
+        cudaError_t e = cudaMemcpyAsync(p->stage_grid, grid_host, sizeof(double2) * grid_elems(p->B),
+                                        cudaMemcpyHostToDevice, s);
+        st = e == cudaSuccess ? run_forward(p, reinterpret_cast<const double *>(p->stage_grid),
+                                            reinterpret_cast<double *>(p->stage_coef), s)
+                              : fail_cuda("grid copy", e);
+    }
+    if (st == SOFT_OK) {
+        const cudaError_t e = cudaMemcpyAsync(coef_host, p->stage_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B),
+                                              cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = fail_cuda("coefficient copy", e);
+    }
+    return finish_host_call(p, s, st);
 }
 
 soft_status soft_inverse_host(soft_plan p, const double *coef_host, double *grid_host, void *stream) {
@@ -948,14 +1077,19 @@ soft_status soft_inverse_host(soft_plan p, const double *coef_host, double *grid
     soft_status st = ensure_staging(p);
     if (st != SOFT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool pipelined = fp64_layout(p->dtype) && own_slice_fft(p);
+    if (pipelined) st = ensure_copy_stream(p);
+    if (st != SOFT_OK) return st;
     cudaError_t e = cudaMemcpyAsync(p->stage_coef, coef_host, sizeof(double2) * (size_t)soft_num_coeffs(p->B),
                                     cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    st = run_inverse(p, reinterpret_cast<const double *>(p->stage_coef), reinterpret_cast<double *>(p->stage_grid), s);
-    if (st != SOFT_OK) return st;
-    e = cudaMemcpyAsync(grid_host, p->stage_grid, sizeof(double2) * grid_elems(p->B), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return cuda_status(e);
+    if (e != cudaSuccess) return finish_host_call(p, s, fail_cuda("coefficient copy", e));
+    st = run_inverse(p, reinterpret_cast<const double *>(p->stage_coef), reinterpret_cast<double *>(p->stage_grid), s,
+                     0, pipelined ? grid_host : nullptr);
+    if (st == SOFT_OK && !pipelined) {
+        e = cudaMemcpyAsync(grid_host, p->stage_grid, sizeof(double2) * grid_elems(p->B), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = fail_cuda("grid copy", e);
+    }
+    return finish_host_call(p, s, st);
 }
 
 soft_status soft_selftest_bounded_wait(soft_plan p, int polls, void *stream) {

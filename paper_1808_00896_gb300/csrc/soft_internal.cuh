@@ -266,15 +266,17 @@ cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s);
 cudaError_t launch_cluster_tables(const Tables &tb, double *seedtab, double *rectab, cudaStream_t s);
 int dwt_forward_fp64_variants(int B);
 int dwt_inverse_fp64_variants(int B);
-// Double-float 2-D FFT of the beta slices (fft_df.cu), for power-of-two 2B:
-// `in` [j][i][k] FP64 -> `out` [j][m][m'] FP64, exp(sign i ...), unnormalised;
-// `work` (n^3 x 16 bytes) may alias `in` or `out`; `rexp`: n^2 ints of scratch.
+// Double-float 2-D FFT of `nslices` consecutive beta slices (fft_df.cu), for
+// power-of-two 2B: `in` [j][i][k] FP64 -> `out` [j][m][m'] FP64, exp(sign i
+// ...), unnormalised; `work` (nslices n^2 x 16 bytes) may alias `in` or `out`;
+// `rexp`: nslices n ints of scratch; all at the range's first slice.
 bool df_fft_supported(int B);
 cudaError_t launch_df_twiddles(int B, float4 *tw, cudaStream_t s);
 cudaError_t launch_df_fft2(int B, const double2 *in, double2 *out, float4 *work, const float4 *tw, int sign,
-                           int *rexp, cudaStream_t s);
-// FP64 2-D FFT of the beta slices (fft_fp64.cu), for power-of-two 2B: same
-// layouts and sign convention; `out` may be `in`.  The twiddle table holds
+                           int *rexp, cudaStream_t s, int nslices);
+// FP64 2-D FFT of `nslices` consecutive beta slices (fft_fp64.cu), for
+// power-of-two 2B: same layouts and sign convention; `out` may be `in`; both
+// at the range's first slice.  The twiddle table holds
 // fft64_twiddle_count(B) entries (the + table, then the - table), each
 // w = exp(i theta) factored as m (1 + i tau) (swap = 0; m1 = m2 = m) or
 // i m (1 + i tau) (swap = 1; m1 = -m, m2 = m), |tau| <= 1.
@@ -285,7 +287,8 @@ struct FftTw64 {
 bool fft64_supported(int B);
 size_t fft64_twiddle_count(int B);
 cudaError_t launch_fft64_twiddles(int B, FftTw64 *tw, cudaStream_t s);
-cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw64 *tw, int sign, cudaStream_t s);
+cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw64 *tw, int sign, cudaStream_t s,
+                            int nslices);
 // FP64-accurate tensor-core DWT / iDWT (dwt_fp64tc.cu); same S layout and
 // flags as the FP64 launchers; need the plan's per-cluster tables.
 cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s,
