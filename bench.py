@@ -256,7 +256,7 @@ def run_corr(args) -> None:
     import numpy as np
     import torch
 
-    from paper_1808_00896_gb300 import Plan, batched_correlate, synth
+    from paper_1808_00896_gb300 import Plan, batched_correlate, capi, synth
     from paper_1808_00896_gb300 import build as build_mod
 
     world, rank, local = dist_setup()
@@ -284,10 +284,12 @@ def run_corr(args) -> None:
     sampler.start()
     busy_warmup(lambda i: batched_correlate(plans, fs, gs, grids, bi, bv), 0, lambda: torch.cuda.synchronize(dev))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_launch0 = capi.soft_launch_count()
     ev0.record(stream)
     for _ in range(args.steps):
         batched_correlate(plans, fs, gs, grids, bi, bv)
     ev1.record(stream)
+    gpu_launches = capi.soft_launch_count() - n_launch0
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -330,7 +332,7 @@ def run_corr(args) -> None:
                        "parallelism": f"replicas x{world}", "l2": "per-step working set > 1 GB (> L2)"},
             "e2e": {"value": world * len(reqs) * e2e_steps / e2e_dt, "unit": "correlations/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * len(reqs), "steps": e2e_steps},
-            "gpu_launches": None,
+            "gpu_launches": gpu_launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s",
                          "frac": achieved / peak_gflops, "traffic": None, "kernel": "idwt_fp64_persistent_kernel",
                          "note": "whole-step time (FFTs, coefficient build and arg-max included)"},
@@ -345,7 +347,7 @@ def run_batched(args) -> None:
     """Batched workloads: nb same-B transforms per step (forward + inverse)."""
     import torch
 
-    from paper_1808_00896_gb300 import Plan, batched_forward, batched_inverse, synth
+    from paper_1808_00896_gb300 import Plan, batched_forward, batched_inverse, capi, synth
     from paper_1808_00896_gb300 import build as build_mod
 
     world, rank, local = dist_setup()
@@ -379,10 +381,12 @@ def run_batched(args) -> None:
     sampler.start()
     busy_warmup(lambda i: step(), 0, lambda: torch.cuda.synchronize(dev))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_launch0 = capi.soft_launch_count()
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
+    gpu_launches = capi.soft_launch_count() - n_launch0
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -411,7 +415,7 @@ def run_batched(args) -> None:
             "vs_baseline": None, "dtype": "f64" if dtype == "fp64" else dtype, "data": "synthetic",
             "config": {"workload": desc, "B": B, "mode": dtype, "batch": nb, "coefficients": kind,
                        "parallelism": f"replicas x{world}", "l2": "per-step working set > L2"},
-            "e2e": None, "gpu_launches": None, "roofline": roofline, "clocks": clocks, "cpu_baseline": None,
+            "e2e": None, "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks, "cpu_baseline": None,
         }
         print(json.dumps(line), flush=True)
     for p in plans:
@@ -470,10 +474,12 @@ def run_ours(args) -> None:
     busy_warmup(lambda i: step(i % R), 0, lambda: torch.cuda.synchronize(dev))
     capi.soft_plan_enable_timing(plan.handle, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_launch0 = capi.soft_launch_count()
     ev0.record(stream)
     for s in range(args.steps):
         step(s % R)
     ev1.record(stream)
+    gpu_launches = capi.soft_launch_count() - n_launch0
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -556,7 +562,7 @@ def run_ours(args) -> None:
                        "l2": f"{R} rotating input sets of {(grid_bytes + coef_bytes) / 2**20:.1f} MiB "
                              f"(> 129 MB L2 per pass)" if R > 1 else "single input larger than L2",
                        "parallelism": f"replicas x{world}"},
-            "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roofline, "clocks": clocks,
+            "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

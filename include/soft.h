@@ -64,6 +64,12 @@ typedef enum {
 /* Largest bandwidth B the kernels accept. */
 int soft_max_bandwidth(void);
 
+/* Number of this library's kernels launched in the process so far, over all
+ * plans and devices (monotonic).  The kernels of a batch's CUDA graph count
+ * at each replay of the graph (not when it is captured).  Kernels that cuFFT
+ * runs are not counted.  Thread-safe. */
+unsigned long long soft_launch_count(void);
+
 /* Number of Fourier coefficients with l < B: B(4B^2-1)/3 (Sec. 2.4).
  * Returns -1 for B < 1. */
 int64_t soft_num_coeffs(int B);

@@ -28,6 +28,7 @@ SOFT_FP64_TC = 3
 _vp, _i, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
 SIGNATURES = {
     "soft_max_bandwidth": (_i, []),
+    "soft_launch_count": (ctypes.c_ulonglong, []),
     "soft_num_coeffs": (_i64, [_i]),
     "soft_coef_index": (_i64, [_i, _i, _i, _i]),
     "soft_status_string": (ctypes.c_char_p, [_i]),
@@ -98,6 +99,10 @@ def check(status: int, what: str) -> None:
 # Thin wrappers with the C names (pointers and streams as Python ints).
 def soft_max_bandwidth() -> int:
     return load().soft_max_bandwidth()
+
+
+def soft_launch_count() -> int:
+    return int(load().soft_launch_count())
 
 
 def soft_num_coeffs(B: int) -> int:

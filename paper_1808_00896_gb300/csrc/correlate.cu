@@ -98,6 +98,7 @@ cudaError_t launch_corr_coeffs(int B, const double2 *f, const double2 *g, const 
     const int R = 2 * B - 1;
     const int blocks = std::min((R * R + 255) / 256, 152 * 8);
     corr_coeffs_kernel<<<blocks, 256, 0, s>>>(B, f, g, runoff, coef);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -105,9 +106,11 @@ cudaError_t launch_corr_coeffs(int B, const double2 *f, const double2 *g, const 
 cudaError_t launch_argmax_real(const double2 *data, int64_t count, double *scratch_v, int64_t *scratch_i,
                                int64_t *index_out, double *value_out, cudaStream_t s) {
     argmax_pass1<<<kArgmaxParts, 256, 0, s>>>(data, count, scratch_v, scratch_i);
+    count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     argmax_pass2<<<1, 512, 0, s>>>(scratch_v, scratch_i, kArgmaxParts, index_out, value_out);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -352,6 +352,7 @@ cudaError_t run_forward(const Tables &tb, const double2 *S, double *coef, cudaSt
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     dwt_forward_fp64_kernel<NT, JPT, TPI><<<tb.ncl, NT, bytes, s>>>(tb, S, coef, flags);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -363,6 +364,7 @@ cudaError_t run_inverse(const Tables &tb, const double *coef, double2 *S, cudaSt
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     dwt_inverse_fp64_kernel<NT, JPT><<<tb.ncl, NT, bytes, s>>>(tb, coef, S, flags);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -372,6 +374,7 @@ cudaError_t launch_tables(int B, double *w, double *cosb, double *lcos, double *
                           cudaStream_t s) {
     const int n = 2 * B;
     tables_kernel<<<(n + 1 + 127) / 128, 128, 0, s>>>(B, w, cosb, lcos, lsin, lfact);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -381,6 +384,7 @@ cudaError_t launch_cluster_tables(const Tables &tb, double *seedtab, double *rec
     t.rectab = nullptr;
     const size_t bytes = sizeof(double) * 4 * (size_t)tb.B;
     cluster_tables_kernel<<<tb.ncl, 256, bytes, s>>>(t, seedtab, rectab);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -389,6 +393,7 @@ cudaError_t launch_zero_nyquist(int B, double2 *S, cudaStream_t s) {
     const int64_t total = (int64_t)n * (2 * n - 1);
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
     zero_nyquist_kernel<<<blocks, 256, 0, s>>>(B, S);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -433,6 +438,7 @@ cudaError_t run_idwt_persistent(const BatchXform *xf, const int2 *items, int nit
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
     idwt_fp64_persistent_kernel<NT, JPT><<<grid, NT, bytes, s>>>(xf, items, nitems, counter);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -773,6 +773,7 @@ cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *c
     {
         const int64_t nn = 4LL * tb.B * tb.B;
         colexp_kernel<<<(unsigned)std::min<int64_t>((nn + 255) / 256, 152 * 16), 256, 0, s>>>(S, 2 * tb.B, tb.colexp);
+        count_launch();
         cudaError_t e0 = cudaGetLastError();
         if (e0 != cudaSuccess) return e0;
     }
@@ -784,6 +785,7 @@ cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *c
         cudaFuncSetAttribute(dwt_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     dwt_forward_tc_kernel<<<tb.ncl, kThreads, bytes, s>>>(tb, S, reinterpret_cast<double *>(coef), flags);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -798,6 +800,7 @@ cudaError_t launch_dwt_inverse_tc(const Tables &tb, const double2 *coef, double2
         cudaFuncSetAttribute(dwt_inverse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     dwt_inverse_tc_kernel<<<tb.ncl, kThreads, bytes, s>>>(tb, reinterpret_cast<const double *>(coef), S, flags);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -589,6 +589,7 @@ cudaError_t run_forward_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     dwt_forward_mixed_kernel<MODE, KC, NB, LD><<<mb.tb.ncl, LD ? 2 * KC : KC, bytes, s>>>(mb, flags);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -599,6 +600,7 @@ cudaError_t run_inverse_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     dwt_inverse_mixed_kernel<MODE, NB, LD><<<mb.tb.ncl, LD ? 2 * kNT : kNT, bytes, s>>>(mb, flags);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -639,6 +641,7 @@ cudaError_t inverse_mixed_nb(const MixedBatch &mb, int nb, cudaStream_t s, int f
 cudaError_t launch_log_weights(int B, const double *w, double *lw, cudaStream_t s) {
     const int n = 2 * B;
     log_weights_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, w, lw);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -677,28 +680,33 @@ cudaError_t launch_dwt_inverse_mixed(int mode, const Tables &tb, const double *c
 
 cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t s) {
     bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(polls, err);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_zero_nyquist32(int B, float2 *S, cudaStream_t s) {
     const int n = 2 * B;
     zero_nyquist32_kernel<<<grid_for((int64_t)(2 * n - 1) * n), 256, 0, s>>>(B, S);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_transpose32(const float2 *X, float2 *Y, int rows, int64_t cols, cudaStream_t s) {
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
     transpose32_kernel<<<grid, dim3(32, 8), 0, s>>>(X, Y, rows, cols);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_f64_to_f32(const double2 *in, float2 *out, int64_t count, cudaStream_t s) {
     f64_to_f32_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_f32_to_f64(const float2 *in, double2 *out, int64_t count, cudaStream_t s) {
     f32_to_f64_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+    count_launch();
     return cudaGetLastError();
 }
 

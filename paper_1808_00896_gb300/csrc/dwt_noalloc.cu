@@ -146,6 +146,7 @@ extern "C" soft_status soft_dwt_forward_noalloc(int B, const double *S, double *
     if (e == cudaSuccess) e = launch_log_weights(B, w, lw, s);
     if (e == cudaSuccess) {
         noalloc_layout_kernel<<<64, 256, 0, s>>>(B, clusters, runoff);
+        count_launch();
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)

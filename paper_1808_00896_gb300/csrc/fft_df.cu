@@ -292,6 +292,7 @@ bool df_fft_supported(int B) {
 cudaError_t launch_df_twiddles(int B, float4 *tw, cudaStream_t s) {
     const int n = 2 * B;
     twiddle_kernel<<<(n / 2 + 127) / 128, 128, 0, s>>>(n, tw);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -312,6 +313,7 @@ cudaError_t launch_df_fft2(int B, const double2 *in, double2 *out, float4 *work,
     if (e != cudaSuccess) return e;
     fft_rows_kernel<<<(unsigned)((nrows + rpb - 1) / rpb), kFftThreads, rbytes, s>>>(in, work, nrows, n, logn, rpb,
                                                                                      tw, conj, rexp);
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int kb = std::min(n, std::max(4, 4096 / n));
@@ -320,6 +322,7 @@ cudaError_t launch_df_fft2(int B, const double2 *in, double2 *out, float4 *work,
     if (e != cudaSuccess) return e;
     fft_cols_kernel<<<(unsigned)((int64_t)nslices * (n / kb)), kFftThreads, cbytes, s>>>(work, out, n, logn, kb, tw,
                                                                                           conj, rexp);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -212,9 +212,11 @@ size_t fft64_twiddle_count(int B) { return (size_t)2 * (size_t)B; }
 cudaError_t launch_fft64_twiddles(int B, FftTw64 *tw, cudaStream_t s) {
     const int n = 2 * B, half = n / 2;
     twiddle64_kernel<<<(half + 127) / 128, 128, 0, s>>>(n, +1, tw);
+    count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     twiddle64_kernel<<<(half + 127) / 128, 128, 0, s>>>(n, -1, tw + half);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -235,6 +237,7 @@ cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw6
     if (e != cudaSuccess) return e;
     fft64_rows_kernel<<<(unsigned)((nrows + rpb - 1) / rpb), kThreads, rbytes, s>>>(in, out, nrows, n, logn, rpb, t,
                                                                                       conj);
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int kb = std::min(n, std::max(2, kTile / n));
@@ -242,6 +245,7 @@ cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw6
     e = cudaFuncSetAttribute(fft64_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
     if (e != cudaSuccess) return e;
     fft64_cols_kernel<<<(unsigned)((int64_t)nslices * (n / kb)), kThreads, cbytes, s>>>(out, n, logn, kb, t, conj);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -2,8 +2,9 @@
 //
 // A plan owns, on one device: the quadrature and beta tables (computed by a
 // kernel), the cluster work list, the coefficient run-offset table, the S
-// workspace ((2B)^3 complex doubles) and a batched 2-D cuFFT plan over the 2B
-// beta slices.  The transforms are the two steps of Sec. 2.4: a 2-D FFT per
+// workspace ((2B)^3 complex doubles) and the slice-FFT tables (the library's
+// own FFT for power-of-two 2B, else a batched 2-D cuFFT plan over the 2B beta
+// slices).  The transforms are the two steps of Sec. 2.4: a 2-D FFT per
 // beta slice and the DWT per order pair (forward), or the iDWT per order pair
 // and a 2-D FFT per slice (inverse).
 #include "soft.h"
@@ -12,6 +13,7 @@
 #include <cufft.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -26,8 +28,17 @@ using namespace softgb;
 namespace {
 
 constexpr uint64_t kPlanMagic = 0x534f46545f504c4eULL;  // "SOFT_PLN"
+std::atomic<unsigned long long> g_launches{0};
+thread_local unsigned long long t_launches = 0;  // this thread's share, to size graph captures
 
 }  // namespace
+
+void softgb::count_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
+
+unsigned long long soft_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 struct soft_plan_s {
     uint64_t magic;
@@ -470,6 +481,7 @@ struct BatchGraph {
     std::vector<soft_plan_s *> plans;
     std::vector<const void *> key;  // every pointer argument, in order
     cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;  // kernel launches recorded in the graph
     BatchXform *d_xf = nullptr;
     int2 *d_items = nullptr;
     int *d_counter = nullptr;
@@ -697,10 +709,14 @@ soft_status run_batch(int kind, int n, const soft_plan *plans, const void *const
         std::vector<bool> timing(n);
         for (int i = 0; i < n; ++i) { timing[i] = ps[i]->timing; ps[i]->timing = false; }
         cudaGraph_t graph = nullptr;
+        const unsigned long long t0 = t_launches;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         soft_status st = e == cudaSuccess ? record_batch(bg, n, a, b, c, nullptr, best_index, best_value, cs)
                                           : fail_cuda("cudaStreamBeginCapture", e);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        // recorded, not run: the launch count takes them at each replay instead
+        bg->launches = t_launches - t0;
+        g_launches.fetch_sub(bg->launches, std::memory_order_relaxed);
         for (int i = 0; i < n; ++i) ps[i]->timing = timing[i];
         if (st == SOFT_OK && e2 != cudaSuccess) st = fail_cuda("cudaStreamEndCapture", e2);
         if (st == SOFT_OK) {
@@ -717,7 +733,9 @@ soft_status run_batch(int kind, int n, const soft_plan *plans, const void *const
         }
     }
     cudaError_t e = cudaGraphLaunch(bg->exec, user);
-    return e == cudaSuccess ? SOFT_OK : fail_cuda("cudaGraphLaunch", e);
+    if (e != cudaSuccess) return fail_cuda("cudaGraphLaunch", e);
+    g_launches.fetch_add(bg->launches, std::memory_order_relaxed);
+    return SOFT_OK;
 }
 
 }  // namespace

@@ -15,6 +15,10 @@ constexpr int kMaxB = 512;
 constexpr int kMaxMixedBatch = 8;  // transforms sharing one mixed-precision DWT launch
 
 // Per-plan device tables (all FP64 unless stated).
+// Called after every kernel launch of this library: the process-wide count
+// that soft_launch_count() reports.
+void count_launch();
+
 struct Tables {
     int B;
     int ncl;                  // number of symmetry clusters, B(B+1)/2

@@ -205,3 +205,35 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         p.sync()
         assert synth.rel_l2(g.cpu().numpy(), oracle.inverse(B, coef)) < 5e-5
         assert lib.soft_selftest_bounded_wait(p.handle, 0, None) == capi.SOFT_ERR_INVALID_ARG
+
+
+def test_launch_count():
+    """soft_launch_count: an FP64 forward with the library's FFT is 3 launches
+    (rows and columns passes, DWT) and an inverse 4 (S clearing, iDWT, two FFT
+    passes); with cuFFT (2B not a power of two) they are 1 and 2.  A batch's
+    graph counts its kernels at every replay."""
+    for B, fwd, inv in ((16, 3, 4), (3, 1, 2)):
+        grid = torch.from_numpy(synth.random_grid(B, seed=7800 + B)).to(DEV)
+        coef = torch.from_numpy(synth.coefficients(B, "uniform", seed=7900 + B)).to(DEV)
+        with Plan(B, device=DEV) as p:
+            c0 = capi.soft_launch_count()
+            p.forward(grid)
+            c1 = capi.soft_launch_count()
+            p.inverse(coef)
+            c2 = capi.soft_launch_count()
+            p.sync()
+        assert (c1 - c0, c2 - c1) == (fwd, inv), B
+    from paper_1808_00896_gb300 import batched_inverse
+    plans = [Plan(16, device=DEV) for _ in range(3)]
+    coefs = [torch.from_numpy(synth.coefficients(16, "uniform", seed=8000 + i)).to(DEV) for i in range(3)]
+    outs = [p.empty_grid() for p in plans]
+    batched_inverse(plans, coefs, outs)  # captures the graph
+    per = []
+    for _ in range(3):
+        c0 = capi.soft_launch_count()
+        batched_inverse(plans, coefs, outs)
+        per.append(capi.soft_launch_count() - c0)
+    torch.cuda.synchronize(DEV)
+    for p in plans:
+        p.close()
+    assert per[0] > 0 and per == [per[0]] * 3, per
