@@ -237,7 +237,8 @@ void free_plan(soft_plan_s *p) {
     if (p->fft32f_made) cufftDestroy(p->fft32f);
     if (p->fft32i_made) cufftDestroy(p->fft32i);
     cudaFree(p->lw); cudaFree(p->g32); cudaFree(p->S32);
-    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->fwd_order); cudaFree(p->inv_order); cudaFree(p->dftw); cudaFree(p->dfexp); cudaFree(p->tw64); cudaFree(p->colexp);
+    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->fwd_order); cudaFree(p->inv_order);
+    cudaFree(p->dftw); cudaFree(p->dfexp); cudaFree(p->tw64); cudaFree(p->colexp);
     cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
     cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
     cudaFree(p->stage_grid); cudaFree(p->stage_coef);
@@ -420,8 +421,9 @@ soft_status run_forward(soft_plan_s *p, const double *grid, double *coef, cudaSt
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
     // S(m,m';j) = sum_{i,k} f exp(+i(m alpha_i + m' gamma_k)), unnormalised.
-    soft_status st = grid_host ? forward_fft_from_host(p, grid_host, reinterpret_cast<double2 *>(const_cast<double *>(grid)), s)
-                               : slice_fft(p, reinterpret_cast<const double2 *>(grid), p->S, +1, s);
+    soft_status st =
+        grid_host ? forward_fft_from_host(p, grid_host, reinterpret_cast<double2 *>(const_cast<double *>(grid)), s)
+                  : slice_fft(p, reinterpret_cast<const double2 *>(grid), p->S, +1, s);
     if (st != SOFT_OK) return st;
     if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = launch_dwt_forward_plan(p, p->S, reinterpret_cast<double2 *>(coef), s, flags);
