@@ -47,6 +47,10 @@ for _B in (64, 128, 256, 512):
         WORKLOADS[f"b{_B}_{_m}"] = (_B, _m, "gauss_decay",
                                     f"mixed SOFT forward+inverse, B={_B}, {_d} contraction on tcgen05 tensor cores, "
                                     f"FP64 Wigner-d recurrence, FP32 2-D FFTs; complex128 in/out")
+    WORKLOADS[f"b{_B}_real"] = (_B, "fp64_real", "gauss_decay",
+                                f"FP64 SOFT forward+inverse of a real function, B={_B}: soft_forward_real / "
+                                f"soft_inverse_real on a real (2B)^3 float64 grid, one partner of each conjugate "
+                                f"pair contracted")
     WORKLOADS[f"b{_B}_fp64tc"] = (_B, "fp64_tc", "gauss_decay",
                                   f"FP64-accurate SOFT forward+inverse, B={_B}: FP64 Wigner-d recurrence, S and "
                                   f"2-D FFTs, contraction on tcgen05 tensor cores as exact base-128 BF16 digit "
@@ -81,7 +85,7 @@ SM_MAX_MHZ = 2070.0
 # with the source file and the SHA-256 prefix of it that the capture was taken
 # on; reported as null once that file has changed.
 TRAFFIC = {
-    ("dwt_forward_fp64_kernel", 64): (36_885_760 + 15_104, "dwt_fp64.cu", "a3971495f0fcc96d"),
+    ("dwt_forward_fp64_kernel", 64): (36_887_552 + 12_032, "dwt_fp64.cu", "0589e4d08494f908"),
     ("dwt_forward_tc_kernel", 128): (295_284_736 + 46_113_024, "dwt_fp64tc.cu", "c436b9618490a61c"),
 }
 
@@ -446,18 +450,27 @@ def run_ours(args) -> None:
     if B >= 256:
         R = 1  # one input already exceeds L2 several times over
 
-    plan = Plan(B, dtype, device=dev)
+    real = dtype == "fp64_real"  # real grids: soft_forward_real / soft_inverse_real on an FP64 plan
+    plan = Plan(B, "fp64" if real else dtype, device=dev)
     tuned = plan.tune() if args.tune else None
     coefs = [torch.from_numpy(synth.coefficients(B, kind, seed=synth.BASE_SEED + 100 * rank + r)).to(dev)
              for r in range(R)]
     grids = [plan.inverse(c) for c in coefs]
+    if real:
+        # a real grid per input set, and the coefficients of that real function
+        grids = [g.real.contiguous() for g in grids]
+        coefs = [plan.forward_real(g) for g in grids]
     coef_out = plan.empty_coef()
-    grid_out = plan.empty_grid()
+    grid_out = torch.empty((n, n, n), dtype=torch.float64, device=dev) if real else plan.empty_grid()
     stream = torch.cuda.current_stream(dev)
 
     def step(r):
-        plan.forward(grids[r], out=coef_out)
-        plan.inverse(coefs[r], out=grid_out)
+        if real:
+            plan.forward_real(grids[r], out=coef_out)
+            plan.inverse_real(coefs[r], out=grid_out)
+        else:
+            plan.forward(grids[r], out=coef_out)
+            plan.inverse(coefs[r], out=grid_out)
 
     for w in range(args.warmup):
         step(w % R)
@@ -493,42 +506,59 @@ def run_ours(args) -> None:
     ms_per_step = ms_total / args.steps
     value = world * 1000.0 / ms_per_step
 
-    # e2e through the host-buffer entry points with pinned host memory.
+    # e2e with pinned host memory: through the host-buffer entry points, or
+    # (real grids) explicit copies around the device calls, on one stream.
     e2e_steps = max(3, min(args.steps, int(args.e2e_steps)))
-    g_host = torch.empty((n, n, n), dtype=torch.complex128, pin_memory=True)
+    g_host = torch.empty((n, n, n), dtype=grids[0].dtype, pin_memory=True)
     g_host.copy_(grids[0].cpu())
     c_host = torch.empty(synth.num_coeffs(B), dtype=torch.complex128, pin_memory=True)
     c_host.copy_(coefs[0].cpu())
     c_res = torch.empty_like(c_host, pin_memory=True)
     g_res = torch.empty_like(g_host, pin_memory=True)
     gh, ch, cr, gr = g_host.numpy(), c_host.numpy(), c_res.numpy(), g_res.numpy()
-    plan.forward_host(gh, cr)
-    plan.inverse_host(ch, gr)
+    g_dev, c_dev = torch.empty_like(grids[0]), plan.empty_coef()
+
+    def e2e_step():
+        if real:
+            g_dev.copy_(g_host, non_blocking=True)
+            plan.forward_real(g_dev, out=coef_out)
+            c_res.copy_(coef_out, non_blocking=True)
+            c_dev.copy_(c_host, non_blocking=True)
+            plan.inverse_real(c_dev, out=grid_out)
+            g_res.copy_(grid_out, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        else:
+            plan.forward_host(gh, cr)
+            plan.inverse_host(ch, gr)
+
+    e2e_step()
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        plan.forward_host(gh, cr)
-        plan.inverse_host(ch, gr)
+        e2e_step()
     e2e_dt = time.perf_counter() - t0
     e2e_dt = max_over_ranks(e2e_dt)
+    gb = grid_bytes // 2 if real else grid_bytes
     e2e = {"value": world * e2e_steps / e2e_dt, "unit": UNIT,
-           "h2d_bytes_per_step": grid_bytes + coef_bytes, "d2h_bytes_per_step": coef_bytes + grid_bytes,
+           "h2d_bytes_per_step": gb + coef_bytes, "d2h_bytes_per_step": coef_bytes + gb,
            "steps": e2e_steps}
 
     # Roofline of the dominant kernel, from the library's CUDA events.
     fl = dwt_flops(B)
     fwd_ms = phase_ms[1] / max(1, phase_cnt[1])
     inv_ms = phase_ms[2] / max(1, phase_cnt[2])
-    kname = {"fp64": "fp64", "fp64_tc": "tc"}.get(dtype, "mixed")
+    kname = {"fp64": "fp64", "fp64_real": "fp64", "fp64_tc": "tc"}.get(dtype, "mixed")
     dom, dom_ms = (f"dwt_forward_{kname}_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else \
         (f"dwt_inverse_{kname}_kernel", inv_ms)
     peak_gflops = FP64_FLOPS_PER_SM_CLK * N_SM * SM_MAX_MHZ * 1e6 / 1e9
     # FP64 path: contraction + recurrence on the FP64 pipe.  Mixed modes: the
     # FP64 recurrence is the binding term (the contraction runs on tensor cores).
-    algo = fl["contraction"] + fl["recurrence"] if dtype == "fp64" else fl["recurrence"]
+    # Real grids: half the contraction (one partner of each conjugate pair).
+    algo = fl["contraction"] + fl["recurrence"] if dtype == "fp64" else \
+        fl["contraction"] / 2 + fl["recurrence"] if real else fl["recurrence"]
     achieved = algo / (dom_ms * 1e-3) / 1e9
-    tr = TRAFFIC.get((dom, B))
+    tr = None if real else TRAFFIC.get((dom, B))
     traffic = tr[0] if (tr and tr[2] == kernel_source_sha(tr[1])) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s",
                 "frac": achieved / peak_gflops, "traffic": traffic, "kernel": dom,
@@ -537,7 +567,7 @@ def run_ours(args) -> None:
                 "phase_ms_per_launch": {"fft_forward": phase_ms[0] / max(1, phase_cnt[0]),
                                         "dwt_forward": fwd_ms, "dwt_inverse": inv_ms,
                                         "fft_inverse": phase_ms[3] / max(1, phase_cnt[3])}}
-    if dtype != "fp64":
+    if dtype not in ("fp64", "fp64_real"):
         # tensor-core products per real multiply-add of the contraction: 3 split-BF16
         # pairs, 1 TF32, or the 28 digit pairs (levels 0..6) of the FP64-accurate mode
         mult = {"bf16x3": 3, "fp64_tc": 28}.get(dtype, 1)
@@ -556,7 +586,7 @@ def run_ours(args) -> None:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if dtype == "fp64" else dtype, "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if dtype in ("fp64", "fp64_real") else dtype, "data": "synthetic",
             "config": {"workload": desc, "B": B, "mode": dtype, "coefficients": kind, "inputs_rotated": R,
                        "tile_variants": None if tuned is None else {"dwt": tuned["dwt"], "idwt": tuned["idwt"]},
                        "l2": f"{R} rotating input sets of {(grid_bytes + coef_bytes) / 2**20:.1f} MiB "

@@ -118,6 +118,25 @@ soft_status soft_forward(soft_plan p, const double *grid, double *coef, void *st
  *   every beta slice (exp(-i...)).                                      */
 soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *stream);
 
+/* Real grids (SOFT_FP64 plans with power-of-two 2B; SOFT_ERR_UNSUPPORTED
+ * otherwise).  A real function has f(l,-m,-m') = (-1)^(m-m') conj f(l,m,m')
+ * (from the symmetries of Eq. (Wigner_symmetries)), and S(-m,-m';j) =
+ * conj S(m,m';j).  In each symmetry cluster the partners come in such
+ * conjugate pairs, and these calls contract one partner of each pair: half
+ * the DWT / iDWT contraction work.
+ *   soft_forward_real: grid (device, (2B)^3 doubles, layout [j][i][k] as the
+ *     complex grid) -> coef (device, B(4B^2-1)/3 complex), the same values as
+ *     soft_forward of the grid with zero imaginary parts (the conjugate
+ *     partners' coefficients are written from their pair exactly).
+ *   soft_inverse_real: coef -> grid (device, (2B)^3 doubles), the real part
+ *     of soft_inverse.  It reads only the coefficients of the contracted
+ *     partners, so the others are taken to satisfy the symmetry whatever they
+ *     hold; coefficients from soft_forward_real (or of any real function) do.
+ * Both 16-byte aligned, as soft_forward / soft_inverse; asynchronous on
+ * `stream`. */
+soft_status soft_forward_real(soft_plan p, const double *grid, double *coef, void *stream);
+soft_status soft_inverse_real(soft_plan p, const double *coef, double *grid, void *stream);
+
 /* Adjoints, for gradients of objectives through the transforms.  Adjoint is
  * with respect to sum_k conj(a_k) b_k on both sides.  Writing the forward
  * transform as f = V_B T_B W_B E x (Sec. 2.4; E the per-slice 2-D DFT with

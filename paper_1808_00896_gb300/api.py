@@ -25,11 +25,12 @@ def _stream_ptr(device: torch.device, stream=None) -> int:
     return int(s.cuda_stream)
 
 
-def _check_tensor(t: torch.Tensor, numel: int, device: torch.device, what: str) -> None:
+def _check_tensor(t: torch.Tensor, numel: int, device: torch.device, what: str,
+                  dtype: torch.dtype = torch.complex128) -> None:
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{what} must be a torch.Tensor")
-    if t.dtype != torch.complex128:
-        raise TypeError(f"{what} must be complex128, got {t.dtype}")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
     if t.device != device:
         raise ValueError(f"{what} must be on {device}, got {t.device}")
     if not t.is_contiguous():
@@ -119,6 +120,26 @@ class Plan:
         _check_tensor(out, self.n ** 3, self.device, "out")
         capi.check(capi.soft_inverse(self.handle, coef.data_ptr(), out.data_ptr(), _stream_ptr(self.device, stream)),
                    "soft_inverse")
+        return out
+
+    def forward_real(self, grid: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """FSOFT of a real grid: float64 (2B,2B,2B) -> complex coefficients (soft_forward_real).
+        FP64 plans with power-of-two 2B."""
+        _check_tensor(grid, self.n ** 3, self.device, "grid", torch.float64)
+        out = self.empty_coef() if out is None else out
+        _check_tensor(out, self.ncoef, self.device, "out")
+        capi.check(capi.soft_forward_real(self.handle, grid.data_ptr(), out.data_ptr(),
+                                          _stream_ptr(self.device, stream)), "soft_forward_real")
+        return out
+
+    def inverse_real(self, coef: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """iFSOFT to a real grid: coefficients of a real function -> float64 (2B,2B,2B)
+        (soft_inverse_real; reads one partner of each conjugate pair)."""
+        _check_tensor(coef, self.ncoef, self.device, "coef")
+        out = torch.empty((self.n,) * 3, dtype=torch.float64, device=self.device) if out is None else out
+        _check_tensor(out, self.n ** 3, self.device, "out", torch.float64)
+        capi.check(capi.soft_inverse_real(self.handle, coef.data_ptr(), out.data_ptr(),
+                                          _stream_ptr(self.device, stream)), "soft_inverse_real")
         return out
 
     def forward_adjoint(self, coef: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -39,6 +39,8 @@ SIGNATURES = {
     "soft_plan_sync": (_i, [_vp]),
     "soft_forward": (_i, [_vp, _vp, _vp, _vp]),
     "soft_inverse": (_i, [_vp, _vp, _vp, _vp]),
+    "soft_forward_real": (_i, [_vp, _vp, _vp, _vp]),
+    "soft_inverse_real": (_i, [_vp, _vp, _vp, _vp]),
     "soft_forward_adjoint": (_i, [_vp, _vp, _vp, _vp]),
     "soft_inverse_adjoint": (_i, [_vp, _vp, _vp, _vp]),
     "soft_batched_inverse": (_i, [_i, _vp, _vp, _vp, _vp]),
@@ -133,6 +135,14 @@ def soft_forward(plan: int, grid_ptr: int, coef_ptr: int, stream: int = 0) -> in
 
 def soft_inverse(plan: int, coef_ptr: int, grid_ptr: int, stream: int = 0) -> int:
     return load().soft_inverse(plan, coef_ptr, grid_ptr, stream)
+
+
+def soft_forward_real(plan: int, grid_ptr: int, coef_ptr: int, stream: int = 0) -> int:
+    return load().soft_forward_real(plan, grid_ptr, coef_ptr, stream)
+
+
+def soft_inverse_real(plan: int, coef_ptr: int, grid_ptr: int, stream: int = 0) -> int:
+    return load().soft_inverse_real(plan, coef_ptr, grid_ptr, stream)
 
 
 def soft_forward_adjoint(plan: int, coef_ptr: int, grid_ptr: int, stream: int = 0) -> int:

@@ -96,19 +96,27 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
     for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
     cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, rV);
     const int np = cs.np;
+    // Real input (kRealSym): f(l,-m,-m') = (-1)^(m-m') conj f(l,m,m'), and the
+    // partners come in such conjugate pairs (2k, 2k+1), so only the even ones
+    // are contracted (slot c holds partner c * pstep) and the odd ones are
+    // written from them.
+    const bool real = (flags & kRealSym) && np > 1;
+    const int npc = real ? np / 2 : np, pstep = real ? 2 : 1;
 
-    // X: S of every partner, beta index mirrored where the partner's column is
-    // d(.; pi - beta).  The weight w_B(j) is not applied here: it enters T
-    // through the seeds below (T W, since the recurrence is linear in d;
-    // w_B is symmetric under j -> 2B-1-j, so mirrored partners see the same w).
+    // X: S of every contracted partner, beta index mirrored where the
+    // partner's column is d(.; pi - beta).  The weight w_B(j) is not applied
+    // here: it enters T through the seeds below (T W, since the recurrence is
+    // linear in d; w_B is symmetric under j -> 2B-1-j, so mirrored partners see
+    // the same w).
     for (int e = tid; e < n * 8; e += NT) {
-        const int j = e >> 3, p = e & 7;
+        const int j = e >> 3, c = e & 7;
         double2 v = make_double2(0.0, 0.0);
-        if (p < np) {
+        if (c < npc) {
+            const int p = c * pstep;
             const int src = cs.mir[p] ? n - 1 - j : j;
             v = S[((int64_t)src * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)];
         }
-        *reinterpret_cast<double2 *>(&X[j * 16 + 2 * p]) = v;
+        *reinterpret_cast<double2 *>(&X[j * 16 + 2 * c]) = v;
     }
 
     // Recurrence state of this thread's beta samples: seeds w_B(j) d(l0,m,m';beta_j).
@@ -130,11 +138,11 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
     const int half = tid % TPI, ot = tid / TPI;  // phase-B output (degree in tile, column) and beta part
     static_assert(TPI == 1 || TPI == 2 || TPI == 4, "TPI");
     // The 16 lanes (x TPI) of a degree cover its 16 real output columns (8
-    // partners x re/im).  With at most 4 partners the upper 8 columns have no
-    // work, and for TPI <= 2 they would be half-warps that still occupy the
-    // FP64 pipe, so there the lanes take 8 columns x 2 halves of the beta range
-    // (combined by one more shuffle) instead.
-    const bool fold = TPI <= 2 && np <= 4;
+    // partners x re/im).  With at most 4 contracted partners the upper 8
+    // columns have no work, and for TPI <= 2 they would be half-warps that
+    // still occupy the FP64 pipe, so there the lanes take 8 columns x 2 halves
+    // of the beta range (combined by one more shuffle) instead.
+    const bool fold = TPI <= 2 && npc <= 4;
     const int pt = ot >> 4, pc = fold ? (ot & 7) : (ot & 15);
     const int pp = pc >> 1;
     const int upper = fold ? (ot >> 3) & 1 : 0;  // second half of the beta range
@@ -159,7 +167,7 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
         }
         __syncthreads();
         // Phase B
-        const bool active = pt < nt && pp < np;
+        const bool active = pt < nt && pp < npc;
         double acc = 0.0;
         if (active) {
             const double *Tr = T + pt * n + jbeg;
@@ -178,10 +186,15 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
         if (TPI >= 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (fold) acc += __shfl_xor_sync(0xffffffffu, acc, 8 * TPI);  // the two beta halves (fold is CTA-uniform)
         if (active && half == 0 && upper == 0) {
-            const int l = lb + pt;
+            const int l = lb + pt, p = pp * pstep;
             const double v = rV[l - l0];
-            const bool neg = (cs.sign[pp] < 0.0) != (cs.lpar[pp] && (l & 1));
-            coef[2 * (cs.off[pp] + (l - l0)) + (pc & 1)] = (neg ? -v : v) * acc;
+            const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
+            const double f = (neg ? -v : v) * acc;
+            coef[2 * (cs.off[p] + (l - l0)) + (pc & 1)] = f;
+            if (real) {  // partner p + 1 = (-m, -m') of partner p: (-1)^(m-m') conj f
+                const bool flip = ((cs.pm[p] - cs.pmp[p]) & 1) != (pc & 1);
+                coef[2 * (cs.off[p + 1] + (l - l0)) + (pc & 1)] = flip ? -f : f;
+            }
         }
         __syncthreads();
     }
@@ -236,18 +249,24 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
     load_cluster(tb, m, mp, cs);
     cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
     const int np = cs.np;
+    // Real output (kRealSym): S(-m,-m';j) = conj S(m,m';j) for the conjugate
+    // partner pairs (2k, 2k+1); only the even partners are walked (slot c
+    // holds partner c * pstep) and only their coefficients are read.
+    const bool real = (flags & kRealSym) && np > 1;
+    const int npc = real ? np / 2 : np, pstep = real ? 2 : 1;
     for (int e = tid; e < L * 8; e += NT) {
-        const int t = e >> 3, p = e & 7;
+        const int t = e >> 3, c = e & 7;
         double2 v = make_double2(0.0, 0.0);
-        if (p < np) {
+        if (c < npc) {
+            const int p = c * pstep;
             const int l = l0 + t;
             double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
             sg *= rSig[t];
             if (flags & kApplyV) sg *= (2.0 * l + 1.0) / (8.0 * M_PI * B);
-            const double2 c = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + t));
-            v = make_double2(sg * c.x, sg * c.y);
+            const double2 cf = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + t));
+            v = make_double2(sg * cf.x, sg * cf.y);
         }
-        *reinterpret_cast<double2 *>(&F[t * 16 + 2 * p]) = v;
+        *reinterpret_cast<double2 *>(&F[t * 16 + 2 * c]) = v;
     }
 
     double x[JPT], dcur[JPT], dprev[JPT];
@@ -268,20 +287,25 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
     }
     __syncthreads();
 
-    if (np == 8) idwt_walk<NT, JPT, 16>(F, rA, rAc, L, x, dcur, dprev, acc);
-    else         idwt_walk<NT, JPT, 8>(F, rA, rAc, L, x, dcur, dprev, acc);
+    if (npc > 4)      idwt_walk<NT, JPT, 16>(F, rA, rAc, L, x, dcur, dprev, acc);
+    else if (npc > 2) idwt_walk<NT, JPT, 8>(F, rA, rAc, L, x, dcur, dprev, acc);
+    else              idwt_walk<NT, JPT, 4>(F, rA, rAc, L, x, dcur, dprev, acc);
 
 #pragma unroll
     for (int k = 0; k < JPT; ++k) {
         const int j = tid + k * NT;
         if (j < n) {
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                if (p < np) {
+            for (int c = 0; c < 8; ++c) {
+                if (c < npc) {
+                    const int p = c * pstep;
                     const int jj = cs.mir[p] ? n - 1 - j : j;
                     const double wj = (flags & kApplyW) ? tb.w[jj] : 1.0;
-                    S[((int64_t)jj * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)] =
-                        make_double2(wj * acc[k][2 * p], wj * acc[k][2 * p + 1]);
+                    const double2 v = make_double2(wj * acc[k][2 * c], wj * acc[k][2 * c + 1]);
+                    S[((int64_t)jj * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)] = v;
+                    if (real)  // partner p + 1 = (-m, -m'): the conjugate, at the same beta sample
+                        S[((int64_t)jj * n + mod_n(cs.pm[p + 1], n)) * n + mod_n(cs.pmp[p + 1], n)] =
+                            make_double2(v.x, -v.y);
                 }
             }
         }

@@ -109,10 +109,18 @@ __device__ void load_twiddles(FftTw64 *tw, const FftTw64 *__restrict__ twg, int 
     for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) tw[t] = twg[t];
 }
 
+// Element e of the input: complex, or real (REAL_IN, imaginary part 0).
+template <bool REAL_IN>
+__device__ __forceinline__ double2 load_in(const void *in, int64_t e) {
+    if constexpr (REAL_IN) return make_double2(static_cast<const double *>(in)[e], 0.0);
+    else return static_cast<const double2 *>(in)[e];
+}
+
 // Rows pass: nrows rows of n contiguous elements, `rpb` rows per block,
 // in -> out (the same memory is allowed: a block reads its rows before it
-// writes them).
-__global__ void __launch_bounds__(kThreads) fft64_rows_kernel(const double2 *in, double2 *out, int64_t nrows, int n,
+// writes them).  `in` holds double2, or doubles when REAL_IN.
+template <bool REAL_IN>
+__global__ void __launch_bounds__(kThreads) fft64_rows_kernel(const void *in, double2 *out, int64_t nrows, int n,
                                                                int logn, int rpb, const FftTw64 *__restrict__ twg,
                                                                int conj) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -125,21 +133,24 @@ __global__ void __launch_bounds__(kThreads) fft64_rows_kernel(const double2 *in,
         const int n4 = n >> 2;
         for (int q = threadIdx.x; q < rows * n4; q += blockDim.x) {
             const int rl = q / n4, t = q - rl * n4;
-            const double2 *x = in + (r0 + rl) * n + t;
-            first_radix4(x[0], x[n >> 1], x[n4], x[3 * n4], conj != 0, s + rl * n + 4 * bitrev_n(t, logn - 2));
+            const int64_t x = (r0 + rl) * n + t;
+            first_radix4(load_in<REAL_IN>(in, x), load_in<REAL_IN>(in, x + (n >> 1)), load_in<REAL_IN>(in, x + n4),
+                         load_in<REAL_IN>(in, x + 3 * n4), conj != 0, s + rl * n + 4 * bitrev_n(t, logn - 2));
         }
         stages(s, rows, n, n, logn, 4, 2, tw);
     } else {
-        for (int e = threadIdx.x; e < rows * n; e += blockDim.x) s[e] = in[r0 * n + e];  // n = 2: identity order
+        for (int e = threadIdx.x; e < rows * n; e += blockDim.x) s[e] = load_in<REAL_IN>(in, r0 * n + e);  // n = 2
         stages(s, rows, n, n, logn, 1, 0, tw);
     }
     for (int e = threadIdx.x; e < rows * n; e += blockDim.x) out[r0 * n + e] = s[e];
 }
 
 // Columns pass: for every slice and column, the length-n DFT along the middle
-// index (stride n), `kb` adjacent columns per block, in place.  Shared memory
+// index (stride n), `kb` adjacent columns per block, in place, or (REAL_OUT)
+// only the real parts written to `rout` (same layout, doubles).  Shared memory
 // holds column c at s + c (n + 1) (the pad spreads the columns over the banks).
-__global__ void __launch_bounds__(kThreads) fft64_cols_kernel(double2 *data, int n, int logn, int kb,
+template <bool REAL_OUT>
+__global__ void __launch_bounds__(kThreads) fft64_cols_kernel(double2 *data, double *rout, int n, int logn, int kb,
                                                                const FftTw64 *__restrict__ twg, int conj) {
     extern __shared__ __align__(16) unsigned char smraw[];
     FftTw64 *tw = reinterpret_cast<FftTw64 *>(smraw);
@@ -168,7 +179,8 @@ __global__ void __launch_bounds__(kThreads) fft64_cols_kernel(double2 *data, int
     }
     for (int e = threadIdx.x; e < kb * n; e += blockDim.x) {
         const int i = e / kb, c = e - i * kb;
-        base[(int64_t)i * n + c] = s[c * ld + i];
+        if constexpr (REAL_OUT) rout[js * n * n + k0 + (int64_t)i * n + c] = s[c * ld + i].x;
+        else base[(int64_t)i * n + c] = s[c * ld + i];
     }
 }
 
@@ -200,6 +212,38 @@ int ilog2_pow2(int n) {
     return (1 << l) == n ? l : -1;
 }
 
+// The two passes: rows `in` -> `mid` (complex; `in` complex, or real when
+// REAL_IN), then columns in place on `mid`, or (REAL_OUT) from `mid` to the
+// real parts in `rout`.  All pointers at the first of `nslices` slices.
+template <bool REAL_IN, bool REAL_OUT>
+cudaError_t fft64_passes(int B, const void *in, double2 *mid, double *rout, const FftTw64 *tw, int sign,
+                         cudaStream_t s, int nslices) {
+    const int n = 2 * B, logn = ilog2_pow2(n);
+    if (logn < 1 || nslices < 1 || nslices > n) return cudaErrorInvalidValue;
+    const FftTw64 *t = sign < 0 ? tw + n / 2 : tw;
+    const int conj = sign < 0 ? 1 : 0;
+    const int64_t nrows = (int64_t)nslices * n;
+    const int rpb = std::max(1, kTile / n);
+    const size_t twb = sizeof(FftTw64) * (size_t)(n / 2);
+    const size_t rbytes = twb + sizeof(double2) * (size_t)rpb * n;
+    cudaError_t e = cudaFuncSetAttribute(fft64_rows_kernel<REAL_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rbytes);
+    if (e != cudaSuccess) return e;
+    fft64_rows_kernel<REAL_IN><<<(unsigned)((nrows + rpb - 1) / rpb), kThreads, rbytes, s>>>(in, mid, nrows, n, logn,
+                                                                                             rpb, t, conj);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int kb = std::min(n, std::max(2, kTile / n));
+    const size_t cbytes = twb + sizeof(double2) * (size_t)kb * (n + 1);
+    e = cudaFuncSetAttribute(fft64_cols_kernel<REAL_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
+    if (e != cudaSuccess) return e;
+    fft64_cols_kernel<REAL_OUT><<<(unsigned)((int64_t)nslices * (n / kb)), kThreads, cbytes, s>>>(mid, rout, n, logn,
+                                                                                                 kb, t, conj);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 bool fft64_supported(int B) {
@@ -225,28 +269,20 @@ cudaError_t launch_fft64_twiddles(int B, FftTw64 *tw, cudaStream_t s) {
 // be `in`.  Both point at the first slice of the range.
 cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw64 *tw, int sign, cudaStream_t s,
                             int nslices) {
-    const int n = 2 * B, logn = ilog2_pow2(n);
-    if (logn < 1 || nslices < 1 || nslices > n) return cudaErrorInvalidValue;
-    const FftTw64 *t = sign < 0 ? tw + n / 2 : tw;
-    const int conj = sign < 0 ? 1 : 0;
-    const int64_t nrows = (int64_t)nslices * n;
-    const int rpb = std::max(1, kTile / n);
-    const size_t twb = sizeof(FftTw64) * (size_t)(n / 2);
-    const size_t rbytes = twb + sizeof(double2) * (size_t)rpb * n;
-    cudaError_t e = cudaFuncSetAttribute(fft64_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rbytes);
-    if (e != cudaSuccess) return e;
-    fft64_rows_kernel<<<(unsigned)((nrows + rpb - 1) / rpb), kThreads, rbytes, s>>>(in, out, nrows, n, logn, rpb, t,
-                                                                                      conj);
-    count_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int kb = std::min(n, std::max(2, kTile / n));
-    const size_t cbytes = twb + sizeof(double2) * (size_t)kb * (n + 1);
-    e = cudaFuncSetAttribute(fft64_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
-    if (e != cudaSuccess) return e;
-    fft64_cols_kernel<<<(unsigned)((int64_t)nslices * (n / kb)), kThreads, cbytes, s>>>(out, n, logn, kb, t, conj);
-    count_launch();
-    return cudaGetLastError();
+    return fft64_passes<false, false>(B, in, out, nullptr, tw, sign, s, nslices);
+}
+
+// The same for a real grid `in` ((2B)^3 doubles) into the complex `out`.
+cudaError_t launch_fft64_2d_from_real(int B, const double *in, double2 *out, const FftTw64 *tw, int sign,
+                                      cudaStream_t s) {
+    return fft64_passes<true, false>(B, in, out, nullptr, tw, sign, s, 2 * B);
+}
+
+// The same for a complex `in` whose result is real (Hermitian input, up to
+// rounding): `in` is overwritten (the rows pass runs in place) and the real
+// parts of the result go to `out` ((2B)^3 doubles).
+cudaError_t launch_fft64_2d_to_real(int B, double2 *in, double *out, const FftTw64 *tw, int sign, cudaStream_t s) {
+    return fft64_passes<false, true>(B, in, in, out, tw, sign, s, 2 * B);
 }
 
 }  // namespace softgb

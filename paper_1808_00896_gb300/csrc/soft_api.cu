@@ -953,6 +953,45 @@ soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *st
     return run_inverse(p, coef, grid, static_cast<cudaStream_t>(stream));
 }
 
+// Real grids (FP64 plans with power-of-two 2B): the FFT reads or writes real
+// samples and the DWT / iDWT contract only one partner of each conjugate pair
+// (kRealSym).
+soft_status soft_forward_real(soft_plan p, const double *grid, double *coef, void *stream) {
+    soft_status st = check_plan_args(p, grid, coef);
+    if (st != SOFT_OK) return st;
+    if (p->dtype != SOFT_FP64 || !p->tw64) return SOFT_ERR_UNSUPPORTED;
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t *ev = timing_slot(p, 0);
+    if (ev) cudaEventRecord(ev[0], s);
+    cudaError_t e = launch_fft64_2d_from_real(p->B, grid, p->S, p->tw64, +1, s);
+    if (e != cudaSuccess) return fail_cuda("FP64 FFT launch", e);
+    if (ev) cudaEventRecord(ev[1], s);
+    e = launch_dwt_forward_plan(p, p->S, reinterpret_cast<double2 *>(coef), s, kApplyW | kApplyV | kRealSym);
+    if (e != cudaSuccess) return fail_cuda("DWT kernel launch", e);
+    if (ev) cudaEventRecord(ev[2], s);
+    return SOFT_OK;
+}
+
+soft_status soft_inverse_real(soft_plan p, const double *coef, double *grid, void *stream) {
+    soft_status st = check_plan_args(p, coef, grid);
+    if (st != SOFT_OK) return st;
+    if (p->dtype != SOFT_FP64 || !p->tw64) return SOFT_ERR_UNSUPPORTED;
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t *ev = timing_slot(p, 1);
+    if (ev) cudaEventRecord(ev[0], s);
+    cudaError_t e = launch_zero_nyquist(p->B, p->S, s);
+    if (e != cudaSuccess) return fail_cuda("S clearing kernel launch", e);
+    e = launch_dwt_inverse_plan(p, reinterpret_cast<const double2 *>(coef), p->S, s, kRealSym);
+    if (e != cudaSuccess) return fail_cuda("iDWT kernel launch", e);
+    if (ev) cudaEventRecord(ev[1], s);
+    e = launch_fft64_2d_to_real(p->B, p->S, grid, p->tw64, -1, s);
+    if (e != cudaSuccess) return fail_cuda("FP64 FFT launch", e);
+    if (ev) cudaEventRecord(ev[2], s);
+    return SOFT_OK;
+}
+
 soft_status soft_forward_adjoint(soft_plan p, const double *coef, double *grid, void *stream) {
     soft_status st = check_plan_args(p, coef, grid);
     if (st != SOFT_OK) return st;

@@ -237,7 +237,11 @@ __device__ inline void load_cluster(const Tables &tb, int m, int mp, ClusterSmem
 // and their adjoints, with the same kernels,
 //   forward^H  = E^H W T^T V     (iDWT with kApplyV on the coefficients, kApplyW on S)
 //   inverse^H  = T E             (DWT with no flag).
-enum DwtFlags : int { kApplyW = 1, kApplyV = 2 };
+// kRealSym (FP64 kernels): the grid is real, so f(l,-m,-m') =
+// (-1)^(m-m') conj f(l,m,m') and S(-m,-m';j) = conj S(m,m';j); of each
+// conjugate pair of partners (2k, 2k+1) only 2k is contracted and 2k+1 is
+// written from it (the forward writes its coefficients, the iDWT its S).
+enum DwtFlags : int { kApplyW = 1, kApplyV = 2, kRealSym = 4 };
 
 // One transform of a batch for the persistent inverse DWT (FP64, B <= 128).
 struct BatchXform {
@@ -293,6 +297,12 @@ size_t fft64_twiddle_count(int B);
 cudaError_t launch_fft64_twiddles(int B, FftTw64 *tw, cudaStream_t s);
 cudaError_t launch_fft64_2d(int B, const double2 *in, double2 *out, const FftTw64 *tw, int sign, cudaStream_t s,
                             int nslices);
+// All 2B slices of a real grid `in` ((2B)^3 doubles) into the complex `out`.
+cudaError_t launch_fft64_2d_from_real(int B, const double *in, double2 *out, const FftTw64 *tw, int sign,
+                                      cudaStream_t s);
+// All 2B slices of a complex `in` with a real result (Hermitian input): `in`
+// is overwritten and the real parts go to `out` ((2B)^3 doubles).
+cudaError_t launch_fft64_2d_to_real(int B, double2 *in, double *out, const FftTw64 *tw, int sign, cudaStream_t s);
 // FP64-accurate tensor-core DWT / iDWT (dwt_fp64tc.cu); same S layout and
 // flags as the FP64 launchers; need the plan's per-cluster tables.
 cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s,
