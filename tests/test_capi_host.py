@@ -90,6 +90,10 @@ def test_null_plan_handling(lib):
     assert lib.soft_forward(None, None, None, None) == capi.SOFT_ERR_INVALID_ARG
     assert lib.soft_inverse(None, None, None, None) == capi.SOFT_ERR_INVALID_ARG
     assert lib.soft_plan_sync(None) == capi.SOFT_ERR_INVALID_ARG
+    assert lib.soft_forward_real(None, None, None, None) == capi.SOFT_ERR_INVALID_ARG
+    assert lib.soft_inverse_real(None, None, None, None) == capi.SOFT_ERR_INVALID_ARG
+    assert lib.soft_forward_host(None, None, None, None) == capi.SOFT_ERR_INVALID_ARG
+    assert lib.soft_inverse_host(None, None, None, None) == capi.SOFT_ERR_INVALID_ARG
     assert capi.status_string(capi.SOFT_ERR_TIMEOUT) == "SOFT_ERR_TIMEOUT"
     assert capi.status_string(99) == "SOFT_ERR_UNKNOWN"
 
@@ -103,3 +107,12 @@ def test_header_enums_match_the_binding():
             "SOFT_ERR_TIMEOUT", "SOFT_ERR_DEVICE"} <= set(found)
     for name, value in found.items():
         assert getattr(capi, name) == int(value), name
+
+
+def test_launch_count_without_gpu(lib):
+    """Calls rejected on the host launch nothing: the counter does not move."""
+    c0 = capi.soft_launch_count()
+    assert c0 >= 0
+    assert lib.soft_forward(None, None, None, None) == capi.SOFT_ERR_INVALID_ARG
+    assert lib.soft_forward_real(None, None, None, None) == capi.SOFT_ERR_INVALID_ARG
+    assert capi.soft_launch_count() == c0
