@@ -1,0 +1,57 @@
+"""Host-side pieces of bench.py, on the CPU: the algorithmic work the roofline
+divides by, counted by brute force over the clusters, and the workload table.
+"""
+import os
+
+import pytest
+
+import bench
+
+
+def _clusters(B):
+    """Representatives m >= m' >= 0 and their partner counts (1, 4 or 8), as
+    the symmetry relations of Eq. (Wigner_symmetries) group the order pairs."""
+    for m in range(B):
+        for mp in range(m + 1):
+            yield m, mp, 1 if m == mp == 0 else 4 if (mp == 0 or m == mp) else 8
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 8, 17, 64])
+def test_dwt_flops_by_brute_force(B):
+    fl = bench.dwt_flops(B)
+    n = 2 * B
+    # every order pair (m, m') with |m|, |m'| < B has the run l = max(|m|,|m'|) .. B-1
+    runs = sum(B - max(abs(m), abs(mp)) for m in range(1 - B, B) for mp in range(1 - B, B))
+    assert runs == B * (4 * B * B - 1) // 3
+    # each coefficient: 2B real-weighted complex terms, one FMA (2 flops) per real part
+    assert fl["contraction"] == runs * n * 2 * 2
+    # the clusters cover every order pair once
+    assert sum(np_ for _, _, np_ in _clusters(B)) == (2 * B - 1) ** 2
+    # one Wigner-d column block per cluster: B - m degrees x 2B samples, 2 FMAs each
+    entries = sum((B - m) * n for m, _, _ in _clusters(B))
+    assert fl["t_entries"] == entries
+    assert fl["recurrence"] == 4 * entries
+
+
+def test_dwt_flops_at_the_benchmark_size():
+    fl = bench.dwt_flops(64)
+    assert fl["contraction"] + fl["recurrence"] == 202_375_168  # the bench line's algorithmic_flops_per_launch
+
+
+def test_workloads_are_well_formed():
+    for name, (B, mode, kind, desc) in bench.WORKLOADS.items():
+        assert 1 <= B <= 512 and desc
+        assert mode in ("fp64", "fp64_real", "fp64_tc", "bf16x3", "tf32"), name
+        assert kind in ("uniform", "gauss_decay"), name
+        if mode == "fp64_real":  # the real entry points need power-of-two 2B
+            assert (2 * B) & (2 * B - 1) == 0, name
+    assert bench.WORKLOADS["b64"][:2] == (64, "fp64")  # the default workload
+
+
+def test_traffic_entries_name_existing_sources():
+    for (kernel, B), (nbytes, src, sha) in bench.TRAFFIC.items():
+        path = os.path.join(bench.ROOT, "paper_1808_00896_gb300", "csrc", src)
+        assert os.path.exists(path), src
+        assert kernel in open(path).read(), (kernel, src)
+        assert nbytes > 16 * (2 * B) ** 3, "a forward DWT reads all of S at least once"
+        assert len(sha) == 16
