@@ -56,9 +56,11 @@ typedef enum {
     SOFT_FP64 = 0,         /* every step in FP64 */
     SOFT_MIXED_BF16X3 = 1, /* contraction on tcgen05 tensor cores, split BF16 x3 (rel-L2 <= 5e-5) */
     SOFT_MIXED_TF32 = 2,   /* contraction on tcgen05 tensor cores, TF32 (rel-L2 <= 2e-3) */
-    SOFT_FP64_TC = 3       /* FP64 recurrence, S and FFTs; contraction on tcgen05 tensor cores as exact
-                            * fixed-point BF16 digit products (7 base-128 digits per operand, FP32 TMEM
-                            * sums exact for the leading levels), FP64 accuracy (rel-L2 <= 1e-10) */
+    SOFT_FP64_TC = 3       /* FP64 recurrence and S; 2-D FFTs in double-float arithmetic (pairs of
+                            * floats, ~48 bits; cuFFT Z2Z when 2B is not a power of two); contraction
+                            * on tcgen05 tensor cores as exact fixed-point BF16 digit products (7
+                            * base-128 digits per operand, FP32 TMEM sums exact for the leading
+                            * levels); FP64 accuracy (rel-L2 <= 1e-10) */
 } soft_dtype;
 
 /* Largest bandwidth B the kernels accept. */
