@@ -259,7 +259,8 @@ soft_status soft_plan_set_variant(soft_plan p, int kernel, int variant);
  * path can be exercised without a real failure.  Asynchronous on `stream`. */
 soft_status soft_selftest_bounded_wait(soft_plan p, int polls, void *stream);
 
-/* Per-phase timing.  When enabled, every soft_forward / soft_inverse records
+/* Per-phase timing.  When enabled, every soft_forward / soft_inverse (and
+ * soft_forward_real / soft_inverse_real) records
  * CUDA events (on the call's stream) around its 2-D FFT and its (i)DWT
  * kernel(s); soft_plan_read_timing() waits for them, adds up the elapsed
  * times since the last read and resets the sums.  ms_out[4] receives the
