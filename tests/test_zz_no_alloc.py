@@ -8,7 +8,6 @@ in a row (different bandwidths, so the second call must not depend on what the
 first left in the shared array), with the FP64 tolerance of the other parity
 tests.  This file is named to be collected last.
 """
-import ctypes
 
 import numpy as np
 import pytest
