@@ -2,17 +2,28 @@
 
 One step = one forward transform (2-D FFTs + DWT) and one inverse transform
 (iDWT + 2-D FFTs) of one band-limited function at bandwidth B, through the C
-ABI.  Default workload: B = 64 in FP64 (128^3 complex128 grid, 32 MiB;
-coefficients complex Gaussian scaled by 1/(l+1)).  The inputs rotate over
-enough distinct grids/coefficient vectors that one pass over them exceeds the
-129 MB L2, so no step starts with its input cached.
+ABI.  Default workload: B = 256 in FP64 (512^3 complex128 grid, 2 GiB;
+coefficients complex Gaussian scaled by 1/(l+1)).  Below B = 256 the inputs
+rotate over enough distinct grids/coefficient vectors that one pass over them
+exceeds the 129 MB L2; from B = 256 up one input alone exceeds it.
 
 Printed JSON line (rank 0):
   value        device-timed fwd+inv pairs/s over the timed steps (CUDA events)
   e2e          the same through soft_forward_host / soft_inverse_host with
                pinned host buffers, host<->device copies inside the timing
   roofline     dominant kernel (the FP64 DWT or iDWT) against the FP64 pipe
-  cpu_baseline the FP64 CPU oracle on a bounded sample, single core
+  rel_l2       the timed outputs against the FP64 oracle: forward coefficients
+               of sampled order pairs (all lengths), inverse values at sampled
+               grid points, each computed one by one by the oracle
+  modes        (default workload, one GPU) the same measurement for B = 128,
+               256, 512 in each precision mode (fp64, fp64_tc, bf16x3, tf32):
+               pairs/s, per-phase ms, FP64-pipe fraction, tensor TFLOP/s and
+               rel-L2 against the oracle, on identical inputs per B
+  cpu_baseline the FP64 CPU oracle on all host cores (OpenMP over order pairs
+               and slices) at the workload's B, plus a single-thread figure;
+               a full round trip when it fits the time budget, else a timed
+               sample of every stride-th row of order pairs and slice,
+               extrapolated (labelled)
 
 Multi-GPU (torchrun): the transforms are independent, so every rank runs its
 own replica of the workload (weak scaling, no collective on the data path).
@@ -197,59 +208,152 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline_oracle(B: int, kind: str, budget_s: float) -> dict:
-    """The FP64 oracle, as it stands, on one host core: full forward+inverse
-    round trips at bandwidth B until `budget_s` seconds have elapsed (>= 1)."""
-    import numpy as np
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
+
+class OracleTimer:
+    """Times the FP64 CPU oracle's forward+inverse round trip at bandwidth B on
+    a given number of threads.  A full round trip at B >= 256 takes minutes on
+    one core, so it can also take a timed SAMPLE: the oracle's strided runs
+    process every stride-th row of order pairs and every stride-th beta slice
+    plus the full run's fixed costs (the copies of the grid), and a run with a
+    stride above 4B measures those fixed costs alone.  The full time is then
+    extrapolated as fixed + stride x (sample - fixed)."""
+
+    def __init__(self, B: int, coef, grid):
+        import numpy as np
+
+        import oracle
+        self.oracle = oracle
+        oracle.build()
+        self.B = B
+        self.coef = coef
+        self.grid = grid
+        self.gbuf = np.zeros_like(grid)
+        self.cbuf = np.zeros_like(coef)
+
+    def _round_trip(self, stride: int) -> float:
+        t0 = time.perf_counter()
+        if stride == 1:
+            self.oracle.inverse(self.B, self.coef)
+            self.oracle.forward(self.B, self.grid)
+        else:
+            self.oracle.inverse_strided(self.B, self.coef, stride, out=self.gbuf)
+            self.oracle.forward_strided(self.B, self.grid, stride, out=self.cbuf)
+        return time.perf_counter() - t0
+
+    def fixed(self) -> float:
+        return self._round_trip(1 << 30)
+
+    def sampled(self, stride: int, fixed: float) -> float:
+        """Extrapolated seconds of one full round trip from one strided run."""
+        if stride <= 1:
+            return self._round_trip(1)
+        return fixed + stride * max(0.0, self._round_trip(stride) - fixed)
+
+    def measure(self, threads: int, budget_s: float, allow_full: bool = True) -> dict:
+        """Seconds per full round trip on `threads` threads within about
+        budget_s of CPU time: a full run when the first sample's estimate
+        fits, else the extrapolated sample at the smallest stride that fits."""
+        prev = self.oracle.set_threads(threads)
+        try:
+            B = self.B
+            rows = 2 * B - 1
+            s0 = max(1, rows // 16)  # a first sample of 16 rows
+            fixed = self.fixed()
+            est = self.sampled(s0, fixed)
+            if allow_full and est <= budget_s:
+                t, stride, how = self._round_trip(1), 1, f"1 full B={B} round trip"
+            else:
+                stride = max(1, min(s0, math.ceil(est / max(1e-3, budget_s))))
+                t = est if stride == s0 else self.sampled(stride, fixed)
+                how = (f"B={B} round trip extrapolated from a timed sample of every {stride}-th row of order pairs "
+                       f"and beta slice ({(rows + stride - 1) // stride} of {rows} rows): fixed costs "
+                       f"{fixed:.2f} s + {stride} x the sampled per-row work")
+            used = self.oracle.threads()
+        finally:
+            self.oracle.set_threads(prev)
+        return {"seconds": t, "how": how, "threads": used, "stride": stride}
+
+
+def cpu_baseline_oracle(B: int, kind: str, budget_s: float, seed: int) -> dict:
+    """The FP64 oracle, as it stands, at bandwidth B: on all host cores
+    (OpenMP) and on one thread, each as a full round trip when it fits the
+    budget, else a timed sample extrapolated to the full round trip."""
     import oracle
     from paper_1808_00896_gb300 import synth
     oracle.build()
-    coef = synth.coefficients(B, kind, seed=synth.BASE_SEED + 7)
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        g = oracle.inverse(B, coef)
-        oracle.forward(B, g)
-        k += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} full B={B} FP64 forward+inverse round trip(s) in {dt:.1f} s, single thread"}
+    coef = synth.coefficients(B, kind, seed=seed)
+    grid = synth.random_grid(B, seed=seed + 1)  # the oracle's time does not depend on the values
+    tm = OracleTimer(B, coef, grid)
+    cores = host_cores()
+    allc = tm.measure(cores, budget_s)
+    one = tm.measure(1, budget_s / 2, allow_full=B <= 64)
+    return {"value": 1.0 / allc["seconds"], "unit": UNIT, "cores": allc["threads"], "kind": "oracle",
+            "sample": f"{allc['how']} on {allc['threads']} threads (OpenMP over order pairs and slices; "
+                      f"nproc {cores})",
+            "single_thread": {"value": 1.0 / one["seconds"], "unit": UNIT, "cores": 1, "sample": one["how"]},
+            "omp_speedup": one["seconds"] / allc["seconds"]}
+
+
+def workload_config(args, B: int, dtype: str, kind: str, world: int) -> dict:
+    """The `config` dict of a workload, the same for both arms."""
+    n = 2 * B
+    grid_bytes = 16 * n ** 3
+    coef_bytes = 16 * (B * (4 * B * B - 1) // 3)
+    R = 1 if B >= 256 else max(1, min(8, math.ceil(2 * L2_BYTES / (grid_bytes + coef_bytes))))
+    return {"workload": WORKLOADS[args.workload][3], "B": B, "mode": dtype, "coefficients": kind,
+            "inputs_rotated": R, "tile_variants": None,
+            "l2": f"{R} rotating input sets of {(grid_bytes + coef_bytes) / 2**20:.1f} MiB (> 129 MB L2 per pass)"
+            if R > 1 else "single input larger than L2",
+            "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args) -> None:
-    """--impl reference: the CPU oracle timed as it stands on one host core, on
-    the same workload, metric and unit.  One oracle round trip at B = 64 takes
-    seconds, so the run is bounded: one untimed warm-up round trip, then at
-    most --steps round trips and at most --ref-seconds of timed work."""
+    """--impl reference: the CPU oracle timed as it stands on the machine's host
+    cores (OpenMP over order pairs and slices), on the same workload, metric,
+    unit and config.  Each step is a bounded sample: the oracle's strided
+    round trip over every stride-th row of order pairs and beta slice, with
+    the stride picked so a step takes a few seconds, extrapolated to the full
+    round trip as fixed + stride x (sample - fixed) (fixed costs measured once
+    in the warm-up)."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    B, _, kind, desc = WORKLOADS[args.workload]
+    B, dtype, kind, desc = WORKLOADS[args.workload]
     import oracle
     from paper_1808_00896_gb300 import synth
     oracle.build()
     coef = synth.coefficients(B, kind, seed=synth.BASE_SEED + 7)
-    oracle.forward(B, oracle.inverse(B, coef))  # warm-up (page-in, caches)
-    t0 = time.perf_counter()
-    k = 0
-    while k < args.steps:
-        oracle.forward(B, oracle.inverse(B, coef))
-        k += 1
-        if time.perf_counter() - t0 >= args.ref_seconds:
-            break
-    dt = time.perf_counter() - t0
-    value = k / dt
-    sample = (f"{k} of the requested {args.steps} full B={B} FP64 forward+inverse round trips "
-              f"(capped at {args.ref_seconds:.0f} s), single thread, after 1 untimed warm-up round trip")
+    grid = synth.random_grid(B, seed=synth.BASE_SEED + 8)
+    tm = OracleTimer(B, coef, grid)
+    cores = host_cores()
+    oracle.set_threads(cores)
+    fixed = tm.fixed()
+    rows = 2 * B - 1
+    s0 = max(1, rows // 16)
+    est = tm.sampled(s0, fixed)  # warm-up and first estimate
+    per_step = max(0.5, min(6.0, args.ref_seconds / max(1, args.steps + args.warmup)))
+    stride = max(1, min(s0, math.ceil(est / per_step)))
+    for _ in range(max(0, args.warmup - 1)):
+        tm.sampled(stride, fixed)
+    ts = [tm.sampled(stride, fixed) for _ in range(args.steps)]
+    dt = sum(ts)
+    value = args.steps / dt
+    how = ("full round trips" if stride == 1 else
+           f"round trips extrapolated from timed samples of every {stride}-th row of order pairs and beta slice "
+           f"({(rows + stride - 1) // stride} of {rows} rows; fixed costs {fixed:.2f} s measured once)")
+    sample = f"{args.steps} B={B} FP64 {how}, {oracle.threads()} threads (nproc {cores}), after {args.warmup} warm-up"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "executed_steps": k, "warmup": args.warmup, "ms_per_step": 1000 * dt / k,
+        "steps": args.steps, "executed_steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": desc, "B": B, "coefficients": kind},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": workload_config(args, B, dtype, kind, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -426,6 +530,206 @@ def run_batched(args) -> None:
         p.close()
 
 
+MODES = ("fp64", "fp64_tc", "bf16x3", "tf32")
+MODE_BS = (128, 256, 512)
+# stated rel-L2 bounds against the FP64 oracle, per mode
+MODE_BOUND = {"fp64": 1e-10, "fp64_tc": 1e-10, "bf16x3": 5e-5, "tf32": 2e-3}
+# tensor-core products per real multiply-add of the contraction: 3 split-BF16
+# pairs, 1 TF32, or the 28 digit pairs (levels 0..6) of the FP64-accurate mode
+TENSOR_MULT = {"bf16x3": 3, "tf32": 1, "fp64_tc": 28}
+PEAK_FP64_GFLOPS = FP64_FLOPS_PER_SM_CLK * N_SM * SM_MAX_MHZ * 1e6 / 1e9
+PEAK_SOURCE = "derived: nominal FP64 1.25 TFLOP/s = 4 flop/clk/SM x 152 SM x 2070 MHz"
+
+
+def sample_pairs(B: int, seed: int, count: int = 16) -> list:
+    """Order pairs whose runs span every length: the extreme cases, then one
+    random pair on each of evenly spaced shells max(|m|,|m'|) = l0."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    pairs = [(0, 0), (B - 1, B - 1), (1 - B, B - 1), (B // 2, -(B // 3))]
+    k = 0
+    while len(pairs) < count:
+        l0 = int(round(k * (B - 1) / max(1, count - 5)))
+        k += 1
+        other = int(rng.integers(-l0, l0 + 1)) if l0 > 0 else 0
+        sgn = 1 if rng.integers(0, 2) else -1
+        pr = (sgn * l0, other) if rng.integers(0, 2) else (other, sgn * l0)
+        if pr not in pairs:
+            pairs.append(pr)
+    return pairs
+
+
+def sample_points(B: int, seed: int, count: int = 16) -> list:
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    n = 2 * B
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (1, B, n - 2)]
+    while len(pts) < count:
+        pts.append(tuple(int(v) for v in rng.integers(0, n, size=3)))
+    return pts  # (i, j, k)
+
+
+class OracleRef:
+    """The FP64 oracle's values for one bandwidth's inputs at sampled order
+    pairs (forward coefficients, whole runs) and sampled grid points (inverse),
+    each computed one by one; compares device outputs against them."""
+
+    def __init__(self, B: int, grid_host, coef_host, seed: int, threads: int, real: bool = False):
+        import numpy as np
+
+        import oracle
+        oracle.build()
+        self.B = B
+        self.pairs = sample_pairs(B, seed)
+        self.pts = sample_points(B, seed + 1)
+        prev = oracle.set_threads(threads)
+        try:
+            self.fwd = np.concatenate(oracle.forward_pairs(B, grid_host, self.pairs))
+            self.inv = oracle.inverse_points(B, coef_host, self.pts)
+        finally:
+            oracle.set_threads(prev)
+        if real:
+            self.inv = self.inv.real
+        from paper_1808_00896_gb300 import capi
+        idx = []
+        for m, mp in self.pairs:
+            l0 = max(abs(m), abs(mp))
+            o = capi.soft_coef_index(B, l0, m, mp)
+            idx.extend(range(o, o + B - l0))
+        n = 2 * B
+        self.coef_idx = np.array(idx, dtype=np.int64)
+        self.grid_idx = np.array([(j * n + i) * n + k for (i, j, k) in self.pts], dtype=np.int64)
+
+    def errors(self, coef_dev, grid_dev) -> dict:
+        import torch
+
+        from paper_1808_00896_gb300 import synth
+        ci = torch.from_numpy(self.coef_idx).to(coef_dev.device)
+        gi = torch.from_numpy(self.grid_idx).to(grid_dev.device)
+        f = coef_dev.reshape(-1)[ci].cpu().numpy()
+        g = grid_dev.reshape(-1)[gi].cpu().numpy()
+        return {"forward": synth.rel_l2(f, self.fwd), "inverse": synth.rel_l2(g, self.inv),
+                "sample": f"{len(self.pairs)} order pairs ({len(self.coef_idx)} coefficients, every run length "
+                          f"band) and {len(self.pts)} grid points vs the oracle's one-by-one forms"}
+
+
+def roofline_numbers(B: int, dtype: str, phase_ms, phase_cnt) -> dict:
+    """Dominant (i)DWT kernel's algorithmic FP64 rate from the library's events:
+    contraction + recurrence for FP64 plans, half the contraction on real
+    grids, the FP64 recurrence alone for the tensor-core modes (whose
+    contraction runs on tcgen05; its TFLOP/s is reported beside)."""
+    fl = dwt_flops(B)
+    real = dtype == "fp64_real"
+    fwd_ms = phase_ms[1] / max(1, phase_cnt[1])
+    inv_ms = phase_ms[2] / max(1, phase_cnt[2])
+    kname = {"fp64": "fp64", "fp64_real": "fp64", "fp64_tc": "tc"}.get(dtype, "mixed")
+    dom, dom_ms = (f"dwt_forward_{kname}_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else \
+        (f"dwt_inverse_{kname}_kernel", inv_ms)
+    algo = fl["contraction"] + fl["recurrence"] if dtype == "fp64" else \
+        fl["contraction"] / 2 + fl["recurrence"] if real else fl["recurrence"]
+    achieved = algo / (dom_ms * 1e-3) / 1e9
+    out = {"kernel": dom, "dom_ms": dom_ms, "algo": algo, "achieved": achieved, "frac": achieved / PEAK_FP64_GFLOPS,
+           "phase_ms_per_launch": {"fft_forward": phase_ms[0] / max(1, phase_cnt[0]), "dwt_forward": fwd_ms,
+                                   "dwt_inverse": inv_ms, "fft_inverse": phase_ms[3] / max(1, phase_cnt[3])}}
+    if dtype in TENSOR_MULT:
+        out["tensor_tflops"] = TENSOR_MULT[dtype] * fl["contraction"] / (dom_ms * 1e-3) / 1e12
+    return out
+
+
+def measure_mode(B: int, mode: str, grid_dev, coef_dev, ref: OracleRef, steps_max: int, warmup: int, dev,
+                 target_s: float = 1.5) -> dict:
+    """One (B, mode) record: forward(grid) + inverse(coef) pairs/s with CUDA
+    events over K steps (K picked for about target_s of timed work, at least
+    2), the library's per-phase events, and the timed outputs' rel-L2 against
+    the oracle."""
+    import torch
+
+    from paper_1808_00896_gb300 import Plan, capi
+    plan = Plan(B, mode, device=dev)
+    try:
+        coef_out = plan.empty_coef()
+        grid_out = plan.empty_grid()
+        stream = torch.cuda.current_stream(dev)
+
+        def step():
+            plan.forward(grid_dev, out=coef_out)
+            plan.inverse(coef_dev, out=grid_out)
+
+        t0 = time.perf_counter()
+        for _ in range(warmup):
+            step()
+        plan.sync()
+        tw = (time.perf_counter() - t0) / max(1, warmup)
+        K = int(max(2, min(steps_max, math.ceil(target_s / max(tw, 1e-6)))))
+        capi.soft_plan_read_timing(plan.handle)
+        capi.soft_plan_enable_timing(plan.handle, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(K):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        plan.sync()
+        ms = ev0.elapsed_time(ev1) / K
+        phase_ms, phase_cnt = capi.soft_plan_read_timing(plan.handle)
+        capi.soft_plan_enable_timing(plan.handle, False)
+        rf = roofline_numbers(B, mode, phase_ms, phase_cnt)
+        err = ref.errors(coef_out, grid_out)
+        full = float(torch.linalg.vector_norm(coef_out - coef_dev) / torch.linalg.vector_norm(coef_dev))
+    finally:
+        plan.close()
+    rec = {"B": B, "mode": mode, "pairs_per_s": 1000.0 / ms, "ms_per_pair": ms, "steps": K,
+           "phase_ms": {k: round(v, 4) for k, v in rf["phase_ms_per_launch"].items()},
+           "kernel": rf["kernel"], "fp64_gflops": rf["achieved"], "frac": rf["frac"],
+           "rel_l2_forward": err["forward"], "rel_l2_inverse": err["inverse"],
+           "rel_l2_forward_vs_input_coef": full, "bound": MODE_BOUND[mode],
+           "within_bound": bool(err["forward"] <= MODE_BOUND[mode] and err["inverse"] <= MODE_BOUND[mode])}
+    if "tensor_tflops" in rf:
+        rec["tensor_tflops"] = rf["tensor_tflops"]
+    return rec
+
+
+def run_modes(Bs, args, dev) -> dict:
+    """The per-(B, mode) table: for each B one band-limited input (complex
+    Gaussian coefficients x 1/(l+1), grid = the FP64 GPU inverse of them),
+    the oracle's sampled values, then every mode on the same inputs."""
+    import torch
+
+    from paper_1808_00896_gb300 import Plan, synth
+    recs = []
+    cores = host_cores()
+    t_start = time.perf_counter()
+    for B in Bs:
+        seed = synth.BASE_SEED + 7 + B
+        coef_h = synth.coefficients(B, "gauss_decay", seed=seed)
+        coef_dev = torch.from_numpy(coef_h).to(dev)
+        with Plan(B, "fp64", device=dev) as p:
+            grid_dev = p.inverse(coef_dev)
+            p.sync()
+        grid_h = grid_dev.cpu().numpy()
+        t0 = time.perf_counter()
+        ref = OracleRef(B, grid_h, coef_h, seed, cores)
+        t_oracle = time.perf_counter() - t0
+        del grid_h
+        per_b = []
+        for mode in MODES:
+            per_b.append(measure_mode(B, mode, grid_dev, coef_dev, ref, args.steps, args.warmup, dev))
+            per_b[-1]["oracle_ref_s"] = round(t_oracle, 2)
+        base = next(r["pairs_per_s"] for r in per_b if r["mode"] == "fp64")
+        for r in per_b:
+            r["speedup_vs_fp64"] = r["pairs_per_s"] / base
+        recs.extend(per_b)
+        del grid_dev, coef_dev
+        torch.cuda.empty_cache()
+    return {"records": recs, "inputs": "per B: coefficients complex Gaussian x 1/(l+1) (seed BASE_SEED+7+B), grid = "
+                                      "FP64 GPU inverse of them; identical for every mode",
+            "rel_l2": "timed outputs vs the FP64 oracle: whole runs of 16 sampled order pairs (forward) and 16 grid "
+                      "points (inverse), the oracle's one-by-one forms on all host cores",
+            "frac": "dominant (i)DWT kernel's algorithmic FP64 flops / duration vs the derived FP64 peak "
+                    "(fp64: contraction + recurrence; tensor-core modes: the FP64 recurrence, tensor TFLOP/s beside)",
+            "seconds": round(time.perf_counter() - t_start, 1)}
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -446,13 +750,14 @@ def run_ours(args) -> None:
     n = 2 * B
     grid_bytes = 16 * n ** 3
     coef_bytes = 16 * synth.num_coeffs(B)
-    R = max(1, min(8, math.ceil(2 * L2_BYTES / (grid_bytes + coef_bytes))))
-    if B >= 256:
-        R = 1  # one input already exceeds L2 several times over
+    config = workload_config(args, B, dtype, kind, world)
+    R = config["inputs_rotated"]
 
     real = dtype == "fp64_real"  # real grids: soft_forward_real / soft_inverse_real on an FP64 plan
     plan = Plan(B, "fp64" if real else dtype, device=dev)
     tuned = plan.tune() if args.tune else None
+    if tuned is not None:
+        config["tile_variants"] = {"dwt": tuned["dwt"], "idwt": tuned["idwt"]}
     coefs = [torch.from_numpy(synth.coefficients(B, kind, seed=synth.BASE_SEED + 100 * rank + r)).to(dev)
              for r in range(R)]
     grids = [plan.inverse(c) for c in coefs]
@@ -489,8 +794,8 @@ def run_ours(args) -> None:
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n_launch0 = capi.soft_launch_count()
     ev0.record(stream)
-    for s in range(args.steps):
-        step(s % R)
+    for s_ in range(args.steps):
+        step(s_ % R)
     ev1.record(stream)
     gpu_launches = capi.soft_launch_count() - n_launch0
     torch.cuda.synchronize(dev)
@@ -502,6 +807,7 @@ def run_ours(args) -> None:
     plan.sync()
     phase_ms, phase_cnt = capi.soft_plan_read_timing(plan.handle)
     capi.soft_plan_enable_timing(plan.handle, False)
+    last = (args.steps - 1) % R  # the input set of the last timed step: its outputs are checked below
 
     ms_per_step = ms_total / args.steps
     value = world * 1000.0 / ms_per_step
@@ -517,6 +823,14 @@ def run_ours(args) -> None:
     g_res = torch.empty_like(g_host, pin_memory=True)
     gh, ch, cr, gr = g_host.numpy(), c_host.numpy(), c_res.numpy(), g_res.numpy()
     g_dev, c_dev = torch.empty_like(grids[0]), plan.empty_coef()
+
+    # rel-L2 of the timed outputs against the oracle (outside every timed region)
+    rel = None
+    if rank == 0:
+        ref = OracleRef(B, np.ascontiguousarray(grids[last].cpu().numpy()).astype(np.complex128),
+                        coefs[last].cpu().numpy(), synth.BASE_SEED + 11 + B, host_cores(), real=real)
+        rel = ref.errors(coef_out, grid_out)
+        rel["bound"] = MODE_BOUND.get("fp64" if real else dtype)
 
     def e2e_step():
         if real:
@@ -545,58 +859,41 @@ def run_ours(args) -> None:
            "steps": e2e_steps}
 
     # Roofline of the dominant kernel, from the library's CUDA events.
-    fl = dwt_flops(B)
-    fwd_ms = phase_ms[1] / max(1, phase_cnt[1])
-    inv_ms = phase_ms[2] / max(1, phase_cnt[2])
-    kname = {"fp64": "fp64", "fp64_real": "fp64", "fp64_tc": "tc"}.get(dtype, "mixed")
-    dom, dom_ms = (f"dwt_forward_{kname}_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else \
-        (f"dwt_inverse_{kname}_kernel", inv_ms)
-    peak_gflops = FP64_FLOPS_PER_SM_CLK * N_SM * SM_MAX_MHZ * 1e6 / 1e9
-    # FP64 path: contraction + recurrence on the FP64 pipe.  Mixed modes: the
-    # FP64 recurrence is the binding term (the contraction runs on tensor cores).
-    # Real grids: half the contraction (one partner of each conjugate pair).
-    algo = fl["contraction"] + fl["recurrence"] if dtype == "fp64" else \
-        fl["contraction"] / 2 + fl["recurrence"] if real else fl["recurrence"]
-    achieved = algo / (dom_ms * 1e-3) / 1e9
-    tr = None if real else TRAFFIC.get((dom, B))
+    rf = roofline_numbers(B, dtype, phase_ms, phase_cnt)
+    tr = None if real else TRAFFIC.get((rf["kernel"], B))
     traffic = tr[0] if (tr and tr[2] == kernel_source_sha(tr[1])) else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s",
-                "frac": achieved / peak_gflops, "traffic": traffic, "kernel": dom,
-                "peak_source": "derived: nominal FP64 1.25 TFLOP/s = 4 flop/clk/SM x 152 SM x 2070 MHz",
-                "algorithmic_flops_per_launch": algo,
-                "phase_ms_per_launch": {"fft_forward": phase_ms[0] / max(1, phase_cnt[0]),
-                                        "dwt_forward": fwd_ms, "dwt_inverse": inv_ms,
-                                        "fft_inverse": phase_ms[3] / max(1, phase_cnt[3])}}
-    if dtype not in ("fp64", "fp64_real"):
-        # tensor-core products per real multiply-add of the contraction: 3 split-BF16
-        # pairs, 1 TF32, or the 28 digit pairs (levels 0..6) of the FP64-accurate mode
-        mult = {"bf16x3": 3, "fp64_tc": 28}.get(dtype, 1)
-        roofline["tensor_tflops_achieved"] = mult * fl["contraction"] / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": rf["achieved"], "peak": PEAK_FP64_GFLOPS, "unit": "GFLOP/s",
+                "frac": rf["frac"], "traffic": traffic, "kernel": rf["kernel"], "peak_source": PEAK_SOURCE,
+                "algorithmic_flops_per_launch": rf["algo"], "phase_ms_per_launch": rf["phase_ms_per_launch"]}
+    if "tensor_tflops" in rf:
+        roofline["tensor_tflops_achieved"] = rf["tensor_tflops"]
         roofline["note"] = ("tensor-core contraction: frac is the FP64 Wigner-d recurrence (2 FMA per T entry) "
                             "against the FP64 pipe; tensor_tflops_achieved counts the contraction's tensor-core flops")
+    plan.close()
+    del grids, coefs, g_dev, c_dev, coef_out, grid_out
+    torch.cuda.empty_cache()
+
+    modes = None
+    want_modes = args.modes != "off" and world == 1 and (args.modes != "auto" or args.workload == "b256")
+    if want_modes:
+        Bs = MODE_BS if args.modes == "auto" else tuple(int(x) for x in args.modes.split(","))
+        modes = run_modes(Bs, args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_oracle(min(B, 64), kind, args.cpu_seconds)
-        if B > 64:
-            cpu["sample"] += f" (B={B} oracle is O(B^4); sample taken at B=64, not rescaled)"
-            cpu["value"] = None
+        cpu = cpu_baseline_oracle(B, kind, args.cpu_seconds, synth.BASE_SEED + 7)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if dtype in ("fp64", "fp64_real") else dtype, "data": "synthetic",
-            "config": {"workload": desc, "B": B, "mode": dtype, "coefficients": kind, "inputs_rotated": R,
-                       "tile_variants": None if tuned is None else {"dwt": tuned["dwt"], "idwt": tuned["idwt"]},
-                       "l2": f"{R} rotating input sets of {(grid_bytes + coef_bytes) / 2**20:.1f} MiB "
-                             f"(> 129 MB L2 per pass)" if R > 1 else "single input larger than L2",
-                       "parallelism": f"replicas x{world}"},
-            "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks,
-            "cpu_baseline": cpu,
+            "config": config, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks,
+            "rel_l2": rel, "cpu_baseline": cpu,
         }
+        if modes is not None:
+            line["modes"] = modes
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -607,10 +904,13 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [CORR_WORKLOAD[0]], default="b64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [CORR_WORKLOAD[0]], default="b256")
     ap.add_argument("--e2e-steps", type=int, default=50)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=30.0,
+                    help="budget of the all-core oracle round trip (a full run when it fits, else a sample)")
     ap.add_argument("--ref-seconds", type=float, default=120.0)
+    ap.add_argument("--modes", default="auto",
+                    help="per-mode table: 'auto' (default workload on one GPU), 'off', or B list like '128,256'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune", action="store_true", help="autotune the DWT tile shapes before timing")
     args = ap.parse_args()

@@ -29,6 +29,13 @@ the FFT on SO(3)" (arXiv:1808.00896):
 * ``forward_adjoint`` / ``inverse_adjoint`` -- the adjoints of the two
                                  transforms: E^H W T^T V and T E (E the
                                  per-slice DFT with exp(+i))
+* ``set_threads``             -- OpenMP threads for the loops over independent
+                                 order pairs, slices, sampled pairs and points
+                                 (1 by default; results do not depend on it)
+* ``forward_strided`` / ``inverse_strided`` -- timing samples: every
+                                 stride-th beta slice and row m of order pairs
+                                 only (not a transform; used to time the oracle
+                                 at sizes where a full run takes too long)
 
 Every function is pinned by tests in ``tests/test_oracle_*.py`` to closed
 forms, a textbook routine (sympy's Wigner-d, scipy's Jacobi polynomials),
@@ -49,10 +56,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile soft_oracle.c into liboracle.so with gcc (no fast-math)."""
+    """Compile soft_oracle.c into liboracle.so with gcc (no fast-math), with
+    OpenMP when the compiler has it."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-o", tmp, _SRC]
+        try:
+            subprocess.check_call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -79,6 +91,11 @@ def _load():
             "oracle_dft2_slices": (None, [c_int, c_int, dp, c_int]),
             "oracle_forward": (c_int, [c_int, dp, dp]),
             "oracle_inverse": (c_int, [c_int, dp, dp]),
+            "oracle_forward_strided": (c_int, [c_int, dp, dp, c_int]),
+            "oracle_inverse_strided": (c_int, [c_int, dp, dp, c_int]),
+            "oracle_set_threads": (None, [c_int]),
+            "oracle_get_threads": (c_int, []),
+            "oracle_openmp": (c_int, []),
             "oracle_direct_forward": (c_int, [c_int, dp, dp]),
             "oracle_direct_inverse": (c_int, [c_int, dp, dp]),
             "oracle_forward_pairs": (c_int, [c_int, dp, c_int, ip, dp]),
@@ -105,6 +122,26 @@ def _ip(a: np.ndarray):
 
 def _as_c128(x) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+
+
+def set_threads(n: int) -> int:
+    """Threads for the oracle's parallel loops (over order pairs, beta slices,
+    sampled pairs and sampled points); returns the previous count.  Without
+    OpenMP the loops stay serial whatever is set."""
+    lib = _load()
+    prev = int(lib.oracle_get_threads())
+    lib.oracle_set_threads(int(n))
+    return prev
+
+
+def threads() -> int:
+    """Threads the parallel loops use (1 when built without OpenMP)."""
+    lib = _load()
+    return int(lib.oracle_get_threads()) if lib.oracle_openmp() else 1
+
+
+def openmp() -> bool:
+    return bool(_load().oracle_openmp())
 
 
 def num_coeffs(B: int) -> int:
@@ -200,6 +237,33 @@ def inverse(B: int, coef) -> np.ndarray:
     rc = _load().oracle_inverse(B, _dp(c.view(np.float64)), _dp(out.view(np.float64)))
     if rc:
         raise RuntimeError(f"oracle_inverse failed ({rc})")
+    return out
+
+
+def forward_strided(B: int, grid, stride: int, out: np.ndarray | None = None) -> np.ndarray:
+    """TIMING SAMPLE of ``forward``: only the beta slices j with j % stride
+    == 0 and the rows m of order pairs with (m + B - 1) % stride == stride // 2
+    are processed: about 1/stride of the per-slice and per-pair work, plus the
+    full run's fixed costs (the copy of the grid).  A stride above 4B leaves
+    the fixed costs alone.  Not a transform."""
+    g = _check_grid(B, grid)
+    if out is None:
+        out = np.zeros(num_coeffs(B), dtype=np.complex128)
+    rc = _load().oracle_forward_strided(B, _dp(g.view(np.float64)), _dp(out.view(np.float64)), int(stride))
+    if rc:
+        raise RuntimeError(f"oracle_forward_strided failed ({rc})")
+    return out
+
+
+def inverse_strided(B: int, coef, stride: int, out: np.ndarray | None = None) -> np.ndarray:
+    """TIMING SAMPLE of ``inverse`` (see ``forward_strided``)."""
+    c = _check_coef(B, coef)
+    n = 2 * B
+    if out is None:
+        out = np.zeros((n, n, n), dtype=np.complex128)
+    rc = _load().oracle_inverse_strided(B, _dp(c.view(np.float64)), _dp(out.view(np.float64)), int(stride))
+    if rc:
+        raise RuntimeError(f"oracle_inverse_strided failed ({rc})")
     return out
 
 

@@ -16,13 +16,38 @@
  *     it is this library's choice and the oracle rebuilds it by plain counting.)
  *
  * Accumulation is straight FP64 in the order the formulas are written.
+ *
+ * Threads: when compiled with -fopenmp, the loops over independent order
+ * pairs (m,m'), beta slices, sampled pairs and sampled grid points run on
+ * oracle_set_threads() threads (1 by default).  Each pair, slice or point is
+ * still computed by one thread in the order written above, so the results do
+ * not depend on the thread count.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_PI 3.14159265358979323846264338327950288
+
+static int g_threads = 1;
+
+/* Threads for the parallel loops (clamped to >= 1; ignored without OpenMP). */
+void oracle_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+int oracle_get_threads(void) { return g_threads; }
+
+/* 1 when this build runs its loops with OpenMP. */
+int oracle_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Sampling angles and quadrature weights, Eq. (quadrature) and Eq. (weights) */
@@ -243,14 +268,22 @@ void oracle_dft1(int n, double *x, int stride, int sign)
     free(tmp);
 }
 
-/* In place on each of nslices contiguous n x n slices. */
-void oracle_dft2_slices(int nslices, int n, double *data, int sign)
+/* In place on the contiguous n x n slices s = 0, stride, 2 stride, ... < nslices
+ * (stride 1: every slice; larger strides only serve timing samples). */
+static void dft2_slices_strided(int nslices, int n, double *data, int sign, int stride)
 {
-    for (int s = 0; s < nslices; ++s) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+    for (int s = 0; s < nslices; s += stride) {
         double *sl = data + 2 * (int64_t)s * n * n;
         for (int r = 0; r < n; ++r) oracle_dft1(n, sl + 2 * (int64_t)r * n, 1, sign); /* along k */
         for (int c = 0; c < n; ++c) oracle_dft1(n, sl + 2 * (int64_t)c, n, sign);     /* along i */
     }
+}
+
+/* In place on each of nslices contiguous n x n slices. */
+void oracle_dft2_slices(int nslices, int n, double *data, int sign)
+{
+    dft2_slices_strided(nslices, n, data, sign, 1);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -262,15 +295,33 @@ static int mod_n(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
 /* S(m,m';j) = sum_{i,k} f(alpha_i,beta_j,gamma_k) exp(+i(m alpha_i + m' gamma_k)),
  * i.e. an unnormalised 2-D DFT with the + sign on every beta slice. Stored
  * as S[j][m mod 2B][m' mod 2B]. */
-static double *forward_separation(int B, const double *grid)
+static double *forward_separation(int B, const double *grid, int stride)
 {
     int n = 2 * B;
     size_t cnt = (size_t)2 * n * n * n;
     double *S = (double *)malloc(sizeof(double) * cnt);
     if (!S) return NULL;
     memcpy(S, grid, sizeof(double) * cnt);
-    oracle_dft2_slices(n, n, S, +1);
+    dft2_slices_strided(n, n, S, +1, stride);
     return S;
+}
+
+/* Start of the run of every (m,m') in the coefficient array, in layout order
+ * (index (m+B-1)(2B-1) + (m'+B-1)), counted out as the layout is defined. */
+static int64_t *run_starts(int B)
+{
+    int R = 2 * B - 1;
+    int64_t *o = (int64_t *)malloc(sizeof(int64_t) * (size_t)R * R);
+    if (!o) return NULL;
+    int64_t off = 0;
+    size_t p = 0;
+    for (int m = 1 - B; m <= B - 1; ++m)
+        for (int mp = 1 - B; mp <= B - 1; ++mp) {
+            int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
+            o[p++] = off;
+            off += B - l0;
+        }
+    return o;
 }
 
 /* The DWT of orders (m,m'): f(l,m,m') = (2l+1)/(8 pi B) sum_j w_B(j) d(l,m,m';beta_j) S(m,m';j),
@@ -297,45 +348,77 @@ static void dwt_pair(int B, int m, int mp, const double *S, const double *w, dou
     }
 }
 
-/* Forward SOFT: grid (2B)^3 complex -> coef (B(4B^2-1)/3 complex). Returns 0 on success. */
-int oracle_forward(int B, const double *grid, double *coef)
+/* Forward SOFT: grid (2B)^3 complex -> coef (B(4B^2-1)/3 complex). Returns 0 on success.
+ * stride > 1 is a TIMING SAMPLE, not a transform: only the slices j with
+ * j mod stride = 0 and the rows m of order pairs with (m+B-1) mod stride =
+ * stride/2 (the middle of each block of rows, so that the sampled rows'
+ * lengths average like all rows') are computed, every pair (m,m') of a
+ * sampled row in layout order, so the per-pair and per-slice work is about
+ * 1/stride of the full run's while the memory access pattern stays that of
+ * the full run.  A stride above 4B leaves only the fixed costs (the copy of
+ * the grid, one slice).  The other coefficients are left as they are and the
+ * computed ones read unprocessed slices. */
+int oracle_forward_strided(int B, const double *grid, double *coef, int stride)
 {
-    if (B < 1) return 1;
-    int n = 2 * B;
-    double *S = forward_separation(B, grid);
+    if (B < 1 || stride < 1) return 1;
+    int n = 2 * B, R = 2 * B - 1, npairs = R * R, err = 0;
+    double *S = forward_separation(B, grid, stride);
     double *w = (double *)malloc(sizeof(double) * n);
-    double *dcol = (double *)malloc(sizeof(double) * (size_t)n * B);
-    if (!S || !w || !dcol) { free(S); free(w); free(dcol); return 2; }
+    int64_t *offs = run_starts(B);
+    if (!S || !w || !offs) { free(S); free(w); free(offs); return 2; }
     oracle_weights(B, w);
-    int64_t off = 0;
-    for (int m = 1 - B; m <= B - 1; ++m)
-        for (int mp = 1 - B; mp <= B - 1; ++mp) {
-            int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
-            dwt_pair(B, m, mp, S, w, dcol, coef + 2 * off);
-            off += B - l0;
+#pragma omp parallel num_threads(g_threads)
+    {
+        double *dcol = (double *)malloc(sizeof(double) * (size_t)n * B);
+#pragma omp for schedule(dynamic, 4)
+        for (int p = 0; p < npairs; ++p) {
+            if ((p / R) % stride != stride / 2) continue;
+            if (!dcol) {
+#pragma omp atomic write
+                err = 2;
+                continue;
+            }
+            int m = p / R + 1 - B, mp = p % R + 1 - B;
+            dwt_pair(B, m, mp, S, w, dcol, coef + 2 * offs[p]);
         }
-    free(S); free(w); free(dcol);
-    return 0;
+        free(dcol);
+    }
+    free(S); free(w); free(offs);
+    return err;
 }
+
+int oracle_forward(int B, const double *grid, double *coef) { return oracle_forward_strided(B, grid, coef, 1); }
 
 /* Inverse SOFT: the iDWT S(j;m,m') = sum_l d(l,m,m';beta_j) f(l,m,m') (the
  * transposed matrix T_B^T), then f(alpha_i,beta_j,gamma_k) = sum_{m,m'} S
  * exp(-i(m alpha_i + m' gamma_k)), an unnormalised 2-D DFT with the - sign.
- * Frequencies +-B (index B) carry nothing. */
-int oracle_inverse(int B, const double *coef, double *grid)
+ * Frequencies +-B (index B) carry nothing.  stride > 1 is a TIMING SAMPLE as
+ * in oracle_forward_strided (the same rows m and slices j; the grid is then
+ * not the transform). */
+int oracle_inverse_strided(int B, const double *coef, double *grid, int stride)
 {
-    if (B < 1) return 1;
-    int n = 2 * B;
+    if (B < 1 || stride < 1) return 1;
+    int n = 2 * B, R = 2 * B - 1, npairs = R * R, err = 0;
     size_t cnt = (size_t)2 * n * n * n;
-    double *dcol = (double *)malloc(sizeof(double) * B);
-    if (!dcol) return 2;
+    int64_t *offs = run_starts(B);
+    if (!offs) return 2;
     memset(grid, 0, sizeof(double) * cnt);
-    int64_t off = 0;
-    for (int m = 1 - B; m <= B - 1; ++m)
-        for (int mp = 1 - B; mp <= B - 1; ++mp) {
+#pragma omp parallel num_threads(g_threads)
+    {
+        double *dcol = (double *)malloc(sizeof(double) * B);
+#pragma omp for schedule(dynamic, 4)
+        for (int p = 0; p < npairs; ++p) {
+            if ((p / R) % stride != stride / 2) continue;
+            if (!dcol) {
+#pragma omp atomic write
+                err = 2;
+                continue;
+            }
+            int m = p / R + 1 - B, mp = p % R + 1 - B;
             int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
             int L = B - l0;
             int mi = mod_n(m, n), mk = mod_n(mp, n);
+            int64_t off = offs[p];
             for (int j = 0; j < n; ++j) {
                 oracle_wigner_d_column(B, m, mp, oracle_beta(B, j), dcol);
                 double re = 0.0, im = 0.0;
@@ -347,12 +430,16 @@ int oracle_inverse(int B, const double *coef, double *grid)
                 s[0] = re;
                 s[1] = im;
             }
-            off += L;
         }
-    free(dcol);
-    oracle_dft2_slices(n, n, grid, -1);
+        free(dcol);
+    }
+    free(offs);
+    if (err) return err;
+    dft2_slices_strided(n, n, grid, -1, stride);
     return 0;
 }
+
+int oracle_inverse(int B, const double *coef, double *grid) { return oracle_inverse_strided(B, coef, grid, 1); }
 
 /* ------------------------------------------------------------------------ */
 /* Direct O(B^6) transforms straight from Eq. (quadrature) and Eq.           */
@@ -434,55 +521,70 @@ int oracle_direct_inverse(int B, const double *coef, double *grid)
 int oracle_forward_pairs(int B, const double *grid, int npairs, const int *pairs, double *out)
 {
     if (B < 1) return 1;
-    int n = 2 * B;
+    int n = 2 * B, err = 0;
     double *w = (double *)malloc(sizeof(double) * n);
-    double *dcol = (double *)malloc(sizeof(double) * (size_t)n * B);
-    double *Sj = (double *)malloc(sizeof(double) * 2 * n);
-    double *ek = (double *)malloc(sizeof(double) * 2 * n);
-    double *ei = (double *)malloc(sizeof(double) * 2 * n);
-    if (!w || !dcol || !Sj || !ek || !ei) { free(w); free(dcol); free(Sj); free(ek); free(ei); return 2; }
+    int64_t *start = (int64_t *)malloc(sizeof(int64_t) * (npairs > 0 ? npairs : 1));
+    if (!w || !start) { free(w); free(start); return 2; }
     oracle_weights(B, w);
     int64_t o = 0;
     for (int p = 0; p < npairs; ++p) {
-        int m = pairs[2 * p], mp = pairs[2 * p + 1];
-        int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
-        if (l0 >= B) continue;
-        for (int t = 0; t < n; ++t) {
-            ek[2 * t] = cos(mp * oracle_alpha(B, t)); ek[2 * t + 1] = sin(mp * oracle_alpha(B, t));
-            ei[2 * t] = cos(m * oracle_alpha(B, t));  ei[2 * t + 1] = sin(m * oracle_alpha(B, t));
-        }
-        for (int j = 0; j < n; ++j) {
-            double sr = 0.0, si = 0.0;
-            for (int i = 0; i < n; ++i) {
-                double gr = 0.0, gi = 0.0;
-                const double *row = grid + 2 * (((size_t)j * n + i) * n);
-                for (int k = 0; k < n; ++k) {
-                    gr += row[2 * k] * ek[2 * k] - row[2 * k + 1] * ek[2 * k + 1];
-                    gi += row[2 * k] * ek[2 * k + 1] + row[2 * k + 1] * ek[2 * k];
-                }
-                sr += gr * ei[2 * i] - gi * ei[2 * i + 1];
-                si += gr * ei[2 * i + 1] + gi * ei[2 * i];
-            }
-            Sj[2 * j] = sr;
-            Sj[2 * j + 1] = si;
-        }
-        for (int j = 0; j < n; ++j) oracle_wigner_d_column(B, m, mp, oracle_beta(B, j), dcol + (size_t)j * B);
-        for (int t = 0; t < B - l0; ++t) {
-            int l = l0 + t;
-            double re = 0.0, im = 0.0;
-            for (int j = 0; j < n; ++j) {
-                double f = w[j] * dcol[(size_t)j * B + t];
-                re += f * Sj[2 * j];
-                im += f * Sj[2 * j + 1];
-            }
-            double v = (2.0 * l + 1.0) / (8.0 * OR_PI * B);
-            out[2 * (o + t)] = v * re;
-            out[2 * (o + t) + 1] = v * im;
-        }
-        o += B - l0;
+        int l0 = abs(pairs[2 * p]) > abs(pairs[2 * p + 1]) ? abs(pairs[2 * p]) : abs(pairs[2 * p + 1]);
+        start[p] = o;
+        if (l0 < B) o += B - l0;
     }
-    free(w); free(dcol); free(Sj); free(ek); free(ei);
-    return 0;
+#pragma omp parallel num_threads(g_threads)
+    {
+        double *dcol = (double *)malloc(sizeof(double) * (size_t)n * B);
+        double *Sj = (double *)malloc(sizeof(double) * 2 * n);
+        double *ek = (double *)malloc(sizeof(double) * 2 * n);
+        double *ei = (double *)malloc(sizeof(double) * 2 * n);
+#pragma omp for schedule(dynamic, 1)
+        for (int p = 0; p < npairs; ++p) {
+            if (!dcol || !Sj || !ek || !ei) {
+#pragma omp atomic write
+                err = 2;
+                continue;
+            }
+            int m = pairs[2 * p], mp = pairs[2 * p + 1];
+            int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
+            if (l0 >= B) continue;
+            for (int t = 0; t < n; ++t) {
+                ek[2 * t] = cos(mp * oracle_alpha(B, t)); ek[2 * t + 1] = sin(mp * oracle_alpha(B, t));
+                ei[2 * t] = cos(m * oracle_alpha(B, t));  ei[2 * t + 1] = sin(m * oracle_alpha(B, t));
+            }
+            for (int j = 0; j < n; ++j) {
+                double sr = 0.0, si = 0.0;
+                for (int i = 0; i < n; ++i) {
+                    double gr = 0.0, gi = 0.0;
+                    const double *row = grid + 2 * (((size_t)j * n + i) * n);
+                    for (int k = 0; k < n; ++k) {
+                        gr += row[2 * k] * ek[2 * k] - row[2 * k + 1] * ek[2 * k + 1];
+                        gi += row[2 * k] * ek[2 * k + 1] + row[2 * k + 1] * ek[2 * k];
+                    }
+                    sr += gr * ei[2 * i] - gi * ei[2 * i + 1];
+                    si += gr * ei[2 * i + 1] + gi * ei[2 * i];
+                }
+                Sj[2 * j] = sr;
+                Sj[2 * j + 1] = si;
+            }
+            for (int j = 0; j < n; ++j) oracle_wigner_d_column(B, m, mp, oracle_beta(B, j), dcol + (size_t)j * B);
+            for (int t = 0; t < B - l0; ++t) {
+                int l = l0 + t;
+                double re = 0.0, im = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    double f = w[j] * dcol[(size_t)j * B + t];
+                    re += f * Sj[2 * j];
+                    im += f * Sj[2 * j + 1];
+                }
+                double v = (2.0 * l + 1.0) / (8.0 * OR_PI * B);
+                out[2 * (start[p] + t)] = v * re;
+                out[2 * (start[p] + t) + 1] = v * im;
+            }
+        }
+        free(dcol); free(Sj); free(ek); free(ei);
+    }
+    free(w); free(start);
+    return err;
 }
 
 /* Inverse transform at single grid points: pts = [i0,j0,k0, i1,j1,k1, ...].
@@ -490,33 +592,42 @@ int oracle_forward_pairs(int B, const double *grid, int npairs, const int *pairs
 int oracle_inverse_points(int B, const double *coef, int npts, const int *pts, double *out)
 {
     if (B < 1) return 1;
-    double *dcol = (double *)malloc(sizeof(double) * B);
-    if (!dcol) return 2;
-    for (int p = 0; p < npts; ++p) {
-        int i = pts[3 * p], j = pts[3 * p + 1], k = pts[3 * p + 2];
-        double re = 0.0, im = 0.0;
-        int64_t off = 0;
-        for (int m = 1 - B; m <= B - 1; ++m)
-            for (int mp = 1 - B; mp <= B - 1; ++mp) {
-                int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
-                int L = B - l0;
-                oracle_wigner_d_column(B, m, mp, oracle_beta(B, j), dcol);
-                double sr = 0.0, si = 0.0;
-                for (int t = 0; t < L; ++t) {
-                    sr += dcol[t] * coef[2 * (off + t)];
-                    si += dcol[t] * coef[2 * (off + t) + 1];
-                }
-                double ang = -(m * oracle_alpha(B, i) + mp * oracle_alpha(B, k));
-                double c = cos(ang), s = sin(ang);
-                re += sr * c - si * s;
-                im += sr * s + si * c;
-                off += L;
+    int err = 0;
+#pragma omp parallel num_threads(g_threads)
+    {
+        double *dcol = (double *)malloc(sizeof(double) * B);
+#pragma omp for schedule(dynamic, 1)
+        for (int p = 0; p < npts; ++p) {
+            if (!dcol) {
+#pragma omp atomic write
+                err = 2;
+                continue;
             }
-        out[2 * p] = re;
-        out[2 * p + 1] = im;
+            int i = pts[3 * p], j = pts[3 * p + 1], k = pts[3 * p + 2];
+            double re = 0.0, im = 0.0;
+            int64_t off = 0;
+            for (int m = 1 - B; m <= B - 1; ++m)
+                for (int mp = 1 - B; mp <= B - 1; ++mp) {
+                    int l0 = abs(m) > abs(mp) ? abs(m) : abs(mp);
+                    int L = B - l0;
+                    oracle_wigner_d_column(B, m, mp, oracle_beta(B, j), dcol);
+                    double sr = 0.0, si = 0.0;
+                    for (int t = 0; t < L; ++t) {
+                        sr += dcol[t] * coef[2 * (off + t)];
+                        si += dcol[t] * coef[2 * (off + t) + 1];
+                    }
+                    double ang = -(m * oracle_alpha(B, i) + mp * oracle_alpha(B, k));
+                    double c = cos(ang), s = sin(ang);
+                    re += sr * c - si * s;
+                    im += sr * s + si * c;
+                    off += L;
+                }
+            out[2 * p] = re;
+            out[2 * p + 1] = im;
+        }
+        free(dcol);
     }
-    free(dcol);
-    return 0;
+    return err;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -566,7 +677,7 @@ int oracle_inverse_adjoint(int B, const double *grid, double *coef)
 {
     if (B < 1) return 1;
     int n = 2 * B;
-    double *S = forward_separation(B, grid);
+    double *S = forward_separation(B, grid, 1);
     double *dcol = (double *)malloc(sizeof(double) * (size_t)n * B);
     if (!S || !dcol) { free(S); free(dcol); return 2; }
     int64_t off = 0;

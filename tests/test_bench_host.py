@@ -45,7 +45,7 @@ def test_workloads_are_well_formed():
         assert kind in ("uniform", "gauss_decay"), name
         if mode == "fp64_real":  # the real entry points need power-of-two 2B
             assert (2 * B) & (2 * B - 1) == 0, name
-    assert bench.WORKLOADS["b64"][:2] == (64, "fp64")  # the default workload
+    assert bench.WORKLOADS["b256"][:2] == (256, "fp64")  # the default workload
 
 
 def test_traffic_entries_name_existing_sources():
