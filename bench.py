@@ -62,6 +62,9 @@ for _B in (64, 128, 256, 512):
                                 f"FP64 SOFT forward+inverse of a real function, B={_B}: soft_forward_real / "
                                 f"soft_inverse_real on a real (2B)^3 float64 grid, one partner of each conjugate "
                                 f"pair contracted")
+    WORKLOADS[f"b{_B}_clenshaw"] = (_B, "fp64_clenshaw", "gauss_decay",
+                                    f"FP64 SOFT forward+inverse, B={_B}, inverse DWT by Clenshaw's algorithm "
+                                    f"(backward summation over the degrees, the iDWT's last tile-shape variant)")
     WORKLOADS[f"b{_B}_fp64tc"] = (_B, "fp64_tc", "gauss_decay",
                                   f"FP64-accurate SOFT forward+inverse, B={_B}: FP64 Wigner-d recurrence, S and "
                                   f"2-D FFTs, contraction on tcgen05 tensor cores as exact base-128 BF16 digit "
@@ -542,14 +545,15 @@ PEAK_SOURCE = "derived: nominal FP64 1.25 TFLOP/s = 4 flop/clk/SM x 152 SM x 207
 
 
 def sample_pairs(B: int, seed: int, count: int = 16) -> list:
-    """Order pairs whose runs span every length: the extreme cases, then one
-    random pair on each of evenly spaced shells max(|m|,|m'|) = l0."""
+    """Order pairs whose runs span every length: the extreme cases, then
+    random pairs on evenly spaced shells max(|m|,|m'|) = l0 <= B - 1."""
     import numpy as np
     rng = np.random.default_rng(seed)
-    pairs = [(0, 0), (B - 1, B - 1), (1 - B, B - 1), (B // 2, -(B // 3))]
+    pairs = [(0, 0), (B - 1, B - 1), (1 - B, B - 1), (B // 2, -(B // 3))][:max(1, min(count, (2 * B - 1) ** 2))]
+    want = min(count, (2 * B - 1) ** 2)
     k = 0
-    while len(pairs) < count:
-        l0 = int(round(k * (B - 1) / max(1, count - 5)))
+    while len(pairs) < want:
+        l0 = min(B - 1, int(round((k % max(1, count - 4)) * (B - 1) / max(1, count - 5))))
         k += 1
         other = int(rng.integers(-l0, l0 + 1)) if l0 > 0 else 0
         sgn = 1 if rng.integers(0, 2) else -1
@@ -622,10 +626,10 @@ def roofline_numbers(B: int, dtype: str, phase_ms, phase_cnt) -> dict:
     real = dtype == "fp64_real"
     fwd_ms = phase_ms[1] / max(1, phase_cnt[1])
     inv_ms = phase_ms[2] / max(1, phase_cnt[2])
-    kname = {"fp64": "fp64", "fp64_real": "fp64", "fp64_tc": "tc"}.get(dtype, "mixed")
-    dom, dom_ms = (f"dwt_forward_{kname}_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else \
-        (f"dwt_inverse_{kname}_kernel", inv_ms)
-    algo = fl["contraction"] + fl["recurrence"] if dtype == "fp64" else \
+    kname = {"fp64": "fp64", "fp64_real": "fp64", "fp64_clenshaw": "fp64", "fp64_tc": "tc"}.get(dtype, "mixed")
+    inv_name = "idwt_clenshaw_fp64_kernel" if dtype == "fp64_clenshaw" else f"dwt_inverse_{kname}_kernel"
+    dom, dom_ms = (f"dwt_forward_{kname}_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else (inv_name, inv_ms)
+    algo = fl["contraction"] + fl["recurrence"] if dtype in ("fp64", "fp64_clenshaw") else \
         fl["contraction"] / 2 + fl["recurrence"] if real else fl["recurrence"]
     achieved = algo / (dom_ms * 1e-3) / 1e9
     out = {"kernel": dom, "dom_ms": dom_ms, "algo": algo, "achieved": achieved, "frac": achieved / PEAK_FP64_GFLOPS,
@@ -754,8 +758,10 @@ def run_ours(args) -> None:
     R = config["inputs_rotated"]
 
     real = dtype == "fp64_real"  # real grids: soft_forward_real / soft_inverse_real on an FP64 plan
-    plan = Plan(B, "fp64" if real else dtype, device=dev)
+    plan = Plan(B, "fp64" if dtype in ("fp64_real", "fp64_clenshaw") else dtype, device=dev)
     tuned = plan.tune() if args.tune else None
+    if dtype == "fp64_clenshaw":
+        plan.set_variant(1, plan.num_variants(1) - 1)  # the Clenshaw iDWT
     if tuned is not None:
         config["tile_variants"] = {"dwt": tuned["dwt"], "idwt": tuned["idwt"]}
     coefs = [torch.from_numpy(synth.coefficients(B, kind, seed=synth.BASE_SEED + 100 * rank + r)).to(dev)
@@ -830,7 +836,7 @@ def run_ours(args) -> None:
         ref = OracleRef(B, np.ascontiguousarray(grids[last].cpu().numpy()).astype(np.complex128),
                         coefs[last].cpu().numpy(), synth.BASE_SEED + 11 + B, host_cores(), real=real)
         rel = ref.errors(coef_out, grid_out)
-        rel["bound"] = MODE_BOUND.get("fp64" if real else dtype)
+        rel["bound"] = MODE_BOUND.get("fp64" if dtype in ("fp64_real", "fp64_clenshaw") else dtype)
 
     def e2e_step():
         if real:
@@ -887,8 +893,8 @@ def run_ours(args) -> None:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if dtype in ("fp64", "fp64_real") else dtype, "data": "synthetic",
-            "config": config, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks,
+            "vs_baseline": None, "dtype": "f64" if dtype.startswith("fp64") and dtype != "fp64_tc" else dtype,
+            "data": "synthetic", "config": config, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks,
             "rel_l2": rel, "cpu_baseline": cpu,
         }
         if modes is not None:

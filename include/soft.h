@@ -72,6 +72,18 @@ int soft_max_bandwidth(void);
  * runs are not counted.  Thread-safe. */
 unsigned long long soft_launch_count(void);
 
+/* Number of device allocations the library holds right now, over all plans,
+ * batch graphs and devices (each plan buffer, staging buffer and workspace
+ * counts one).  Every failure path frees what it allocated, so the count
+ * returns to its earlier value once the plans involved are destroyed.
+ * Test support, not from the paper; with it goes a failure-injection hook:
+ * when the environment variable SOFT_TEST_ALLOC_BUDGET=N is set at
+ * soft_plan_create, that plan may make N device allocations in all (at
+ * creation and later, e.g. the host-call staging buffers or the correlation
+ * workspace) and the next one fails with SOFT_ERR_OUT_OF_MEMORY.  Unset, it
+ * has no effect.  Thread-safe. */
+long long soft_live_allocations(void);
+
 /* Number of Fourier coefficients with l < B: B(4B^2-1)/3 (Sec. 2.4).
  * Returns -1 for B < 1. */
 int64_t soft_num_coeffs(int B);
@@ -222,9 +234,14 @@ soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *s
  *   - B must be <= 256; larger B returns SOFT_ERR_UNSUPPORTED (detail in
  *     soft_last_error()).
  *   - The first call on a device looks up the array's device address (one-time
- *     set-up); make that first call before any stream capture.
+ *     set-up); make that first call before any stream capture.  A failed
+ *     lookup returns SOFT_ERR_CUDA (detail in soft_last_error()) and is not
+ *     kept: the next call tries again.
  *   - All calls share the array: calls whose GPU work overlaps (different
  *     streams, or devices sharing it) race and must be serialised by the caller.
+ *   - The FP64 DWT kernel it runs has no device-side failure mode (no waits,
+ *     no internal checks), so there is no device error word to read: the
+ *     returned status covers arguments, set-up and launches.
  *   - No cudaMalloc, cudaFree or allocating library call is made. */
 soft_status soft_dwt_forward_noalloc(int B, const double *S, double *coef, void *stream);
 

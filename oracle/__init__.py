@@ -339,6 +339,8 @@ def forward_pairs(B: int, grid, pairs) -> list[np.ndarray]:
     holding l = max(|m|,|m'|)..B-1."""
     g = _check_grid(B, grid)
     pairs = [(int(m), int(mp)) for m, mp in pairs]
+    if any(max(abs(m), abs(mp)) >= B for m, mp in pairs):
+        raise ValueError("every order pair needs |m|, |m'| < B")
     flat = np.ascontiguousarray(np.array(pairs, dtype=np.int32).reshape(-1))
     lens = [B - max(abs(m), abs(mp)) for m, mp in pairs]
     out = np.zeros(sum(lens), dtype=np.complex128)
@@ -357,6 +359,8 @@ def inverse_points(B: int, coef, points) -> np.ndarray:
     """Inverse transform evaluated at grid points (i, j, k) only."""
     c = _check_coef(B, coef)
     flat = np.ascontiguousarray(np.array(points, dtype=np.int32).reshape(-1))
+    if flat.size % 3 or (flat.size and (flat.min() < 0 or flat.max() >= 2 * B)):
+        raise ValueError("grid points are (i, j, k) triples with 0 <= i, j, k < 2B")
     out = np.zeros(len(flat) // 3, dtype=np.complex128)
     rc = _load().oracle_inverse_points(B, _dp(c.view(np.float64)), len(out), _ip(flat),
                                        _dp(out.view(np.float64)))

@@ -29,6 +29,7 @@ _vp, _i, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
 SIGNATURES = {
     "soft_max_bandwidth": (_i, []),
     "soft_launch_count": (ctypes.c_ulonglong, []),
+    "soft_live_allocations": (ctypes.c_longlong, []),
     "soft_num_coeffs": (_i64, [_i]),
     "soft_coef_index": (_i64, [_i, _i, _i, _i]),
     "soft_status_string": (ctypes.c_char_p, [_i]),
@@ -105,6 +106,10 @@ def soft_max_bandwidth() -> int:
 
 def soft_launch_count() -> int:
     return int(load().soft_launch_count())
+
+
+def soft_live_allocations() -> int:
+    return int(load().soft_live_allocations())
 
 
 def soft_num_coeffs(B: int) -> int:

@@ -231,34 +231,41 @@ __device__ __forceinline__ void idwt_walk(const double *F, const double *rA, con
     }
 }
 
-// One cluster of the inverse DWT; every thread of the CTA calls it.  smem holds
-// F[B][16] and the recurrence coefficients (3 x B doubles).
-template <int NT, int JPT>
-__device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__restrict__ coef,
-                                             double2 *__restrict__ S, int flags, int cidx, int m, int mp,
-                                             double *smem, ClusterSmem &cs) {
-    const int B = tb.B, n = 2 * B, tid = threadIdx.x;
-    const int l0 = m, L = B - l0;
+// Set-up of one cluster of an inverse DWT, by every thread of the CTA: the
+// partner table, the rescaled recurrence coefficients and
+//   F[t][2c (+1)] = sign_p(l) sig_t (V_l) f(l, m_p, m'_p)  (re, im),  l = l0 + t,
+// the sign- and scale-folded coefficients of contracted partner p = c pstep.
+// smem holds F[B][16] and the recurrence coefficients (4 x B doubles).  Real
+// output (kRealSym): S(-m,-m';j) = conj S(m,m';j) for the conjugate partner
+// pairs (2k, 2k+1); only the even partners are contracted (slot c holds
+// partner c * pstep) and only their coefficients are read.  Ends with a barrier.
+struct IdwtShape {
+    int npc, pstep;
+    bool real;
+};
 
+template <int NT>
+__device__ __forceinline__ IdwtShape idwt_setup(const Tables &tb, const double *__restrict__ coef, int flags,
+                                                int cidx, int m, int mp, double *smem, ClusterSmem &cs) {
+    const int B = tb.B, tid = threadIdx.x;
+    const int l0 = m, L = B - l0;
     double *F = smem;                  // [B][16]
     double *rA = F + (size_t)B * 16;
     double *rAc = rA + B;
     double *rBc = rAc + B;
     double *rSig = rBc + B;
-
     load_cluster(tb, m, mp, cs);
     cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
     const int np = cs.np;
-    // Real output (kRealSym): S(-m,-m';j) = conj S(m,m';j) for the conjugate
-    // partner pairs (2k, 2k+1); only the even partners are walked (slot c
-    // holds partner c * pstep) and only their coefficients are read.
-    const bool real = (flags & kRealSym) && np > 1;
-    const int npc = real ? np / 2 : np, pstep = real ? 2 : 1;
+    IdwtShape sh;
+    sh.real = (flags & kRealSym) && np > 1;
+    sh.npc = sh.real ? np / 2 : np;
+    sh.pstep = sh.real ? 2 : 1;
     for (int e = tid; e < L * 8; e += NT) {
         const int t = e >> 3, c = e & 7;
         double2 v = make_double2(0.0, 0.0);
-        if (c < npc) {
-            const int p = c * pstep;
+        if (c < sh.npc) {
+            const int p = c * sh.pstep;
             const int l = l0 + t;
             double sg = (cs.lpar[p] && (l & 1)) ? -cs.sign[p] : cs.sign[p];
             sg *= rSig[t];
@@ -268,6 +275,42 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
         }
         *reinterpret_cast<double2 *>(&F[t * 16 + 2 * c]) = v;
     }
+    __syncthreads();
+    return sh;
+}
+
+// Stores beta sample j's contracted columns acc (times w_B(j') for the
+// adjoint's W) into S: partner p at j' = j, or 2B-1-j for mirrored partners,
+// and for real output also its conjugate partner.
+__device__ __forceinline__ void idwt_store(const Tables &tb, double2 *__restrict__ S, int flags, const ClusterSmem &cs,
+                                           const IdwtShape &sh, int j, const double (&acc)[16]) {
+    const int n = 2 * tb.B;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (c < sh.npc) {
+            const int p = c * sh.pstep;
+            const int jj = cs.mir[p] ? n - 1 - j : j;
+            const double wj = (flags & kApplyW) ? tb.w[jj] : 1.0;
+            const double2 v = make_double2(wj * acc[2 * c], wj * acc[2 * c + 1]);
+            S[((int64_t)jj * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)] = v;
+            if (sh.real)  // partner p + 1 = (-m, -m'): the conjugate, at the same beta sample
+                S[((int64_t)jj * n + mod_n(cs.pm[p + 1], n)) * n + mod_n(cs.pmp[p + 1], n)] = make_double2(v.x, -v.y);
+        }
+    }
+}
+
+// One cluster of the inverse DWT; every thread of the CTA calls it.  smem holds
+// F[B][16] and the recurrence coefficients (4 x B doubles).
+template <int NT, int JPT>
+__device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__restrict__ coef,
+                                             double2 *__restrict__ S, int flags, int cidx, int m, int mp,
+                                             double *smem, ClusterSmem &cs) {
+    const int B = tb.B, n = 2 * B, tid = threadIdx.x;
+    const int L = B - m;
+    const IdwtShape sh = idwt_setup<NT>(tb, coef, flags, cidx, m, mp, smem, cs);
+    const double *F = smem;
+    const double *rA = F + (size_t)B * 16;
+    const double *rAc = rA + B;
 
     double x[JPT], dcur[JPT], dprev[JPT];
     double acc[JPT][16];
@@ -285,30 +328,80 @@ __device__ __forceinline__ void idwt_cluster(const Tables &tb, const double *__r
             for (int c = 0; c < 16; ++c) acc[k][c] = 0.0;
         }
     }
-    __syncthreads();
 
-    if (npc > 4)      idwt_walk<NT, JPT, 16>(F, rA, rAc, L, x, dcur, dprev, acc);
-    else if (npc > 2) idwt_walk<NT, JPT, 8>(F, rA, rAc, L, x, dcur, dprev, acc);
-    else              idwt_walk<NT, JPT, 4>(F, rA, rAc, L, x, dcur, dprev, acc);
+    if (sh.npc > 4)      idwt_walk<NT, JPT, 16>(F, rA, rAc, L, x, dcur, dprev, acc);
+    else if (sh.npc > 2) idwt_walk<NT, JPT, 8>(F, rA, rAc, L, x, dcur, dprev, acc);
+    else                 idwt_walk<NT, JPT, 4>(F, rA, rAc, L, x, dcur, dprev, acc);
 
 #pragma unroll
     for (int k = 0; k < JPT; ++k) {
         const int j = tid + k * NT;
-        if (j < n) {
+        if (j < n) idwt_store(tb, S, flags, cs, sh, j, acc[k]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse DWT by Clenshaw's algorithm (a tile-shape variant of the FP64 iDWT;
+// Sec. 2.4 names Clenshaw's algorithm as the O(B^4) way to run the DWT/iDWT
+// along the three-term recurrence).  With d(l0+t) = sig_t e_t and e_{t+1} =
+// a_t(x) e_t - e_{t-1}, a_t(x) = A'_t x - Ac'_t, e_{-1} = 0, the sum
+//   S_c(j) = sum_t e_t(x_j) g_t(c),   g_t(c) = F[t][c] (sig_t folded in),
+// runs backwards over the degrees with no Wigner-d value formed:
+//   b_t = g_t + a_t(x_j) b_{t+1} - b_{t+2},  b_L = b_{L+1} = 0,  S_c(j) = e_0(x_j) b_0
+// (summing by parts, the coefficient of every b_s, s >= 1, is the recurrence
+// and vanishes).  Cost: one FMA for a_t per sample and degree, then an FMA and
+// a subtraction per column -- 2 FP64 operations per column against the
+// forward-recurrence iDWT's 1 FMA per column plus 2 shared ones, so with the
+// 16 partner columns it does ~1.8x the FP64 work; each thread carries b_{t+1}
+// and b_{t+2} of every column (32 doubles), so it takes one beta sample at a
+// time and the CTA loops over the samples in blocks of NT.
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ void clenshaw_walk(const double *F, const double *rA, const double *rAc, int L, double x,
+                                              double (&b1)[16]) {
+    double b2[16];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                if (c < npc) {
-                    const int p = c * pstep;
-                    const int jj = cs.mir[p] ? n - 1 - j : j;
-                    const double wj = (flags & kApplyW) ? tb.w[jj] : 1.0;
-                    const double2 v = make_double2(wj * acc[k][2 * c], wj * acc[k][2 * c + 1]);
-                    S[((int64_t)jj * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)] = v;
-                    if (real)  // partner p + 1 = (-m, -m'): the conjugate, at the same beta sample
-                        S[((int64_t)jj * n + mod_n(cs.pm[p + 1], n)) * n + mod_n(cs.pmp[p + 1], n)] =
-                            make_double2(v.x, -v.y);
-                }
-            }
+    for (int c = 0; c < 16; ++c) { b1[c] = 0.0; b2[c] = 0.0; }
+    for (int t = L - 1; t >= 0; --t) {
+        const double a = fma(rA[t], x, -rAc[t]);
+        const double *Fr = F + t * 16;
+#pragma unroll
+        for (int c = 0; c < NC; c += 2) {
+            const double2 g = *reinterpret_cast<const double2 *>(Fr + c);
+            const double n0 = fma(a, b1[c], g.x - b2[c]);
+            const double n1 = fma(a, b1[c + 1], g.y - b2[c + 1]);
+            b2[c] = b1[c];
+            b2[c + 1] = b1[c + 1];
+            b1[c] = n0;
+            b1[c + 1] = n1;
         }
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) idwt_clenshaw_fp64_kernel(Tables tb, const double *__restrict__ coef,
+                                                               double2 *__restrict__ S, int flags) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ ClusterSmem cs;
+    const int B = tb.B, n = 2 * B;
+    const int cidx = tb.inv_order ? tb.inv_order[blockIdx.x] : (int)blockIdx.x;
+    const int2 rep = tb.clusters[cidx];
+    const int m = rep.x, mp = rep.y, L = B - m;
+    const IdwtShape sh = idwt_setup<NT>(tb, coef, flags, cidx, m, mp, smem, cs);
+    const double *F = smem;
+    const double *rA = F + (size_t)B * 16;
+    const double *rAc = rA + B;
+    const double lognorm = seed_lognorm(tb, m, mp);
+    for (int j = threadIdx.x; j < n; j += NT) {
+        const double x = tb.cosb[j];
+        const double e0 = cluster_seed(tb, cidx, j, m, mp, lognorm, false);
+        double b[16];
+        if (sh.npc > 4)      clenshaw_walk<16>(F, rA, rAc, L, x, b);
+        else if (sh.npc > 2) clenshaw_walk<8>(F, rA, rAc, L, x, b);
+        else                 clenshaw_walk<4>(F, rA, rAc, L, x, b);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) b[c] *= e0;
+        idwt_store(tb, S, flags, cs, sh, j, b);
     }
 }
 
@@ -475,12 +568,28 @@ cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items,
     return cudaErrorInvalidValue;
 }
 
-int dwt_inverse_fp64_variants(int B) { return 2 * B <= 256 ? 2 : 2 * B <= 512 ? 3 : 2; }
+// Tile-shape variants of the iDWT; the last one is Clenshaw's algorithm.
+int dwt_inverse_fp64_variants(int B) { return (2 * B <= 256 ? 2 : 2 * B <= 512 ? 3 : 2) + 1; }
+
+template <int NT>
+cudaError_t run_inverse_clenshaw(const Tables &tb, const double *coef, double2 *S, cudaStream_t s, int flags) {
+    const int B = tb.B;
+    const size_t bytes = sizeof(double) * ((size_t)B * 16 + 4 * (size_t)B);
+    cudaError_t e = cudaFuncSetAttribute(idwt_clenshaw_fp64_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    idwt_clenshaw_fp64_kernel<NT><<<tb.ncl, NT, bytes, s>>>(tb, coef, S, flags);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dwt_inverse_fp64(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s, int flags) {
     const int n = 2 * tb.B;
     const double *c = reinterpret_cast<const double *>(coef);
     const int v = tb.inv_variant;
+    if (v == dwt_inverse_fp64_variants(tb.B) - 1)
+        return n <= 64 ? run_inverse_clenshaw<64>(tb, c, S, s, flags) : n <= 128 ? run_inverse_clenshaw<128>(tb, c, S, s, flags)
+                                                                          : run_inverse_clenshaw<256>(tb, c, S, s, flags);
     if (n <= 64) return v == 1 ? run_inverse<32, 2>(tb, c, S, s, flags) : run_inverse<64, 1>(tb, c, S, s, flags);
     if (n <= 128) return v == 1 ? run_inverse<64, 2>(tb, c, S, s, flags) : run_inverse<128, 1>(tb, c, S, s, flags);
     if (n <= 256) return v == 1 ? run_inverse<128, 2>(tb, c, S, s, flags) : run_inverse<256, 1>(tb, c, S, s, flags);

@@ -11,8 +11,10 @@
 //     three MMAs hi*hi + hi*lo + lo*hi per K step, ~2^-16 relative products)
 //     or as TF32 (one MMA per K step, ~2^-11);
 //   * the cluster's partners (8 x re/im = the N = 16 columns) are the B operand;
-//   * tcgen05.mma accumulates in FP32 in TMEM (M = 128 rows, N = 16); the
-//     epilogue applies V_l and the partner signs in FP64.
+//   * tcgen05.mma accumulates each K chunk in FP32 in TMEM (M = 64 or 128
+//     rows, N = 16 per transform); the chunk partials are combined across
+//     chunks by compensated (TwoSum) FP32 sums kept in TMEM, and the epilogue
+//     adds hi + lo and applies V_l and the partner signs in FP64.
 // Forward: M = degrees l (tiles of 128), K = beta samples (chunks of 128);
 // the recurrence state of every beta sample is carried across degree tiles in
 // shared memory.  Inverse: M = beta samples (tiles of 128), K = degrees
@@ -63,7 +65,10 @@ struct Operands {
 
 // TMEM columns for an N-column FP32 accumulator (power of two, >= 32).
 template <int NC>
-constexpr uint32_t tmem_cols() { return NC <= 32 ? 32u : NC <= 64 ? 64u : NC <= 128 ? 128u : 256u; }
+constexpr uint32_t tmem_cols() {
+    static_assert(NC <= 512, "TMEM holds 512 columns");
+    return NC <= 32 ? 32u : NC <= 64 ? 64u : NC <= 128 ? 128u : NC <= 256 ? 256u : 512u;
+}
 
 // Store one value into plane(s) of an operand tile at (r, k).
 template <int MODE>
@@ -181,12 +186,53 @@ struct MixedBatch {
 };
 
 // ---------------------------------------------------------------------------
-// Forward DWT (mixed).  One CTA per cluster, NT threads = NT beta samples per
-// K chunk (one recurrence chain per thread), M tiles of 64 degrees, N = 16 NB
-// columns: the T tile produced once serves the NB transforms of the batch.
-//   dynamic smem: operands | dprev[2B] | dcur[2B] | rA,rAc,rV [B each]; the
-//   table-building scratch (Bc, sig) lives in the operand area, which is not
-//   yet in use then.
+// Compensated sums over K chunks (FP32 partials, error-free TwoSum
+// accumulation), in TMEM beside the accumulator.  For a CTA with NC = 16 NB
+// accumulator columns the TMEM layout is
+//   [0, NC)       the accumulator of the current K chunk (FP32, fresh each chunk)
+//   [NC, 2 NC)    running sum hi,   [2 NC, 3 NC) running sum lo
+// so hi + lo holds the sum over the finished chunks of the FP32 chunk partials
+// to ~2^-48 of their magnitude.  drain_chunk() is called by warps 0..3 (each
+// reads its own TMEM lane quarter) after the chunk's MMA has completed.
+// ---------------------------------------------------------------------------
+template <int NB>
+__device__ __forceinline__ void drain_chunk(uint32_t tmem_row, bool first) {
+    constexpr int NC = 16 * NB;
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+        uint32_t x[16], hi[16], lo[16];
+        tc::tmem_ld16(tmem_row + 16 * b, x);
+        if (first) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) { hi[c] = x[c]; lo[c] = 0u; }
+        } else {
+            tc::tmem_ld16(tmem_row + NC + 16 * b, hi);
+            tc::tmem_ld16(tmem_row + 2 * NC + 16 * b, lo);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                float h = __uint_as_float(hi[c]), l = __uint_as_float(lo[c]);
+                tc::comp_add(h, l, __uint_as_float(x[c]));
+                hi[c] = __float_as_uint(h);
+                lo[c] = __float_as_uint(l);
+            }
+        }
+        tc::tmem_st16(tmem_row + NC + 16 * b, hi);
+        tc::tmem_st16(tmem_row + 2 * NC + 16 * b, lo);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward DWT (mixed).  One CTA per cluster, KC producer threads = KC beta
+// samples per K chunk (one recurrence chain per thread), M tiles of 64
+// degrees, N = 16 NB columns: the T tile produced once serves the NB
+// transforms of the batch.  The operands are double-buffered: while the
+// tensor cores run chunk k from one stage, the producers generate chunk k+1's
+// Wigner-d rows into the other; after chunk k's MMA completes its FP32
+// partial is added into the compensated TMEM sums (drain_chunk), and after a
+// tile's last chunk the epilogue applies V_l and the partner signs in FP64.
+//   dynamic smem: stage 0 | stage 1 (A planes, then B planes, each) |
+//                 dprev[2B] | dcur[2B] | rA,rAc,rV [B each]; the
+//   table-building scratch (Bc, sig) lives in stage 0, not yet in use then.
 // ---------------------------------------------------------------------------
 template <int MODE, int KC, int NB, bool LD>
 __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(MixedBatch mb, int flags) {
@@ -195,6 +241,7 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
     constexpr int NT = LD ? 2 * KC : KC;
     constexpr int TM = kFwdTile, NC = 16 * NB;
     using O = Operands<MODE, TM, KC, NC>;
+    constexpr uint32_t TCOLS = tmem_cols<3 * NC>();
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
     __shared__ uint32_t tmem_slot;
@@ -205,12 +252,10 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
     const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 
-    unsigned char *A = smem;                    // A planes (T tile), then B planes (X chunk)
-    unsigned char *X = smem + O::PLANES * O::A_BYTES;
-    double *dprev = reinterpret_cast<double *>(smem + O::BYTES);
+    double *dprev = reinterpret_cast<double *>(smem + 2 * O::BYTES);
     double *dcur = dprev + n;
     double *rA = dcur + n, *rAc = rA + B, *rV = rAc + B;
-    double *rBc = reinterpret_cast<double *>(smem), *rSig = rBc + B;  // scratch inside the operand area
+    double *rBc = reinterpret_cast<double *>(smem), *rSig = rBc + B;  // scratch inside stage 0
 
     load_cluster(tb, m, mp, cs);
     for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
@@ -229,27 +274,36 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
             dprev[j] = 0.0;
         }
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, tmem_cols<NC>());
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, TCOLS);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's TMEM lane quarter
     const int np = cs.np;
     const int nchunks = (n + KC - 1) / KC;
+    const int total = ((L + TM - 1) / TM) * nchunks;  // (tile, chunk) steps
     uint32_t phase = 0;
     bool ok = true;
-    unsigned char *acol = A + (tid / O::KPC) * O::A_LBO + (tid % O::KPC) * O::EB;  // this thread's column; row r at +16 r
 
-    for (int lb = l0; lb < B && ok; lb += TM) {
-        const int rows = min(TM, B - lb);
-        for (int c = 0; c < nchunks && ok; ++c) {
-            // K extent of this chunk, rounded up to whole MMA K steps (the padding is zero).
-            const int kvalid = min(KC, n - c * KC);
-            const int ksteps = (kvalid + kstep_elems<MODE>() - 1) / kstep_elems<MODE>();
-            const int kfill = ksteps * kstep_elems<MODE>();
+    // Step `it` fills stage it & 1 with chunk it and issues its MMA; before the
+    // issue it folds chunk it-1's finished partial into the sums (and finishes
+    // that tile if it was its last chunk).  Stage it & 1 was last read by the
+    // MMA of chunk it-2, which step it-1 waited for.
+    for (int it = 0; it <= total; ++it) {
+        const bool issue = it < total;
+        const int tile = it / nchunks, c = it % nchunks;
+        const int lb = l0 + tile * TM, rows = issue ? min(TM, B - lb) : 0;
+        unsigned char *A = smem + (it & 1) * O::BYTES;
+        unsigned char *X = A + O::PLANES * O::A_BYTES;
+        const int kvalid = min(KC, n - c * KC);
+        const int ksteps = (kvalid + kstep_elems<MODE>() - 1) / kstep_elems<MODE>();
+        const int kfill = ksteps * kstep_elems<MODE>();
+        if (issue) {
             // A: column tid = beta sample j, rows = degrees lb..lb+rows-1.  Rows past
             // `rows` are left as they are: they only reach TMEM lanes that are never read.
+            unsigned char *acol = A + (tid / O::KPC) * O::A_LBO + (tid % O::KPC) * O::EB;
             const int j = c * KC + tid;
             if (tid >= KC) {
                 // loader threads: no column of A
@@ -326,53 +380,67 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
                 put_b8<MODE>(X, O::B_BYTES, O::B_LBO, 16 * b + 2 * p + 1, k0, im);
             }
             tc::fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) issue_chunk<MODE, TM, KC, NC>(tmem, A, X, c == 0, ksteps, &mbar);
+        }
+        if (it > 0) {
+            // chunk it-1's MMA: wait for it, then fold its partial into the sums
             const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
             phase ^= 1u;
             ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
-        }
-        if (!ok) break;
-        // Epilogue: degree lb + 16 w + i sits in TMEM lane 32 w + i (i < 16) of warp w < 4;
-        // transform b's 16 columns start at column 16 b.
-        tc::fence_after_sync();
-        if (warp < 4) {
-            const int r = 16 * warp + lane;
-            const int l = lb + r, q = l - l0;
-            const bool live = lane < 16 && r < rows;
+            if (!ok) break;
+            tc::fence_after_sync();
+            const int pt = (it - 1) / nchunks, pc = (it - 1) % nchunks;
+            if (warp < 4) {
+                drain_chunk<NB>(trow, pc == 0);
+                if (pc == nchunks - 1) {
+                    // Epilogue of tile pt: degree l = plb + 16 w + i sits in TMEM lane 32 w + i
+                    // (i < 16); (hi + lo) V_l sig_l and the partner sign in FP64.
+                    const int plb = l0 + pt * TM, prow = min(TM, B - plb);
+                    const int r = 16 * warp + lane;
+                    const int l = plb + r, q = l - l0;
+                    const bool live = lane < 16 && r < prow;
 #pragma unroll 1
-            for (int b = 0; b < NB; ++b) {
-                uint32_t d[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * b, d);
-                if (live) {
-                    // V_l sig_l and the partner sign applied in FP32 (the accumulator's precision)
-                    const float v = tc::f64_to_f32_rn(rV[q]);
+                    for (int b = 0; b < NB; ++b) {
+                        uint32_t hi[16], lo[16];
+                        tc::tmem_ld16(trow + NC + 16 * b, hi);
+                        tc::tmem_ld16(trow + 2 * NC + 16 * b, lo);
+                        if (live) {
+                            const double v = rV[q];
 #pragma unroll
-                    for (int p = 0; p < 8; ++p) {
-                        if (p >= np) break;
-                        const float vs = ((cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1))) ? -v : v;
-                        double2 out;
-                        out.x = tc::f32_to_f64(vs * __uint_as_float(d[2 * p]));
-                        out.y = tc::f32_to_f64(vs * __uint_as_float(d[2 * p + 1]));
-                        *reinterpret_cast<double2 *>(mb.coef[b] + 2 * (cs.off[p] + q)) = out;
+                            for (int p = 0; p < 8; ++p) {
+                                if (p >= np) break;
+                                const double vs = ((cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1))) ? -v : v;
+                                double2 out;
+                                out.x = vs * (tc::f32_to_f64(__uint_as_float(hi[2 * p])) +
+                                              tc::f32_to_f64(__uint_as_float(lo[2 * p])));
+                                out.y = vs * (tc::f32_to_f64(__uint_as_float(hi[2 * p + 1])) +
+                                              tc::f32_to_f64(__uint_as_float(lo[2 * p + 1])));
+                                *reinterpret_cast<double2 *>(mb.coef[b] + 2 * (cs.off[p] + q)) = out;
+                            }
+                        }
                     }
                 }
             }
+            tc::fence_before_sync();
         }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
+        __syncthreads();  // stage it & 1 complete; the accumulator is free for chunk it
+        if (issue && tid == 0) {
+            tc::fence_after_sync();
+            issue_chunk<MODE, TM, KC, NC>(tmem, A, X, true, ksteps, &mbar);
+        }
     }
     if (!ok && tid == 0 && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols<NC>());
+    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
 }
 
 // ---------------------------------------------------------------------------
 // Inverse DWT (mixed).  One CTA per cluster, looping over tiles of 128 beta
 // samples; K = degrees in chunks of 64; N = 16 NB columns (the sign-folded
 // coefficients of the NB transforms), so each generated T tile serves the batch.
+// Each chunk's MMA starts a fresh FP32 accumulator, and its partial is folded
+// into the compensated TMEM sums (drain_chunk) before the next chunk: the sum
+// over l is FP32 within a chunk of 64 degrees and compensated across chunks.
 //   dynamic smem: operands | rA,rAc,rBc,rSig [B each]
 // ---------------------------------------------------------------------------
 template <int MODE, int NB, bool LD>
@@ -381,6 +449,7 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     constexpr int NT = LD ? 2 * kNT : kNT;
     constexpr int NC = 16 * NB;
     using O = Operands<MODE, kTile, kChunk, NC>;
+    constexpr uint32_t TCOLS = tmem_cols<3 * NC>();
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
     __shared__ uint32_t tmem_slot;
@@ -400,12 +469,13 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
     for (int t = tid; t < L; t += NT)
         fsc[t] = tc::f64_to_f32_rn(rSig[t] * ((flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0));
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, tmem_cols<NC>());
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, TCOLS);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's TMEM lane quarter
     const int np = cs.np;
     const double lognorm = seed_lognorm(tb, m, mp);
     uint32_t phase = 0;
@@ -472,26 +542,36 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
             }
             tc::fence_proxy_async();
             __syncthreads();
-            if (tid == 0) issue_chunk<MODE, kTile, kChunk, NC>(tmem, A, F, c == 0, ksteps, &mbar);
+            if (tid == 0) issue_chunk<MODE, kTile, kChunk, NC>(tmem, A, F, true, ksteps, &mbar);
             const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
             phase ^= 1u;
             ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
+            if (!ok) break;
+            tc::fence_after_sync();
+            if (warp < 4) drain_chunk<NB>(trow, c == 0);
+            tc::fence_before_sync();  // the next chunk's barrier orders the drain before its MMA
         }
         if (!ok) break;
         tc::fence_after_sync();
 #pragma unroll 1
         for (int b = 0; b < NB && warp < 4; ++b) {
-            uint32_t d[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * b, d);
+            uint32_t hi[16], lo[16];
+            tc::tmem_ld16(trow + NC + 16 * b, hi);
+            tc::tmem_ld16(trow + 2 * NC + 16 * b, lo);
             if (active) {
                 float2 *Sb = const_cast<float2 *>(mb.S[b]);
 #pragma unroll
                 for (int p = 0; p < 8; ++p) {
                     if (p >= np) break;
                     const int jj = cs.mir[p] ? n - 1 - j : j;
-                    const float wj = (flags & kApplyW) ? tc::f64_to_f32_rn(tb.w[jj]) : 1.0f;
+                    // (hi + lo) times w_B(j) (the adjoint's W) in FP64, rounded once to the FP32 S
+                    const double wj = (flags & kApplyW) ? tb.w[jj] : 1.0;
+                    const double re = wj * (tc::f32_to_f64(__uint_as_float(hi[2 * p])) +
+                                            tc::f32_to_f64(__uint_as_float(lo[2 * p])));
+                    const double im = wj * (tc::f32_to_f64(__uint_as_float(hi[2 * p + 1])) +
+                                            tc::f32_to_f64(__uint_as_float(lo[2 * p + 1])));
                     Sb[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + jj] =
-                        make_float2(wj * __uint_as_float(d[2 * p]), wj * __uint_as_float(d[2 * p + 1]));
+                        make_float2(tc::f64_to_f32_rn(re), tc::f64_to_f32_rn(im));
                 }
             }
         }
@@ -502,7 +582,7 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     if (!ok && tid == 0 && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols<NC>());
+    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
 }
 
 // Self-test of the bounded wait used by the mixed kernels: one CTA polls an
@@ -574,7 +654,8 @@ int grid_for(int64_t count) { return (int)std::min<int64_t>((count + 255) / 256,
 template <int MODE, int KC, int NB>
 size_t mixed_forward_smem(int B) {
     static_assert(Operands<MODE, kFwdTile, KC, 16 * NB>::BYTES >= 2 * kMaxB * (int)sizeof(double), "scratch must fit");
-    return Operands<MODE, kFwdTile, KC, 16 * NB>::BYTES + sizeof(double) * (2 * (size_t)(2 * B) + 3 * (size_t)B);
+    return 2 * (size_t)Operands<MODE, kFwdTile, KC, 16 * NB>::BYTES +
+           sizeof(double) * (2 * (size_t)(2 * B) + 3 * (size_t)B);
 }
 
 template <int MODE, int NB>

@@ -15,6 +15,11 @@
 // library keeps until the process exits.  The tables are rebuilt by kernels on
 // the caller's stream at every call, so nothing from an earlier call is relied
 // on; concurrent calls that overlap on the GPU share the array and race.
+//
+// The kernels it runs have no device-side failure mode: the FP64 DWT kernel
+// has no waits and no internal consistency checks (unlike the tensor-core
+// kernels, which record timeouts in a plan's error word), so there is no
+// error word here; argument, set-up and launch errors are returned.
 #include "soft.h"
 #include "soft_internal.cuh"
 
@@ -94,11 +99,32 @@ __global__ void noalloc_layout_kernel(int B, int2 *clusters, int64_t *runoff) {
     }
 }
 
-// Device address of the static array, looked up once per device.
+// Device address of the static array, looked up once per device.  Only a
+// successful lookup is kept: a failed one (say, made inside a stream capture)
+// is retried by the next call.
 constexpr int kMaxDevices = 64;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices] = {};
+std::mutex g_scratch_mu[kMaxDevices];
+
+cudaError_t scratch_address(int dev, unsigned char **out) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu[dev]);
+    if (!g_scratch_ptr[dev]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();  // the lookup's error is not sticky: clear it for the caller
+            return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+        }
+        g_scratch_ptr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+soft_status fail(const char *where, cudaError_t e) {
+    set_last_error_message(where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SOFT_ERR_OUT_OF_MEMORY : SOFT_ERR_CUDA;
+}
 
 }  // namespace
 }  // namespace softgb
@@ -116,16 +142,17 @@ extern "C" soft_status soft_dwt_forward_noalloc(int B, const double *S, double *
         return SOFT_ERR_UNSUPPORTED;
     }
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SOFT_ERR_CUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail("soft_dwt_forward_noalloc: cudaGetDevice", e);
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_last_error_message("soft_dwt_forward_noalloc", "device ordinal beyond the supported 64");
+        return SOFT_ERR_UNSUPPORTED;
+    }
     // Set-up, once per device, with that device current: the device address of the array.
-    std::call_once(g_scratch_once[dev], [dev] {
-        void *ptr = nullptr;
-        g_scratch_err[dev] = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(ptr);
-    });
-    if (g_scratch_err[dev] != cudaSuccess || !g_scratch_ptr[dev]) return SOFT_ERR_CUDA;
+    unsigned char *base = nullptr;
+    e = scratch_address(dev, &base);
+    if (e != cudaSuccess) return fail("soft_dwt_forward_noalloc: cudaGetSymbolAddress", e);
 
-    unsigned char *base = g_scratch_ptr[dev];
     const NoAllocLayout L = noalloc_layout(B);
     Tables tb;
     tb.B = B;
@@ -142,7 +169,7 @@ extern "C" soft_status soft_dwt_forward_noalloc(int B, const double *S, double *
     tb.clusters = clusters; tb.runoff = runoff; tb.err = nullptr;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_tables(B, w, cosb, lcos, lsin, lfact, s);
+    e = launch_tables(B, w, cosb, lcos, lsin, lfact, s);
     if (e == cudaSuccess) e = launch_log_weights(B, w, lw, s);
     if (e == cudaSuccess) {
         noalloc_layout_kernel<<<64, 256, 0, s>>>(B, clusters, runoff);
@@ -151,5 +178,5 @@ extern "C" soft_status soft_dwt_forward_noalloc(int B, const double *S, double *
     }
     if (e == cudaSuccess)
         e = launch_dwt_forward_fp64(tb, reinterpret_cast<const double2 *>(S), reinterpret_cast<double2 *>(coef), s);
-    return e == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+    return e == cudaSuccess ? SOFT_OK : fail("soft_dwt_forward_noalloc: kernel launch", e);
 }

@@ -29,6 +29,7 @@ namespace {
 
 constexpr uint64_t kPlanMagic = 0x534f46545f504c4eULL;  // "SOFT_PLN"
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<long long> g_live_allocs{0};  // device allocations the library holds (soft_live_allocations)
 thread_local unsigned long long t_launches = 0;  // this thread's share, to size graph captures
 
 }  // namespace
@@ -39,6 +40,8 @@ void softgb::count_launch() {
 }
 
 unsigned long long soft_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+long long soft_live_allocations(void) { return g_live_allocs.load(std::memory_order_relaxed); }
 
 struct soft_plan_s {
     uint64_t magic;
@@ -80,6 +83,9 @@ struct soft_plan_s {
     static constexpr int kMaxRec = 4096;
     bool timing;
     int fwd_variant, inv_variant;  // tile-shape variants chosen by soft_plan_set_variant
+    // Allocation-failure injection for tests: device allocations this plan may
+    // still make (-1 = no limit), from SOFT_TEST_ALLOC_BUDGET at creation.
+    long long alloc_budget;
     int nrec;
     int rec_kind[kMaxRec];             // 0 = forward, 1 = inverse
     std::vector<cudaEvent_t> events;   // 3 * kMaxRec, created on first use
@@ -130,6 +136,49 @@ soft_status fail_cufft(const char *where, cufftResult r) {
 }
 
 bool valid(const soft_plan_s *p) { return p != nullptr && p->magic == kPlanMagic; }
+
+// Every device allocation of the library goes through dev_alloc / dev_free,
+// which keep the count soft_live_allocations() reports.  An allocation made
+// for plan p fails as out of memory once p's test budget is used up.
+cudaError_t dev_alloc(soft_plan_s *p, void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (p && p->alloc_budget >= 0) {
+        if (p->alloc_budget == 0) return cudaErrorMemoryAllocation;
+        --p->alloc_budget;
+    }
+    const cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) g_live_allocs.fetch_add(1, std::memory_order_relaxed);
+    else *ptr = nullptr;
+    return e;
+}
+
+template <class T>
+cudaError_t dev_alloc(soft_plan_s *p, T **ptr, size_t bytes) {
+    void *v = nullptr;
+    const cudaError_t e = dev_alloc(p, &v, bytes);
+    *ptr = static_cast<T *>(v);
+    return e;
+}
+
+template <class T>
+void dev_free(T *&ptr) {
+    if (ptr) {
+        cudaFree(const_cast<void *>(static_cast<const void *>(ptr)));
+        g_live_allocs.fetch_sub(1, std::memory_order_relaxed);
+        ptr = nullptr;
+    }
+}
+
+// SOFT_TEST_ALLOC_BUDGET=N (a test hook, off when unset): a plan created
+// while it is set may make N device allocations in all; the next fails as
+// out of memory.  Read once per soft_plan_create.
+long long alloc_budget_from_env() {
+    const char *v = std::getenv("SOFT_TEST_ALLOC_BUDGET");
+    if (!v || !*v) return -1;
+    char *end = nullptr;
+    const long long n = std::strtoll(v, &end, 10);
+    return (end && *end == '\0' && n >= 0) ? n : -1;
+}
 
 }  // namespace
 
@@ -236,13 +285,13 @@ void free_plan(soft_plan_s *p) {
     if (p->fft_made) cufftDestroy(p->fft);
     if (p->fft32f_made) cufftDestroy(p->fft32f);
     if (p->fft32i_made) cufftDestroy(p->fft32i);
-    cudaFree(p->lw); cudaFree(p->g32); cudaFree(p->S32);
-    cudaFree(p->seedtab); cudaFree(p->rectab); cudaFree(p->fwd_order); cudaFree(p->inv_order);
-    cudaFree(p->dftw); cudaFree(p->dfexp); cudaFree(p->tw64); cudaFree(p->colexp);
-    cudaFree(p->w); cudaFree(p->cosb); cudaFree(p->lcos); cudaFree(p->lsin); cudaFree(p->lfact);
-    cudaFree(p->clusters); cudaFree(p->runoff); cudaFree(p->S); cudaFree(p->err);
-    cudaFree(p->stage_grid); cudaFree(p->stage_coef);
-    cudaFree(p->corr_coef); cudaFree(p->amax_v); cudaFree(p->amax_i);
+    dev_free(p->lw); dev_free(p->g32); dev_free(p->S32);
+    dev_free(p->seedtab); dev_free(p->rectab); dev_free(p->fwd_order); dev_free(p->inv_order);
+    dev_free(p->dftw); dev_free(p->dfexp); dev_free(p->tw64); dev_free(p->colexp);
+    dev_free(p->w); dev_free(p->cosb); dev_free(p->lcos); dev_free(p->lsin); dev_free(p->lfact);
+    dev_free(p->clusters); dev_free(p->runoff); dev_free(p->S); dev_free(p->err);
+    dev_free(p->stage_grid); dev_free(p->stage_coef);
+    dev_free(p->corr_coef); dev_free(p->amax_v); dev_free(p->amax_i);
     p->magic = 0;
     delete p;
 }
@@ -455,16 +504,12 @@ soft_status run_inverse(soft_plan_s *p, const double *coef, double *grid, cudaSt
 
 soft_status ensure_staging(soft_plan_s *p) {
     if (!p->stage_grid) {
-        if (cudaMalloc(&p->stage_grid, sizeof(double2) * grid_elems(p->B)) != cudaSuccess) {
-            p->stage_grid = nullptr;
-            return SOFT_ERR_OUT_OF_MEMORY;
-        }
+        const cudaError_t e = dev_alloc(p, &p->stage_grid, sizeof(double2) * grid_elems(p->B));
+        if (e != cudaSuccess) return fail_cuda("host-call grid staging buffer", e);
     }
     if (!p->stage_coef) {
-        if (cudaMalloc(&p->stage_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B)) != cudaSuccess) {
-            p->stage_coef = nullptr;
-            return SOFT_ERR_OUT_OF_MEMORY;
-        }
+        const cudaError_t e = dev_alloc(p, &p->stage_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B));
+        if (e != cudaSuccess) return fail_cuda("host-call coefficient staging buffer", e);
     }
     return SOFT_OK;
 }
@@ -489,7 +534,7 @@ struct BatchGraph {
     int *d_counter = nullptr;
     ~BatchGraph() {
         if (exec) cudaGraphExecDestroy(exec);
-        cudaFree(d_xf); cudaFree(d_items); cudaFree(d_counter);
+        dev_free(d_xf); dev_free(d_items); dev_free(d_counter);
     }
 };
 
@@ -676,8 +721,8 @@ soft_status run_batch(int kind, int n, const soft_plan *plans, const void *const
         for (int i = 0; i < n; ++i) {
             soft_plan_s *p = ps[i];
             if (kind == kBatchCorrelate && !p->corr_coef) {
-                cudaError_t e = cudaMalloc(&p->corr_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B));
-                if (e != cudaSuccess) { p->corr_coef = nullptr; delete bg; return fail_cuda("correlation workspace", e); }
+                cudaError_t e = dev_alloc(p, &p->corr_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B));
+                if (e != cudaSuccess) { delete bg; return fail_cuda("correlation workspace", e); }
             }
             xf[i].tb = p->tables();
             xf[i].coef = kind == kBatchCorrelate ? reinterpret_cast<const double *>(p->corr_coef)
@@ -696,9 +741,9 @@ soft_status run_batch(int kind, int n, const soft_plan *plans, const void *const
                          [](const std::pair<int64_t, int2> &x, const std::pair<int64_t, int2> &y) { return x.first > y.first; });
         std::vector<int2> hitems(items.size());
         for (size_t t = 0; t < items.size(); ++t) hitems[t] = items[t].second;
-        cudaError_t e = cudaMalloc(&bg->d_xf, sizeof(BatchXform) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&bg->d_items, sizeof(int2) * std::max<size_t>(1, hitems.size()));
-        if (e == cudaSuccess) e = cudaMalloc(&bg->d_counter, sizeof(int));
+        cudaError_t e = dev_alloc(ps[0], &bg->d_xf, sizeof(BatchXform) * n);
+        if (e == cudaSuccess) e = dev_alloc(ps[0], &bg->d_items, sizeof(int2) * std::max<size_t>(1, hitems.size()));
+        if (e == cudaSuccess) e = dev_alloc(ps[0], &bg->d_counter, sizeof(int));
         if (e == cudaSuccess) e = cudaMemcpy(bg->d_xf, xf.data(), sizeof(BatchXform) * n, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !hitems.empty())
             e = cudaMemcpy(bg->d_items, hitems.data(), sizeof(int2) * hitems.size(), cudaMemcpyHostToDevice);
@@ -786,6 +831,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
     p->magic = kPlanMagic;
     p->B = B;
     p->dtype = dtype;
+    p->alloc_budget = alloc_budget_from_env();
     if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return SOFT_ERR_CUDA; }
 
     const int n = 2 * B;
@@ -808,7 +854,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
 
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **ptr, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+        if (e == cudaSuccess) e = dev_alloc(p, ptr, bytes);
     };
     alloc((void **)&p->w, sizeof(double) * n);
     alloc((void **)&p->cosb, sizeof(double) * n);
@@ -839,7 +885,7 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
         alloc((void **)&p->g32, sizeof(float2) * grid_elems(B));
         alloc((void **)&p->S32, sizeof(float2) * grid_elems(B));
     }
-    if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+    if (e != cudaSuccess) { free_plan(p); return fail_cuda("plan workspace", e); }
 
     e = cudaMemcpy(p->clusters, cl.data(), sizeof(int2) * cl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && p->fwd_order && p->inv_order) {
@@ -1040,8 +1086,8 @@ soft_status soft_correlate(soft_plan p, const double *f_sh, const double *g_sh, 
     if ((best_index == nullptr) != (best_value == nullptr)) return SOFT_ERR_INVALID_ARG;
     DeviceGuard g(p->device);
     if (!p->corr_coef) {
-        cudaError_t e = cudaMalloc(&p->corr_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B));
-        if (e != cudaSuccess) { p->corr_coef = nullptr; return fail_cuda("correlation workspace", e); }
+        cudaError_t e = dev_alloc(p, &p->corr_coef, sizeof(double2) * (size_t)soft_num_coeffs(p->B));
+        if (e != cudaSuccess) return fail_cuda("correlation workspace", e);
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_corr_coeffs(p->B, reinterpret_cast<const double2 *>(f_sh),

@@ -131,6 +131,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
+// 32 lanes x 16 columns of 32-bit values into TMEM (this warp's lane quarter);
+// waits until the stores are done.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
+    asm volatile("tcgen05.wait::st.sync.aligned;");
+}
+
+// Error-free sum of two FP32 values (Knuth's TwoSum): s + e == a + b exactly,
+// s = fl(a + b).  Six FP32 additions, no branch; the compiler may not reorder
+// them (no fast-math).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated running sum (hi, lo), |lo| <~ ulp(hi): adds x with the rounding
+// error of hi + x carried into lo, so that hi + lo tracks the exact sum of the
+// added values to about 2^-48 of their magnitude per step.
+__device__ __forceinline__ void comp_add(float &hi, float &lo, float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+}
+
 // ---------------------------------------------------------------------------
 // FP64 -> FP32 by integer operations (truncation toward zero, 2^-23 relative;
 // underflow below the FP32 normal range gives 0, overflow gives inf).  Used on

@@ -41,7 +41,7 @@ def test_dwt_flops_at_the_benchmark_size():
 def test_workloads_are_well_formed():
     for name, (B, mode, kind, desc) in bench.WORKLOADS.items():
         assert 1 <= B <= 512 and desc
-        assert mode in ("fp64", "fp64_real", "fp64_tc", "bf16x3", "tf32"), name
+        assert mode in ("fp64", "fp64_real", "fp64_clenshaw", "fp64_tc", "bf16x3", "tf32"), name
         assert kind in ("uniform", "gauss_decay"), name
         if mode == "fp64_real":  # the real entry points need power-of-two 2B
             assert (2 * B) & (2 * B - 1) == 0, name
@@ -55,3 +55,35 @@ def test_traffic_entries_name_existing_sources():
         assert kernel in open(path).read(), (kernel, src)
         assert nbytes > 16 * (2 * B) ** 3, "a forward DWT reads all of S at least once"
         assert len(sha) == 16
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 8, 64, 512])
+def test_sampled_pairs_and_points_are_in_range(B):
+    pairs = bench.sample_pairs(B, seed=B)
+    assert len(pairs) == len(set(pairs)) == min(16, (2 * B - 1) ** 2)
+    assert all(max(abs(m), abs(mp)) < B for m, mp in pairs)
+    if B >= 8:  # runs of every length band, the longest and the shortest included
+        l0s = {max(abs(m), abs(mp)) for m, mp in pairs}
+        assert 0 in l0s and B - 1 in l0s and len(l0s) >= 8
+    pts = bench.sample_points(B, seed=B)
+    assert all(0 <= v < 2 * B for p in pts for v in p)
+
+
+def test_oracle_ref_indexing_against_the_oracle_itself():
+    """OracleRef gathers the sampled runs and points from full output arrays;
+    fed the oracle's own full transforms it must report rounding-level errors."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1808_00896_gb300 import synth
+    B = 8
+    coef = synth.coefficients(B, "gauss_decay", seed=3)
+    grid = oracle.inverse(B, coef)
+    ref = bench.OracleRef(B, grid, coef, seed=4, threads=2)
+    err = ref.errors(torch.from_numpy(oracle.forward(B, grid)), torch.from_numpy(grid))
+    assert err["forward"] < 1e-13 and err["inverse"] < 1e-13
+    # a wrong run is seen
+    bad = oracle.forward(B, grid)
+    bad[ref.coef_idx[0]] += 1.0
+    assert ref.errors(torch.from_numpy(bad), torch.from_numpy(grid))["forward"] > 1e-3

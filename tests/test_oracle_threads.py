@@ -59,3 +59,13 @@ def test_strided_sample_touches_only_sampled_pairs(threads4):
             assert not run.any(), (m, mp)
         else:
             assert np.all(run != 0), (m, mp)
+
+
+def test_sampled_forms_reject_out_of_range_indices():
+    B = 4
+    grid = synth.random_grid(B, seed=940)
+    coef = synth.coefficients(B, "uniform", seed=941)
+    with pytest.raises(ValueError):
+        oracle.forward_pairs(B, grid, [(0, 0), (B, 0)])
+    with pytest.raises(ValueError):
+        oracle.inverse_points(B, coef, [(0, 0, 2 * B)])
