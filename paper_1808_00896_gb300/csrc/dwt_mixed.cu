@@ -663,9 +663,19 @@ size_t mixed_inverse_smem(int B) {
     return Operands<MODE, kTile, kChunk, 16 * NB>::BYTES + sizeof(double) * 4 * (size_t)B + sizeof(float) * (size_t)B;
 }
 
+// Dynamic shared memory large enough that no more CTAs share an SM than its
+// 512 TMEM columns hold (a CTA that cannot allocate would wait in
+// tcgen05.alloc, holding its SM slot): with K = 512 / tcols CTAs allowed,
+// K + 1 of them must not fit the SM's 228 KB (1 KB of it reserved per CTA).
+size_t tmem_limited_smem(size_t bytes, uint32_t tcols) {
+    const size_t k = 512 / tcols;
+    const size_t floor_bytes = 233472 / (k + 1) - 1000;
+    return std::max(bytes, floor_bytes);
+}
+
 template <int MODE, int KC, int NB, bool LD>
 cudaError_t run_forward_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
-    const size_t bytes = mixed_forward_smem<MODE, KC, NB>(mb.tb.B);
+    const size_t bytes = tmem_limited_smem(mixed_forward_smem<MODE, KC, NB>(mb.tb.B), tmem_cols<3 * 16 * NB>());
     cudaError_t e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<MODE, KC, NB, LD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -676,7 +686,7 @@ cudaError_t run_forward_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
 
 template <int MODE, int NB, bool LD>
 cudaError_t run_inverse_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
-    const size_t bytes = mixed_inverse_smem<MODE, NB>(mb.tb.B);
+    const size_t bytes = tmem_limited_smem(mixed_inverse_smem<MODE, NB>(mb.tb.B), tmem_cols<3 * 16 * NB>());
     cudaError_t e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<MODE, NB, LD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
