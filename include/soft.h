@@ -185,10 +185,15 @@ soft_status soft_correlate(soft_plan p, const double *f_sh, const double *g_sh, 
  * of device pointers.  The first call with a given (plans, pointers) captures
  * the whole batch into a CUDA graph on a private stream (instantiated once,
  * cached, most recent 16 kept; destroying a member plan drops it) and every
- * call replays it on `stream`.  FP64 inverse transforms with B <= 128 share
- * one persistent inverse-DWT launch that schedules all their (transform,
- * symmetry cluster) work items, heaviest first, through an atomic counter;
- * other entries run their per-plan kernels inside the same graph.
+ * call replays it on `stream`.  The SOFT_FP64 transforms of a batch, of any
+ * bandwidths, share one persistent DWT (forward) or iDWT (inverse,
+ * correlation) launch that schedules all their (transform, symmetry cluster)
+ * work items, heaviest first, through an atomic counter, in the tile shape of
+ * the batch's largest B (iDWT results equal the per-plan calls' bit for bit;
+ * DWT results equal them bit for bit when that shape is the plan's own, else
+ * to rounding); mixed-precision transforms of one (mode, B) share one
+ * tensor-core launch per group of up to 8; SOFT_FP64_TC entries run their
+ * per-plan kernels inside the same graph.
  *   soft_batched_inverse:   coefs[i] -> grids[i]
  *   soft_batched_forward:   grids[i] -> coefs[i]
  *   soft_batched_correlate: (f_sh[i], g_sh[i]) -> grids[i] = C_i on the Euler

@@ -73,16 +73,15 @@ __global__ void zero_nyquist_kernel(int B, double2 *S) {
 //          writing the tile of T.
 // Phase B: thread (t, c) forms sum_j T[t][j] X[j][c] for output column c.
 // ---------------------------------------------------------------------------
+// One cluster of the forward DWT; every thread of the CTA calls it (the CTA
+// kernel below and the persistent batch kernel).  smem as above, for this B.
 template <int NT, int JPT, int TPI>
-__global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, const double2 *__restrict__ S,
-                                                               double *__restrict__ coef, int flags) {
+__device__ __forceinline__ void dwt_cluster(const Tables &tb, const double2 *__restrict__ S,
+                                            double *__restrict__ coef, int flags, int cidx, int m, int mp,
+                                            double *smem, ClusterSmem &cs) {
     constexpr int LT = NT / (16 * TPI);
-    extern __shared__ __align__(16) double smem[];
-    __shared__ ClusterSmem cs;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x;
-    const int cidx = tb.fwd_order ? tb.fwd_order[blockIdx.x] : (int)blockIdx.x;
-    const int2 rep = tb.clusters[cidx];
-    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+    const int l0 = m, L = B - l0;
 
     double *X = smem;              // [n][16]
     double *T = X + (size_t)n * 16; // [LT][n]
@@ -198,6 +197,16 @@ __global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, cons
         }
         __syncthreads();
     }
+}
+
+template <int NT, int JPT, int TPI>
+__global__ void __launch_bounds__(NT, 1) dwt_forward_fp64_kernel(Tables tb, const double2 *__restrict__ S,
+                                                               double *__restrict__ coef, int flags) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ ClusterSmem cs;
+    const int cidx = tb.fwd_order ? tb.fwd_order[blockIdx.x] : (int)blockIdx.x;
+    const int2 rep = tb.clusters[cidx];
+    dwt_cluster<NT, JPT, TPI>(tb, S, coef, flags, cidx, rep.x, rep.y, smem, cs);
 }
 
 // ---------------------------------------------------------------------------
@@ -436,11 +445,12 @@ __global__ void __launch_bounds__(256) cluster_tables_kernel(Tables tb, double *
         seedtab[(size_t)c * n + j] = seed_rep(m, mp, lognorm, tb.lcos[j], tb.lsin[j]);
 }
 
-// Persistent inverse DWT over a batch of FP64 transforms of bandwidth <= 128:
+// Persistent DWT / iDWT over a batch of FP64 transforms of any bandwidths:
 // one CTA per SM slot pulls (transform, cluster) items, heaviest first, from an
 // atomic counter until the list is exhausted.  No CTA waits on another.  The
-// tile shape (NT threads x JPT beta samples) is the single-transform iDWT's
-// for the batch's largest bandwidth, so NT * JPT covers its 2B samples.
+// tile shape (NT threads x JPT beta samples, TPI threads per forward output)
+// is the single-transform kernel's for the batch's largest bandwidth, so
+// NT * JPT covers its 2B samples, and shared memory is sized for it.
 template <int NT, int JPT>
 __global__ void __launch_bounds__(NT) idwt_fp64_persistent_kernel(const BatchXform *__restrict__ xf,
                                                                   const int2 *__restrict__ items, int nitems,
@@ -458,6 +468,26 @@ __global__ void __launch_bounds__(NT) idwt_fp64_persistent_kernel(const BatchXfo
         const int2 rep = X.tb.clusters[w.y];
         idwt_cluster<NT, JPT>(X.tb, X.coef, X.S, X.flags, w.y, rep.x, rep.y, smem, cs);
         __syncthreads();  // smem and `item` are reused by the next item
+    }
+}
+
+template <int NT, int JPT, int TPI>
+__global__ void __launch_bounds__(NT) dwt_fp64_persistent_kernel(const BatchXform *__restrict__ xf,
+                                                                 const int2 *__restrict__ items, int nitems,
+                                                                 int *__restrict__ counter) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ ClusterSmem cs;
+    __shared__ int item;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = item;
+        if (it >= nitems) break;
+        const int2 w = items[it];
+        const BatchXform &X = xf[w.x];
+        const int2 rep = X.tb.clusters[w.y];
+        dwt_cluster<NT, JPT, TPI>(X.tb, X.Sin, X.coef_out, X.flags, w.y, rep.x, rep.y, smem, cs);
+        __syncthreads();
     }
 }
 
@@ -540,31 +570,68 @@ cudaError_t launch_dwt_forward_fp64(const Tables &tb, const double2 *S, double2 
     return run_forward<256, 4, 2>(tb, S, c, s, flags);
 }
 
+// Grid of a persistent kernel: every resident CTA slot of the device, at most one per item.
+template <class K>
+cudaError_t persistent_grid(K kernel, int nt, size_t bytes, int nitems, int *grid) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
+    return cudaSuccess;
+}
+
 template <int NT, int JPT>
 cudaError_t run_idwt_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
                                 cudaStream_t s) {
     const size_t bytes = sizeof(double) * ((size_t)maxB * 16 + 4 * (size_t)maxB);
-    cudaError_t e = cudaFuncSetAttribute(idwt_fp64_persistent_kernel<NT, JPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int grid = 0;
+    cudaError_t e = persistent_grid(idwt_fp64_persistent_kernel<NT, JPT>, NT, bytes, nitems, &grid);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, idwt_fp64_persistent_kernel<NT, JPT>, NT, bytes);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
     idwt_fp64_persistent_kernel<NT, JPT><<<grid, NT, bytes, s>>>(xf, items, nitems, counter);
     count_launch();
     return cudaGetLastError();
 }
 
+template <int NT, int JPT, int TPI>
+cudaError_t run_dwt_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
+                               cudaStream_t s) {
+    const int n = 2 * maxB;
+    const size_t bytes = sizeof(double) * ((size_t)n * 16 + (size_t)(NT / (16 * TPI)) * n + 5 * (size_t)maxB);
+    int grid = 0;
+    cudaError_t e = persistent_grid(dwt_fp64_persistent_kernel<NT, JPT, TPI>, NT, bytes, nitems, &grid);
+    if (e != cudaSuccess) return e;
+    dwt_fp64_persistent_kernel<NT, JPT, TPI><<<grid, NT, bytes, s>>>(xf, items, nitems, counter);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Shapes for the batch's largest 2B: the single-transform iDWT's (up to 2B =
+// 128 its two-samples-per-thread variant, which keeps small clusters from
+// leaving most of a CTA idle).  The iDWT's sums do not depend on the shape.
 cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
                                         cudaStream_t s) {
     const int n = 2 * maxB;
     if (n <= 64) return run_idwt_persistent<32, 2>(xf, items, nitems, counter, maxB, s);
     if (n <= 128) return run_idwt_persistent<64, 2>(xf, items, nitems, counter, maxB, s);
     if (n <= 256) return run_idwt_persistent<256, 1>(xf, items, nitems, counter, maxB, s);
+    if (n <= 512) return run_idwt_persistent<256, 2>(xf, items, nitems, counter, maxB, s);
+    if (n <= 1024) return run_idwt_persistent<256, 4>(xf, items, nitems, counter, maxB, s);
+    return cudaErrorInvalidValue;
+}
+
+// The single-transform DWT's default shape for the batch's largest 2B.
+cudaError_t launch_dwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
+                                       cudaStream_t s) {
+    const int n = 2 * maxB;
+    if (n <= 256) return run_dwt_persistent<256, 1, 1>(xf, items, nitems, counter, maxB, s);
+    if (n <= 512) return run_dwt_persistent<256, 2, 2>(xf, items, nitems, counter, maxB, s);
+    if (n <= 1024) return run_dwt_persistent<256, 4, 2>(xf, items, nitems, counter, maxB, s);
     return cudaErrorInvalidValue;
 }
 

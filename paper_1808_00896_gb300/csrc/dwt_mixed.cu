@@ -13,8 +13,9 @@
 //   * the cluster's partners (8 x re/im = the N = 16 columns) are the B operand;
 //   * tcgen05.mma accumulates each K chunk in FP32 in TMEM (M = 64 or 128
 //     rows, N = 16 per transform); the chunk partials are combined across
-//     chunks by compensated (TwoSum) FP32 sums kept in TMEM, and the epilogue
-//     adds hi + lo and applies V_l and the partner signs in FP64.
+//     chunks by compensated (TwoSum) FP32 sums kept in TMEM; the forward's
+//     epilogue adds hi + lo and applies V_l and the partner signs in FP64, the
+//     inverse's rounds hi + lo once to its FP32 S.
 // Forward: M = degrees l (tiles of 128), K = beta samples (chunks of 128);
 // the recurrence state of every beta sample is carried across degree tiles in
 // shared memory.  Inverse: M = beta samples (tiles of 128), K = degrees
@@ -225,14 +226,15 @@ __device__ __forceinline__ void drain_chunk(uint32_t tmem_row, bool first) {
 // Forward DWT (mixed).  One CTA per cluster, KC producer threads = KC beta
 // samples per K chunk (one recurrence chain per thread), M tiles of 64
 // degrees, N = 16 NB columns: the T tile produced once serves the NB
-// transforms of the batch.  The operands are double-buffered: while the
-// tensor cores run chunk k from one stage, the producers generate chunk k+1's
-// Wigner-d rows into the other; after chunk k's MMA completes its FP32
-// partial is added into the compensated TMEM sums (drain_chunk), and after a
+// transforms of the batch.  Each chunk's MMA starts a fresh FP32
+// accumulator; once it completes, its partial is added into the compensated
+// TMEM sums (drain_chunk) before the operands are refilled, and after a
 // tile's last chunk the epilogue applies V_l and the partner signs in FP64.
-//   dynamic smem: stage 0 | stage 1 (A planes, then B planes, each) |
-//                 dprev[2B] | dcur[2B] | rA,rAc,rV [B each]; the
-//   table-building scratch (Bc, sig) lives in stage 0, not yet in use then.
+// (A second operand stage, to overlap the next chunk's recurrence with the
+// MMA, halves the CTAs per SM and measured slower.)
+//   dynamic smem: operands (A planes, then B planes) | dprev[2B] | dcur[2B] |
+//                 rA,rAc,rV [B each]; the table-building scratch (Bc, sig)
+//   lives in the operand area, not yet in use then.
 // ---------------------------------------------------------------------------
 template <int MODE, int KC, int NB, bool LD>
 __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(MixedBatch mb, int flags) {
@@ -252,10 +254,10 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
     const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
 
-    double *dprev = reinterpret_cast<double *>(smem + 2 * O::BYTES);
+    double *dprev = reinterpret_cast<double *>(smem + O::BYTES);
     double *dcur = dprev + n;
     double *rA = dcur + n, *rAc = rA + B, *rV = rAc + B;
-    double *rBc = reinterpret_cast<double *>(smem), *rSig = rBc + B;  // scratch inside stage 0
+    double *rBc = reinterpret_cast<double *>(smem), *rSig = rBc + B;  // scratch inside the operand area
 
     load_cluster(tb, m, mp, cs);
     for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
@@ -287,19 +289,59 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
     uint32_t phase = 0;
     bool ok = true;
 
-    // Step `it` fills stage it & 1 with chunk it and issues its MMA; before the
-    // issue it folds chunk it-1's finished partial into the sums (and finishes
-    // that tile if it was its last chunk).  Stage it & 1 was last read by the
-    // MMA of chunk it-2, which step it-1 waited for.
+    // Step `it` waits for chunk it-1's MMA, folds its partial into the sums
+    // (and finishes that tile if it was its last chunk), then refills the
+    // operands with chunk it and issues its MMA.
     for (int it = 0; it <= total; ++it) {
         const bool issue = it < total;
         const int tile = it / nchunks, c = it % nchunks;
         const int lb = l0 + tile * TM, rows = issue ? min(TM, B - lb) : 0;
-        unsigned char *A = smem + (it & 1) * O::BYTES;
+        unsigned char *A = smem;
         unsigned char *X = A + O::PLANES * O::A_BYTES;
         const int kvalid = min(KC, n - c * KC);
         const int ksteps = (kvalid + kstep_elems<MODE>() - 1) / kstep_elems<MODE>();
         const int kfill = ksteps * kstep_elems<MODE>();
+        if (it > 0) {
+            // chunk it-1's MMA: wait for it, then fold its partial into the sums
+            const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
+            phase ^= 1u;
+            ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
+            if (!ok) break;
+            tc::fence_after_sync();
+            const int pt = (it - 1) / nchunks, pc = (it - 1) % nchunks;
+            if (warp < 4) {
+                drain_chunk<NB>(trow, pc == 0);
+                if (pc == nchunks - 1) {
+                    // Epilogue of tile pt: degree l = plb + 16 w + i sits in TMEM lane 32 w + i
+                    // (i < 16); (hi + lo) V_l sig_l and the partner sign in FP64.
+                    const int plb = l0 + pt * TM, prow = min(TM, B - plb);
+                    const int r = 16 * warp + lane;
+                    const int l = plb + r, q = l - l0;
+                    const bool live = lane < 16 && r < prow;
+#pragma unroll 1
+                    for (int b = 0; b < NB; ++b) {
+                        uint32_t hi[16], lo[16];
+                        tc::tmem_ld16(trow + NC + 16 * b, hi);
+                        tc::tmem_ld16(trow + 2 * NC + 16 * b, lo);
+                        if (live) {
+                            const double v = rV[q];
+#pragma unroll
+                            for (int p = 0; p < 8; ++p) {
+                                if (p >= np) break;
+                                const double vs = ((cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1))) ? -v : v;
+                                double2 out;
+                                out.x = vs * (tc::f32_to_f64(__uint_as_float(hi[2 * p])) +
+                                              tc::f32_to_f64(__uint_as_float(lo[2 * p])));
+                                out.y = vs * (tc::f32_to_f64(__uint_as_float(hi[2 * p + 1])) +
+                                              tc::f32_to_f64(__uint_as_float(lo[2 * p + 1])));
+                                *reinterpret_cast<double2 *>(mb.coef[b] + 2 * (cs.off[p] + q)) = out;
+                            }
+                        }
+                    }
+                }
+            }
+            tc::fence_before_sync();
+        }
         if (issue) {
             // A: column tid = beta sample j, rows = degrees lb..lb+rows-1.  Rows past
             // `rows` are left as they are: they only reach TMEM lanes that are never read.
@@ -381,48 +423,7 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
             }
             tc::fence_proxy_async();
         }
-        if (it > 0) {
-            // chunk it-1's MMA: wait for it, then fold its partial into the sums
-            const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
-            phase ^= 1u;
-            ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
-            if (!ok) break;
-            tc::fence_after_sync();
-            const int pt = (it - 1) / nchunks, pc = (it - 1) % nchunks;
-            if (warp < 4) {
-                drain_chunk<NB>(trow, pc == 0);
-                if (pc == nchunks - 1) {
-                    // Epilogue of tile pt: degree l = plb + 16 w + i sits in TMEM lane 32 w + i
-                    // (i < 16); (hi + lo) V_l sig_l and the partner sign in FP64.
-                    const int plb = l0 + pt * TM, prow = min(TM, B - plb);
-                    const int r = 16 * warp + lane;
-                    const int l = plb + r, q = l - l0;
-                    const bool live = lane < 16 && r < prow;
-#pragma unroll 1
-                    for (int b = 0; b < NB; ++b) {
-                        uint32_t hi[16], lo[16];
-                        tc::tmem_ld16(trow + NC + 16 * b, hi);
-                        tc::tmem_ld16(trow + 2 * NC + 16 * b, lo);
-                        if (live) {
-                            const double v = rV[q];
-#pragma unroll
-                            for (int p = 0; p < 8; ++p) {
-                                if (p >= np) break;
-                                const double vs = ((cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1))) ? -v : v;
-                                double2 out;
-                                out.x = vs * (tc::f32_to_f64(__uint_as_float(hi[2 * p])) +
-                                              tc::f32_to_f64(__uint_as_float(lo[2 * p])));
-                                out.y = vs * (tc::f32_to_f64(__uint_as_float(hi[2 * p + 1])) +
-                                              tc::f32_to_f64(__uint_as_float(lo[2 * p + 1])));
-                                *reinterpret_cast<double2 *>(mb.coef[b] + 2 * (cs.off[p] + q)) = out;
-                            }
-                        }
-                    }
-                }
-            }
-            tc::fence_before_sync();
-        }
-        __syncthreads();  // stage it & 1 complete; the accumulator is free for chunk it
+        __syncthreads();  // operands of chunk it complete; the accumulator is free for it
         if (issue && tid == 0) {
             tc::fence_after_sync();
             issue_chunk<MODE, TM, KC, NC>(tmem, A, X, true, ksteps, &mbar);
@@ -564,14 +565,13 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
                 for (int p = 0; p < 8; ++p) {
                     if (p >= np) break;
                     const int jj = cs.mir[p] ? n - 1 - j : j;
-                    // (hi + lo) times w_B(j) (the adjoint's W) in FP64, rounded once to the FP32 S
-                    const double wj = (flags & kApplyW) ? tb.w[jj] : 1.0;
-                    const double re = wj * (tc::f32_to_f64(__uint_as_float(hi[2 * p])) +
-                                            tc::f32_to_f64(__uint_as_float(lo[2 * p])));
-                    const double im = wj * (tc::f32_to_f64(__uint_as_float(hi[2 * p + 1])) +
-                                            tc::f32_to_f64(__uint_as_float(lo[2 * p + 1])));
-                    Sb[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + jj] =
-                        make_float2(tc::f64_to_f32_rn(re), tc::f64_to_f32_rn(im));
+                    // hi + lo rounded once to the FP32 of S (|lo| <= ulp(hi): the nearest
+                    // float to the compensated sum), times w_B(j) for the adjoint's W; FP32
+                    // only, so the epilogue takes nothing from the recurrence's FP64 pipe
+                    const float wj = (flags & kApplyW) ? tc::f64_to_f32_rn(tb.w[jj]) : 1.0f;
+                    const float re = __uint_as_float(hi[2 * p]) + __uint_as_float(lo[2 * p]);
+                    const float im = __uint_as_float(hi[2 * p + 1]) + __uint_as_float(lo[2 * p + 1]);
+                    Sb[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * n + jj] = make_float2(wj * re, wj * im);
                 }
             }
         }
@@ -654,8 +654,7 @@ int grid_for(int64_t count) { return (int)std::min<int64_t>((count + 255) / 256,
 template <int MODE, int KC, int NB>
 size_t mixed_forward_smem(int B) {
     static_assert(Operands<MODE, kFwdTile, KC, 16 * NB>::BYTES >= 2 * kMaxB * (int)sizeof(double), "scratch must fit");
-    return 2 * (size_t)Operands<MODE, kFwdTile, KC, 16 * NB>::BYTES +
-           sizeof(double) * (2 * (size_t)(2 * B) + 3 * (size_t)B);
+    return (size_t)Operands<MODE, kFwdTile, KC, 16 * NB>::BYTES + sizeof(double) * (2 * (size_t)(2 * B) + 3 * (size_t)B);
 }
 
 template <int MODE, int NB>

@@ -517,9 +517,11 @@ soft_status ensure_staging(soft_plan_s *p) {
 // ---------------------------------------------------------------------------
 // Batches: a list of transforms (any mix of bandwidths and modes, one plan per
 // entry) captured once into a CUDA graph and replayed on the caller's stream.
-// FP64 inverse transforms with B <= 128 share one persistent inverse-DWT
-// launch over all their clusters, heaviest first; everything else runs through
-// the per-plan path inside the same graph.
+// The FP64 transforms of a batch, of any bandwidths, share one persistent
+// DWT (forward) or iDWT (inverse, correlation) launch over all their
+// (transform, cluster) items, heaviest first; mixed-precision transforms of
+// one (mode, B) share one tensor-core launch per group of up to 8; FP64-TC
+// transforms run their per-plan kernels inside the same graph.
 // ---------------------------------------------------------------------------
 enum BatchKind { kBatchInverse = 0, kBatchForward = 1, kBatchCorrelate = 2 };
 
@@ -561,7 +563,7 @@ soft_status record_batch(BatchGraph *bg, int n, const void *const *a, const void
     int maxB = 1;
     for (int i = 0; i < n; ++i) {
         soft_plan_s *p = bg->plans[i];
-        if (bg->kind != kBatchForward && p->dtype == SOFT_FP64 && p->B <= kPersistentMaxB) {
+        if (p->dtype == SOFT_FP64) {
             pers.push_back(i);
             maxB = std::max(maxB, p->B);
         } else {
@@ -569,7 +571,21 @@ soft_status record_batch(BatchGraph *bg, int n, const void *const *a, const void
         }
     }
     cudaError_t e = cudaSuccess;
-    if (!pers.empty()) {
+    if (!pers.empty() && bg->kind == kBatchForward) {
+        // every FP64 transform's slice FFTs into its plan's S, then one persistent
+        // DWT launch over all their (transform, cluster) items
+        e = cudaMemsetAsync(bg->d_counter, 0, sizeof(int), cs);
+        if (e != cudaSuccess) return fail_cuda("batched forward DWT", e);
+        int nitems = 0;
+        for (int i : pers) {
+            soft_plan_s *p = bg->plans[i];
+            soft_status st = slice_fft(p, static_cast<const double2 *>(a[i]), p->S, +1, cs);
+            if (st != SOFT_OK) return st;
+            nitems += p->ncl;
+        }
+        e = launch_dwt_fp64_persistent(bg->d_xf, bg->d_items, nitems, bg->d_counter, maxB, cs);
+        if (e != cudaSuccess) return fail_cuda("batched forward DWT", e);
+    } else if (!pers.empty()) {
         e = cudaMemsetAsync(bg->d_counter, 0, sizeof(int), cs);
         for (int i : pers) {
             soft_plan_s *p = bg->plans[i];
@@ -728,13 +744,19 @@ soft_status run_batch(int kind, int n, const soft_plan *plans, const void *const
             xf[i].coef = kind == kBatchCorrelate ? reinterpret_cast<const double *>(p->corr_coef)
                                                  : static_cast<const double *>(a[i]);
             xf[i].S = p->S;
-            xf[i].flags = 0;
-            if (kind != kBatchForward && p->dtype == SOFT_FP64 && p->B <= kPersistentMaxB)
+            xf[i].Sin = p->S;
+            xf[i].coef_out = kind == kBatchForward ? static_cast<double *>(const_cast<void *>(b[i])) : nullptr;
+            xf[i].flags = kind == kBatchForward ? (kApplyW | kApplyV) : 0;
+            if (p->dtype == SOFT_FP64)
                 for (int cidx = 0; cidx < p->ncl; ++cidx) {
                     const int2 cl = p->h_clusters[cidx];
                     const int np = (cl.x == 0 && cl.y == 0) ? 1 : (cl.y == 0 || cl.x == cl.y) ? 4 : 8;
-                    // FP64 work of the item: 2B samples x (B - m) degrees x (real columns + 2)
-                    items.push_back({(int64_t)(p->B - cl.x) * (2 * p->B) * (np == 8 ? 18 : 10), make_int2(i, cidx)});
+                    // FP64 work of the item, 2B samples x (B - m) degrees x: the iDWT's real
+                    // columns + 2 of recurrence; the DWT's 16 columns whatever the partner
+                    // count (its folded half-warps still occupy the FP64 pipe), 8 partners first
+                    const int64_t deg = (int64_t)(p->B - cl.x) * (2 * p->B);
+                    items.push_back({kind == kBatchForward ? deg * 18 + np : deg * (np == 8 ? 18 : 10),
+                                     make_int2(i, cidx)});
                 }
         }
         std::stable_sort(items.begin(), items.end(),

@@ -243,16 +243,20 @@ __device__ inline void load_cluster(const Tables &tb, int m, int mp, ClusterSmem
 // written from it (the forward writes its coefficients, the iDWT its S).
 enum DwtFlags : int { kApplyW = 1, kApplyV = 2, kRealSym = 4 };
 
-// One transform of a batch for the persistent inverse DWT (FP64, B <= 128).
+// One transform of a batch for the persistent FP64 DWT / iDWT kernels.
 struct BatchXform {
     Tables tb;
-    const double *coef;  // interleaved complex coefficients
-    double2 *S;          // the plan's S workspace, layout [j][m][m']
+    const double *coef;  // iDWT: interleaved complex coefficients (input)
+    double2 *S;          // iDWT: the plan's S workspace, layout [j][m][m'] (output)
+    const double2 *Sin;  // DWT: the plan's S after the forward FFT (input)
+    double *coef_out;    // DWT: interleaved complex coefficients (output)
     int flags;
 };
-constexpr int kPersistentMaxB = 128;
+// Persistent launches over (transform, cluster) items of every bandwidth.
 cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
                                         cudaStream_t s);
+cudaError_t launch_dwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
+                                       cudaStream_t s);
 
 // Launchers (correlate.cu).
 cudaError_t launch_corr_coeffs(int B, const double2 *f, const double2 *g, const int64_t *runoff, double2 *coef,

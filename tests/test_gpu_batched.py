@@ -151,3 +151,34 @@ def test_batched_mixed_groups_equal_single_calls():
     finally:
         for p in plans:
             p.close()
+
+
+def test_batched_forward_persistent_over_bandwidths():
+    """FP64 forward transforms of B = 8 .. 256 in one persistent DWT launch
+    (the tile shape of B = 256): bit for bit equal to per-plan calls where
+    that shape is the plan's own (2B in (256, 512]), equal to rounding
+    elsewhere; other modes in the same batch run their own kernels."""
+    specs = [(8, "fp64"), (129, "fp64"), (256, "fp64"), (64, "fp64"), (33, "fp64_tc"), (32, "bf16x3")]
+    plans = [Plan(B, m, device=DEV) for B, m in specs]
+    try:
+        for rnd in range(2):
+            grids = [torch.from_numpy(synth.random_grid(p.B, seed=300 + 10 * rnd + i)).to(DEV)
+                     for i, p in enumerate(plans)]
+            coefs = [p.empty_coef() for p in plans]
+            batched_forward(plans, grids, coefs)
+            torch.cuda.synchronize(DEV)
+            for p, g, c in zip(plans, grids, coefs):
+                ref = p.forward(g)
+                p.sync()
+                if p.dtype == "fp64" and 256 < 2 * p.B <= 512:
+                    assert torch.equal(c, ref), p.B
+                else:
+                    tol = 1e-13 if p.dtype.startswith("fp64") else 1e-6
+                    assert synth.rel_l2(c.cpu().numpy(), ref.cpu().numpy()) < tol, (p.B, p.dtype)
+        # and against the oracle for the smallest and a middle one
+        for i in (0, 3):
+            B = plans[i].B
+            assert synth.rel_l2(coefs[i].cpu().numpy(), oracle.forward(B, grids[i].cpu().numpy())) < 1e-10
+    finally:
+        for p in plans:
+            p.close()

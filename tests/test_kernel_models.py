@@ -203,12 +203,12 @@ def test_forward_lane_mapping(NT, TPI, n, npc):
 
 # ---------------------------------------------------------------------------
 # Mixed-precision forward DWT pipeline (dwt_mixed.cu, dwt_forward_mixed_kernel):
-# step `it` fills operand stage it & 1 with chunk it, waits for chunk it-1's
-# MMA, folds its partial into the compensated sums (the first chunk of a
-# tile starts them), finishes the tile after its last chunk, then issues
-# chunk it's MMA.  A host model of that schedule: no stage is refilled while
-# an MMA that reads it may still run, every chunk is drained exactly once and
-# in order, and every degree tile gets one epilogue after its last chunk.
+# step `it` waits for chunk it-1's MMA, folds its partial into the compensated
+# sums (the first chunk of a tile starts them), finishes the tile after its
+# last chunk, then refills the one operand stage with chunk it and issues its
+# MMA.  A host model of that schedule: the stage is never refilled while an
+# MMA that reads it may still run, every chunk is drained exactly once and in
+# order, and every degree tile gets one epilogue after its last chunk.
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("L,n", [(1, 2), (5, 16), (64, 128), (65, 128), (130, 256), (512, 1024), (200, 1024)])
 @pytest.mark.parametrize("KC", [128, 256])
@@ -217,18 +217,16 @@ def test_mixed_forward_pipeline_schedule(L, n, KC):
     nch = -(-n // KC)
     ntiles = -(-L // TM)
     total = ntiles * nch
-    pending = {}   # stage -> chunk whose MMA reads it and has not been waited for
+    pending = None  # chunk whose MMA reads the stage and has not been waited for
     issued = []
     drained = []
     epilogues = []
     starts = []
     for it in range(total + 1):
-        if it < total:
-            st = it & 1
-            assert st not in pending, (it, pending)  # the stage's last reader has completed
         if it > 0:
             prev = it - 1
-            assert pending.pop(prev & 1) == prev   # wait for chunk it-1's MMA
+            assert pending == prev  # wait for chunk it-1's MMA
+            pending = None
             pc = prev % nch
             if pc == 0:
                 starts.append(prev // nch)
@@ -236,8 +234,9 @@ def test_mixed_forward_pipeline_schedule(L, n, KC):
             if pc == nch - 1:
                 epilogues.append(prev // nch)
         if it < total:
-            pending[it & 1] = it
+            assert pending is None  # the stage's last reader has completed
+            pending = it
             issued.append(it)
-    assert not pending
+    assert pending is None
     assert issued == drained == list(range(total))
     assert epilogues == starts == list(range(ntiles))
