@@ -147,17 +147,19 @@ __global__ void __launch_bounds__(kThreads) fft64_rows_kernel(const void *in, do
 
 // Columns pass: for every slice and column, the length-n DFT along the middle
 // index (stride n), `kb` adjacent columns per block, in place, or (REAL_OUT)
-// only the real parts written to `rout` (same layout, doubles).  Shared memory
-// holds column c at s + c (n + 1) (the pad spreads the columns over the banks).
+// only the real parts written to `rout` (same layout, doubles).  Only the
+// first `ncols` columns of each slice are transformed (n for complex data, B
+// for the m' >= 0 half of a real grid's transform).  Shared memory holds
+// column c at s + c (n + 1) (the pad spreads the columns over the banks).
 template <bool REAL_OUT>
 __global__ void __launch_bounds__(kThreads) fft64_cols_kernel(double2 *data, double *rout, int n, int logn, int kb,
-                                                               const FftTw64 *__restrict__ twg, int conj) {
+                                                               const FftTw64 *__restrict__ twg, int conj, int ncols) {
     extern __shared__ __align__(16) unsigned char smraw[];
     FftTw64 *tw = reinterpret_cast<FftTw64 *>(smraw);
     double2 *s = reinterpret_cast<double2 *>(smraw + sizeof(FftTw64) * (n >> 1));
     load_twiddles(tw, twg, n);
     const int ld = n + 1;
-    const int tiles = n / kb;
+    const int tiles = ncols / kb;
     const int64_t js = blockIdx.x / tiles;
     const int k0 = (blockIdx.x % tiles) * kb;
     double2 *base = data + js * n * n + k0;
@@ -182,6 +184,112 @@ __global__ void __launch_bounds__(kThreads) fft64_cols_kernel(double2 *data, dou
         if constexpr (REAL_OUT) rout[js * n * n + k0 + (int64_t)i * n + c] = s[c * ld + i].x;
         else base[(int64_t)i * n + c] = s[c * ld + i];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Real grids.  A real row x[0..n) has X[n-k] = conj X[k], so only X[0..N),
+// N = n/2, is formed, from one N-point complex DFT of the packed samples
+// z[t] = x[2t] + i x[2t+1]:
+//   E[k] = (Z[k] + conj Z[N-k]) / 2,  O[k] = (Z[k] - conj Z[N-k]) / (2i)  (indices mod N),
+//   X[k] = E[k] + w^k O[k],  w = exp(s 2 pi i / n):
+// E and O are the DFTs of the even and odd samples (real sequences, so their
+// DFTs are conjugate-symmetric), recombined as in one decimation-in-time step.
+// The inverse runs it backwards: for a Hermitian row (X[n-k] = conj X[k], the
+// Nyquist term X[N] zero as in the plan's S) the real samples come from one
+// N-point DFT of
+//   Z[k] = (X[k] + conj X[N-k]) + i v^k (X[k] - conj X[N-k]),  v = exp(s 2 pi i / n),
+// as x[2t] = Re z[t], x[2t+1] = Im z[t] (the sum over k split into k < N and
+// k + N, with X[k + N] = conj X[N - k] and v^N = -1).
+// ---------------------------------------------------------------------------
+
+// w b for w in the factored form of bfly().
+__device__ __forceinline__ double2 twmul(const FftTw64 &w, const double2 b) {
+    const double zr = fma(-w.tau, b.y, b.x), zi = fma(w.tau, b.x, b.y);
+    const double p = w.swap ? zi : zr, q = w.swap ? zr : zi;
+    return make_double2(w.m1 * p, w.m2 * q);
+}
+
+// The tables of a real-row kernel: the n-point twiddles w^k (k < N) and the
+// N-point ones exp(s 2 pi i t / N) = w^(2t) (t < N/2).
+__device__ void load_real_twiddles(FftTw64 *tw, FftTw64 *twN, const FftTw64 *__restrict__ twg, int N) {
+    for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
+    for (int t = threadIdx.x; t < (N >> 1); t += blockDim.x) twN[t] = twg[2 * t];
+}
+
+// The N-point DFT (N = 2^logN) of `rows` rows held in natural order at
+// zin + r N (global or shared memory), into s + r N in natural order.
+__device__ __forceinline__ void half_dft(const double2 *zin, double2 *s, int rows, int N, int logN, const FftTw64 *twN,
+                                         bool conj) {
+    if (logN >= 2) {
+        const int N4 = N >> 2;
+        for (int q = threadIdx.x; q < rows * N4; q += blockDim.x) {
+            const int rl = q / N4, t = q - rl * N4;
+            const double2 *z = zin + (int64_t)rl * N + t;
+            first_radix4(z[0], z[N >> 1], z[N4], z[3 * N4], conj, s + rl * N + 4 * bitrev_n(t, logN - 2));
+        }
+        stages(s, rows, N, N, logN, 4, 2, twN);
+    } else {  // N = 1 or 2: bit-reversed order is the natural one
+        for (int e = threadIdx.x; e < rows * N; e += blockDim.x) s[e] = zin[e];
+        stages(s, rows, N, N, logN, 1, 0, twN);
+    }
+}
+
+// Rows pass of a real grid: nrows real rows of n samples (`in`) -> X[0..N) of
+// each row at out + row n (columns N..n-1 of `out` are not written).
+__global__ void __launch_bounds__(kThreads) fft64_rows_r2c_kernel(const double *in, double2 *out, int64_t nrows, int n,
+                                                                   int logN, int rpb, const FftTw64 *__restrict__ twg,
+                                                                   int conj) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = n >> 1;
+    FftTw64 *tw = reinterpret_cast<FftTw64 *>(smraw);  // [N]
+    FftTw64 *twN = tw + N;                              // [max(1, N/2)]
+    double2 *s = reinterpret_cast<double2 *>(twN + max(1, N >> 1));  // [rpb][N]
+    load_real_twiddles(tw, twN, twg, N);
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int rows = (int)std::min<int64_t>(rpb, nrows - r0);
+    __syncthreads();
+    half_dft(reinterpret_cast<const double2 *>(in) + r0 * N, s, rows, N, logN, twN, conj != 0);
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+        const int rl = e / N, k = e - rl * N;
+        const double2 a = s[rl * N + k], b = s[rl * N + ((N - k) & (N - 1))];
+        const double2 E = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+        const double2 O = make_double2(0.5 * (a.y + b.y), 0.5 * (b.x - a.x));
+        const double2 wO = twmul(tw[k], O);
+        out[(r0 + rl) * n + k] = make_double2(E.x + wO.x, E.y + wO.y);
+    }
+}
+
+// Rows pass back to a real grid: X[0..N) of each row at in + row n (X[N] = 0)
+// -> nrows real rows of n samples in `out`.
+__global__ void __launch_bounds__(kThreads) fft64_rows_c2r_kernel(const double2 *in, double *out, int64_t nrows, int n,
+                                                                   int logN, int rpb, const FftTw64 *__restrict__ twg,
+                                                                   int conj) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = n >> 1;
+    FftTw64 *tw = reinterpret_cast<FftTw64 *>(smraw);
+    FftTw64 *twN = tw + N;
+    double2 *xs = reinterpret_cast<double2 *>(twN + max(1, N >> 1));  // [rpb][N]: X, then the DFT
+    double2 *zs = xs + (size_t)rpb * N;                                // [rpb][N]: Z
+    load_real_twiddles(tw, twN, twg, N);
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int rows = (int)std::min<int64_t>(rpb, nrows - r0);
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+        const int rl = e / N, k = e - rl * N;
+        xs[e] = in[(r0 + rl) * n + k];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+        const int rl = e / N, k = e - rl * N;
+        const double2 a = xs[e];
+        const double2 b = k ? xs[rl * N + N - k] : make_double2(0.0, 0.0);  // X[N - k]; X[N] = 0
+        const double2 A = make_double2(a.x + b.x, a.y - b.y);                 // X[k] + conj X[N-k]
+        const double2 C = twmul(tw[k], make_double2(a.x - b.x, a.y + b.y));   // v^k (X[k] - conj X[N-k])
+        zs[e] = make_double2(A.x - C.y, A.y + C.x);                           // A + i C
+    }
+    __syncthreads();
+    half_dft(zs, xs, rows, N, logN, twN, conj != 0);
+    double2 *o = reinterpret_cast<double2 *>(out) + r0 * N;  // (x[2t], x[2t+1]) = (Re z[t], Im z[t])
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) o[e] = xs[e];
 }
 
 // tw[t] for t < n/2: exp(sign 2 pi i t / n) in the factored form of bfly().
@@ -239,7 +347,51 @@ cudaError_t fft64_passes(int B, const void *in, double2 *mid, double *rout, cons
     e = cudaFuncSetAttribute(fft64_cols_kernel<REAL_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
     if (e != cudaSuccess) return e;
     fft64_cols_kernel<REAL_OUT><<<(unsigned)((int64_t)nslices * (n / kb)), kThreads, cbytes, s>>>(mid, rout, n, logn,
-                                                                                                 kb, t, conj);
+                                                                                                 kb, t, conj, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// The half-spectrum passes of a real grid (all 2B slices): r2c rows `in` ->
+// `S` columns 0..B-1, then those columns in place; or (c2r) those columns of
+// `S` in place, then rows to the real `out`.
+cudaError_t fft64_real_passes(int B, bool r2c, const double *in, double2 *S, double *out, const FftTw64 *tw, int sign,
+                              cudaStream_t s) {
+    const int n = 2 * B, logn = ilog2_pow2(n), N = B;
+    if (logn < 1) return cudaErrorInvalidValue;
+    const FftTw64 *t = sign < 0 ? tw + n / 2 : tw;
+    const int conj = sign < 0 ? 1 : 0;
+    const int64_t nrows = (int64_t)n * n;
+    const int rpb = std::max(1, kTile / N);
+    const size_t twb = sizeof(FftTw64) * ((size_t)N + std::max(1, N / 2));
+    const int kb = std::min(N, std::max(2, kTile / n));
+    const size_t cbytes = sizeof(FftTw64) * (size_t)(n / 2) + sizeof(double2) * (size_t)kb * (n + 1);
+    cudaError_t e = cudaFuncSetAttribute(fft64_cols_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cbytes);
+    if (e != cudaSuccess) return e;
+    const unsigned cgrid = (unsigned)((int64_t)n * (N / kb));
+    if (r2c) {
+        const size_t rbytes = twb + sizeof(double2) * (size_t)rpb * N;
+        e = cudaFuncSetAttribute(fft64_rows_r2c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rbytes);
+        if (e != cudaSuccess) return e;
+        fft64_rows_r2c_kernel<<<(unsigned)((nrows + rpb - 1) / rpb), kThreads, rbytes, s>>>(in, S, nrows, n, logn - 1,
+                                                                                           rpb, t, conj);
+        count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        fft64_cols_kernel<false><<<cgrid, kThreads, cbytes, s>>>(S, nullptr, n, logn, kb, t, conj, N);
+        count_launch();
+        return cudaGetLastError();
+    }
+    fft64_cols_kernel<false><<<cgrid, kThreads, cbytes, s>>>(S, nullptr, n, logn, kb, t, conj, N);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t rbytes = twb + 2 * sizeof(double2) * (size_t)rpb * N;
+    e = cudaFuncSetAttribute(fft64_rows_c2r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rbytes);
+    if (e != cudaSuccess) return e;
+    fft64_rows_c2r_kernel<<<(unsigned)((nrows + rpb - 1) / rpb), kThreads, rbytes, s>>>(S, out, nrows, n, logn - 1,
+                                                                                       rpb, t, conj);
     count_launch();
     return cudaGetLastError();
 }
@@ -283,6 +435,19 @@ cudaError_t launch_fft64_2d_from_real(int B, const double *in, double2 *out, con
 // parts of the result go to `out` ((2B)^3 doubles).
 cudaError_t launch_fft64_2d_to_real(int B, double2 *in, double *out, const FftTw64 *tw, int sign, cudaStream_t s) {
     return fft64_passes<false, true>(B, in, in, out, tw, sign, s, 2 * B);
+}
+
+// Real grid `in` -> the m' = 0..B-1 half of S (columns B..2B-1 of every slice
+// are left as they are): real-row DFTs, then the B columns.
+cudaError_t launch_fft64_2d_r2c(int B, const double *in, double2 *S, const FftTw64 *tw, int sign, cudaStream_t s) {
+    return fft64_real_passes(B, true, in, S, nullptr, tw, sign, s);
+}
+
+// The m' = 0..B-1 half of a Hermitian S (S(-m,-m') = conj S(m,m'), the
+// m' = -B column zero) -> the real grid `out`; S's columns 0..B-1 are
+// overwritten.
+cudaError_t launch_fft64_2d_c2r(int B, double2 *S, double *out, const FftTw64 *tw, int sign, cudaStream_t s) {
+    return fft64_real_passes(B, false, nullptr, S, out, tw, sign, s);
 }
 
 }  // namespace softgb

@@ -1021,9 +1021,10 @@ soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *st
     return run_inverse(p, coef, grid, static_cast<cudaStream_t>(stream));
 }
 
-// Real grids (FP64 plans with power-of-two 2B): the FFT reads or writes real
-// samples and the DWT / iDWT contract only one partner of each conjugate pair
-// (kRealSym).
+// Real grids (FP64 plans with power-of-two 2B): the slice FFTs run on the
+// m' >= 0 half of the spectrum (real-row DFTs of half length; every
+// contracted partner has m' >= 0) and the DWT / iDWT contract only one
+// partner of each conjugate pair (kRealSym).
 soft_status soft_forward_real(soft_plan p, const double *grid, double *coef, void *stream) {
     soft_status st = check_plan_args(p, grid, coef);
     if (st != SOFT_OK) return st;
@@ -1032,7 +1033,7 @@ soft_status soft_forward_real(soft_plan p, const double *grid, double *coef, voi
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
-    cudaError_t e = launch_fft64_2d_from_real(p->B, grid, p->S, p->tw64, +1, s);
+    cudaError_t e = launch_fft64_2d_r2c(p->B, grid, p->S, p->tw64, +1, s);  // the m' >= 0 half the DWT reads
     if (e != cudaSuccess) return fail_cuda("FP64 FFT launch", e);
     if (ev) cudaEventRecord(ev[1], s);
     e = launch_dwt_forward_plan(p, p->S, reinterpret_cast<double2 *>(coef), s, kApplyW | kApplyV | kRealSym);
@@ -1054,7 +1055,7 @@ soft_status soft_inverse_real(soft_plan p, const double *coef, double *grid, voi
     e = launch_dwt_inverse_plan(p, reinterpret_cast<const double2 *>(coef), p->S, s, kRealSym);
     if (e != cudaSuccess) return fail_cuda("iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
-    e = launch_fft64_2d_to_real(p->B, p->S, grid, p->tw64, -1, s);
+    e = launch_fft64_2d_c2r(p->B, p->S, grid, p->tw64, -1, s);
     if (e != cudaSuccess) return fail_cuda("FP64 FFT launch", e);
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;

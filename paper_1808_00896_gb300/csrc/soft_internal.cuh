@@ -307,6 +307,11 @@ cudaError_t launch_fft64_2d_from_real(int B, const double *in, double2 *out, con
 // All 2B slices of a complex `in` with a real result (Hermitian input): `in`
 // is overwritten and the real parts go to `out` ((2B)^3 doubles).
 cudaError_t launch_fft64_2d_to_real(int B, double2 *in, double *out, const FftTw64 *tw, int sign, cudaStream_t s);
+// Half-spectrum forms for real grids: real `in` -> columns m' = 0..B-1 of
+// every slice of S (the rest untouched), and the Hermitian S's columns
+// 0..B-1 (overwritten) -> the real `out`.
+cudaError_t launch_fft64_2d_r2c(int B, const double *in, double2 *S, const FftTw64 *tw, int sign, cudaStream_t s);
+cudaError_t launch_fft64_2d_c2r(int B, double2 *S, double *out, const FftTw64 *tw, int sign, cudaStream_t s);
 // FP64-accurate tensor-core DWT / iDWT (dwt_fp64tc.cu); same S layout and
 // flags as the FP64 launchers; need the plan's per-cluster tables.
 cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s,

@@ -240,3 +240,49 @@ def test_mixed_forward_pipeline_schedule(L, n, KC):
     assert pending is None
     assert issued == drained == list(range(total))
     assert epilogues == starts == list(range(ntiles))
+
+
+# ---------------------------------------------------------------------------
+# Real-grid slice FFT (fft_fp64.cu, fft64_rows_r2c_kernel / _c2r_kernel): the
+# unpacking identities of the half-length complex DFT, modelled in numpy and
+# checked against the direct DFT (exp(s 2 pi i k t / n), unnormalised).
+# ---------------------------------------------------------------------------
+def _dft(x, s):
+    n = len(x)
+    k = np.arange(n)
+    return np.exp(s * 2j * np.pi * np.outer(k, k) / n) @ x
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 64])
+@pytest.mark.parametrize("s", [1, -1])
+def test_real_row_r2c_unpacking(n, s):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n)
+    N = n // 2
+    Z = _dft(x[0::2] + 1j * x[1::2], s)          # the N-point DFT of the packed samples
+    k = np.arange(N)
+    b = Z[(N - k) % N]
+    E = 0.5 * (Z + np.conj(b))
+    O = (Z - np.conj(b)) / 2j
+    X = E + np.exp(s * 2j * np.pi * k / n) * O
+    assert np.allclose(X, _dft(x, s)[:N], rtol=0, atol=1e-12 * n)
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 64])
+@pytest.mark.parametrize("s", [1, -1])
+def test_real_row_c2r_packing(n, s):
+    rng = np.random.default_rng(100 + n)
+    N = n // 2
+    X = np.zeros(n, dtype=complex)
+    X[0] = rng.standard_normal()
+    X[1:N] = rng.standard_normal(N - 1) + 1j * rng.standard_normal(N - 1)
+    X[N + 1:] = np.conj(X[1:N][::-1])             # Hermitian, Nyquist term 0
+    want = _dft(X, s)
+    assert np.abs(want.imag).max() < 1e-12 * n
+    k = np.arange(N)
+    b = np.where(k > 0, X[(N - k) % n], 0)        # X[N - k], with X[N] = 0
+    Z = (X[:N] + np.conj(b)) + 1j * np.exp(s * 2j * np.pi * k / n) * (X[:N] - np.conj(b))
+    z = _dft(Z, s)
+    x = np.empty(n)
+    x[0::2], x[1::2] = z.real, z.imag
+    assert np.allclose(x, want.real, rtol=0, atol=1e-12 * n)
