@@ -132,12 +132,15 @@ soft_status soft_forward(soft_plan p, const double *grid, double *coef, void *st
  *   every beta slice (exp(-i...)).                                      */
 soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *stream);
 
-/* Real grids (SOFT_FP64 plans with power-of-two 2B; SOFT_ERR_UNSUPPORTED
- * otherwise).  A real function has f(l,-m,-m') = (-1)^(m-m') conj f(l,m,m')
- * (from the symmetries of Eq. (Wigner_symmetries)), and S(-m,-m';j) =
- * conj S(m,m';j).  In each symmetry cluster the partners come in such
- * conjugate pairs, and these calls contract one partner of each pair: half
- * the DWT / iDWT contraction work.
+/* Real grids (SOFT_FP64 and SOFT_FP64_TC plans with power-of-two 2B;
+ * SOFT_ERR_UNSUPPORTED otherwise).  A real function has f(l,-m,-m') =
+ * (-1)^(m-m') conj f(l,m,m') (from the symmetries of Eq. (Wigner_symmetries)),
+ * and S(-m,-m';j) = conj S(m,m';j).  In each symmetry cluster the partners
+ * come in such conjugate pairs, and these calls contract one partner of each
+ * pair: half the DWT / iDWT contraction work.  Every contracted partner has
+ * m' >= 0, so the slice FFTs (FP64 in both modes) run on that half of the
+ * spectrum: real-row DFTs of half length, and the column DFTs of m' = 0..B-1
+ * only.
  *   soft_forward_real: grid (device, (2B)^3 doubles, layout [j][i][k] as the
  *     complex grid) -> coef (device, B(4B^2-1)/3 complex), the same values as
  *     soft_forward of the grid with zero imaginary parts (the conjugate

@@ -124,7 +124,7 @@ class Plan:
 
     def forward_real(self, grid: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """FSOFT of a real grid: float64 (2B,2B,2B) -> complex coefficients (soft_forward_real).
-        FP64 plans with power-of-two 2B."""
+        FP64 and FP64-TC plans with power-of-two 2B."""
         _check_tensor(grid, self.n ** 3, self.device, "grid", torch.float64)
         out = self.empty_coef() if out is None else out
         _check_tensor(out, self.ncoef, self.device, "out")

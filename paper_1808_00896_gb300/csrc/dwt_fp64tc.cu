@@ -359,6 +359,10 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
     const int wshift = (flags & kApplyW) ? -tb.wexp : 0;  // 2^wshift max_j w_B(j) < 1 for the weighted seeds
     cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, rV);  // rV *= sig; ends with a barrier
     const int np = cs.np;
+    // Real input (kRealSym): of each conjugate partner pair (2k, 2k+1) only 2k is
+    // contracted (the odd partners' operand rows stay zero) and 2k+1 is written
+    // from it: f(l,-m,-m') = (-1)^(m-m') conj f(l,m,m').
+    const bool real = (flags & kRealSym) && np > 1;
     for (int t = tid; t < L; t += NT) {
         const int a = exponent_of(rSig[t]) + wshift;
         ralpha[t] = a;
@@ -369,7 +373,8 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
     if (tid < kCols) {
         const int p = tid >> 1;
         int e = 0;
-        if (p < np) e = tb.colexp[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * 2 + (tid & 1)];
+        if (p < np && !(real && (p & 1)))
+            e = tb.colexp[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * 2 + (tid & 1)];
         colexp[tid] = e == 0 ? 0 : e - 1023 + 1;
     }
     if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
@@ -442,11 +447,16 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
                 if (lane < 16 && r < trows) {
                     const double v = rV[q];
 #pragma unroll
-                    for (int p = 0; p < 8; ++p) {
+                    for (int p = 0; p < 8; p += 1 + (int)real) {
                         if (p >= np) break;
                         const double vs = ((cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1))) ? -v : v;
-                        *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p] + q)) =
-                            make_double2(vs * v16[2 * p], vs * v16[2 * p + 1]);
+                        const double2 f = make_double2(vs * v16[2 * p], vs * v16[2 * p + 1]);
+                        *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p] + q)) = f;
+                        if (real) {  // partner p + 1 = (-m, -m'): (-1)^(m-m') conj f
+                            const bool odd = (cs.pm[p] - cs.pmp[p]) & 1;
+                            *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p + 1] + q)) =
+                                odd ? make_double2(-f.x, f.y) : make_double2(f.x, -f.y);
+                        }
                     }
                 }
             }
@@ -466,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
                         double v[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u) v[u] = 0.0;
-                        if (p < np) {
+                        if (p < np && !(real && (p & 1))) {
                             const int64_t colp = (int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n);
                             const double *Sd = reinterpret_cast<const double *>(S) + h;
 #pragma unroll
@@ -571,6 +581,11 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
     load_cluster(tb, m, mp, cs);
     cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rG, rSig, nullptr);  // rG: scratch until here
     const int np = cs.np;
+    // Real output (kRealSym): S(-m,-m';j) = conj S(m,m';j) for the conjugate
+    // partner pairs (2k, 2k+1): only 2k is contracted (its coefficients alone
+    // are read; the odd partners' operand rows stay zero) and 2k+1 is written
+    // as its conjugate at the same beta sample.
+    const bool real = (flags & kRealSym) && np > 1;
     for (int t = tid; t < L; t += NT) {
         const int a = exponent_of(rSig[t]);
         ralpha[t] = a;
@@ -582,7 +597,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
     {
         unsigned long long m0 = 0, m1 = 0;
         const int p = tid & 7;
-        if (p < np)
+        if (p < np && !(real && (p & 1)))
 #pragma unroll 4
             for (int t = tid >> 3; t < L; t += NT / 8) {
                 const double2 c = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + t));
@@ -651,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
                 epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), colexp, v16);
                 if (jt < n) {
 #pragma unroll
-                    for (int p = 0; p < 8; ++p) {
+                    for (int p = 0; p < 8; p += 1 + (int)real) {
                         if (p >= np) break;
                         const int jj = cs.mir[p] ? n - 1 - jt : jt;
                         double re = v16[2 * p], im = v16[2 * p + 1];
@@ -661,6 +676,9 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
                             im *= wj;
                         }
                         S[((int64_t)jj * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)] = make_double2(re, im);
+                        if (real)  // partner p + 1 = (-m, -m'): the conjugate, at the same beta sample
+                            S[((int64_t)jj * n + mod_n(cs.pm[p + 1], n)) * n + mod_n(cs.pmp[p + 1], n)] =
+                                make_double2(re, -im);
                     }
                 }
             }
@@ -685,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
                             v[u] = 0.0;
                             al[u] = -colexp[q2];
                             const int k = k0 + u;
-                            if (p < np && k < cnt) {
+                            if (p < np && !(real && (p & 1)) && k < cnt) {
                                 const int q = lb + k - l0, l = lb + k;
                                 const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
                                 const double cv = coef[2 * (cs.off[p] + q) + (q2 & 1)];

@@ -60,7 +60,8 @@ struct soft_plan_s {
     int *fwd_order, *inv_order;  // FP64 and FP64-TC plans: the DWT and iDWT dispatch orders (Tables)
     float4 *dftw;              // FP64-TC plans with power-of-two 2B: double-float FFT twiddles (else null)
     int *dfexp;                // and its row scales (n^2 ints)
-    FftTw64 *tw64;             // FP64 plans with power-of-two 2B: FP64 FFT twiddles (else null: cuFFT Z2Z)
+    FftTw64 *tw64;             // FP64 / FP64-TC plans with power-of-two 2B: FP64 FFT twiddles (FP64 plans'
+                               // slice FFT, both plans' real-grid FFT; else null: cuFFT Z2Z)
     int *colexp;               // FP64-TC plans: per-(m, m') exponents of S for the DWT's column scales
     int wexp;                  // 2^wexp > max_j w_B(j)
     // Mixed-precision plans: FP32 grid staging and S in layout [m][m'][j], FP32 cuFFT plans.
@@ -900,7 +901,8 @@ soft_status soft_plan_create(soft_plan *out, int B, int dtype) {
         alloc((void **)&p->dftw, sizeof(float4) * (size_t)(n / 2));
         alloc((void **)&p->dfexp, sizeof(int) * (size_t)n * n);
     }
-    if (dtype == SOFT_FP64 && fft64_supported(B)) alloc((void **)&p->tw64, sizeof(FftTw64) * fft64_twiddle_count(B));
+    // FP64 twiddles: the FP64 plans' slice FFT, and the real-grid FFT of FP64 and FP64-TC plans
+    if (fp64_layout(dtype) && fft64_supported(B)) alloc((void **)&p->tw64, sizeof(FftTw64) * fft64_twiddle_count(B));
     if (fp64_layout(dtype)) {
         alloc((void **)&p->S, sizeof(double2) * grid_elems(B));
     } else {
@@ -1021,14 +1023,15 @@ soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *st
     return run_inverse(p, coef, grid, static_cast<cudaStream_t>(stream));
 }
 
-// Real grids (FP64 plans with power-of-two 2B): the slice FFTs run on the
+// Real grids (FP64 and FP64-TC plans with power-of-two 2B): the slice FFTs
+// (in FP64 for both) run on the
 // m' >= 0 half of the spectrum (real-row DFTs of half length; every
 // contracted partner has m' >= 0) and the DWT / iDWT contract only one
 // partner of each conjugate pair (kRealSym).
 soft_status soft_forward_real(soft_plan p, const double *grid, double *coef, void *stream) {
     soft_status st = check_plan_args(p, grid, coef);
     if (st != SOFT_OK) return st;
-    if (p->dtype != SOFT_FP64 || !p->tw64) return SOFT_ERR_UNSUPPORTED;
+    if (!fp64_layout(p->dtype) || !p->tw64) return SOFT_ERR_UNSUPPORTED;
     DeviceGuard g(p->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t *ev = timing_slot(p, 0);
@@ -1045,7 +1048,7 @@ soft_status soft_forward_real(soft_plan p, const double *grid, double *coef, voi
 soft_status soft_inverse_real(soft_plan p, const double *coef, double *grid, void *stream) {
     soft_status st = check_plan_args(p, coef, grid);
     if (st != SOFT_OK) return st;
-    if (p->dtype != SOFT_FP64 || !p->tw64) return SOFT_ERR_UNSUPPORTED;
+    if (!fp64_layout(p->dtype) || !p->tw64) return SOFT_ERR_UNSUPPORTED;
     DeviceGuard g(p->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t *ev = timing_slot(p, 1);

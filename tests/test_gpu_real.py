@@ -5,7 +5,9 @@ symmetries of Eq. (Wigner_symmetries)); the real entry points contract one
 partner of each such conjugate pair.  The oracle has no real mode: it runs the
 complex transforms on the same data (zero imaginary parts in, real part out),
 so every comparison here is against the plain definition.  Bound: rel-L2
-<= 1e-10, as the FP64 path.
+<= 1e-10, as the FP64 path, for FP64 and FP64-TC plans alike (both run the
+half-spectrum FP64 slice FFT; the FP64-TC kernels contract the even partners
+on the tensor cores).
 """
 import numpy as np
 import pytest
@@ -70,35 +72,39 @@ def odd_partner(m, mp):
 
 
 POW2_B = [1, 2, 4, 8, 16, 32, 64, 128]
+MODES = ["fp64", "fp64_tc"]
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("B", POW2_B)
-def test_forward_real_parity(B):
+def test_forward_real_parity(B, mode):
     g = real_grid(B, 8100 + B)
     want = oracle.forward(B, g.astype(np.complex128))
-    with Plan(B, device=DEV) as p:
+    with Plan(B, mode, device=DEV) as p:
         f = p.forward_real(torch.from_numpy(g).to(DEV)).cpu().numpy()
         p.sync()
     assert np.isfinite(f).all()
     assert synth.rel_l2(f, want) < TOL
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("B", POW2_B)
-def test_inverse_real_parity(B):
+def test_inverse_real_parity(B, mode):
     c = symmetrize(B, synth.coefficients(B, "gauss_decay", seed=8200 + B))
     want = oracle.inverse(B, c)
     assert np.linalg.norm(want.imag) <= 1e-12 * np.linalg.norm(want.real)  # the oracle agrees it is real
-    with Plan(B, device=DEV) as p:
+    with Plan(B, mode, device=DEV) as p:
         g = p.inverse_real(torch.from_numpy(c).to(DEV)).cpu().numpy()
         p.sync()
     assert g.dtype == np.float64 and np.isfinite(g).all()
     assert synth.rel_l2(g, want.real) < TOL
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("B", [4, 16])
-def test_forward_real_output_is_exactly_symmetric(B):
+def test_forward_real_output_is_exactly_symmetric(B, mode):
     g = real_grid(B, 8300 + B)
-    with Plan(B, device=DEV) as p:
+    with Plan(B, mode, device=DEV) as p:
         f = p.forward_real(torch.from_numpy(g).to(DEV)).cpu().numpy()
         p.sync()
     for m, mp, o, L in runs(B):
@@ -107,8 +113,9 @@ def test_forward_real_output_is_exactly_symmetric(B):
             assert np.array_equal(f[o:o + L], (-1.0) ** (m - mp) * np.conj(f[o2:o2 + L])), (m, mp)
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("B", [2, 8, 32])
-def test_inverse_real_reads_one_partner_per_pair(B):
+def test_inverse_real_reads_one_partner_per_pair(B, mode):
     """The second partner of every conjugate pair is never read: NaN there
     leaves the result unchanged."""
     c = symmetrize(B, synth.coefficients(B, "uniform", seed=8400 + B))
@@ -119,18 +126,19 @@ def test_inverse_real_reads_one_partner_per_pair(B):
             poisoned[o:o + L] = complex(np.nan, np.nan)
             count += L
     assert count == (len(c) - B) // 2  # all but the self-conjugate (0, 0) run, halved
-    with Plan(B, device=DEV) as p:
+    with Plan(B, mode, device=DEV) as p:
         g = p.inverse_real(torch.from_numpy(c).to(DEV)).cpu().numpy()
         h = p.inverse_real(torch.from_numpy(poisoned).to(DEV)).cpu().numpy()
         p.sync()
     assert np.array_equal(g, h)
 
 
-def test_round_trip_band_limited_real():
+@pytest.mark.parametrize("mode", MODES)
+def test_round_trip_band_limited_real(mode):
     B = 32
     c = symmetrize(B, synth.coefficients(B, "gauss_decay", seed=8500))
     g = np.ascontiguousarray(oracle.inverse(B, c).real)
-    with Plan(B, device=DEV) as p:
+    with Plan(B, mode, device=DEV) as p:
         f = p.forward_real(torch.from_numpy(g).to(DEV)).cpu().numpy()
         back = p.inverse_real(torch.from_numpy(f).to(DEV)).cpu().numpy()
         p.sync()
@@ -138,13 +146,14 @@ def test_round_trip_band_limited_real():
     assert synth.rel_l2(back, g) < TOL
 
 
-def test_sampled_real_B256():
+@pytest.mark.parametrize("mode", MODES)
+def test_sampled_real_B256(mode):
     """Full size: sampled order pairs of the forward (both partners of a
     conjugate pair) against the oracle's one-by-one form."""
     B = 256
     rng = np.random.default_rng(8600)
     g = real_grid(B, 8601)
-    with Plan(B, device=DEV) as p:
+    with Plan(B, mode, device=DEV) as p:
         f = p.forward_real(torch.from_numpy(g).to(DEV)).cpu().numpy()
         p.sync()
     pairs = []
@@ -156,9 +165,9 @@ def test_sampled_real_B256():
     assert synth.rel_l2(np.concatenate(got), np.concatenate(want)) < TOL
 
 
-@pytest.mark.parametrize("B,mode", [(3, "fp64"), (8, "fp64_tc"), (8, "bf16x3")])
+@pytest.mark.parametrize("B,mode", [(3, "fp64"), (3, "fp64_tc"), (8, "bf16x3")])
 def test_real_entry_points_unsupported(B, mode):
-    """Real entry points need an FP64 plan with power-of-two 2B."""
+    """Real entry points need an FP64 or FP64-TC plan with power-of-two 2B."""
     with Plan(B, mode, device=DEV) as p:
         g = torch.zeros((2 * B,) * 3, dtype=torch.float64, device=DEV)
         c = p.empty_coef()
