@@ -62,6 +62,10 @@ for _B in (64, 128, 256, 512):
                                 f"FP64 SOFT forward+inverse of a real function, B={_B}: soft_forward_real / "
                                 f"soft_inverse_real on a real (2B)^3 float64 grid, one partner of each conjugate "
                                 f"pair contracted")
+    WORKLOADS[f"b{_B}_fp64tc_real"] = (_B, "fp64_tc_real", "gauss_decay",
+                                       f"FP64-accurate SOFT forward+inverse of a real function, B={_B}: "
+                                       f"soft_forward_real / soft_inverse_real on an FP64-TC plan (tensor-core "
+                                       f"contraction of one partner per conjugate pair, FP64 half-spectrum FFT)")
     WORKLOADS[f"b{_B}_clenshaw"] = (_B, "fp64_clenshaw", "gauss_decay",
                                     f"FP64 SOFT forward+inverse, B={_B}, inverse DWT by Clenshaw's algorithm "
                                     f"(backward summation over the degrees, the iDWT's last tile-shape variant)")
@@ -649,10 +653,11 @@ def roofline_numbers(B: int, dtype: str, phase_ms, phase_cnt) -> dict:
     grids, the FP64 recurrence alone for the tensor-core modes (whose
     contraction runs on tcgen05; its TFLOP/s is reported beside)."""
     fl = dwt_flops(B)
-    real = dtype == "fp64_real"
+    real = dtype == "fp64_real"  # FP64 real grids: half the contraction on the FP64 pipe
     fwd_ms = phase_ms[1] / max(1, phase_cnt[1])
     inv_ms = phase_ms[2] / max(1, phase_cnt[2])
-    kname = {"fp64": "fp64", "fp64_real": "fp64", "fp64_clenshaw": "fp64", "fp64_tc": "tc"}.get(dtype, "mixed")
+    kname = {"fp64": "fp64", "fp64_real": "fp64", "fp64_clenshaw": "fp64", "fp64_tc": "tc",
+             "fp64_tc_real": "tc"}.get(dtype, "mixed")
     inv_name = "idwt_clenshaw_fp64_kernel" if dtype == "fp64_clenshaw" else f"dwt_inverse_{kname}_kernel"
     dom, dom_ms = (f"dwt_forward_{kname}_kernel", fwd_ms) if phase_ms[1] >= phase_ms[2] else (inv_name, inv_ms)
     algo = fl["contraction"] + fl["recurrence"] if dtype in ("fp64", "fp64_clenshaw") else \
@@ -661,8 +666,10 @@ def roofline_numbers(B: int, dtype: str, phase_ms, phase_cnt) -> dict:
     out = {"kernel": dom, "dom_ms": dom_ms, "algo": algo, "achieved": achieved, "frac": achieved / PEAK_FP64_GFLOPS,
            "phase_ms_per_launch": {"fft_forward": phase_ms[0] / max(1, phase_cnt[0]), "dwt_forward": fwd_ms,
                                    "dwt_inverse": inv_ms, "fft_inverse": phase_ms[3] / max(1, phase_cnt[3])}}
-    if dtype in TENSOR_MULT:
-        out["tensor_tflops"] = TENSOR_MULT[dtype] * fl["contraction"] / (dom_ms * 1e-3) / 1e12
+    if dtype in TENSOR_MULT or dtype == "fp64_tc_real":
+        half = 0.5 if dtype == "fp64_tc_real" else 1.0  # one partner of each conjugate pair
+        mult = TENSOR_MULT[dtype.replace("_real", "")]
+        out["tensor_tflops"] = half * mult * fl["contraction"] / (dom_ms * 1e-3) / 1e12
     return out
 
 
@@ -788,8 +795,9 @@ def run_ours(args) -> None:
     config = workload_config(args, B, dtype, kind, world)
     R = config["inputs_rotated"]
 
-    real = dtype == "fp64_real"  # real grids: soft_forward_real / soft_inverse_real on an FP64 plan
-    plan = Plan(B, "fp64" if dtype in ("fp64_real", "fp64_clenshaw") else dtype, device=dev)
+    real = dtype in ("fp64_real", "fp64_tc_real")  # real grids: soft_forward_real / soft_inverse_real
+    plan = Plan(B, {"fp64_real": "fp64", "fp64_clenshaw": "fp64", "fp64_tc_real": "fp64_tc"}.get(dtype, dtype),
+                device=dev)
     tuned = plan.tune() if args.tune else None
     if dtype == "fp64_clenshaw":
         plan.set_variant(1, plan.num_variants(1) - 1)  # the Clenshaw iDWT
@@ -867,7 +875,7 @@ def run_ours(args) -> None:
         ref = OracleRef(B, np.ascontiguousarray(grids[last].cpu().numpy()).astype(np.complex128),
                         coefs[last].cpu().numpy(), synth.BASE_SEED + 11 + B, host_cores(), real=real)
         rel = ref.errors(coef_out, grid_out)
-        rel["bound"] = MODE_BOUND.get("fp64" if dtype in ("fp64_real", "fp64_clenshaw") else dtype)
+        rel["bound"] = MODE_BOUND.get("fp64" if dtype in ("fp64_real", "fp64_clenshaw", "fp64_tc_real") else dtype)
 
     def e2e_step():
         if real:
@@ -924,7 +932,8 @@ def run_ours(args) -> None:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if dtype.startswith("fp64") and dtype != "fp64_tc" else dtype,
+            "vs_baseline": None,
+            "dtype": "f64" if dtype in ("fp64", "fp64_real", "fp64_clenshaw") else dtype.replace("_real", ""),
             "data": "synthetic", "config": config, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks,
             "rel_l2": rel, "cpu_baseline": cpu,
         }

@@ -41,9 +41,9 @@ def test_dwt_flops_at_the_benchmark_size():
 def test_workloads_are_well_formed():
     for name, (B, mode, kind, desc) in bench.WORKLOADS.items():
         assert 1 <= B <= 512 and desc
-        assert mode in ("fp64", "fp64_real", "fp64_clenshaw", "fp64_tc", "bf16x3", "tf32"), name
+        assert mode in ("fp64", "fp64_real", "fp64_clenshaw", "fp64_tc", "fp64_tc_real", "bf16x3", "tf32"), name
         assert kind in ("uniform", "gauss_decay"), name
-        if mode == "fp64_real":  # the real entry points need power-of-two 2B
+        if mode.endswith("_real"):  # the real entry points need power-of-two 2B
             assert (2 * B) & (2 * B - 1) == 0, name
     assert bench.WORKLOADS["b256"][:2] == (256, "fp64")  # the default workload
 
