@@ -322,139 +322,212 @@ __device__ __forceinline__ bool converter_wait_mma(PipeBars &pb, uint32_t &mph) 
 }
 
 // ---------------------------------------------------------------------------
-// Forward DWT.  One CTA per cluster; tiles of TM = 64 degrees (M), K chunks of
-// KC = 128 beta samples, one producer per sample; the producers keep the
-// recurrence state of their (up to 8) samples in registers.
-// Converter schedule per chunk c: B operand of c into buffer c % 2 (while the
+// Forward DWT, persistent.  One CTA per SM walks the clusters
+// fwd_order[blockIdx.x + k gridDim.x], k = 0, 1, ... (longest first, dealt out
+// round robin); tiles of TM = 64 degrees (M), K chunks of KC = 128 beta
+// samples, one producer per sample; the producers keep the recurrence state
+// of their (up to 8) samples in registers.  The roles of the one-cluster
+// design run on across cluster boundaries, and a fourth one prepares each
+// cluster's tables ahead of use:
+//   set-up     (warp 13) fills slot k & 1 with cluster k's partner table,
+//              column scales, recurrence coefficients and digit exponents as
+//              soon as cluster k-2 has released it, so the prologue of a
+//              cluster overlaps the previous cluster's work;
+// and the TMEM allocation, barrier set-up and launch happen once per SM
+// instead of once per cluster.  Slot hand-off by mbarriers: slot_full (the
+// set-up warp's 32 arrivals), slot_empty (every producer after its last
+// group of the cluster, every converter after the cluster's last epilogue).
+// Converter schedule per chunk: B operand of c into buffer c % 2 (while the
 // MMAs of c - 1 run), wait for those MMAs (then the epilogue when c - 1 closed
-// a tile), A digits of the staged groups, MMAs of c.
+// a tile, possibly of the previous cluster), A digits of the staged groups,
+// MMAs of c.
 //   dynamic smem: A planes [7] | B operand [2] | staging [kStages][8 rows][KC] |
-//                 rA, rAc, rV [B] | alpha [B] (int)
-//   (the table-building scratch rBc, rSig lives in the operand area)
+//                 slot [2] { rA, rAc [B doubles], alpha [B ints] }
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, const double2 *__restrict__ S,
-                                                                     double *__restrict__ coef, int flags) {
-    constexpr int NT = kThreads, KC = kProd, TM = 64, G = 8, NG = TM / G, MAXC = 2 * kMaxB / KC;
+constexpr int kSetup = kIssuer + 32;        // warp 13: the per-cluster tables
+constexpr int kThreadsFwd = kSetup + 32;    // 448 threads
+
+struct SlotHdr {
+    ClusterSmem cs;
+    int colexp[kCols];
+};
+
+// Doubles per table slot of the persistent forward: rA, rAc, then B ints.
+__host__ __device__ constexpr size_t fwd_slot_doubles(int B) { return 2 * (size_t)B + ((size_t)B + 1) / 2; }
+
+__global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables tb, const double2 *__restrict__ S,
+                                                                        double *__restrict__ coef, int flags) {
+    constexpr int KC = kProd, TM = 64, G = 8, NG = TM / G, MAXC = 2 * kMaxB / KC;
     constexpr int A_LBO = TM * 16 + 16, A_PLANE = (KC / 8) * A_LBO;
     constexpr int B_LBO = kNB * 16 + 16, B_BYTES = (KC / 8) * B_LBO;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ ClusterSmem cs;
+    __shared__ SlotHdr hdr[2];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) PipeBars pb;
-    __shared__ int colexp[kCols];
+    __shared__ __align__(8) uint64_t slot_full[2], slot_empty[2];
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int cidx = tb.fwd_order ? tb.fwd_order[blockIdx.x] : (int)blockIdx.x;
-    const int2 rep = tb.clusters[cidx];
-    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+    const int nchunks = (n + KC - 1) / KC;
+    const int wshift = (flags & kApplyW) ? -tb.wexp : 0;  // 2^wshift max_j w_B(j) < 1 for the weighted seeds
 
     unsigned char *A = smem;
     unsigned char *X = smem + kDig * A_PLANE;  // [2][B_BYTES]
     double *stage = reinterpret_cast<double *>(X + 2 * B_BYTES);  // [kStages][G][KC]
-    double *rA = stage + kStages * G * KC, *rAc = rA + B, *rV = rAc + B;
-    int *ralpha = reinterpret_cast<int *>(rV + B);
-    double *rBc = reinterpret_cast<double *>(smem), *rSig = rBc + B;
+    double *slotd = stage + kStages * G * KC;
+    const size_t SLOT = fwd_slot_doubles(B);
+    auto slot_rA = [&](int s) { return slotd + s * SLOT; };
+    auto slot_rAc = [&](int s) { return slotd + s * SLOT + B; };
+    auto slot_alpha = [&](int s) { return reinterpret_cast<int *>(slotd + s * SLOT + 2 * B); };
+    // The k-th cluster of this CTA (false past the end of the list).
+    auto cluster_of = [&](int k, int &cidx, int &m, int &mp) {
+        const int idx = blockIdx.x + k * gridDim.x;
+        if (idx >= tb.ncl) return false;
+        cidx = tb.fwd_order ? tb.fwd_order[idx] : idx;
+        const int2 rep = tb.clusters[cidx];
+        m = rep.x;
+        mp = rep.y;
+        return true;
+    };
 
-    load_cluster(tb, m, mp, cs);
-    for (int t = tid; t < L; t += NT) rV[t] = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
-    const int wshift = (flags & kApplyW) ? -tb.wexp : 0;  // 2^wshift max_j w_B(j) < 1 for the weighted seeds
-    cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, rV);  // rV *= sig; ends with a barrier
-    const int np = cs.np;
-    // Real input (kRealSym): of each conjugate partner pair (2k, 2k+1) only 2k is
-    // contracted (the odd partners' operand rows stay zero) and 2k+1 is written
-    // from it: f(l,-m,-m') = (-1)^(m-m') conj f(l,m,m').
-    const bool real = (flags & kRealSym) && np > 1;
-    for (int t = tid; t < L; t += NT) {
-        const int a = exponent_of(rSig[t]) + wshift;
-        ralpha[t] = a;
-        rV[t] = ldexp_bits(rV[t], -a);  // V_l sig_t 2^-alpha_t
-    }
-    // Column scales of S_p (re and im), from the per-(m, m') exponents written
-    // by colexp_kernel before this launch (the mirror does not change a maximum).
-    if (tid < kCols) {
-        const int p = tid >> 1;
-        int e = 0;
-        if (p < np && !(real && (p & 1)))
-            e = tb.colexp[((int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n)) * 2 + (tid & 1)];
-        colexp[tid] = e == 0 ? 0 : e - 1023 + 1;
-    }
     if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
-    if (tid == 0) init_pipe(pb);
+    if (tid == 0) {
+        init_pipe(pb);
+        for (int s2 = 0; s2 < 2; ++s2) {
+            tc::mbar_init(&slot_full[s2], 32);
+            tc::mbar_init(&slot_empty[s2], kProd + kConv);
+        }
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
-    const int nchunks = (n + KC - 1) / KC;
     bool ok = true;
 
-    if (tid < kProd) {
+    if (warp == kSetup / 32) {
+        // ---- set-up: the tables of cluster k into slot k & 1 ----
+        for (int k = 0; ok; ++k) {
+            int cidx, m, mp;
+            if (!cluster_of(k, cidx, m, mp)) break;
+            const int s = k & 1;
+            if (k >= 2) {  // slot s last held cluster k - 2
+                const bool done = tc::mbar_wait(&slot_empty[s], ((k >> 1) - 1) & 1, kWaitPolls);
+                ok = __all_sync(0xffffffffu, done);
+                if (!ok) break;
+            }
+            SlotHdr &h = hdr[s];
+            if (lane == 0) fill_cluster(tb, m, mp, h.cs);
+            const int L = B - m;
+            const double *src = tb.rectab + (size_t)cidx * B * 3;
+            double *rA = slot_rA(s), *rAc = slot_rAc(s);
+            int *alpha = slot_alpha(s);
+            for (int t = lane; t < L; t += 32) {
+                rA[t] = src[3 * t];
+                rAc[t] = src[3 * t + 1];
+                alpha[t] = exponent_of(src[3 * t + 2]) + wshift;  // digit exponent of row t: sig_t's, with the weight scale
+            }
+            __syncwarp();
+            if (lane < kCols) {
+                // column scales of S_p (re and im), from the per-(m, m') exponents written by
+                // colexp_kernel before this launch (the mirror does not change a maximum)
+                const int p = lane >> 1, np = h.cs.np;
+                const bool real = (flags & kRealSym) && np > 1;
+                int e = 0;
+                if (p < np && !(real && (p & 1)))
+                    e = tb.colexp[((int64_t)mod_n(h.cs.pm[p], n) * n + mod_n(h.cs.pmp[p], n)) * 2 + (lane & 1)];
+                h.colexp[lane] = e == 0 ? 0 : e - 1023 + 1;
+            }
+            tc::mbar_arrive(&slot_full[s]);
+        }
+    } else if (tid < kProd) {
         // ---- producers: sample j = c KC + t of every chunk c, rows in groups of G ----
         const int t = tid;
-        double xr[MAXC], dc[MAXC], dp[MAXC];
+        double xr[MAXC];
 #pragma unroll
         for (int c = 0; c < MAXC; ++c) {
             const int j = c * KC + t;
-            xr[c] = 0.0; dc[c] = 0.0; dp[c] = 0.0;
-            if (j < n) {
-                xr[c] = tb.cosb[j];
-                const double sd = tb.seedtab[(size_t)cidx * n + j];
-                dc[c] = (flags & kApplyW) ? sd * tb.w[j] : sd;
-            }
+            xr[c] = j < n ? tb.cosb[j] : 0.0;
         }
         uint32_t gi = 0;
-        for (int lb = l0; lb < B && ok; lb += TM) {
-            const int rows = min(TM, B - lb);
+        for (int k = 0; ok; ++k) {
+            int cidx, m, mp;
+            if (!cluster_of(k, cidx, m, mp)) break;
+            const int s = k & 1, l0 = m;
+            ok = tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls);
+            if (!ok) break;
+            const double *rA = slot_rA(s), *rAc = slot_rAc(s);
+            double dc[MAXC], dp[MAXC];
 #pragma unroll
             for (int c = 0; c < MAXC; ++c) {
-                if (c >= nchunks || !ok) break;
-                const bool col = c * KC + t < n;
-#pragma unroll 1
-                for (int g = 0; g < NG; ++g, ++gi) {  // rolled: the chunk loop around it is unrolled
-                    ok = producer_acquire(pb, gi);
-                    if (!ok) break;
-                    double *st = stage + (gi % kStages) * G * KC + t;
-#pragma unroll
-                    for (int rr = 0; rr < G; ++rr) {
-                        const int r = g * G + rr;
-                        double v = 0.0;
-                        if (col && r < rows) {
-                            v = dc[c];
-                            const int q = lb + r - l0;
-                            const double nx = fma(fma(rA[q], xr[c], -rAc[q]), dc[c], -dp[c]);
-                            dp[c] = dc[c];
-                            dc[c] = nx;
-                        }
-                        st[rr * KC] = v;
-                    }
-                    tc::mbar_arrive(&pb.full[gi % kStages]);
+                const int j = c * KC + t;
+                dc[c] = 0.0;
+                dp[c] = 0.0;
+                if (j < n) {
+                    const double sd = tb.seedtab[(size_t)cidx * n + j];
+                    dc[c] = (flags & kApplyW) ? sd * tb.w[j] : sd;
                 }
             }
+            for (int lb = l0; lb < B && ok; lb += TM) {
+                const int rows = min(TM, B - lb);
+#pragma unroll
+                for (int c = 0; c < MAXC; ++c) {
+                    if (c >= nchunks || !ok) break;
+                    const bool col = c * KC + t < n;
+#pragma unroll 1
+                    for (int g = 0; g < NG; ++g, ++gi) {  // rolled: the chunk loop around it is unrolled
+                        ok = producer_acquire(pb, gi);
+                        if (!ok) break;
+                        double *st = stage + (gi % kStages) * G * KC + t;
+#pragma unroll
+                        for (int rr = 0; rr < G; ++rr) {
+                            const int r = g * G + rr;
+                            double v = 0.0;
+                            if (col && r < rows) {
+                                v = dc[c];
+                                const int q = lb + r - l0;
+                                const double nx = fma(fma(rA[q], xr[c], -rAc[q]), dc[c], -dp[c]);
+                                dp[c] = dc[c];
+                                dc[c] = nx;
+                            }
+                            st[rr * KC] = v;
+                        }
+                        tc::mbar_arrive(&pb.full[gi % kStages]);
+                    }
+                }
+            }
+            if (ok) tc::mbar_arrive(&slot_empty[s]);  // this producer is done with the slot's tables
         }
-    } else if (tid < kIssuer) {
+    } else if (tid >= kProd && tid < kIssuer) {
         // ---- converters ----
         const int t = tid - kProd;
         const int wq = warp & 3;  // TMEM lane quarter of this warp
         uint32_t gi = 0, mph = 0, cc = 0;
         bool pending = false;     // MMAs committed and not yet waited for
-        int plb = 0, prows = 0;   // the tile those MMAs close (prows > 0), for the deferred epilogue
-        auto epilogue = [&](int tlb, int trows) {
-            // Degree tlb + 16 w + i sits in TMEM lane 32 w + i (i < 16), w = lane quarter (warps 4-7).
+        // the tile those MMAs close (prows > 0), for the deferred epilogue, and its cluster
+        int plb = 0, prows = 0, pslot = 0, pl0 = 0, pcidx = 0;
+        bool plast = false;       // ... and whether that tile is its cluster's last
+        auto epilogue = [&]() {
+            // Degree plb + 16 w + i sits in TMEM lane 32 w + i (i < 16), w = lane quarter (warps 4-7).
             tc::fence_after_sync();
             if (t < 128) {
+                const SlotHdr &h = hdr[pslot];
+                const int np = h.cs.np;
+                const bool real = (flags & kRealSym) && np > 1;
                 const int r = 16 * wq + lane;
-                const int l = tlb + r, q = l - l0;
+                const int l = plb + r, q = l - pl0;
                 double v16[kCols];
-                epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), colexp, v16);
-                if (lane < 16 && r < trows) {
-                    const double v = rV[q];
+                epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), h.colexp, v16);
+                if (lane < 16 && r < prows) {
+                    // V_l sig_t 2^-alpha_t
+                    const double V = (flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0;
+                    const double v = ldexp_bits(V * tb.rectab[((size_t)pcidx * B + q) * 3 + 2], -slot_alpha(pslot)[q]);
 #pragma unroll
                     for (int p = 0; p < 8; p += 1 + (int)real) {
                         if (p >= np) break;
-                        const double vs = ((cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1))) ? -v : v;
+                        const double vs = ((h.cs.sign[p] < 0.0) != (h.cs.lpar[p] && (l & 1))) ? -v : v;
                         const double2 f = make_double2(vs * v16[2 * p], vs * v16[2 * p + 1]);
-                        *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p] + q)) = f;
+                        *reinterpret_cast<double2 *>(coef + 2 * (h.cs.off[p] + q)) = f;
                         if (real) {  // partner p + 1 = (-m, -m'): (-1)^(m-m') conj f
-                            const bool odd = (cs.pm[p] - cs.pmp[p]) & 1;
-                            *reinterpret_cast<double2 *>(coef + 2 * (cs.off[p + 1] + q)) =
+                            const bool odd = (h.cs.pm[p] - h.cs.pmp[p]) & 1;
+                            *reinterpret_cast<double2 *>(coef + 2 * (h.cs.off[p + 1] + q)) =
                                 odd ? make_double2(-f.x, f.y) : make_double2(f.x, -f.y);
                         }
                     }
@@ -462,85 +535,108 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_forward_tc_kernel(Tables tb, 
             }
             tc::fence_before_sync();
         };
-        for (int lb = l0; lb < B && ok; lb += TM) {
-            const int rows = min(TM, B - lb);
-            for (int c = 0; c < nchunks && ok; ++c, ++cc) {
-                const int kvalid = min(KC, n - c * KC);
-                const int ksteps = (kvalid + 15) / 16;
-                const int kfill = ksteps * 16;
-                unsigned char *Xc = X + (cc & 1) * B_BYTES;
-                {
-                    // B operand: partner p, re (h = 0) or im (h = 1), beta samples k0..k0+7
-                    const int p = t & 7, h = (t >> 3) & 1, k0 = 8 * (t >> 4);
-                    if (k0 < kfill) {
-                        double v[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) v[u] = 0.0;
-                        if (p < np && !(real && (p & 1))) {
-                            const int64_t colp = (int64_t)mod_n(cs.pm[p], n) * n + mod_n(cs.pmp[p], n);
-                            const double *Sd = reinterpret_cast<const double *>(S) + h;
-#pragma unroll
-                            for (int u = 0; u < 8; ++u)
-                                if (k0 + u < kvalid) {
-                                    const int jj = c * KC + k0 + u;
-                                    v[u] = Sd[2 * ((int64_t)(cs.mir[p] ? n - 1 - jj : jj) * n * n + colp)];
-                                }
-                        }
-                        const int a = -colexp[2 * p + h];
-                        const int al[4] = {a, a, a, a};
-                        const double v0[4] = {v[0], v[1], v[2], v[3]}, v1[4] = {v[4], v[5], v[6], v[7]};
-                        put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h, k0, v0, al);
-                        put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h, k0 + 4, v1, al);
-                    }
-                }
-                if (pending) {
-                    ok = converter_wait_mma(pb, mph);
-                    pending = false;
-                    if (!ok) break;
-                    if (prows > 0) epilogue(plb, prows);
-                }
-                // A operand: staged row 8 g + t / 32, samples 4 (t % 32) .. + 3
-                const int rr = t >> 5, k4 = 4 * (t & 31);
-                for (int g = 0; g < NG; ++g, ++gi) {
-                    ok = converter_acquire(pb, gi);
-                    if (!ok) break;
-                    const int r = g * G + rr;
-                    if (r < rows && k4 < kfill) {
-                        const double2 *src =
-                            reinterpret_cast<const double2 *>(stage + (gi % kStages) * G * KC + rr * KC + k4);
-                        const double2 w0 = src[0], w1 = src[1];
-                        const double v[4] = {w0.x, w0.y, w1.x, w1.y};
-                        const int a = ralpha[lb + r - l0];
-                        const int al[4] = {a, a, a, a};
-                        put_digits4(A, A_PLANE, A_LBO, r, k4, v, al);
-                    }
-                    tc::mbar_arrive(&pb.empty[gi % kStages]);
-                }
+        for (int k = 0; ok; ++k) {
+            int cidx, m, mp;
+            if (!cluster_of(k, cidx, m, mp)) break;
+            const int s = k & 1, l0 = m;
+            {
+                const bool done = tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls);
+                ok = tc::group_and(kBarConv, kConv, done);
                 if (!ok) break;
-                tc::fence_proxy_async();
-                tc::group_sync(kBarConv, kConv);
-                if (t == 0) tc::mbar_arrive(&pb.ready);
-                pending = true;
-                plb = lb;
-                prows = c == nchunks - 1 ? rows : 0;
+            }
+            const SlotHdr &h = hdr[s];
+            const int np = h.cs.np;
+            const bool real = (flags & kRealSym) && np > 1;
+            const int *alpha = slot_alpha(s);
+            for (int lb = l0; lb < B && ok; lb += TM) {
+                const int rows = min(TM, B - lb);
+                for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+                    const int kvalid = min(KC, n - c * KC);
+                    const int ksteps = (kvalid + 15) / 16;
+                    const int kfill = ksteps * 16;
+                    unsigned char *Xc = X + (cc & 1) * B_BYTES;
+                    {
+                        // B operand: partner p, re (h2 = 0) or im (h2 = 1), beta samples k0..k0+7
+                        const int p = t & 7, h2 = (t >> 3) & 1, k0 = 8 * (t >> 4);
+                        if (k0 < kfill) {
+                            double v[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) v[u] = 0.0;
+                            if (p < np && !(real && (p & 1))) {
+                                const int64_t colp = (int64_t)mod_n(h.cs.pm[p], n) * n + mod_n(h.cs.pmp[p], n);
+                                const double *Sd = reinterpret_cast<const double *>(S) + h2;
+#pragma unroll
+                                for (int u = 0; u < 8; ++u)
+                                    if (k0 + u < kvalid) {
+                                        const int jj = c * KC + k0 + u;
+                                        v[u] = Sd[2 * ((int64_t)(h.cs.mir[p] ? n - 1 - jj : jj) * n * n + colp)];
+                                    }
+                            }
+                            const int a = -h.colexp[2 * p + h2];
+                            const int al[4] = {a, a, a, a};
+                            const double v0[4] = {v[0], v[1], v[2], v[3]}, v1[4] = {v[4], v[5], v[6], v[7]};
+                            put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h2, k0, v0, al);
+                            put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h2, k0 + 4, v1, al);
+                        }
+                    }
+                    if (pending) {
+                        ok = converter_wait_mma(pb, mph);
+                        pending = false;
+                        if (!ok) break;
+                        if (prows > 0) epilogue();
+                        if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
+                    }
+                    // A operand: staged row 8 g + t / 32, samples 4 (t % 32) .. + 3
+                    const int rr = t >> 5, k4 = 4 * (t & 31);
+                    for (int g = 0; g < NG; ++g, ++gi) {
+                        ok = converter_acquire(pb, gi);
+                        if (!ok) break;
+                        const int r = g * G + rr;
+                        if (r < rows && k4 < kfill) {
+                            const double2 *src =
+                                reinterpret_cast<const double2 *>(stage + (gi % kStages) * G * KC + rr * KC + k4);
+                            const double2 w0 = src[0], w1 = src[1];
+                            const double v[4] = {w0.x, w0.y, w1.x, w1.y};
+                            const int a = alpha[lb + r - l0];
+                            const int al[4] = {a, a, a, a};
+                            put_digits4(A, A_PLANE, A_LBO, r, k4, v, al);
+                        }
+                        tc::mbar_arrive(&pb.empty[gi % kStages]);
+                    }
+                    if (!ok) break;
+                    tc::fence_proxy_async();
+                    tc::group_sync(kBarConv, kConv);
+                    if (t == 0) tc::mbar_arrive(&pb.ready);
+                    pending = true;
+                    plb = lb;
+                    prows = c == nchunks - 1 ? rows : 0;
+                    plast = c == nchunks - 1 && lb + TM >= B;
+                    pslot = s;
+                    pl0 = l0;
+                    pcidx = cidx;
+                }
             }
         }
         if (pending) {
             // the last tile's MMAs (or, after a timeout, MMAs still in flight)
             const bool done = converter_wait_mma(pb, mph);
-            if (ok && done && prows > 0) epilogue(plb, prows);
+            if (ok && done && prows > 0) epilogue();
             ok = ok && done;
         }
     } else if (tid == kIssuer) {
         // ---- issuer: the MMAs of every chunk, in the converters' order ----
         uint32_t rph = 0, cc = 0;
-        for (int lb = l0; lb < B && ok; lb += TM)
-            for (int c = 0; c < nchunks && ok; ++c, ++cc) {
-                ok = issuer_acquire(pb, rph);
-                if (!ok) break;
-                const int ksteps = (min(KC, n - c * KC) + 15) / 16;
-                issue_levels<TM>(tmem, A, A_PLANE, A_LBO, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps, &pb.mma);
-            }
+        for (int k = 0; ok; ++k) {
+            int cidx, m, mp;
+            if (!cluster_of(k, cidx, m, mp)) break;
+            for (int lb = m; lb < B && ok; lb += TM)
+                for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+                    ok = issuer_acquire(pb, rph);
+                    if (!ok) break;
+                    const int ksteps = (min(KC, n - c * KC) + 15) / 16;
+                    issue_levels<TM>(tmem, A, A_PLANE, A_LBO, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps, &pb.mma);
+                }
+        }
     }
     if (!ok && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
@@ -798,11 +894,17 @@ cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *c
     constexpr int KC = kProd, A_PLANE = (KC / 8) * (64 * 16 + 16), B_BYTES = (KC / 8) * (kNB * 16 + 16);
     const int B = tb.B;
     const size_t bytes = (size_t)kDig * A_PLANE + 2 * (size_t)B_BYTES +
-                         sizeof(double) * (kStages * 8 * (size_t)KC + 3 * (size_t)B) + sizeof(int) * (size_t)B;
+                         sizeof(double) * (kStages * 8 * (size_t)KC + 2 * fwd_slot_doubles(B));
     cudaError_t e =
         cudaFuncSetAttribute(dwt_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    dwt_forward_tc_kernel<<<tb.ncl, kThreads, bytes, s>>>(tb, S, reinterpret_cast<double *>(coef), flags);
+    // persistent: one CTA per SM (the shared memory allows no second one)
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(tb.ncl, sms));
+    dwt_forward_tc_kernel<<<grid, kThreadsFwd, bytes, s>>>(tb, S, reinterpret_cast<double *>(coef), flags);
     count_launch();
     return cudaGetLastError();
 }

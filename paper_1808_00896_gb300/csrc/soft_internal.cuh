@@ -215,20 +215,23 @@ struct ClusterSmem {
     int64_t off[8];
 };
 
-__device__ inline void load_cluster(const Tables &tb, int m, int mp, ClusterSmem &cs) {
-    if (threadIdx.x == 0) {
-        const Partners P = make_partners(m, mp);
-        cs.np = P.np;
-        for (int p = 0; p < 8; ++p) {
-            const bool on = p < P.np;
-            cs.pm[p] = on ? P.m[p] : 0;
-            cs.pmp[p] = on ? P.mp[p] : 0;
-            cs.mir[p] = on ? P.mirror[p] : 0;
-            cs.lpar[p] = on ? P.lpar[p] : 0;
-            cs.sign[p] = on ? P.sign[p] : 0.0;
-            cs.off[p] = on ? tb.runoff[runoff_index(tb.B, P.m[p], P.mp[p])] : 0;
-        }
+// Fills cs for representative (m, m'); called by one thread.
+__device__ inline void fill_cluster(const Tables &tb, int m, int mp, ClusterSmem &cs) {
+    const Partners P = make_partners(m, mp);
+    cs.np = P.np;
+    for (int p = 0; p < 8; ++p) {
+        const bool on = p < P.np;
+        cs.pm[p] = on ? P.m[p] : 0;
+        cs.pmp[p] = on ? P.mp[p] : 0;
+        cs.mir[p] = on ? P.mirror[p] : 0;
+        cs.lpar[p] = on ? P.lpar[p] : 0;
+        cs.sign[p] = on ? P.sign[p] : 0.0;
+        cs.off[p] = on ? tb.runoff[runoff_index(tb.B, P.m[p], P.mp[p])] : 0;
     }
+}
+
+__device__ inline void load_cluster(const Tables &tb, int m, int mp, ClusterSmem &cs) {
+    if (threadIdx.x == 0) fill_cluster(tb, m, mp, cs);
 }
 
 // Scalings applied by the DWT kernels.  The transforms use
