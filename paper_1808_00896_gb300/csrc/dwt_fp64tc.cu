@@ -535,46 +535,18 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
             }
             tc::fence_before_sync();
         };
-        // This thread's 8 raw S values of chunk cch for the cluster in slot hh:
-        // partner p, re (h2 = 0) or im (h2 = 1), beta samples k0..k0+7 (0 past the chunk).
-        const int bp = t & 7, bh = (t >> 3) & 1, bk0 = 8 * (t >> 4);
-        auto load_raw = [&](const SlotHdr &hh, int cch, double (&v)[8]) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = 0.0;
-            const int kvalid = min(KC, n - cch * KC);
-            const bool real = (flags & kRealSym) && hh.cs.np > 1;
-            if (bk0 < kvalid && bp < hh.cs.np && !(real && (bp & 1))) {
-                const int64_t colp = (int64_t)mod_n(hh.cs.pm[bp], n) * n + mod_n(hh.cs.pmp[bp], n);
-                const double *Sd = reinterpret_cast<const double *>(S) + bh;
-                const bool mir = hh.cs.mir[bp];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (bk0 + u < kvalid) {
-                        const int jj = cch * KC + bk0 + u;
-                        v[u] = Sd[2 * ((int64_t)(mir ? n - 1 - jj : jj) * n * n + colp)];
-                    }
-            }
-        };
-        // Waits (bounded, group-uniform verdict) until slot k & 1 holds cluster k's tables.
-        auto wait_slot = [&](int k) {
-            const bool done = tc::mbar_wait(&slot_full[k & 1], (k >> 1) & 1, kWaitPolls);
-            return tc::group_and(kBarConv, kConv, done);
-        };
-        // The S values of the next chunk are loaded one chunk ahead (pv), so that
-        // their latency hides behind the current chunk's digit conversion.
-        double pv[8];
-        bool have = false;   // pv holds the raw values of the chunk about to start
-        int waited = -1;     // the highest cluster whose slot this group has waited for
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
             if (!cluster_of(k, cidx, m, mp)) break;
             const int s = k & 1, l0 = m;
-            if (waited < k) {
-                ok = wait_slot(k);
+            {
+                const bool done = tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls);
+                ok = tc::group_and(kBarConv, kConv, done);
                 if (!ok) break;
-                waited = k;
             }
             const SlotHdr &h = hdr[s];
+            const int np = h.cs.np;
+            const bool real = (flags & kRealSym) && np > 1;
             const int *alpha = slot_alpha(s);
             for (int lb = l0; lb < B && ok; lb += TM) {
                 const int rows = min(TM, B - lb);
@@ -584,20 +556,27 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                     const int kfill = ksteps * 16;
                     unsigned char *Xc = X + (cc & 1) * B_BYTES;
                     {
-                        // B operand: partner bp, re / im, beta samples bk0..bk0+7 of chunk c
-                        double v[8];
-                        if (have) {
+                        // B operand: partner p, re (h2 = 0) or im (h2 = 1), beta samples k0..k0+7
+                        const int p = t & 7, h2 = (t >> 3) & 1, k0 = 8 * (t >> 4);
+                        if (k0 < kfill) {
+                            double v[8];
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) v[u] = pv[u];
-                        } else {
-                            load_raw(h, c, v);
-                        }
-                        if (bk0 < kfill) {
-                            const int a = -h.colexp[2 * bp + bh];
+                            for (int u = 0; u < 8; ++u) v[u] = 0.0;
+                            if (p < np && !(real && (p & 1))) {
+                                const int64_t colp = (int64_t)mod_n(h.cs.pm[p], n) * n + mod_n(h.cs.pmp[p], n);
+                                const double *Sd = reinterpret_cast<const double *>(S) + h2;
+#pragma unroll
+                                for (int u = 0; u < 8; ++u)
+                                    if (k0 + u < kvalid) {
+                                        const int jj = c * KC + k0 + u;
+                                        v[u] = Sd[2 * ((int64_t)(h.cs.mir[p] ? n - 1 - jj : jj) * n * n + colp)];
+                                    }
+                            }
+                            const int a = -h.colexp[2 * p + h2];
                             const int al[4] = {a, a, a, a};
                             const double v0[4] = {v[0], v[1], v[2], v[3]}, v1[4] = {v[4], v[5], v[6], v[7]};
-                            put_digits4(Xc, 16 * kCols, B_LBO, 2 * bp + bh, bk0, v0, al);
-                            put_digits4(Xc, 16 * kCols, B_LBO, 2 * bp + bh, bk0 + 4, v1, al);
+                            put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h2, k0, v0, al);
+                            put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h2, k0 + 4, v1, al);
                         }
                     }
                     if (pending) {
@@ -606,26 +585,6 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                         if (!ok) break;
                         if (prows > 0) epilogue();
                         if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
-                    }
-                    // prefetch the next chunk's S values: the next chunk of this cluster, or
-                    // the first chunk of the next cluster (whose slot is waited for here,
-                    // after this group has released the slot before it)
-                    have = false;
-                    if (c + 1 < nchunks) {
-                        load_raw(h, c + 1, pv);
-                        have = true;
-                    } else if (lb + TM < B) {
-                        load_raw(h, 0, pv);
-                        have = true;
-                    } else {
-                        int c2, m2, mp2;
-                        if (cluster_of(k + 1, c2, m2, mp2)) {
-                            ok = wait_slot(k + 1);
-                            if (!ok) break;
-                            waited = k + 1;
-                            load_raw(hdr[(k + 1) & 1], 0, pv);
-                            have = true;
-                        }
                     }
                     // A operand: staged row 8 g + t / 32, samples 4 (t % 32) .. + 3
                     const int rr = t >> 5, k4 = 4 * (t & 31);
