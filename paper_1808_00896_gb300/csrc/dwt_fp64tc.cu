@@ -266,11 +266,11 @@ __device__ __forceinline__ void reduce_column_exponents(unsigned long long m0, u
 // parallel instead of in one warp's instruction stream.  Hand-off through
 // mbarriers (full: 128 producer arrivals, empty: 256 converter arrivals,
 // ready: one converter arrival per chunk, mma: the tcgen05 commit);
-// every wait is bounded.  Converters, which synchronise among themselves to
-// agree on when the operands are complete, take each verdict with an
-// AND-reducing named barrier so that a timeout makes the whole group leave
-// together; producers and the issuer synchronise with nobody but the mbarriers
-// and leave individually.
+// every wait is bounded.  Converters, which synchronise among themselves once
+// per chunk to agree that the operands are complete, take that barrier as an
+// AND reduction of their wait verdicts so that a timeout makes the whole group
+// leave together; producers and the issuer synchronise with nobody but the
+// mbarriers and leave individually.
 // ---------------------------------------------------------------------------
 constexpr int kProd = 128;    // producer threads (warps 0-3)
 constexpr int kConv = 256;    // converter threads (warps 4-11)
@@ -308,11 +308,16 @@ __device__ __forceinline__ bool producer_acquire(PipeBars &pb, uint32_t gi) {
     return tc::mbar_wait(&pb.empty[gi % kStages], ((gi / kStages) & 1) ^ 1u, kWaitPolls);
 }
 
-// Converter: wait until staging buffer gi % kStages holds group gi.
+// Converter: wait until staging buffer gi % kStages holds group gi.  Each
+// converter decides alone here (no barrier per group): a converter that gives
+// up skips the rest of its chunk, and the AND-reducing barrier that closes
+// every chunk (chunk_done) gives the whole group that verdict.
 __device__ __forceinline__ bool converter_acquire(PipeBars &pb, uint32_t gi) {
-    const bool done = tc::mbar_wait(&pb.full[gi % kStages], (gi / kStages) & 1, kWaitPolls);
-    return tc::group_and(kBarConv, kConv, done);
+    return tc::mbar_wait(&pb.full[gi % kStages], (gi / kStages) & 1, kWaitPolls);
 }
+
+// Converter: all converters have written the chunk's operands (or one gave up).
+__device__ __forceinline__ bool chunk_done(bool ok) { return tc::group_and(kBarConv, kConv, ok); }
 
 // Converter: wait for the chunk MMAs committed last.
 __device__ __forceinline__ bool converter_wait_mma(PipeBars &pb, uint32_t &mph) {
@@ -520,8 +525,9 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                     const double V = (flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0;
                     const double v = ldexp_bits(V * tb.rectab[((size_t)pcidx * B + q) * 3 + 2], -slot_alpha(pslot)[q]);
 #pragma unroll
-                    for (int p = 0; p < 8; p += 1 + (int)real) {
+                    for (int p = 0; p < 8; ++p) {
                         if (p >= np) break;
+                        if (real && (p & 1)) continue;  // written from its pair below
                         const double vs = ((h.cs.sign[p] < 0.0) != (h.cs.lpar[p] && (l & 1))) ? -v : v;
                         const double2 f = make_double2(vs * v16[2 * p], vs * v16[2 * p + 1]);
                         *reinterpret_cast<double2 *>(coef + 2 * (h.cs.off[p] + q)) = f;
@@ -603,9 +609,9 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                         }
                         tc::mbar_arrive(&pb.empty[gi % kStages]);
                     }
-                    if (!ok) break;
                     tc::fence_proxy_async();
-                    tc::group_sync(kBarConv, kConv);
+                    ok = chunk_done(ok);
+                    if (!ok) break;
                     if (t == 0) tc::mbar_arrive(&pb.ready);
                     pending = true;
                     plb = lb;
@@ -762,8 +768,9 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
                 epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), colexp, v16);
                 if (jt < n) {
 #pragma unroll
-                    for (int p = 0; p < 8; p += 1 + (int)real) {
+                    for (int p = 0; p < 8; ++p) {
                         if (p >= np) break;
+                        if (real && (p & 1)) continue;  // written from its pair below
                         const int jj = cs.mir[p] ? n - 1 - jt : jt;
                         double re = v16[2 * p], im = v16[2 * p + 1];
                         if (flags & kApplyW) {
@@ -833,9 +840,9 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
                     }
                     tc::mbar_arrive(&pb.empty[gi % kStages]);
                 }
-                if (!ok) break;
                 tc::fence_proxy_async();
-                tc::group_sync(kBarConv, kConv);
+                ok = chunk_done(ok);
+                if (!ok) break;
                 if (t == 0) tc::mbar_arrive(&pb.ready);
                 pending = true;
                 pjb = lb + KC >= B ? jb : -1;
