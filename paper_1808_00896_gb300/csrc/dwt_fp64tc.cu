@@ -362,7 +362,7 @@ __host__ __device__ constexpr size_t fwd_slot_doubles(int B) { return 2 * (size_
 
 __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables tb, const double2 *__restrict__ S,
                                                                         double *__restrict__ coef, int flags) {
-    constexpr int KC = kProd, TM = 64, G = 8, NG = TM / G, MAXC = 2 * kMaxB / KC;
+    constexpr int KC = kProd, TM = 64, G = 8, MAXC = 2 * kMaxB / KC;
     constexpr int A_LBO = TM * 16 + 16, A_PLANE = (KC / 8) * A_LBO;
     constexpr int B_LBO = kNB * 16 + 16, B_BYTES = (KC / 8) * B_LBO;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -472,28 +472,39 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
             }
             for (int lb = l0; lb < B && ok; lb += TM) {
                 const int rows = min(TM, B - lb);
+                const int ngroups = (rows + G - 1) / G;  // groups past the cluster's last degree are skipped
 #pragma unroll
                 for (int c = 0; c < MAXC; ++c) {
                     if (c >= nchunks || !ok) break;
                     const bool col = c * KC + t < n;
 #pragma unroll 1
-                    for (int g = 0; g < NG; ++g, ++gi) {  // rolled: the chunk loop around it is unrolled
+                    for (int g = 0; g < ngroups; ++g, ++gi) {  // rolled: the chunk loop around it is unrolled
                         ok = producer_acquire(pb, gi);
                         if (!ok) break;
                         double *st = stage + (gi % kStages) * G * KC + t;
+                        const int nv = min(G, rows - g * G);  // warp-uniform
+                        const int q0 = lb + g * G - l0;
+                        if (!col) {
+                            for (int rr = 0; rr < nv; ++rr) st[rr * KC] = 0.0;
+                        } else if (nv == G) {
+                            // a whole group: straight-line code, no predicated FP64 work
 #pragma unroll
-                        for (int rr = 0; rr < G; ++rr) {
-                            const int r = g * G + rr;
-                            double v = 0.0;
-                            if (col && r < rows) {
-                                v = dc[c];
-                                const int q = lb + r - l0;
-                                const double nx = fma(fma(rA[q], xr[c], -rAc[q]), dc[c], -dp[c]);
+                            for (int rr = 0; rr < G; ++rr) {
+                                st[rr * KC] = dc[c];
+                                const double nx = fma(fma(rA[q0 + rr], xr[c], -rAc[q0 + rr]), dc[c], -dp[c]);
                                 dp[c] = dc[c];
                                 dc[c] = nx;
                             }
-                            st[rr * KC] = v;
+                        } else {
+#pragma unroll 1
+                            for (int rr = 0; rr < nv; ++rr) {
+                                st[rr * KC] = dc[c];
+                                const double nx = fma(fma(rA[q0 + rr], xr[c], -rAc[q0 + rr]), dc[c], -dp[c]);
+                                dp[c] = dc[c];
+                                dc[c] = nx;
+                            }
                         }
+                        // staged rows nv..G-1 are never read: the converters take rows < `rows` only
                         tc::mbar_arrive(&pb.full[gi % kStages]);
                     }
                 }
@@ -592,9 +603,11 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                         if (prows > 0) epilogue();
                         if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
                     }
-                    // A operand: staged row 8 g + t / 32, samples 4 (t % 32) .. + 3
+                    // A operand: staged row 8 g + t / 32, samples 4 (t % 32) .. + 3; the
+                    // groups past the cluster's last degree are neither staged nor read
                     const int rr = t >> 5, k4 = 4 * (t & 31);
-                    for (int g = 0; g < NG; ++g, ++gi) {
+                    const int ngroups = (rows + G - 1) / G;
+                    for (int g = 0; g < ngroups; ++g, ++gi) {
                         ok = converter_acquire(pb, gi);
                         if (!ok) break;
                         const int r = g * G + rr;
@@ -732,16 +745,27 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
                     ok = producer_acquire(pb, gi);
                     if (!ok) break;
                     double v[8];
+                    const int nv = active ? max(0, min(8, cnt - 8 * g)) : 0;  // degrees of this group
+                    const int q0 = lb + 8 * g - l0;
+                    if (nv == 8) {
+                        // a whole group: straight-line code, no predicated FP64 work
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int k = 8 * g + u;
-                        v[u] = 0.0;
-                        if (active && k < cnt) {
+                        for (int u = 0; u < 8; ++u) {
                             v[u] = dc;
-                            const int q = lb + k - l0;
-                            const double nx = fma(fma(rA[q], x, -rAc[q]), dc, -dp);
+                            const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
                             dp = dc;
                             dc = nx;
+                        }
+                    } else {  // the chunk's last, partial group (at most one per chunk)
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            v[u] = 0.0;
+                            if (u < nv) {
+                                v[u] = dc;
+                                const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
+                                dp = dc;
+                                dc = nx;
+                            }
                         }
                     }
                     double2 *st = reinterpret_cast<double2 *>(stage + ((gi % kStages) * TM + t) * SR);
