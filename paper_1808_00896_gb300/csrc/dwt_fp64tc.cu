@@ -222,31 +222,6 @@ __device__ __forceinline__ void issue_levels(uint32_t tmem, const unsigned char 
     tc::mma_commit(mbar);
 }
 
-// Largest magnitude (as bits) per column over the threads that share `tid & 7`:
-// every thread holds the maxima of columns 2 (tid & 7) and 2 (tid & 7) + 1.
-// Leaves F_c in colexp[16].  All NT threads call it.
-template <int NT>
-__device__ __forceinline__ void reduce_column_exponents(unsigned long long m0, unsigned long long m1,
-                                                        unsigned long long (*part)[kCols], int *colexp) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int off = 8; off < 32; off <<= 1) {
-        m0 = max(m0, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)m0, off));
-        m1 = max(m1, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)m1, off));
-    }
-    if (lane < 8) {
-        part[warp][2 * lane] = m0;
-        part[warp][2 * lane + 1] = m1;
-    }
-    __syncthreads();
-    if (tid < kCols) {
-        unsigned long long mb = 0;
-        for (int w = 0; w < NT / 32; ++w) mb = max(mb, part[w][tid]);
-        colexp[tid] = column_exponent(mb);
-    }
-    __syncthreads();
-}
-
 // ---------------------------------------------------------------------------
 // Both kernels split the CTA into two warp-specialised groups:
 //   producers  (128 threads, warps 0-3) run the FP64 recurrence -- two FMAs
@@ -275,7 +250,8 @@ __device__ __forceinline__ void reduce_column_exponents(unsigned long long m0, u
 constexpr int kProd = 128;    // producer threads (warps 0-3)
 constexpr int kConv = 256;    // converter threads (warps 4-11)
 constexpr int kIssuer = kProd + kConv;  // lane 0 of warp 12 issues the MMAs
-constexpr int kThreads = kIssuer + 32;
+constexpr int kSetup = kIssuer + 32;    // warp 13 prepares the next cluster's tables
+constexpr int kThreadsFwd = kSetup + 32;  // 448 threads (both kernels)
 constexpr int kBarConv = 1;   // named barrier of the converters
 
 constexpr int kStages = 4;    // staging ring depth (groups of 8 rows / degrees)
@@ -349,8 +325,6 @@ __device__ __forceinline__ bool converter_wait_mma(PipeBars &pb, uint32_t &mph) 
 //   dynamic smem: A planes [7] | B operand [2] | staging [kStages][8 rows][KC] |
 //                 slot [2] { rA, rAc [B doubles], alpha [B ints] }
 // ---------------------------------------------------------------------------
-constexpr int kSetup = kIssuer + 32;        // warp 13: the per-cluster tables
-constexpr int kThreadsFwd = kSetup + 32;    // 448 threads
 
 struct SlotHdr {
     ClusterSmem cs;
@@ -664,116 +638,170 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
 }
 
 // ---------------------------------------------------------------------------
-// Inverse DWT.  One CTA per cluster; tiles of 128 beta samples (the TMEM
+// Inverse DWT, persistent as the forward: one CTA per SM walks the clusters
+// inv_order[blockIdx.x + k gridDim.x]; tiles of 128 beta samples (the TMEM
 // lanes, one producer each), K chunks of 64 degrees, staged 8 degrees at a
 // time: staging [kStages][128 rows][SR] with SR = 10 doubles per row (8 used;
-// the pad spreads the rows over the shared-memory banks).  Same converter
-// schedule as the forward.
-//   dynamic smem: A planes [7] | B operand [2] | staging | rA, rAc, rG, rSig [B] | alpha [B] (int)
+// the pad spreads the rows over the shared-memory banks).  The set-up warp
+// fills slot k & 1 with cluster k's partner table, recurrence coefficients,
+// digit exponents, the factors V_l mu_t of its coefficients and the column
+// scales of those products (the largest magnitude of each of the 16 data
+// columns over the degrees).  Same converter schedule as the forward.
+//   dynamic smem: A planes [7] | B operand [2] | staging |
+//                 slot [2] { rA, rAc, rG [B doubles], alpha [B ints] }
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, const double *__restrict__ coef,
-                                                                     double2 *__restrict__ S, int flags) {
-    constexpr int NT = kThreads, TM = kProd, KC = 64, SR = 10;
+__host__ __device__ constexpr size_t inv_slot_doubles(int B) { return 3 * (size_t)B + ((size_t)B + 1) / 2; }
+
+__global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables tb, const double *__restrict__ coef,
+                                                                        double2 *__restrict__ S, int flags) {
+    constexpr int TM = kProd, KC = 64, SR = 10;
     constexpr int A_LBO = TM * 16 + 16, A_PLANE = (KC / 8) * A_LBO;
     constexpr int B_LBO = kNB * 16 + 16, B_BYTES = (KC / 8) * B_LBO;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ ClusterSmem cs;
+    __shared__ SlotHdr hdr[2];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) PipeBars pb;
-    __shared__ unsigned long long part[NT / 32][kCols];
-    __shared__ int colexp[kCols];
-    const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5;
-    const int cidx = tb.inv_order ? tb.inv_order[blockIdx.x] : (int)blockIdx.x;
-    const int2 rep = tb.clusters[cidx];
-    const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+    __shared__ __align__(8) uint64_t slot_full[2], slot_empty[2];
+    const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     unsigned char *A = smem;
     unsigned char *X = smem + kDig * A_PLANE;  // [2][B_BYTES]
     double *stage = reinterpret_cast<double *>(X + 2 * B_BYTES);  // [kStages][TM][SR]
-    double *rA = stage + kStages * TM * SR, *rAc = rA + B, *rG = rAc + B, *rSig = rG + B;
-    int *ralpha = reinterpret_cast<int *>(rSig + B);
+    double *slotd = stage + kStages * TM * SR;
+    const size_t SLOT = inv_slot_doubles(B);
+    auto slot_rA = [&](int s) { return slotd + s * SLOT; };
+    auto slot_rAc = [&](int s) { return slotd + s * SLOT + B; };
+    auto slot_rG = [&](int s) { return slotd + s * SLOT + 2 * B; };
+    auto slot_alpha = [&](int s) { return reinterpret_cast<int *>(slotd + s * SLOT + 3 * B); };
+    auto cluster_of = [&](int k, int &cidx, int &m, int &mp) {
+        const int idx = blockIdx.x + k * gridDim.x;
+        if (idx >= tb.ncl) return false;
+        cidx = tb.inv_order ? tb.inv_order[idx] : idx;
+        const int2 rep = tb.clusters[cidx];
+        m = rep.x;
+        mp = rep.y;
+        return true;
+    };
 
-    load_cluster(tb, m, mp, cs);
-    cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rG, rSig, nullptr);  // rG: scratch until here
-    const int np = cs.np;
-    // Real output (kRealSym): S(-m,-m';j) = conj S(m,m';j) for the conjugate
-    // partner pairs (2k, 2k+1): only 2k is contracted (its coefficients alone
-    // are read; the odd partners' operand rows stay zero) and 2k+1 is written
-    // as its conjugate at the same beta sample.
-    const bool real = (flags & kRealSym) && np > 1;
-    for (int t = tid; t < L; t += NT) {
-        const int a = exponent_of(rSig[t]);
-        ralpha[t] = a;
-        const double v = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
-        rG[t] = v * ldexp_bits(rSig[t], -a);  // V_l mu_t
-    }
-    __syncthreads();
-    // Column maxima of F[t][2p (+1)] = sign_p(l) V_l mu_t f(l, m_p, m'_p).
-    {
-        unsigned long long m0 = 0, m1 = 0;
-        const int p = tid & 7;
-        if (p < np && !(real && (p & 1)))
-#pragma unroll 4
-            for (int t = tid >> 3; t < L; t += NT / 8) {
-                const double2 c = *reinterpret_cast<const double2 *>(coef + 2 * (cs.off[p] + t));
-                m0 = max(m0, abs_bits(rG[t] * c.x));
-                m1 = max(m1, abs_bits(rG[t] * c.y));
-            }
-        reduce_column_exponents<NT>(m0, m1, part, colexp);
-    }
     if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
-    if (tid == 0) init_pipe(pb);
+    if (tid == 0) {
+        init_pipe(pb);
+        for (int s2 = 0; s2 < 2; ++s2) {
+            tc::mbar_init(&slot_full[s2], 32);
+            tc::mbar_init(&slot_empty[s2], kProd + kConv);
+        }
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     bool ok = true;
 
-    if (tid < kProd) {
+    if (warp == kSetup / 32) {
+        // ---- set-up: the tables of cluster k into slot k & 1 ----
+        for (int k = 0; ok; ++k) {
+            int cidx, m, mp;
+            if (!cluster_of(k, cidx, m, mp)) break;
+            const int s = k & 1;
+            if (k >= 2) {  // slot s last held cluster k - 2
+                const bool done = tc::mbar_wait(&slot_empty[s], ((k >> 1) - 1) & 1, kWaitPolls);
+                ok = __all_sync(0xffffffffu, done);
+                if (!ok) break;
+            }
+            SlotHdr &h = hdr[s];
+            if (lane == 0) fill_cluster(tb, m, mp, h.cs);
+            const int l0 = m, L = B - m;
+            const double *src = tb.rectab + (size_t)cidx * B * 3;
+            double *rA = slot_rA(s), *rAc = slot_rAc(s), *rG = slot_rG(s);
+            int *alpha = slot_alpha(s);
+            for (int t = lane; t < L; t += 32) {
+                rA[t] = src[3 * t];
+                rAc[t] = src[3 * t + 1];
+                const double sg = src[3 * t + 2];
+                const int a = exponent_of(sg);
+                alpha[t] = a;
+                const double v = (flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0;
+                rG[t] = v * ldexp_bits(sg, -a);  // V_l mu_t
+            }
+            __syncwarp();
+            // column maxima of F[t][2p (+1)] = sign_p(l) V_l mu_t f(l, m_p, m'_p): lane
+            // (p, quarter) takes partner p = lane & 7 at degrees t = quarter, quarter + 4, ...
+            {
+                const int p = lane & 7, np = h.cs.np;
+                const bool real = (flags & kRealSym) && np > 1;
+                unsigned long long m0 = 0, m1 = 0;
+                if (p < np && !(real && (p & 1)))
+                    for (int t = lane >> 3; t < L; t += 4) {
+                        const double2 c = *reinterpret_cast<const double2 *>(coef + 2 * (h.cs.off[p] + t));
+                        m0 = max(m0, abs_bits(rG[t] * c.x));
+                        m1 = max(m1, abs_bits(rG[t] * c.y));
+                    }
+#pragma unroll
+                for (int off = 8; off < 32; off <<= 1) {
+                    m0 = max(m0, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)m0, off));
+                    m1 = max(m1, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)m1, off));
+                }
+                if (lane < 8) {
+                    h.colexp[2 * lane] = column_exponent(m0);
+                    h.colexp[2 * lane + 1] = column_exponent(m1);
+                }
+            }
+            tc::mbar_arrive(&slot_full[s]);
+        }
+    } else if (tid < kProd) {
         // ---- producers: beta sample j = jb + t walks the degrees ----
         const int t = tid;
         uint32_t gi = 0;
-        for (int jb = 0; jb < n && ok; jb += TM) {
-            const int j = jb + t;
-            const bool active = j < n;
-            double x = 0.0, dc = 0.0, dp = 0.0;
-            if (active) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
-            for (int lb = l0; lb < B && ok; lb += KC) {
-                const int cnt = min(KC, B - lb);
-                const int ngroups = 2 * ((cnt + 15) / 16);  // K padded to whole MMA steps
-                for (int g = 0; g < ngroups; ++g, ++gi) {
-                    ok = producer_acquire(pb, gi);
-                    if (!ok) break;
-                    double v[8];
-                    const int nv = active ? max(0, min(8, cnt - 8 * g)) : 0;  // degrees of this group
-                    const int q0 = lb + 8 * g - l0;
-                    if (nv == 8) {
-                        // a whole group: straight-line code, no predicated FP64 work
+        for (int k = 0; ok; ++k) {
+            int cidx, m, mp;
+            if (!cluster_of(k, cidx, m, mp)) break;
+            const int s = k & 1, l0 = m;
+            ok = tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls);
+            if (!ok) break;
+            const double *rA = slot_rA(s), *rAc = slot_rAc(s);
+            for (int jb = 0; jb < n && ok; jb += TM) {
+                const int j = jb + t;
+                const bool active = j < n;
+                double x = 0.0, dc = 0.0, dp = 0.0;
+                if (active) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
+                for (int lb = l0; lb < B && ok; lb += KC) {
+                    const int cnt = min(KC, B - lb);
+                    const int ngroups = 2 * ((cnt + 15) / 16);  // K padded to whole MMA steps
+                    for (int g = 0; g < ngroups; ++g, ++gi) {
+                        ok = producer_acquire(pb, gi);
+                        if (!ok) break;
+                        double v[8];
+                        const int nv = active ? max(0, min(8, cnt - 8 * g)) : 0;  // degrees of this group
+                        const int q0 = lb + 8 * g - l0;
+                        if (nv == 8) {
+                            // a whole group: straight-line code, no predicated FP64 work
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            v[u] = dc;
-                            const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
-                            dp = dc;
-                            dc = nx;
-                        }
-                    } else {  // the chunk's last, partial group (at most one per chunk)
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            v[u] = 0.0;
-                            if (u < nv) {
+                            for (int u = 0; u < 8; ++u) {
                                 v[u] = dc;
                                 const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
                                 dp = dc;
                                 dc = nx;
                             }
-                        }
-                    }
-                    double2 *st = reinterpret_cast<double2 *>(stage + ((gi % kStages) * TM + t) * SR);
+                        } else {  // the chunk's last, partial group (at most one per chunk)
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) st[h] = make_double2(v[2 * h], v[2 * h + 1]);
-                    tc::mbar_arrive(&pb.full[gi % kStages]);
+                            for (int u = 0; u < 8; ++u) {
+                                v[u] = 0.0;
+                                if (u < nv) {
+                                    v[u] = dc;
+                                    const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
+                                    dp = dc;
+                                    dc = nx;
+                                }
+                            }
+                        }
+                        double2 *st = reinterpret_cast<double2 *>(stage + ((gi % kStages) * TM + t) * SR);
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) st[h] = make_double2(v[2 * h], v[2 * h + 1]);
+                        tc::mbar_arrive(&pb.full[gi % kStages]);
+                    }
                 }
             }
+            if (ok) tc::mbar_arrive(&slot_empty[s]);  // this producer is done with the slot's tables
         }
     } else if (tid < kIssuer) {
         // ---- converters ----
@@ -782,110 +810,140 @@ __global__ void __launch_bounds__(kThreads, 1) dwt_inverse_tc_kernel(Tables tb, 
         const int row = t & 127, half = t >> 7;  // A operand: 4 of the 8 staged degrees of one row
         uint32_t gi = 0, mph = 0, cc = 0;
         bool pending = false;
-        int pjb = -1;  // the tile whose last MMAs are pending (>= 0), for the deferred epilogue
-        auto epilogue = [&](int tjb) {
-            // Beta sample tjb + t sits in TMEM lane t (warps 4-7).
+        // the tile whose last MMAs are pending (pjb >= 0) for the deferred epilogue, its
+        // cluster's slot, and whether it is that cluster's last tile
+        int pjb = -1, pslot = 0;
+        bool plast = false;
+        auto epilogue = [&]() {
+            // Beta sample pjb + t sits in TMEM lane t (warps 4-7).
             tc::fence_after_sync();
             if (t < 128) {
-                const int jt = tjb + t;
+                const SlotHdr &h = hdr[pslot];
+                const int np = h.cs.np;
+                const bool real = (flags & kRealSym) && np > 1;
+                const int jt = pjb + t;
                 double v16[kCols];
-                epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), colexp, v16);
+                epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), h.colexp, v16);
                 if (jt < n) {
 #pragma unroll
                     for (int p = 0; p < 8; ++p) {
                         if (p >= np) break;
                         if (real && (p & 1)) continue;  // written from its pair below
-                        const int jj = cs.mir[p] ? n - 1 - jt : jt;
+                        const int jj = h.cs.mir[p] ? n - 1 - jt : jt;
                         double re = v16[2 * p], im = v16[2 * p + 1];
                         if (flags & kApplyW) {
                             const double wj = tb.w[jj];
                             re *= wj;
                             im *= wj;
                         }
-                        S[((int64_t)jj * n + mod_n(cs.pm[p], n)) * n + mod_n(cs.pmp[p], n)] = make_double2(re, im);
+                        S[((int64_t)jj * n + mod_n(h.cs.pm[p], n)) * n + mod_n(h.cs.pmp[p], n)] =
+                            make_double2(re, im);
                         if (real)  // partner p + 1 = (-m, -m'): the conjugate, at the same beta sample
-                            S[((int64_t)jj * n + mod_n(cs.pm[p + 1], n)) * n + mod_n(cs.pmp[p + 1], n)] =
+                            S[((int64_t)jj * n + mod_n(h.cs.pm[p + 1], n)) * n + mod_n(h.cs.pmp[p + 1], n)] =
                                 make_double2(re, -im);
                     }
                 }
             }
             tc::fence_before_sync();
         };
-        for (int jb = 0; jb < n && ok; jb += TM) {
-            const bool active = jb + row < n;
-            for (int lb = l0, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
-                const int cnt = min(KC, B - lb);
-                const int ksteps = (cnt + 15) / 16;
-                const int kfill = ksteps * 16;
-                unsigned char *Xc = X + (cc & 1) * B_BYTES;
-                {
-                    // B operand: column q2, degrees lb + k0 .. + 3 of F (FP64, formed here)
-                    const int q2 = t & 15, k0 = 4 * (t >> 4);
-                    if (k0 < kfill) {
-                        double v[4];
-                        int al[4];
-                        const int p = q2 >> 1;
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            v[u] = 0.0;
-                            al[u] = -colexp[q2];
-                            const int k = k0 + u;
-                            if (p < np && !(real && (p & 1)) && k < cnt) {
-                                const int q = lb + k - l0, l = lb + k;
-                                const bool neg = (cs.sign[p] < 0.0) != (cs.lpar[p] && (l & 1));
-                                const double cv = coef[2 * (cs.off[p] + q) + (q2 & 1)];
-                                v[u] = (neg ? -rG[q] : rG[q]) * cv;
-                            }
-                        }
-                        put_digits4(Xc, 16 * kCols, B_LBO, q2, k0, v, al);
-                    }
-                }
-                if (pending) {
-                    ok = converter_wait_mma(pb, mph);
-                    pending = false;
-                    if (!ok) break;
-                    if (pjb >= 0) epilogue(pjb);
-                }
-                for (int g = 0; g < 2 * ksteps; ++g, ++gi) {
-                    ok = converter_acquire(pb, gi);
-                    if (!ok) break;
-                    if (active) {
-                        const double2 *src =
-                            reinterpret_cast<const double2 *>(stage + ((gi % kStages) * TM + row) * SR + 4 * half);
-                        const double2 w0 = src[0], w1 = src[1];
-                        const double v[4] = {w0.x, w0.y, w1.x, w1.y};
-                        int al[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = 8 * g + 4 * half + u;
-                            al[u] = k < cnt ? ralpha[lb + k - l0] : 0;
-                        }
-                        put_digits4(A, A_PLANE, A_LBO, row, 8 * g + 4 * half, v, al);
-                    }
-                    tc::mbar_arrive(&pb.empty[gi % kStages]);
-                }
-                tc::fence_proxy_async();
-                ok = chunk_done(ok);
+        for (int k = 0; ok; ++k) {
+            int cidx, m, mp;
+            if (!cluster_of(k, cidx, m, mp)) break;
+            const int s = k & 1, l0 = m;
+            {
+                const bool done = tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls);
+                ok = tc::group_and(kBarConv, kConv, done);
                 if (!ok) break;
-                if (t == 0) tc::mbar_arrive(&pb.ready);
-                pending = true;
-                pjb = lb + KC >= B ? jb : -1;
+            }
+            const SlotHdr &h = hdr[s];
+            const int np = h.cs.np;
+            const bool real = (flags & kRealSym) && np > 1;
+            const double *rG = slot_rG(s);
+            const int *ralpha = slot_alpha(s);
+            for (int jb = 0; jb < n && ok; jb += TM) {
+                const bool active = jb + row < n;
+                for (int lb = l0, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
+                    const int cnt = min(KC, B - lb);
+                    const int ksteps = (cnt + 15) / 16;
+                    const int kfill = ksteps * 16;
+                    unsigned char *Xc = X + (cc & 1) * B_BYTES;
+                    {
+                        // B operand: column q2, degrees lb + k0 .. + 3 of F (FP64, formed here)
+                        const int q2 = t & 15, k0 = 4 * (t >> 4);
+                        if (k0 < kfill) {
+                            double v[4];
+                            int al[4];
+                            const int p = q2 >> 1;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                v[u] = 0.0;
+                                al[u] = -h.colexp[q2];
+                                const int kk = k0 + u;
+                                if (p < np && !(real && (p & 1)) && kk < cnt) {
+                                    const int q = lb + kk - l0, l = lb + kk;
+                                    const bool neg = (h.cs.sign[p] < 0.0) != (h.cs.lpar[p] && (l & 1));
+                                    const double cv = coef[2 * (h.cs.off[p] + q) + (q2 & 1)];
+                                    v[u] = (neg ? -rG[q] : rG[q]) * cv;
+                                }
+                            }
+                            put_digits4(Xc, 16 * kCols, B_LBO, q2, k0, v, al);
+                        }
+                    }
+                    if (pending) {
+                        ok = converter_wait_mma(pb, mph);
+                        pending = false;
+                        if (!ok) break;
+                        if (pjb >= 0) epilogue();
+                        if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
+                    }
+                    for (int g = 0; g < 2 * ksteps; ++g, ++gi) {
+                        ok = converter_acquire(pb, gi);
+                        if (!ok) break;
+                        if (active) {
+                            const double2 *src =
+                                reinterpret_cast<const double2 *>(stage + ((gi % kStages) * TM + row) * SR + 4 * half);
+                            const double2 w0 = src[0], w1 = src[1];
+                            const double v[4] = {w0.x, w0.y, w1.x, w1.y};
+                            int al[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int kk = 8 * g + 4 * half + u;
+                                al[u] = kk < cnt ? ralpha[lb + kk - l0] : 0;
+                            }
+                            put_digits4(A, A_PLANE, A_LBO, row, 8 * g + 4 * half, v, al);
+                        }
+                        tc::mbar_arrive(&pb.empty[gi % kStages]);
+                    }
+                    tc::fence_proxy_async();
+                    ok = chunk_done(ok);
+                    if (!ok) break;
+                    if (t == 0) tc::mbar_arrive(&pb.ready);
+                    pending = true;
+                    pjb = lb + KC >= B ? jb : -1;
+                    plast = lb + KC >= B && jb + TM >= n;
+                    pslot = s;
+                }
             }
         }
         if (pending) {
             const bool done = converter_wait_mma(pb, mph);
-            if (ok && done && pjb >= 0) epilogue(pjb);
+            if (ok && done && pjb >= 0) epilogue();
             ok = ok && done;
         }
     } else if (tid == kIssuer) {
         uint32_t rph = 0, cc = 0;
-        for (int jb = 0; jb < n && ok; jb += TM)
-            for (int lb = l0, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
-                ok = issuer_acquire(pb, rph);
-                if (!ok) break;
-                const int ksteps = (min(KC, B - lb) + 15) / 16;
-                issue_levels<TM>(tmem, A, A_PLANE, A_LBO, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps, &pb.mma);
-            }
+        for (int k = 0; ok; ++k) {
+            int cidx, m, mp;
+            if (!cluster_of(k, cidx, m, mp)) break;
+            for (int jb = 0; jb < n && ok; jb += TM)
+                for (int lb = m, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
+                    ok = issuer_acquire(pb, rph);
+                    if (!ok) break;
+                    const int ksteps = (min(KC, B - lb) + 15) / 16;
+                    issue_levels<TM>(tmem, A, A_PLANE, A_LBO, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps,
+                                     &pb.mma);
+                }
+        }
     }
     if (!ok && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
@@ -946,11 +1004,16 @@ cudaError_t launch_dwt_inverse_tc(const Tables &tb, const double2 *coef, double2
     constexpr int A_PLANE = (KC / 8) * (TM * 16 + 16), B_BYTES = (KC / 8) * (kNB * 16 + 16);
     const int B = tb.B;
     const size_t bytes = (size_t)kDig * A_PLANE + 2 * (size_t)B_BYTES +
-                         sizeof(double) * (kStages * (size_t)TM * SR + 4 * (size_t)B) + sizeof(int) * (size_t)B;
+                         sizeof(double) * (kStages * (size_t)TM * SR + 2 * inv_slot_doubles(B));
     cudaError_t e =
         cudaFuncSetAttribute(dwt_inverse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    dwt_inverse_tc_kernel<<<tb.ncl, kThreads, bytes, s>>>(tb, reinterpret_cast<const double *>(coef), S, flags);
+    int dev = 0, sms = 0;  // persistent: one CTA per SM
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(tb.ncl, sms));
+    dwt_inverse_tc_kernel<<<grid, kThreadsFwd, bytes, s>>>(tb, reinterpret_cast<const double *>(coef), S, flags);
     count_launch();
     return cudaGetLastError();
 }
