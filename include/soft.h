@@ -253,6 +253,56 @@ soft_status soft_dwt_inverse(soft_plan p, const double *coef, double *S, void *s
  *   - No cudaMalloc, cudaFree or allocating library call is made. */
 soft_status soft_dwt_forward_noalloc(int B, const double *S, double *coef, void *stream);
 
+/* Sharding one transform over several GPUs (the beta <-> order-pair exchange:
+ * the slice FFTs need every order pair of a few beta slices, the DWT every
+ * beta slice of a few order pairs; Sec. 2.4's two steps, and Sec. 3's
+ * partition of the DWTs by symmetry cluster).  Rank r of R owns the beta
+ * slices [floor(r 2B / R), floor((r+1) 2B / R)) and the symmetry clusters
+ * soft_cluster_shard() assigns it; one all-to-all between the two steps
+ * moves the S columns (the caller's collective, e.g. NCCL through
+ * torch.distributed).  The paper does not shard a single transform; its
+ * parallelism is over clusters on one machine.
+ *
+ *   soft_cluster_shard: host function.  The representatives (m, m'),
+ *     m >= m' >= 0, of the clusters rank `rank` of `nranks` owns, into
+ *     reps_out[2i], reps_out[2i+1] (room for B(B+1)/2 pairs), their number
+ *     into *count_out: the clusters by decreasing work ((B - m) degrees x
+ *     (8 partners first)), each to the rank with the least work so far (ties
+ *     to the lowest rank).  Every cluster goes to exactly one rank.
+ *   soft_cluster_columns: host function.  The order pairs (m, m') of the
+ *     given clusters' partners, in cluster order and each cluster's partner
+ *     order, into pairs_out[2i], pairs_out[2i+1] (room for 8 count pairs);
+ *     returns their number (the S columns those clusters read and write).
+ *   soft_dwt_forward_clusters / soft_dwt_inverse_clusters: the DWT / iDWT of
+ *     the listed clusters only (reps: host array of `count` representatives):
+ *     the forward writes those clusters' coefficient runs and nothing else of
+ *     coef; the inverse writes those clusters' S columns at every beta slice
+ *     and sets the m = -B and m' = -B entries to 0 at every slice, and writes
+ *     nothing else of S.  S in the full (2B)^3 layout.  SOFT_FP64 and
+ *     SOFT_FP64_TC plans.  Results are those of soft_dwt_forward /
+ *     soft_dwt_inverse for the same clusters, bit for bit.
+ *   soft_gather_columns: out[js][c] = S[j0 + js][m_c][m'_c] for js < nslices
+ *     and the `npairs` order pairs (host array pairs[2c], pairs[2c+1]);
+ *     out: device, nslices x npairs complex doubles.
+ *   soft_scatter_columns: the reverse, S[j0 + js][m_c][m'_c] = in[js][c].
+ *   soft_slice_fft: the 2-D FFT of slices j0 .. j0 + nslices - 1 (sign +1:
+ *     grid -> S with exp(+i...), the forward's; -1: S -> grid with exp(-i...),
+ *     the inverse's; unnormalised), `in` and `out` pointing at slice j0 of
+ *     their arrays (they may be arrays of just those slices).  SOFT_FP64 and
+ *     SOFT_FP64_TC plans with power-of-two 2B.
+ * All asynchronous on `stream`; pointer rules as soft_forward. */
+soft_status soft_cluster_shard(int B, int nranks, int rank, int *reps_out, int *count_out);
+int soft_cluster_columns(int count, const int *reps, int *pairs_out);
+soft_status soft_dwt_forward_clusters(soft_plan p, const double *S, double *coef, const int *reps, int count,
+                                      void *stream);
+soft_status soft_dwt_inverse_clusters(soft_plan p, const double *coef, double *S, const int *reps, int count,
+                                      void *stream);
+soft_status soft_gather_columns(soft_plan p, const double *S, int j0, int nslices, const int *pairs, int npairs,
+                                double *out, void *stream);
+soft_status soft_scatter_columns(soft_plan p, const double *in, int j0, int nslices, const int *pairs, int npairs,
+                                 double *S, void *stream);
+soft_status soft_slice_fft(soft_plan p, const double *in, double *out, int sign, int j0, int nslices, void *stream);
+
 /* Host-buffer forms: grid_host / coef_host are HOST pointers (pageable or
  * pinned).  The call copies the input to plan-owned device staging buffers
  * (allocated on first use), runs the transform on `stream`, copies the

@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB_NAME = "libsoft_gb300.so"
 LIB_PATH = os.path.join(PKG, LIB_NAME)
 
-SOURCES = ["soft_api.cu", "dwt_fp64.cu", "dwt_mixed.cu", "dwt_fp64tc.cu", "fft_df.cu", "fft_fp64.cu", "correlate.cu", "dwt_noalloc.cu"]
+SOURCES = ["soft_api.cu", "dwt_fp64.cu", "dwt_mixed.cu", "dwt_fp64tc.cu", "fft_df.cu", "fft_fp64.cu", "correlate.cu", "dwt_noalloc.cu", "shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -54,6 +54,13 @@ SIGNATURES = {
     "soft_dwt_forward": (_i, [_vp, _vp, _vp, _vp]),
     "soft_dwt_inverse": (_i, [_vp, _vp, _vp, _vp]),
     "soft_dwt_forward_noalloc": (_i, [_i, _vp, _vp, _vp]),
+    "soft_cluster_shard": (_i, [_i, _i, _i, _vp, _vp]),
+    "soft_cluster_columns": (_i, [_i, _vp, _vp]),
+    "soft_dwt_forward_clusters": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "soft_dwt_inverse_clusters": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "soft_gather_columns": (_i, [_vp, _vp, _i, _i, _vp, _i, _vp, _vp]),
+    "soft_scatter_columns": (_i, [_vp, _vp, _i, _i, _vp, _i, _vp, _vp]),
+    "soft_slice_fft": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "soft_forward_host": (_i, [_vp, _vp, _vp, _vp]),
     "soft_inverse_host": (_i, [_vp, _vp, _vp, _vp]),
     "soft_selftest_bounded_wait": (_i, [_vp, _i, _vp]),

@@ -77,6 +77,12 @@ struct soft_plan_s {
     bool copy_made;
     cudaEvent_t hev[kHostChunks + 1];
     double2 *corr_coef;                // correlation coefficients, allocated on first use
+    // Sharded transforms (allocated on first use): the device copies of a
+    // cluster subset (plan cluster indices) and of an order-pair column list,
+    // and the host map (m, m') -> plan cluster index.
+    int *dsub;
+    int2 *dcols;
+    std::vector<int> h_cluster_pos;
     double *amax_v;                    // arg-max partial results (argmax_parts() each)
     int64_t *amax_i;
 
@@ -293,6 +299,7 @@ void free_plan(soft_plan_s *p) {
     dev_free(p->clusters); dev_free(p->runoff); dev_free(p->S); dev_free(p->err);
     dev_free(p->stage_grid); dev_free(p->stage_coef);
     dev_free(p->corr_coef); dev_free(p->amax_v); dev_free(p->amax_i);
+    dev_free(p->dsub); dev_free(p->dcols);
     p->magic = 0;
     delete p;
 }
@@ -808,6 +815,57 @@ soft_status run_batch(int kind, int n, const soft_plan *plans, const void *const
     return SOFT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Sharded transforms: cluster subsets and S column lists.
+// ---------------------------------------------------------------------------
+int partner_count(int m, int mp) { return (m == 0 && mp == 0) ? 1 : (mp == 0 || m == mp) ? 4 : 8; }
+
+// Work of a cluster for the shard balance: the DWT's per-degree cost (16
+// columns, 8 partners first at equal degree count), as the dispatch orders.
+int64_t cluster_work(int B, int m, int mp) { return (int64_t)(B - m) * 16 + partner_count(m, mp); }
+
+// Plan cluster indices of the listed representatives, into the plan's device
+// subset list (allocated on first use), on stream s.
+soft_status upload_subset(soft_plan_s *p, const int *reps, int count, cudaStream_t s) {
+    if (count < 0 || count > p->ncl || (count > 0 && !reps)) return SOFT_ERR_INVALID_ARG;
+    if (p->h_cluster_pos.empty()) {
+        p->h_cluster_pos.assign((size_t)p->B * (p->B + 1) / 2, -1);
+        for (int c = 0; c < p->ncl; ++c) {
+            const int2 r = p->h_clusters[c];
+            p->h_cluster_pos[(size_t)r.x * (r.x + 1) / 2 + r.y] = c;
+        }
+    }
+    if (!p->dsub) {
+        const cudaError_t e = dev_alloc(p, &p->dsub, sizeof(int) * (size_t)p->ncl);
+        if (e != cudaSuccess) return fail_cuda("cluster subset list", e);
+    }
+    std::vector<int> idx((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const int m = reps[2 * i], mp = reps[2 * i + 1];
+        if (mp < 0 || mp > m || m >= p->B) return SOFT_ERR_INVALID_ARG;
+        idx[i] = p->h_cluster_pos[(size_t)m * (m + 1) / 2 + mp];
+    }
+    if (count == 0) return SOFT_OK;
+    // pageable source: the copy is staged before cudaMemcpyAsync returns, so the
+    // temporary may go; stream order keeps earlier kernels' reads of the list first
+    const cudaError_t e = cudaMemcpyAsync(p->dsub, idx.data(), sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, s);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("cluster subset copy", e);
+}
+
+soft_status upload_columns(soft_plan_s *p, const int *pairs, int npairs, cudaStream_t s) {
+    const int R = 2 * p->B - 1;
+    if (npairs < 0 || npairs > R * R || (npairs > 0 && !pairs)) return SOFT_ERR_INVALID_ARG;
+    for (int i = 0; i < npairs; ++i)
+        if (std::abs(pairs[2 * i]) >= p->B || std::abs(pairs[2 * i + 1]) >= p->B) return SOFT_ERR_INVALID_ARG;
+    if (!p->dcols) {
+        const cudaError_t e = dev_alloc(p, &p->dcols, sizeof(int2) * (size_t)R * R);
+        if (e != cudaSuccess) return fail_cuda("column list", e);
+    }
+    if (npairs == 0) return SOFT_OK;
+    const cudaError_t e = cudaMemcpyAsync(p->dcols, pairs, sizeof(int2) * (size_t)npairs, cudaMemcpyHostToDevice, s);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("column list copy", e);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1261,6 +1319,135 @@ soft_status soft_plan_read_timing(soft_plan p, double *ms_out, int64_t *counts_o
         p->counts[k] = 0;
     }
     return SOFT_OK;
+}
+
+soft_status soft_cluster_shard(int B, int nranks, int rank, int *reps_out, int *count_out) {
+    if (B < 1 || B > kMaxB || nranks < 1 || rank < 0 || rank >= nranks || !reps_out || !count_out)
+        return SOFT_ERR_INVALID_ARG;
+    std::vector<int2> cl;
+    for (int m = 0; m < B; ++m)
+        for (int mp = 0; mp <= m; ++mp) cl.push_back(make_int2(m, mp));
+    std::stable_sort(cl.begin(), cl.end(), [B](const int2 &a, const int2 &b) {
+        return cluster_work(B, a.x, a.y) > cluster_work(B, b.x, b.y);
+    });
+    std::vector<int64_t> load((size_t)nranks, 0);
+    int cnt = 0;
+    for (const int2 &c : cl) {
+        const int r = (int)(std::min_element(load.begin(), load.end()) - load.begin());  // lowest rank on ties
+        load[r] += cluster_work(B, c.x, c.y);
+        if (r == rank) {
+            reps_out[2 * cnt] = c.x;
+            reps_out[2 * cnt + 1] = c.y;
+            ++cnt;
+        }
+    }
+    *count_out = cnt;
+    return SOFT_OK;
+}
+
+int soft_cluster_columns(int count, const int *reps, int *pairs_out) {
+    if (count < 0 || (count > 0 && (!reps || !pairs_out))) return -1;
+    int q = 0;
+    for (int i = 0; i < count; ++i) {
+        const int m = reps[2 * i], mp = reps[2 * i + 1];
+        if (mp < 0 || mp > m) return -1;
+        const Partners P = make_partners(m, mp);
+        for (int k = 0; k < P.np; ++k) {
+            pairs_out[2 * q] = P.m[k];
+            pairs_out[2 * q + 1] = P.mp[k];
+            ++q;
+        }
+    }
+    return q;
+}
+
+soft_status soft_dwt_forward_clusters(soft_plan p, const double *S, double *coef, const int *reps, int count,
+                                      void *stream) {
+    soft_status st = check_plan_args(p, S, coef);
+    if (st != SOFT_OK) return st;
+    if (!fp64_layout(p->dtype)) return SOFT_ERR_UNSUPPORTED;
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = upload_subset(p, reps, count, s);
+    if (st != SOFT_OK || count == 0) return st;
+    Tables tb = p->tables();
+    tb.ncl = count;
+    tb.fwd_order = p->dsub;
+    tb.inv_order = p->dsub;
+    const cudaError_t e =
+        p->dtype == SOFT_FP64_TC
+            ? launch_dwt_forward_tc(tb, reinterpret_cast<const double2 *>(S), reinterpret_cast<double2 *>(coef), s)
+            : launch_dwt_forward_fp64(tb, reinterpret_cast<const double2 *>(S), reinterpret_cast<double2 *>(coef), s);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("cluster DWT launch", e);
+}
+
+soft_status soft_dwt_inverse_clusters(soft_plan p, const double *coef, double *S, const int *reps, int count,
+                                      void *stream) {
+    soft_status st = check_plan_args(p, coef, S);
+    if (st != SOFT_OK) return st;
+    if (!fp64_layout(p->dtype)) return SOFT_ERR_UNSUPPORTED;
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = upload_subset(p, reps, count, s);
+    if (st != SOFT_OK) return st;
+    cudaError_t e0 = launch_zero_nyquist(p->B, reinterpret_cast<double2 *>(S), s);  // the -B rows and columns
+    if (e0 != cudaSuccess || count == 0) return e0 == cudaSuccess ? SOFT_OK : fail_cuda("S clearing launch", e0);
+    Tables tb = p->tables();
+    tb.ncl = count;
+    tb.fwd_order = p->dsub;
+    tb.inv_order = p->dsub;
+    const cudaError_t e =
+        p->dtype == SOFT_FP64_TC
+            ? launch_dwt_inverse_tc(tb, reinterpret_cast<const double2 *>(coef), reinterpret_cast<double2 *>(S), s)
+            : launch_dwt_inverse_fp64(tb, reinterpret_cast<const double2 *>(coef), reinterpret_cast<double2 *>(S), s);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("cluster iDWT launch", e);
+}
+
+soft_status soft_gather_columns(soft_plan p, const double *S, int j0, int nslices, const int *pairs, int npairs,
+                                double *out, void *stream) {
+    soft_status st = check_plan_args(p, S, out);
+    if (st != SOFT_OK) return st;
+    const int n = 2 * p->B;
+    if (j0 < 0 || nslices < 0 || j0 + nslices > n) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = upload_columns(p, pairs, npairs, s);
+    if (st != SOFT_OK) return st;
+    const cudaError_t e = launch_gather_columns(reinterpret_cast<const double2 *>(S), p->B, j0, nslices, p->dcols,
+                                                npairs, reinterpret_cast<double2 *>(out), s);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("column gather launch", e);
+}
+
+soft_status soft_scatter_columns(soft_plan p, const double *in, int j0, int nslices, const int *pairs, int npairs,
+                                 double *S, void *stream) {
+    soft_status st = check_plan_args(p, in, S);
+    if (st != SOFT_OK) return st;
+    const int n = 2 * p->B;
+    if (j0 < 0 || nslices < 0 || j0 + nslices > n) return SOFT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = upload_columns(p, pairs, npairs, s);
+    if (st != SOFT_OK) return st;
+    const cudaError_t e = launch_scatter_columns(reinterpret_cast<const double2 *>(in), p->B, j0, nslices, p->dcols,
+                                                 npairs, reinterpret_cast<double2 *>(S), s);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("column scatter launch", e);
+}
+
+soft_status soft_slice_fft(soft_plan p, const double *in, double *out, int sign, int j0, int nslices, void *stream) {
+    if (!valid(p) || !aligned16(in) || !aligned16(out) || (sign != 1 && sign != -1)) return SOFT_ERR_INVALID_ARG;
+    const int n = 2 * p->B;
+    if (j0 < 0 || nslices < 1 || j0 + nslices > n) return SOFT_ERR_INVALID_ARG;
+    if (!fp64_layout(p->dtype) || !own_slice_fft(p)) return SOFT_ERR_UNSUPPORTED;
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double2 *i2 = reinterpret_cast<const double2 *>(in);
+    double2 *o2 = reinterpret_cast<double2 *>(out);
+    const size_t off = (size_t)j0 * n * n;
+    const cudaError_t e =
+        p->dftw ? launch_df_fft2(p->B, i2, o2, reinterpret_cast<float4 *>(p->S) + off, p->dftw, sign,
+                                 p->dfexp + (size_t)j0 * n, s, nslices)
+                : launch_fft64_2d(p->B, i2, o2, p->tw64, sign, s, nslices);
+    return e == cudaSuccess ? SOFT_OK : fail_cuda("slice FFT launch", e);
 }
 
 }  // extern "C"

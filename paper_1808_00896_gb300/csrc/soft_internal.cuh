@@ -261,6 +261,13 @@ cudaError_t launch_idwt_fp64_persistent(const BatchXform *xf, const int2 *items,
 cudaError_t launch_dwt_fp64_persistent(const BatchXform *xf, const int2 *items, int nitems, int *counter, int maxB,
                                        cudaStream_t s);
 
+// Launchers (shard.cu): S columns of `ncols` order pairs (device list) over
+// slices j0 .. j0 + nslices - 1, to / from a dense [nslices][ncols] buffer.
+cudaError_t launch_gather_columns(const double2 *S, int B, int j0, int nslices, const int2 *cols, int ncols,
+                                  double2 *out, cudaStream_t s);
+cudaError_t launch_scatter_columns(const double2 *in, int B, int j0, int nslices, const int2 *cols, int ncols,
+                                   double2 *S, cudaStream_t s);
+
 // Launchers (correlate.cu).
 cudaError_t launch_corr_coeffs(int B, const double2 *f, const double2 *g, const int64_t *runoff, double2 *coef,
                                cudaStream_t s);
