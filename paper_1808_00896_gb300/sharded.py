@@ -130,12 +130,16 @@ class ShardedTransform:
 
     def _gather(self, j0: int, j1: int, cols: np.ndarray, stream=None) -> torch.Tensor:
         out = torch.empty((j1 - j0, len(cols)), dtype=torch.complex128, device=self.device)
+        if out.numel() == 0:
+            return out
         c = np.ascontiguousarray(cols, dtype=np.int32)
         capi.check(self._lib().soft_gather_columns(self.plan.handle, self.S.data_ptr(), j0, j1 - j0, c.ctypes.data,
                                                    len(c), out.data_ptr(), self._s(stream)), "soft_gather_columns")
         return out
 
     def _scatter(self, buf: torch.Tensor, j0: int, j1: int, cols: np.ndarray, stream=None) -> None:
+        if buf.numel() == 0:
+            return
         c = np.ascontiguousarray(cols, dtype=np.int32)
         capi.check(self._lib().soft_scatter_columns(self.plan.handle, buf.data_ptr(), j0, j1 - j0, c.ctypes.data,
                                                     len(c), self.S.data_ptr(), self._s(stream)),
