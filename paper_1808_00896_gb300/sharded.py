@@ -154,8 +154,9 @@ class ShardedTransform:
         """Slice FFTs of this rank's slices into S, then one buffer per rank d:
         d's partner columns over this rank's slices."""
         _check_tensor(grid_local, (self.j1 - self.j0) * self.n ** 2, self.device, "grid_local")
-        capi.check(self._lib().soft_slice_fft(self.plan.handle, grid_local.data_ptr(), self._slice_ptr(self.j0), 1,
-                                              self.j0, self.j1 - self.j0, self._s(stream)), "soft_slice_fft")
+        if self.j1 > self.j0:
+            capi.check(self._lib().soft_slice_fft(self.plan.handle, grid_local.data_ptr(), self._slice_ptr(self.j0),
+                                                  1, self.j0, self.j1 - self.j0, self._s(stream)), "soft_slice_fft")
         return [self._gather(self.j0, self.j1, self.cols[d], stream) for d in range(self.world)]
 
     def forward_finish(self, recvs: list[torch.Tensor], coef: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -198,8 +199,9 @@ class ShardedTransform:
         _check_tensor(grid_local, ns * self.n ** 2, self.device, "grid_local")
         for s, buf in enumerate(recvs):
             self._scatter(buf, self.j0, self.j1, self.cols[s], stream)
-        capi.check(self._lib().soft_slice_fft(self.plan.handle, self._slice_ptr(self.j0), grid_local.data_ptr(), -1,
-                                              self.j0, ns, self._s(stream)), "soft_slice_fft")
+        if ns > 0:
+            capi.check(self._lib().soft_slice_fft(self.plan.handle, self._slice_ptr(self.j0), grid_local.data_ptr(),
+                                                  -1, self.j0, ns, self._s(stream)), "soft_slice_fft")
         return grid_local
 
     def inverse(self, coef: torch.Tensor, grid_local: torch.Tensor | None = None) -> torch.Tensor:
