@@ -195,6 +195,13 @@ struct MixedBatch {
 // so hi + lo holds the sum over the finished chunks of the FP32 chunk partials
 // to ~2^-48 of their magnitude.  drain_chunk() is called by warps 0..3 (each
 // reads its own TMEM lane quarter) after the chunk's MMA has completed.
+// Batches of NB >= 4 transforms drain once per group of kDrainGroup chunks
+// (the group accumulating in FP32, 512 beta samples or 256 degrees), since a
+// drain costs NB times a single transform's and the sums' 2 x 16 NB TMEM
+// columns would halve the CTAs per SM; a tile of one group keeps its FP32
+// accumulator and needs no sums (and no TMEM for them).
+template <int NB>
+constexpr int drain_group() { return NB >= 4 ? 4 : 1; }
 // ---------------------------------------------------------------------------
 template <int NB>
 __device__ __forceinline__ void drain_chunk(uint32_t tmem_row, bool first) {
@@ -243,13 +250,15 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
     constexpr int NT = LD ? 2 * KC : KC;
     constexpr int TM = kFwdTile, NC = 16 * NB;
     using O = Operands<MODE, TM, KC, NC>;
-    constexpr uint32_t TCOLS = tmem_cols<3 * NC>();
+    constexpr int G = drain_group<NB>();
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mbar;
     const Tables &tb = mb.tb;
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool comp = (n + KC - 1) / KC > G;  // more than one drain group per tile: compensated sums in TMEM
+    const uint32_t tcols = comp ? tmem_cols<3 * NC>() : tmem_cols<NC>();
     const int cidx = tb.fwd_order ? tb.fwd_order[blockIdx.x] : (int)blockIdx.x;
     const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
@@ -276,7 +285,7 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
             dprev[j] = 0.0;
         }
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, TCOLS);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, tcols);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc::fence_before_sync();
     __syncthreads();
@@ -310,10 +319,11 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
             tc::fence_after_sync();
             const int pt = (it - 1) / nchunks, pc = (it - 1) % nchunks;
             if (warp < 4) {
-                drain_chunk<NB>(trow, pc == 0);
+                if (comp && (pc % G == G - 1 || pc == nchunks - 1)) drain_chunk<NB>(trow, pc < G);
                 if (pc == nchunks - 1) {
                     // Epilogue of tile pt: degree l = plb + 16 w + i sits in TMEM lane 32 w + i
-                    // (i < 16); (hi + lo) V_l sig_l and the partner sign in FP64.
+                    // (i < 16); (hi + lo) V_l sig_l and the partner sign in FP64 (lo = 0 and hi
+                    // the accumulator itself when the tile is one drain group).
                     const int plb = l0 + pt * TM, prow = min(TM, B - plb);
                     const int r = 16 * warp + lane;
                     const int l = plb + r, q = l - l0;
@@ -321,8 +331,14 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
 #pragma unroll 1
                     for (int b = 0; b < NB; ++b) {
                         uint32_t hi[16], lo[16];
-                        tc::tmem_ld16(trow + NC + 16 * b, hi);
-                        tc::tmem_ld16(trow + 2 * NC + 16 * b, lo);
+                        if (comp) {
+                            tc::tmem_ld16(trow + NC + 16 * b, hi);
+                            tc::tmem_ld16(trow + 2 * NC + 16 * b, lo);
+                        } else {
+                            tc::tmem_ld16(trow + 16 * b, hi);
+#pragma unroll
+                            for (int c2 = 0; c2 < 16; ++c2) lo[c2] = 0u;
+                        }
                         if (live) {
                             const double v = rV[q];
 #pragma unroll
@@ -426,13 +442,13 @@ __global__ void __launch_bounds__(LD ? 2 * KC : KC, 1) dwt_forward_mixed_kernel(
         __syncthreads();  // operands of chunk it complete; the accumulator is free for it
         if (issue && tid == 0) {
             tc::fence_after_sync();
-            issue_chunk<MODE, TM, KC, NC>(tmem, A, X, true, ksteps, &mbar);
+            issue_chunk<MODE, TM, KC, NC>(tmem, A, X, c % G == 0, ksteps, &mbar);  // a group starts fresh
         }
     }
     if (!ok && tid == 0 && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+    if (warp == 0) tc::tmem_dealloc(tmem, tcols);
 }
 
 // ---------------------------------------------------------------------------
@@ -450,7 +466,7 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     constexpr int NT = LD ? 2 * kNT : kNT;
     constexpr int NC = 16 * NB;
     using O = Operands<MODE, kTile, kChunk, NC>;
-    constexpr uint32_t TCOLS = tmem_cols<3 * NC>();
+    constexpr int G = drain_group<NB>();
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ClusterSmem cs;
     __shared__ uint32_t tmem_slot;
@@ -460,6 +476,8 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     const int cidx = tb.inv_order ? tb.inv_order[blockIdx.x] : (int)blockIdx.x;
     const int2 rep = tb.clusters[cidx];
     const int m = rep.x, mp = rep.y, l0 = m, L = B - l0;
+    const bool comp = (L + kChunk - 1) / kChunk > G;  // more than one drain group: compensated sums in TMEM
+    const uint32_t tcols = comp ? tmem_cols<3 * NC>() : tmem_cols<NC>();
 
     unsigned char *A = smem;
     unsigned char *F = smem + O::PLANES * O::A_BYTES;
@@ -470,7 +488,7 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     cluster_recurrence<NT>(tb, cidx, l0, L, m, mp, rA, rAc, rBc, rSig, nullptr);
     for (int t = tid; t < L; t += NT)
         fsc[t] = tc::f64_to_f32_rn(rSig[t] * ((flags & kApplyV) ? (2.0 * (l0 + t) + 1.0) / (8.0 * M_PI * B) : 1.0));
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, TCOLS);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, tcols);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc::fence_before_sync();
     __syncthreads();
@@ -543,13 +561,13 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
             }
             tc::fence_proxy_async();
             __syncthreads();
-            if (tid == 0) issue_chunk<MODE, kTile, kChunk, NC>(tmem, A, F, true, ksteps, &mbar);
+            if (tid == 0) issue_chunk<MODE, kTile, kChunk, NC>(tmem, A, F, c % G == 0, ksteps, &mbar);
             const bool done = tc::mbar_wait(&mbar, phase, kWaitPolls);
             phase ^= 1u;
             ok = __syncthreads_and(done);  // CTA-wide verdict keeps every barrier uniform
             if (!ok) break;
             tc::fence_after_sync();
-            if (warp < 4) drain_chunk<NB>(trow, c == 0);
+            if (warp < 4 && comp && (c % G == G - 1 || lb + kChunk >= B)) drain_chunk<NB>(trow, c < G);
             tc::fence_before_sync();  // the next chunk's barrier orders the drain before its MMA
         }
         if (!ok) break;
@@ -557,8 +575,14 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
 #pragma unroll 1
         for (int b = 0; b < NB && warp < 4; ++b) {
             uint32_t hi[16], lo[16];
-            tc::tmem_ld16(trow + NC + 16 * b, hi);
-            tc::tmem_ld16(trow + 2 * NC + 16 * b, lo);
+            if (comp) {
+                tc::tmem_ld16(trow + NC + 16 * b, hi);
+                tc::tmem_ld16(trow + 2 * NC + 16 * b, lo);
+            } else {  // one drain group: the FP32 accumulator itself
+                tc::tmem_ld16(trow + 16 * b, hi);
+#pragma unroll
+                for (int c2 = 0; c2 < 16; ++c2) lo[c2] = 0u;
+            }
             if (active) {
                 float2 *Sb = const_cast<float2 *>(mb.S[b]);
 #pragma unroll
@@ -582,7 +606,7 @@ __global__ void __launch_bounds__(LD ? 2 * kNT : kNT, 1) dwt_inverse_mixed_kerne
     if (!ok && tid == 0 && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+    if (warp == 0) tc::tmem_dealloc(tmem, tcols);
 }
 
 // Self-test of the bounded wait used by the mixed kernels: one CTA polls an
@@ -674,7 +698,9 @@ size_t tmem_limited_smem(size_t bytes, uint32_t tcols) {
 
 template <int MODE, int KC, int NB, bool LD>
 cudaError_t run_forward_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
-    const size_t bytes = tmem_limited_smem(mixed_forward_smem<MODE, KC, NB>(mb.tb.B), tmem_cols<3 * 16 * NB>());
+    const bool comp = (2 * mb.tb.B + KC - 1) / KC > drain_group<NB>();
+    const size_t bytes = tmem_limited_smem(mixed_forward_smem<MODE, KC, NB>(mb.tb.B),
+                                           comp ? tmem_cols<3 * 16 * NB>() : tmem_cols<16 * NB>());
     cudaError_t e = cudaFuncSetAttribute(dwt_forward_mixed_kernel<MODE, KC, NB, LD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -685,7 +711,9 @@ cudaError_t run_forward_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
 
 template <int MODE, int NB, bool LD>
 cudaError_t run_inverse_mixed(const MixedBatch &mb, cudaStream_t s, int flags) {
-    const size_t bytes = tmem_limited_smem(mixed_inverse_smem<MODE, NB>(mb.tb.B), tmem_cols<3 * 16 * NB>());
+    const bool comp = (mb.tb.B + kChunk - 1) / kChunk > drain_group<NB>();  // the longest cluster's
+    const size_t bytes = tmem_limited_smem(mixed_inverse_smem<MODE, NB>(mb.tb.B),
+                                           comp ? tmem_cols<3 * 16 * NB>() : tmem_cols<16 * NB>());
     cudaError_t e = cudaFuncSetAttribute(dwt_inverse_mixed_kernel<MODE, NB, LD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

@@ -203,43 +203,47 @@ def test_forward_lane_mapping(NT, TPI, n, npc):
 
 # ---------------------------------------------------------------------------
 # Mixed-precision forward DWT pipeline (dwt_mixed.cu, dwt_forward_mixed_kernel):
-# step `it` waits for chunk it-1's MMA, folds its partial into the compensated
-# sums (the first chunk of a tile starts them), finishes the tile after its
-# last chunk, then refills the one operand stage with chunk it and issues its
-# MMA.  A host model of that schedule: the stage is never refilled while an
-# MMA that reads it may still run, every chunk is drained exactly once and in
-# order, and every degree tile gets one epilogue after its last chunk.
+# step `it` waits for chunk it-1's MMA, folds the accumulator into the
+# compensated sums at the end of each drain group of G chunks (the tile's
+# first group starts them; a tile of one group keeps its accumulator), finishes
+# the tile after its last chunk, then refills the one operand stage with chunk
+# it and issues its MMA (accumulating unless it starts a group).  A host model
+# of that schedule with the accumulator's contents tracked: the stage is never
+# refilled while an MMA that reads it may still run, every chunk's product
+# reaches the tile's result exactly once, and every tile gets one epilogue.
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("L,n", [(1, 2), (5, 16), (64, 128), (65, 128), (130, 256), (512, 1024), (200, 1024)])
 @pytest.mark.parametrize("KC", [128, 256])
-def test_mixed_forward_pipeline_schedule(L, n, KC):
+@pytest.mark.parametrize("G", [1, 4])
+def test_mixed_forward_pipeline_schedule(L, n, KC, G):
     TM = 64
     nch = -(-n // KC)
     ntiles = -(-L // TM)
     total = ntiles * nch
-    pending = None  # chunk whose MMA reads the stage and has not been waited for
-    issued = []
-    drained = []
-    epilogues = []
-    starts = []
+    comp = nch > G
+    pending = None   # chunk whose MMA reads the stage and has not been waited for
+    acc = []         # chunks summed in the TMEM accumulator
+    sums = None      # chunks in the compensated (hi, lo) sums
+    results = {}
     for it in range(total + 1):
         if it > 0:
             prev = it - 1
             assert pending == prev  # wait for chunk it-1's MMA
             pending = None
             pc = prev % nch
-            if pc == 0:
-                starts.append(prev // nch)
-            drained.append(prev)
+            if comp and (pc % G == G - 1 or pc == nch - 1):
+                sums = list(acc) if pc < G else sums + acc   # first drain of the tile starts the sums
             if pc == nch - 1:
-                epilogues.append(prev // nch)
+                results[prev // nch] = sums if comp else list(acc)
         if it < total:
             assert pending is None  # the stage's last reader has completed
+            c = it % nch
+            acc = [it] if c % G == 0 else acc + [it]   # a group starts a fresh accumulator
             pending = it
-            issued.append(it)
     assert pending is None
-    assert issued == drained == list(range(total))
-    assert epilogues == starts == list(range(ntiles))
+    assert sorted(results) == list(range(ntiles))
+    for t, chunks in results.items():
+        assert sorted(chunks) == list(range(t * nch, (t + 1) * nch)), (t, chunks)
 
 
 # ---------------------------------------------------------------------------
