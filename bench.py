@@ -112,7 +112,7 @@ SM_MAX_MHZ = 2070.0
 TRAFFIC = {
     ("dwt_forward_fp64_kernel", 64): (36_887_552 + 12_032, "dwt_fp64.cu", "0589e4d08494f908"),
     ("dwt_forward_fp64_kernel", 256): (3_089_268_992 + 362_294_016, "dwt_fp64.cu", "1fc2456028276ded"),
-    ("dwt_forward_tc_kernel", 128): (295_284_736 + 46_113_024, "dwt_fp64tc.cu", "c436b9618490a61c"),
+    ("dwt_forward_tc_kernel", 128): (294_754_304 + 45_530_880, "dwt_fp64tc.cu", "6a14f327ef286fb1"),
 }
 
 
