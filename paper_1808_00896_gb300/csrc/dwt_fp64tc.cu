@@ -43,6 +43,9 @@
 #include "soft_internal.cuh"
 #include "tcgen05.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 namespace softgb {
@@ -56,44 +59,45 @@ constexpr uint32_t kWaitPolls = 1u << 22;
 
 __device__ __forceinline__ int mod_n(int a, int n) { return a < 0 ? a + n : a; }
 
-// FP32 bit pattern of a small integer (|q| < 2^22), exactly; its upper half is
-// the BF16 of q when |q| <= 256.  One integer add and one FP32 add.
-__device__ __forceinline__ uint32_t small_int_bits(int q) {
-    return __float_as_uint(__int_as_float(0x4B400000 + q) - 12582912.0f);
+// FP32 bit pattern of f - 64 for a 7-bit field f <= 255 (BF16 in the upper
+// half): 0x4B400000 | f is the float 1.5 2^23 + f, so one bitwise OR (which
+// merges with the field's mask) and one FP32 add.
+__device__ __forceinline__ uint32_t field_digit_bits(uint32_t f) {
+    return __float_as_uint(__uint_as_float(0x4B400000u | f) - 12582976.0f);
 }
 
-// Balanced base-128 digits of N = round(v 2^(alpha + 48)) for |v 2^alpha| <= 1:
-// N = sum_i q_i 128^(6 - i), so v 2^alpha ~= sum_i q_i 2^(-6-7i), |q_i| <= 64.
-// Returned as FP32 bit patterns (BF16 in the upper halves).  Integer operations
-// only; magnitudes below 2^-49 of the scale give 0.
+// Balanced base-128 digits of N = floor(v 2^(alpha + 48) + 1/2) for
+// |v 2^alpha| <= 1: N = sum_i q_i 128^(6 - i), so v 2^alpha ~= sum_i q_i
+// 2^(-6-7i) to within 2^-49, |q_i| <= 64.  Returned as FP32 bit patterns
+// (BF16 in the upper halves).  Integer operations only; magnitudes below 2^-49
+// of the scale give 0.
+//
+// With K7 = sum_i 64 128^i, P = N + K7 >= 0 has the ordinary base-128 digits
+// q_i + 64 (the leading one up to 128, the others in [0, 127]): the balanced
+// digits with the lower six in [-64, 63] are unique, so the seven digits are
+// independent bit fields of P instead of a carry chain.  P comes from
+// T = floor(v 2^(alpha + 49)) (an arithmetic shift of the signed significand)
+// as P = (T + 1 + 2 K7) >> 1, so the digit fields are read from
+// Q = T + 1 + 2 K7 one bit higher up.
+constexpr long long kDigitOffset = 64ll * ((1ll << 49) - 1) / 127;  // K7
+
 __device__ __forceinline__ void digits7(double v, int alpha, uint32_t (&q)[kDig]) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const uint32_t bh = (uint32_t)(b >> 32);
-    const int e = (int)((bh >> 20) & 0x7FF);
-    // floor(|v| 2^(alpha + 49)) = significand >> s, s >= 3 within the bound; zero
-    // (and subnormal) inputs shift everything out.
-    const int s = e == 0 ? 63 : min(max(1026 - alpha - e, 0), 63);
-    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    long long N = (long long)(((M >> s) + 1) >> 1);  // round half away from zero
-    if (bh >> 31) N = -N;
-    // N = hi 2^21 + lo, lo in [0, 2^21): three digits from lo, the carry into hi,
-    // then three more digits and the leading one from hi, all in 32-bit arithmetic.
-    int lo = (int)(N & 0x1FFFFF);
-    int hi = (int)(N >> 21);
-#pragma unroll
-    for (int i = kDig - 1; i >= 4; --i) {
-        const int t = lo + 64;
-        q[i] = small_int_bits((t & 127) - 64);
-        lo = t >> 7;
-    }
-    hi += lo;
-#pragma unroll
-    for (int i = 3; i >= 1; --i) {
-        const int t = hi + 64;
-        q[i] = small_int_bits((t & 127) - 64);
-        hi = t >> 7;
-    }
-    q[0] = small_int_bits(hi);
+    const long long b = __double_as_longlong(v);
+    const int e = (int)(((unsigned long long)b >> 52) & 0x7FF);
+    // |v| 2^(alpha + 49) = significand >> s, s >= 3 within the bound; zero (and
+    // subnormal) inputs shift everything out
+    const int s = min(1026 - alpha - e, 63);
+    const long long M = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    const long long T = (b < 0 ? -M : M) >> s;
+    const unsigned long long Q = (unsigned long long)(T + (2 * kDigitOffset + 1));  // < 2^51
+    const uint32_t lo = (uint32_t)Q, hi = (uint32_t)(Q >> 22);  // digit i at bit 1 + 7 (6 - i) of Q
+    q[6] = field_digit_bits((lo >> 1) & 127);
+    q[5] = field_digit_bits((lo >> 8) & 127);
+    q[4] = field_digit_bits((lo >> 15) & 127);
+    q[3] = field_digit_bits(hi & 127);
+    q[2] = field_digit_bits((hi >> 7) & 127);
+    q[1] = field_digit_bits((hi >> 14) & 127);
+    q[0] = field_digit_bits(hi >> 21);
 }
 
 // Unbiased exponent of a positive normal double.
@@ -209,13 +213,18 @@ __device__ __forceinline__ void issue_levels(uint32_t tmem, const unsigned char 
                                              const unsigned char *Bop, uint32_t b_lbo, bool first, int ksteps,
                                              uint64_t *mbar) {
     tc::fence_after_sync();
-    const uint32_t abase = tc::smem_u32(A), bbase = tc::smem_u32(Bop);
+    // Descriptors advance by adding (byte offset >> 4) to their 14-bit start
+    // address field: every offset is a multiple of 16 bytes, and shared-memory
+    // addresses stay below 2^18 bytes, so the field never carries.
+    const uint64_t ad0 = tc::smem_desc(tc::smem_u32(A), a_lbo, 128), bd0 = tc::smem_desc(tc::smem_u32(Bop), b_lbo, 128);
     for (int s = 0; s < ksteps; ++s) {
-        const uint64_t bd = tc::smem_desc(bbase + s * 2 * b_lbo, b_lbo, 128);
+        const uint64_t bd = bd0 + (uint64_t)((s * 2 * b_lbo) >> 4);
+        const uint64_t as = ad0 + (uint64_t)((s * 2 * (int)a_lbo) >> 4);
 #pragma unroll
         for (int i = 0; i < kDig; ++i) {
-            const uint32_t idesc = tc::instr_desc(1, M, kCols * (kDig - i));
-            const uint64_t ad = tc::smem_desc(abase + i * a_plane + s * 2 * a_lbo, a_lbo, 128);
+            constexpr uint32_t kIdesc0 = tc::instr_desc(1, M, kCols * kDig);
+            const uint32_t idesc = kIdesc0 - ((uint32_t)(kCols * i) >> 3 << 17);  // N = 16 (7 - i)
+            const uint64_t ad = as + (uint64_t)((i * a_plane) >> 4);
             tc::mma_bf16(tmem + kCols * i, ad, bd, idesc, (first && s == 0 && i == 0) ? 0u : 1u);
         }
     }
@@ -226,8 +235,8 @@ __device__ __forceinline__ void issue_levels(uint32_t tmem, const unsigned char 
 // Both kernels split the CTA into two warp-specialised groups:
 //   producers  (128 threads, warps 0-3) run the FP64 recurrence -- two FMAs
 //              per Wigner-d entry and nothing else -- and write the raw FP64
-//              values into a staging ring of kStages groups, 8 rows (forward)
-//              or 8 degrees (inverse) per group;
+//              values into a staging ring of kStages groups, kGroup rows
+//              (forward) or degrees (inverse) per group;
 //   converters (256 threads, warps 4-11) cut staged values and the data
 //              operand into digits (4 values per thread and task) and run the
 //              epilogue (warps 4-7, one per TMEM lane quarter).  Two converter
@@ -239,9 +248,13 @@ __device__ __forceinline__ void issue_levels(uint32_t tmem, const unsigned char 
 //              warp the issue overlaps the converters' next B operand.
 // So the FP64 pipe (producers) and the integer pipes (converters) work in
 // parallel instead of in one warp's instruction stream.  Hand-off through
-// mbarriers (full: 128 producer arrivals, empty: 256 converter arrivals,
-// ready: one converter arrival per chunk, mma: the tcgen05 commit);
-// every wait is bounded.  Converters, which synchronise among themselves once
+// mbarriers (full: one arrival per producer warp, empty: one per converter
+// warp, each after a __syncwarp that orders the warp's staging accesses
+// before its lane 0's release; ready: one converter arrival per chunk, mma:
+// the tcgen05 commit); every wait is bounded and its verdict warp-uniform.
+// A ring of two 16-row groups hands off half as often as four 8-row ones
+// for the same staging bytes: each hand-off costs the single producer warp
+// of a scheduler FP64-pipe time that no other warp fills.  Converters, which synchronise among themselves once
 // per chunk to agree that the operands are complete, take that barrier as an
 // AND reduction of their wait verdicts so that a timeout makes the whole group
 // leave together; producers and the issuer synchronise with nobody but the
@@ -254,20 +267,24 @@ constexpr int kSetup = kIssuer + 32;    // warp 13 prepares the next cluster's t
 constexpr int kThreadsFwd = kSetup + 32;  // 448 threads (both kernels)
 constexpr int kBarConv = 1;   // named barrier of the converters
 
-constexpr int kStages = 4;    // staging ring depth (groups of 8 rows / degrees)
+constexpr int kStages = 2;    // staging ring depth (groups)
+constexpr int kGroup = 16;    // rows (forward) or degrees (inverse) per staged group
 
 struct PipeBars {
     uint64_t full[kStages], empty[kStages], ready, mma;
+    uint64_t data[2];  // TMA copies of the data operand into B buffer 0 / 1 (forward)
 };
 
 __device__ __forceinline__ void init_pipe(PipeBars &pb) {
 #pragma unroll
     for (int b = 0; b < kStages; ++b) {
-        tc::mbar_init(&pb.full[b], kProd);
-        tc::mbar_init(&pb.empty[b], kConv);
+        tc::mbar_init(&pb.full[b], kProd / 32);
+        tc::mbar_init(&pb.empty[b], kConv / 32);
     }
     tc::mbar_init(&pb.ready, 1);
     tc::mbar_init(&pb.mma, 1);
+    tc::mbar_init(&pb.data[0], 1);
+    tc::mbar_init(&pb.data[1], 1);
 }
 
 // Issuer: wait until the converters have written the operands of the next chunk.
@@ -278,18 +295,29 @@ __device__ __forceinline__ bool issuer_acquire(PipeBars &pb, uint32_t &rph) {
 }
 
 // Producer: wait until staging buffer gi % kStages is free (its previous group
-// consumed).  Producers take no named barrier anywhere, so each decides alone:
-// one that gives up stops arriving, and the converters' own bounded waits end.
+// consumed).  Producers take no named barrier anywhere, so each warp decides
+// alone: one that gives up stops arriving, and the converters' own bounded
+// waits end.  Warp-collective; the verdict is the same on every lane.
 __device__ __forceinline__ bool producer_acquire(PipeBars &pb, uint32_t gi) {
-    return tc::mbar_wait(&pb.empty[gi % kStages], ((gi / kStages) & 1) ^ 1u, kWaitPolls);
+    return __all_sync(0xffffffffu, tc::mbar_wait(&pb.empty[gi % kStages], ((gi / kStages) & 1) ^ 1u, kWaitPolls));
 }
 
 // Converter: wait until staging buffer gi % kStages holds group gi.  Each
-// converter decides alone here (no barrier per group): a converter that gives
+// converter warp decides alone here (no barrier per group): a warp that gives
 // up skips the rest of its chunk, and the AND-reducing barrier that closes
-// every chunk (chunk_done) gives the whole group that verdict.
+// every chunk (chunk_done) gives the whole group that verdict.  Warp-collective.
 __device__ __forceinline__ bool converter_acquire(PipeBars &pb, uint32_t gi) {
-    return tc::mbar_wait(&pb.full[gi % kStages], (gi / kStages) & 1, kWaitPolls);
+    return __all_sync(0xffffffffu, tc::mbar_wait(&pb.full[gi % kStages], (gi / kStages) & 1, kWaitPolls));
+}
+
+// Producer / converter warp: its staging writes / reads of group gi are done.
+__device__ __forceinline__ void release_full(PipeBars &pb, uint32_t gi) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) tc::mbar_arrive(&pb.full[gi % kStages]);
+}
+__device__ __forceinline__ void release_empty(PipeBars &pb, uint32_t gi) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) tc::mbar_arrive(&pb.empty[gi % kStages]);
 }
 
 // Converter: all converters have written the chunk's operands (or one gave up).
@@ -322,7 +350,7 @@ __device__ __forceinline__ bool converter_wait_mma(PipeBars &pb, uint32_t &mph) 
 // MMAs of c - 1 run), wait for those MMAs (then the epilogue when c - 1 closed
 // a tile, possibly of the previous cluster), A digits of the staged groups,
 // MMAs of c.
-//   dynamic smem: A planes [7] | B operand [2] | staging [kStages][8 rows][KC] |
+//   dynamic smem: A planes [7] | B operand [2] | staging [kStages][kGroup rows][KC] |
 //                 slot [2] { rA, rAc [B doubles], alpha [B ints] }
 // ---------------------------------------------------------------------------
 
@@ -334,9 +362,9 @@ struct SlotHdr {
 // Doubles per table slot of the persistent forward: rA, rAc, then B ints.
 __host__ __device__ constexpr size_t fwd_slot_doubles(int B) { return 2 * (size_t)B + ((size_t)B + 1) / 2; }
 
-__global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables tb, const double2 *__restrict__ S,
+__global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables tb, const __grid_constant__ CUtensorMap tmS,
                                                                         double *__restrict__ coef, int flags) {
-    constexpr int KC = kProd, TM = 64, G = 8, MAXC = 2 * kMaxB / KC;
+    constexpr int KC = kProd, TM = 64, G = kGroup, MAXC = 2 * kMaxB / KC;
     constexpr int A_LBO = TM * 16 + 16, A_PLANE = (KC / 8) * A_LBO;
     constexpr int B_LBO = kNB * 16 + 16, B_BYTES = (KC / 8) * B_LBO;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -461,13 +489,31 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                         if (!col) {
                             for (int rr = 0; rr < nv; ++rr) st[rr * KC] = 0.0;
                         } else if (nv == G) {
-                            // a whole group: straight-line code, no predicated FP64 work
+                            // a whole group: straight-line code, no predicated FP64 work, in
+                            // halves of 8 rows.  A half's coefficients are loaded before its
+                            // first staging store (a store could alias them, so later loads
+                            // would wait for it), and the first FMA of a row, which does not
+                            // depend on the recurrence, runs two rows ahead of the second, so
+                            // that the dependent chain finds the FP64 pipe busy rather than
+                            // idle while it waits.
 #pragma unroll
-                            for (int rr = 0; rr < G; ++rr) {
-                                st[rr * KC] = dc[c];
-                                const double nx = fma(fma(rA[q0 + rr], xr[c], -rAc[q0 + rr]), dc[c], -dp[c]);
-                                dp[c] = dc[c];
-                                dc[c] = nx;
+                            for (int hh = 0; hh < G; hh += 8) {
+                                double ca[8], cb[8];
+#pragma unroll
+                                for (int rr = 0; rr < 8; ++rr) {
+                                    ca[rr] = rA[q0 + hh + rr];
+                                    cb[rr] = rAc[q0 + hh + rr];
+                                }
+                                double u0 = fma(ca[0], xr[c], -cb[0]), u1 = fma(ca[1], xr[c], -cb[1]);
+#pragma unroll
+                                for (int rr = 0; rr < 8; ++rr) {
+                                    st[(hh + rr) * KC] = dc[c];
+                                    const double nx = fma(u0, dc[c], -dp[c]);
+                                    u0 = u1;
+                                    if (rr + 2 < 8) u1 = fma(ca[rr + 2], xr[c], -cb[rr + 2]);
+                                    dp[c] = dc[c];
+                                    dc[c] = nx;
+                                }
                             }
                         } else {
 #pragma unroll 1
@@ -479,7 +525,7 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                             }
                         }
                         // staged rows nv..G-1 are never read: the converters take rows < `rows` only
-                        tc::mbar_arrive(&pb.full[gi % kStages]);
+                        release_full(pb, gi);
                     }
                 }
             }
@@ -526,6 +572,47 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
             }
             tc::fence_before_sync();
         };
+        // B operand task of this thread: partner bp (re and im), beta samples
+        // bk0..bk0+3 of a chunk.  The partners' S columns reach the chunk's B buffer
+        // by TMA one (tile, chunk) step ahead, as boxes of BJ samples x (re, im) (box
+        // row r of partner p at byte p PS + 16 r, PS = 16 BJ rounded up to the 128-byte
+        // alignment of a TMA destination; a mirrored partner's box is the reversed
+        // sample range), and are cut into digits in place.  The partner boxes share
+        // their bank alignment, so a thread reads its four rows starting at row
+        // bp mod 4: the 8 lanes of a sample quad then spread over 4 row residues.
+        const int bp = lane & 7, bk0 = 4 * (4 * (warp - 4) + (lane >> 3)), brot = bp & 3;
+        const int BJ = min(KC, n), PS = (16 * BJ + 127) & ~127;
+        auto b_used = [&](const SlotHdr &h, int p) {
+            return p < h.cs.np && !((flags & kRealSym) && h.cs.np > 1 && (p & 1));
+        };
+        // thread 0: the copies of chunk c of the cluster in h into B buffer `buf`
+        auto issue_b = [&](const SlotHdr &h, int c, int buf) {
+            uint32_t bytes = 0;
+#pragma unroll 1
+            for (int p = 0; p < 8; ++p)
+                if (b_used(h, p)) bytes += 16u * BJ;
+            tc::mbar_arrive_expect_tx(&pb.data[buf], bytes);
+#pragma unroll 1
+            for (int p = 0; p < 8; ++p)
+                if (b_used(h, p))
+                    tc::tma_load_4d(X + buf * B_BYTES + p * PS, &tmS, 0, mod_n(h.cs.pmp[p], n),
+                                    mod_n(h.cs.pm[p], n), h.cs.mir[p] ? n - c * KC - BJ : c * KC, &pb.data[buf]);
+        };
+        // this thread's raw values of chunk c from B buffer Xb: w[u] = sample bk0 + ((u + brot) & 3)
+        auto read_raw = [&](const SlotHdr &h, int c, const unsigned char *Xb, double2 (&w)[4]) {
+            const int kvalid = min(KC, n - c * KC);
+            const bool mir = h.cs.mir[bp], used = b_used(h, bp);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = bk0 + ((u + brot) & 3);
+                const int r = mir ? BJ - 1 - k : k;
+                w[u] = used && k < kvalid ? *reinterpret_cast<const double2 *>(Xb + bp * PS + 16 * r)
+                                          : make_double2(0.0, 0.0);
+            }
+        };
+        uint32_t dph = 0;     // bit b: parity of pb.data[b]'s next completion
+        int inflight = -1;    // B buffer whose copies are issued and not yet seen complete
+        double2 wn[4];        // raw values of this step
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
             if (!cluster_of(k, cidx, m, mp)) break;
@@ -536,8 +623,6 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                 if (!ok) break;
             }
             const SlotHdr &h = hdr[s];
-            const int np = h.cs.np;
-            const bool real = (flags & kRealSym) && np > 1;
             const int *alpha = slot_alpha(s);
             for (int lb = l0; lb < B && ok; lb += TM) {
                 const int rows = min(TM, B - lb);
@@ -545,30 +630,35 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                     const int kvalid = min(KC, n - c * KC);
                     const int ksteps = (kvalid + 15) / 16;
                     const int kfill = ksteps * 16;
-                    unsigned char *Xc = X + (cc & 1) * B_BYTES;
+                    const int buf = cc & 1;
+                    unsigned char *Xc = X + buf * B_BYTES;
+                    if (inflight != buf) {  // the cluster's first step: copy now (the buffer's MMAs are done)
+                        if (t == 0) issue_b(h, c, buf);
+                        inflight = buf;
+                    }
                     {
-                        // B operand: partner p, re (h2 = 0) or im (h2 = 1), beta samples k0..k0+7
-                        const int p = t & 7, h2 = (t >> 3) & 1, k0 = 8 * (t >> 4);
-                        if (k0 < kfill) {
-                            double v[8];
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) v[u] = 0.0;
-                            if (p < np && !(real && (p & 1))) {
-                                const int64_t colp = (int64_t)mod_n(h.cs.pm[p], n) * n + mod_n(h.cs.pmp[p], n);
-                                const double *Sd = reinterpret_cast<const double *>(S) + h2;
-#pragma unroll
-                                for (int u = 0; u < 8; ++u)
-                                    if (k0 + u < kvalid) {
-                                        const int jj = c * KC + k0 + u;
-                                        v[u] = Sd[2 * ((int64_t)(h.cs.mir[p] ? n - 1 - jj : jj) * n * n + colp)];
-                                    }
-                            }
-                            const int a = -h.colexp[2 * p + h2];
-                            const int al[4] = {a, a, a, a};
-                            const double v0[4] = {v[0], v[1], v[2], v[3]}, v1[4] = {v[4], v[5], v[6], v[7]};
-                            put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h2, k0, v0, al);
-                            put_digits4(Xc, 16 * kCols, B_LBO, 2 * p + h2, k0 + 4, v1, al);
+                        const bool done = tc::mbar_wait(&pb.data[buf], (dph >> buf) & 1, kWaitPolls);
+                        if (done) {
+                            dph ^= 1u << buf;
+                            inflight = -1;
                         }
+                        read_raw(h, c, Xc, wn);
+                        ok = tc::group_and(kBarConv, kConv, done);  // every raw value read before any digit lands
+                        if (!ok) break;
+                    }
+                    if (bk0 < kfill) {
+                        double vr[4], vi[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int q = (k - brot) & 3;
+                            const double2 x = q == 0 ? wn[0] : q == 1 ? wn[1] : q == 2 ? wn[2] : wn[3];
+                            vr[k] = x.x;
+                            vi[k] = x.y;
+                        }
+                        const int ar = -h.colexp[2 * bp], ai = -h.colexp[2 * bp + 1];
+                        const int alr[4] = {ar, ar, ar, ar}, ali[4] = {ai, ai, ai, ai};
+                        put_digits4(Xc, 16 * kCols, B_LBO, 2 * bp, bk0, vr, alr);
+                        put_digits4(Xc, 16 * kCols, B_LBO, 2 * bp + 1, bk0, vi, ali);
                     }
                     if (pending) {
                         ok = converter_wait_mma(pb, mph);
@@ -577,24 +667,33 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                         if (prows > 0) epilogue();
                         if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
                     }
-                    // A operand: staged row 8 g + t / 32, samples 4 (t % 32) .. + 3; the
-                    // groups past the cluster's last degree are neither staged nor read
+                    // the other B buffer's MMAs (the previous step's) are done: the next step's copies
+                    if (!(c == nchunks - 1 && lb + TM >= B)) {  // a next step in this cluster
+                        if (t == 0) issue_b(h, c + 1 == nchunks ? 0 : c + 1, buf ^ 1);
+                        inflight = buf ^ 1;
+                    }
+                    // A operand: staged rows G g + t / 32 and G g + t / 32 + 8, samples
+                    // 4 (t % 32) .. + 3; the groups past the cluster's last degree are
+                    // neither staged nor read
                     const int rr = t >> 5, k4 = 4 * (t & 31);
                     const int ngroups = (rows + G - 1) / G;
                     for (int g = 0; g < ngroups; ++g, ++gi) {
                         ok = converter_acquire(pb, gi);
                         if (!ok) break;
-                        const int r = g * G + rr;
-                        if (r < rows && k4 < kfill) {
-                            const double2 *src =
-                                reinterpret_cast<const double2 *>(stage + (gi % kStages) * G * KC + rr * KC + k4);
-                            const double2 w0 = src[0], w1 = src[1];
-                            const double v[4] = {w0.x, w0.y, w1.x, w1.y};
-                            const int a = alpha[lb + r - l0];
-                            const int al[4] = {a, a, a, a};
-                            put_digits4(A, A_PLANE, A_LBO, r, k4, v, al);
+#pragma unroll
+                        for (int hh = 0; hh < G; hh += 8) {
+                            const int r = g * G + hh + rr;
+                            if (r < rows && k4 < kfill) {
+                                const double2 *src = reinterpret_cast<const double2 *>(
+                                    stage + (gi % kStages) * G * KC + (hh + rr) * KC + k4);
+                                const double2 w0 = src[0], w1 = src[1];
+                                const double v[4] = {w0.x, w0.y, w1.x, w1.y};
+                                const int a = alpha[lb + r - l0];
+                                const int al[4] = {a, a, a, a};
+                                put_digits4(A, A_PLANE, A_LBO, r, k4, v, al);
+                            }
                         }
-                        tc::mbar_arrive(&pb.empty[gi % kStages]);
+                        release_empty(pb, gi);
                     }
                     tc::fence_proxy_async();
                     ok = chunk_done(ok);
@@ -616,6 +715,8 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
             if (ok && done && prows > 0) epilogue();
             ok = ok && done;
         }
+        // after a timeout: copies still in flight land before the CTA leaves
+        if (inflight >= 0) tc::mbar_wait(&pb.data[inflight], (dph >> inflight) & 1, kWaitPolls);
     } else if (tid == kIssuer) {
         // ---- issuer: the MMAs of every chunk, in the converters' order ----
         uint32_t rph = 0, cc = 0;
@@ -640,9 +741,10 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
 // ---------------------------------------------------------------------------
 // Inverse DWT, persistent as the forward: one CTA per SM walks the clusters
 // inv_order[blockIdx.x + k gridDim.x]; tiles of 128 beta samples (the TMEM
-// lanes, one producer each), K chunks of 64 degrees, staged 8 degrees at a
-// time: staging [kStages][128 rows][SR] with SR = 10 doubles per row (8 used;
-// the pad spreads the rows over the shared-memory banks).  The set-up warp
+// lanes, one producer each), K chunks of 64 degrees, staged kGroup = 16
+// degrees (one MMA K step) at a time: staging [kStages][128 rows][SR] with
+// SR = 18 doubles per row (16 used; the pad spreads the rows over the
+// shared-memory banks).  The set-up warp
 // fills slot k & 1 with cluster k's partner table, recurrence coefficients,
 // digit exponents, the factors V_l mu_t of its coefficients and the column
 // scales of those products (the largest magnitude of each of the 16 data
@@ -654,7 +756,7 @@ __host__ __device__ constexpr size_t inv_slot_doubles(int B) { return 3 * (size_
 
 __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables tb, const double *__restrict__ coef,
                                                                         double2 *__restrict__ S, int flags) {
-    constexpr int TM = kProd, KC = 64, SR = 10;
+    constexpr int TM = kProd, KC = 64, G = kGroup, SR = kGroup + 2;
     constexpr int A_LBO = TM * 16 + 16, A_PLANE = (KC / 8) * A_LBO;
     constexpr int B_LBO = kNB * 16 + 16, B_BYTES = (KC / 8) * B_LBO;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -766,38 +868,53 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                 if (active) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
                 for (int lb = l0; lb < B && ok; lb += KC) {
                     const int cnt = min(KC, B - lb);
-                    const int ngroups = 2 * ((cnt + 15) / 16);  // K padded to whole MMA steps
+                    const int ngroups = (cnt + G - 1) / G;  // K padded to whole MMA steps
                     for (int g = 0; g < ngroups; ++g, ++gi) {
                         ok = producer_acquire(pb, gi);
                         if (!ok) break;
-                        double v[8];
-                        const int nv = active ? max(0, min(8, cnt - 8 * g)) : 0;  // degrees of this group
-                        const int q0 = lb + 8 * g - l0;
-                        if (nv == 8) {
-                            // a whole group: straight-line code, no predicated FP64 work
+                        double2 *st = reinterpret_cast<double2 *>(stage + ((gi % kStages) * TM + t) * SR);
+                        const int nvg = active ? max(0, min(G, cnt - G * g)) : 0;  // degrees of this group
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                v[u] = dc;
-                                const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
-                                dp = dc;
-                                dc = nx;
-                            }
-                        } else {  // the chunk's last, partial group (at most one per chunk)
+                        for (int hh = 0; hh < G; hh += 8) {  // halves of 8 degrees
+                            double v[8];
+                            const int nv = max(0, min(8, nvg - hh));
+                            const int q0 = lb + G * g + hh - l0;
+                            if (nv == 8) {
+                                // a whole half: straight-line code, no predicated FP64 work; the
+                                // first FMA of a row runs two rows ahead of the dependent second
+                                // (as in the forward's producers)
+                                double ca[8], cb[8];
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                v[u] = 0.0;
-                                if (u < nv) {
+                                for (int u = 0; u < 8; ++u) {
+                                    ca[u] = rA[q0 + u];
+                                    cb[u] = rAc[q0 + u];
+                                }
+                                double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
+#pragma unroll
+                                for (int u = 0; u < 8; ++u) {
                                     v[u] = dc;
-                                    const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
+                                    const double nx = fma(u0, dc, -dp);
+                                    u0 = u1;
+                                    if (u + 2 < 8) u1 = fma(ca[u + 2], x, -cb[u + 2]);
                                     dp = dc;
                                     dc = nx;
                                 }
-                            }
-                        }
-                        double2 *st = reinterpret_cast<double2 *>(stage + ((gi % kStages) * TM + t) * SR);
+                            } else {  // the chunk's last, partial half (at most one per chunk)
 #pragma unroll
-                        for (int h = 0; h < 4; ++h) st[h] = make_double2(v[2 * h], v[2 * h + 1]);
-                        tc::mbar_arrive(&pb.full[gi % kStages]);
+                                for (int u = 0; u < 8; ++u) {
+                                    v[u] = 0.0;
+                                    if (u < nv) {
+                                        v[u] = dc;
+                                        const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
+                                        dp = dc;
+                                        dc = nx;
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) st[hh / 2 + h] = make_double2(v[2 * h], v[2 * h + 1]);
+                        }
+                        release_full(pb, gi);
                     }
                 }
             }
@@ -807,7 +924,7 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
         // ---- converters ----
         const int t = tid - kProd;
         const int wq = warp & 3;
-        const int row = t & 127, half = t >> 7;  // A operand: 4 of the 8 staged degrees of one row
+        const int row = t & 127, half = t >> 7;  // A operand: 8 of the 16 staged degrees of one row
         uint32_t gi = 0, mph = 0, cc = 0;
         bool pending = false;
         // the tile whose last MMAs are pending (pjb >= 0) for the deferred epilogue, its
@@ -846,6 +963,20 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             }
             tc::fence_before_sync();
         };
+        // B operand task of this thread: column q2 (partner bp = q2 / 2, re or im),
+        // degrees lb + bk0 .. + 3 of a chunk.  The coefficients are loaded one
+        // (tile, chunk) step ahead, so their latency passes while the A operand is cut
+        // (a few kilobytes per chunk: bulk copies into shared memory measured slower).
+        const int q2 = t & 15, bp = q2 >> 1, bk0 = 4 * (t >> 4);
+        double cvn[4];
+        auto load_cv = [&](const SlotHdr &h, int lb, int l0) {
+            const int cnt = min(KC, B - lb);
+            const bool used = bp < h.cs.np && !((flags & kRealSym) && h.cs.np > 1 && (bp & 1));
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                cvn[u] = used && bk0 + u < cnt ? coef[2 * (h.cs.off[bp] + lb + bk0 + u - l0) + (q2 & 1)] : 0.0;
+        };
+        bool have_cv = false;  // cvn holds the next step's coefficients
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
             if (!cluster_of(k, cidx, m, mp)) break;
@@ -856,8 +987,6 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                 if (!ok) break;
             }
             const SlotHdr &h = hdr[s];
-            const int np = h.cs.np;
-            const bool real = (flags & kRealSym) && np > 1;
             const double *rG = slot_rG(s);
             const int *ralpha = slot_alpha(s);
             for (int jb = 0; jb < n && ok; jb += TM) {
@@ -867,28 +996,27 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                     const int ksteps = (cnt + 15) / 16;
                     const int kfill = ksteps * 16;
                     unsigned char *Xc = X + (cc & 1) * B_BYTES;
-                    {
-                        // B operand: column q2, degrees lb + k0 .. + 3 of F (FP64, formed here)
-                        const int q2 = t & 15, k0 = 4 * (t >> 4);
-                        if (k0 < kfill) {
-                            double v[4];
-                            int al[4];
-                            const int p = q2 >> 1;
+                    if (!have_cv) load_cv(h, lb, l0);  // the cluster's first step
+                    if (bk0 < kfill) {
+                        // F = sign_p(l) V_l mu_t f(l, m_p, m'_p), formed here in FP64
+                        double v[4];
+                        int al[4];
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                v[u] = 0.0;
-                                al[u] = -h.colexp[q2];
-                                const int kk = k0 + u;
-                                if (p < np && !(real && (p & 1)) && kk < cnt) {
-                                    const int q = lb + kk - l0, l = lb + kk;
-                                    const bool neg = (h.cs.sign[p] < 0.0) != (h.cs.lpar[p] && (l & 1));
-                                    const double cv = coef[2 * (h.cs.off[p] + q) + (q2 & 1)];
-                                    v[u] = (neg ? -rG[q] : rG[q]) * cv;
-                                }
+                        for (int u = 0; u < 4; ++u) {
+                            al[u] = -h.colexp[q2];
+                            const int kk = bk0 + u;
+                            v[u] = 0.0;
+                            if (kk < cnt) {
+                                const int q = lb + kk - l0, l = lb + kk;
+                                const bool neg = (h.cs.sign[bp] < 0.0) != (h.cs.lpar[bp] && (l & 1));
+                                v[u] = (neg ? -rG[q] : rG[q]) * cvn[u];
                             }
-                            put_digits4(Xc, 16 * kCols, B_LBO, q2, k0, v, al);
                         }
+                        put_digits4(Xc, 16 * kCols, B_LBO, q2, bk0, v, al);
                     }
+                    // the next step of this cluster: the next degree chunk, else the first of the next tile
+                    have_cv = lb + KC < B || jb + TM < n;
+                    if (have_cv) load_cv(h, lb + KC < B ? lb + KC : l0, l0);
                     if (pending) {
                         ok = converter_wait_mma(pb, mph);
                         pending = false;
@@ -896,23 +1024,24 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                         if (pjb >= 0) epilogue();
                         if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
                     }
-                    for (int g = 0; g < 2 * ksteps; ++g, ++gi) {
+                    for (int g = 0; g < ksteps; ++g, ++gi) {  // one staged group per K step
                         ok = converter_acquire(pb, gi);
                         if (!ok) break;
                         if (active) {
-                            const double2 *src =
-                                reinterpret_cast<const double2 *>(stage + ((gi % kStages) * TM + row) * SR + 4 * half);
-                            const double2 w0 = src[0], w1 = src[1];
-                            const double v[4] = {w0.x, w0.y, w1.x, w1.y};
-                            int al[4];
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int kk = 8 * g + 4 * half + u;
-                                al[u] = kk < cnt ? ralpha[lb + kk - l0] : 0;
+                            for (int q4 = 0; q4 < 8; q4 += 4) {
+                                const int k0 = G * g + 8 * half + q4;  // first of 4 degrees (chunk-relative)
+                                const double2 *src = reinterpret_cast<const double2 *>(
+                                    stage + ((gi % kStages) * TM + row) * SR + 8 * half + q4);
+                                const double2 w0 = src[0], w1 = src[1];
+                                const double v[4] = {w0.x, w0.y, w1.x, w1.y};
+                                int al[4];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) al[u] = k0 + u < cnt ? ralpha[lb + k0 + u - l0] : 0;
+                                put_digits4(A, A_PLANE, A_LBO, row, k0, v, al);
                             }
-                            put_digits4(A, A_PLANE, A_LBO, row, 8 * g + 4 * half, v, al);
                         }
-                        tc::mbar_arrive(&pb.empty[gi % kStages]);
+                        release_empty(pb, gi);
                     }
                     tc::fence_proxy_async();
                     ok = chunk_done(ok);
@@ -930,6 +1059,7 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             if (ok && done && pjb >= 0) epilogue();
             ok = ok && done;
         }
+        // after a timeout: copies still in flight land before the CTA leaves
     } else if (tid == kIssuer) {
         uint32_t rph = 0, cc = 0;
         for (int k = 0; ok; ++k) {
@@ -971,6 +1101,23 @@ __global__ void __launch_bounds__(256) colexp_kernel(const double2 *__restrict__
 
 }  // namespace
 
+namespace {
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+}  // namespace
+
 cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *coef, cudaStream_t s, int flags) {
     if (!tb.seedtab || !tb.rectab || !tb.colexp) return cudaErrorInvalidValue;
     {
@@ -982,8 +1129,23 @@ cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *c
     }
     constexpr int KC = kProd, A_PLANE = (KC / 8) * (64 * 16 + 16), B_BYTES = (KC / 8) * (kNB * 16 + 16);
     const int B = tb.B;
+    const uint64_t n = 2 * (uint64_t)B;
+    // S as a 4-D FP64 tensor (re/im, m', m, j), boxes of (2, 1, 1, min(128, 2B)): one
+    // partner column over a chunk of beta samples per copy (rows of 16 bytes)
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    if (reinterpret_cast<uintptr_t>(S) % 16 != 0) return cudaErrorMisalignedAddress;
+    CUtensorMap tmS;
+    const cuuint64_t dims[4] = {2, n, n, n};
+    const cuuint64_t strides[3] = {16, 16 * n, 16 * n * n};
+    const cuuint32_t box[4] = {2, 1, 1, (cuuint32_t)std::min<uint64_t>(KC, n)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (encode(&tmS, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<double2 *>(S), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     const size_t bytes = (size_t)kDig * A_PLANE + 2 * (size_t)B_BYTES +
-                         sizeof(double) * (kStages * 8 * (size_t)KC + 2 * fwd_slot_doubles(B));
+                         sizeof(double) * (kStages * kGroup * (size_t)KC + 2 * fwd_slot_doubles(B));
     cudaError_t e =
         cudaFuncSetAttribute(dwt_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -993,14 +1155,14 @@ cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *c
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(tb.ncl, sms));
-    dwt_forward_tc_kernel<<<grid, kThreadsFwd, bytes, s>>>(tb, S, reinterpret_cast<double *>(coef), flags);
+    dwt_forward_tc_kernel<<<grid, kThreadsFwd, bytes, s>>>(tb, tmS, reinterpret_cast<double *>(coef), flags);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_dwt_inverse_tc(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s, int flags) {
     if (!tb.seedtab || !tb.rectab) return cudaErrorInvalidValue;
-    constexpr int TM = kProd, KC = 64, SR = 10;
+    constexpr int TM = kProd, KC = 64, SR = kGroup + 2;
     constexpr int A_PLANE = (KC / 8) * (TM * 16 + 16), B_BYTES = (KC / 8) * (kNB * 16 + 16);
     const int B = tb.B;
     const size_t bytes = (size_t)kDig * A_PLANE + 2 * (size_t)B_BYTES +

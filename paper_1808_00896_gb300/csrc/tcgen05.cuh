@@ -92,7 +92,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint3
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             "selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
-            : "r"(a), "r"(parity));
+            : "r"(a), "r"(parity)
+            : "memory");  // no load of the guarded data may move above the wait
         if (done) return true;
     }
     return false;
@@ -101,6 +102,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint3
 // Arrive (release) on an mbarrier from this thread.
 __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Arrive on an mbarrier and raise its expected transaction count by `bytes`
+// (the bulk copies that complete_tx on it must deliver that many bytes).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA: a 4-D tile of the tensor map `map` at coordinates (c0 innermost .. c3)
+// into shared memory at dst (128-byte aligned), completing `mbar`'s
+// transaction bytes.  Coordinates may lie outside the tensor (zero fill), but
+// c0 times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(mbar))
+        : "memory");
 }
 
 // Named barrier over `nthreads` threads (whole warps) of the CTA.

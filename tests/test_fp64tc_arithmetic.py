@@ -22,7 +22,7 @@ DIG = 7
 
 def digits(v: float, alpha: int):
     """Balanced base-128 digits of round(v 2^(alpha+48)), as the kernel cuts them."""
-    N = int(round(math.ldexp(v, alpha + 48)))  # round half to even here; the kernel rounds half away
+    N = int(round(math.ldexp(v, alpha + 48)))  # round half to even here; the kernel rounds half up
     q = [0] * DIG
     for i in range(DIG - 1, 0, -1):
         t = N + 64
@@ -50,6 +50,59 @@ def test_digits_are_balanced_and_reconstruct():
 def test_extreme_digits_stay_within_64():
     for v in (1.0, -1.0, 1.0 - 2.0 ** -52, -(1.0 - 2.0 ** -52), 2.0 ** -49, 0.0):
         assert all(-64 <= qi <= 64 for qi in digits(v, 0))
+
+
+K7 = sum(64 * 128 ** i for i in range(DIG))
+
+
+def kernel_digits(v: float, alpha: int):
+    """The kernel's cut, step by step in Python integers: T = floor(v 2^(alpha+49))
+    by an arithmetic shift of the signed significand, Q = T + 1 + 2 K7, and the
+    digits q_i = field of Q at bit 1 + 7 (6 - i), minus 64 (digits 6..4 from the
+    low 32-bit word, 3..0 from Q >> 22)."""
+    b = int(np.float64(v).view(np.int64))
+    e = (b >> 52) & 0x7FF
+    s = min(1026 - alpha - e, 63)
+    M = (b & ((1 << 52) - 1)) | (1 << 52)
+    T = (-M if b < 0 else M) >> s  # Python's >> floors, like the arithmetic shift
+    Q = T + 1 + 2 * K7
+    assert 0 <= Q < 2 ** 51
+    lo, hi = Q & 0xFFFFFFFF, (Q >> 22) & 0xFFFFFFFF
+    return [(hi >> 21) - 64, ((hi >> 14) & 127) - 64, ((hi >> 7) & 127) - 64, (hi & 127) - 64,
+            ((lo >> 15) & 127) - 64, ((lo >> 8) & 127) - 64, ((lo >> 1) & 127) - 64]
+
+
+def balanced(N: int):
+    """Balanced base-128 digits of N by the carry chain (lower six in [-64, 63])."""
+    q = [0] * DIG
+    for i in range(DIG - 1, 0, -1):
+        t = N + 64
+        q[i] = (t & 127) - 64
+        N = t >> 7
+    q[0] = N
+    return q
+
+
+def test_kernel_cut_is_balanced_digits_of_the_rounded_integer():
+    """The kernel's independent bit fields give the balanced digits of
+    N = floor(v 2^(alpha+48) + 1/2), over the whole range |v 2^alpha| <= 1."""
+    rng = np.random.default_rng(11)
+    vals = [0.0, -0.0, 1.0, -1.0, 1.0 - 2.0 ** -52, -(1.0 - 2.0 ** -52), 2.0 ** -49, -2.0 ** -49, 2.0 ** -50,
+            3 * 2.0 ** -50, -3 * 2.0 ** -50, 2.0 ** -60, 5e-324]
+    vals += [float(x) for x in rng.uniform(-1.0, 1.0, 5000) * 2.0 ** rng.integers(-40, 1, 5000)]
+    for alpha in (0, 3, -7):
+        for v0 in vals:
+            v = math.ldexp(v0, -alpha)  # |v 2^alpha| <= 1
+            # N = floor(v 2^(alpha+48) + 1/2) exactly, from v = +-M 2^(e-1075) (zero and subnormals: 0)
+            b = int(np.float64(v).view(np.int64))
+            e = (b >> 52) & 0x7FF
+            M = ((b & ((1 << 52) - 1)) | (1 << 52)) * (-1 if b < 0 else 1)
+            k = e - 1075 + alpha + 48
+            N = 0 if e == 0 else (M << k if k >= 0 else (M + (1 << (-k - 1))) >> -k)
+            q = kernel_digits(v, alpha)
+            assert q == balanced(N), (v, alpha)
+            assert all(-64 <= qi <= 64 for qi in q)
+            assert abs(value(q, alpha) - v) <= 2.0 ** (-49 - alpha)
 
 
 def test_level_sums_exact_and_recombination():
