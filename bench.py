@@ -85,6 +85,13 @@ for _B, _nb in ((64, 8), (128, 8), (256, 8), (512, 4)):
                             f"{_nb} {'mixed BF16x3' if _m == 'bf16x3' else 'FP64'} SOFT forward+inverse transforms "
                             f"at B={_B} per step through the batched, graph-captured API")
         BATCHED[_name] = [_B] * _nb
+# FP64-TC batches: each entry's own kernels, captured in the batch's graph.
+for _B, _nb in ((64, 8), (128, 8), (256, 4)):
+    _name = f"b{_B}_fp64tc_x{_nb}"
+    WORKLOADS[_name] = (_B, "fp64_tc", "gauss_decay",
+                        f"{_nb} FP64-accurate (FP64-TC) SOFT forward+inverse transforms at B={_B} per step through "
+                        f"the batched, graph-captured API (each transform's own DWT / iDWT launches in one graph)")
+    BATCHED[_name] = [_B] * _nb
 # Mixed bandwidths in one batch: the FP64 transforms share one persistent DWT
 # and one persistent iDWT launch over all their (transform, cluster) items.
 WORKLOADS["mix_fp64"] = (256, "fp64", "gauss_decay",
@@ -92,7 +99,7 @@ WORKLOADS["mix_fp64"] = (256, "fp64", "gauss_decay",
                          "the batched, graph-captured API: one persistent DWT and one persistent iDWT launch over "
                          "all (transform, cluster) items")
 BATCHED["mix_fp64"] = [32, 64, 128, 256, 32, 64, 128, 256]
-# Batched rotational matching: 64 correlation requests, B uniform in {8,...,128}.
+# Batched rotational matching: 64 correlation requests, B uniform over {8, 16, 32, 64, 128}.
 CORR_WORKLOAD = ("corr64", "batched rotational matching: 64 correlation requests, B drawn uniformly from "
                  "{8,16,32,64,128}, SH coefficients complex Gaussian x 1/(l+1); per request: correlation "
                  "coefficients, FP64 inverse SOFT (one graph-captured persistent launch for all iDWTs), "
@@ -540,15 +547,20 @@ def run_batched(args) -> None:
         algo = 2 * sum(dwt_flops(b)["contraction"] + dwt_flops(b)["recurrence"] for b in Bs)
         note = ("whole-step time (FFTs included): the FP64 contraction + recurrence of the batch's DWTs and iDWTs "
                 "(one persistent launch per direction)")
+    elif dtype == "fp64_tc":
+        algo = 2 * nb * fl["recurrence"]  # each transform's own recurrence, DWT and iDWT
+        note = ("whole-step time (FFTs included): the FP64 recurrence of every transform's DWT and iDWT "
+                "(per-transform launches inside the batch's graph)")
     else:
         algo = 2 * fl["recurrence"]  # one shared recurrence per batched DWT launch, 2 launches per step
         note = ("whole-step time (FFTs included): the FP64 recurrence of the 2 batched (i)DWT launches, "
                 "shared by the nb transforms")
+    kernel = {"fp64": "dwt_forward_fp64_kernel", "fp64_tc": "dwt_forward_tc_kernel"}.get(dtype, "dwt_forward_mixed_kernel")
     roofline = {"bound": "alu", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak_gflops, "unit": "GFLOP/s",
-                "frac": algo / (ms * 1e-3) / 1e9 / peak_gflops, "traffic": None,
-                "kernel": "dwt_forward_mixed_kernel" if dtype != "fp64" else "dwt_forward_fp64_kernel", "note": note}
+                "frac": algo / (ms * 1e-3) / 1e9 / peak_gflops, "traffic": None, "kernel": kernel, "note": note}
     if dtype != "fp64":
-        roofline["tensor_tflops_achieved"] = 2 * 3 * nb * fl["contraction"] / (ms * 1e-3) / 1e12
+        # tensor-core products per real multiply-add: 3 (BF16x3), 28 (FP64-TC digit pairs)
+        roofline["tensor_tflops_achieved"] = 2 * (28 if dtype == "fp64_tc" else 3) * nb * fl["contraction"] / (ms * 1e-3) / 1e12
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

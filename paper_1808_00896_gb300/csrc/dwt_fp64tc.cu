@@ -740,36 +740,69 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
 
 // ---------------------------------------------------------------------------
 // Inverse DWT, persistent as the forward: one CTA per SM walks the clusters
-// inv_order[blockIdx.x + k gridDim.x]; tiles of 128 beta samples (the TMEM
-// lanes, one producer each), K chunks of 64 degrees, staged kGroup = 16
-// degrees (one MMA K step) at a time: staging [kStages][128 rows][SR] with
-// SR = 18 doubles per row (16 used; the pad spreads the rows over the
-// shared-memory banks).  The set-up warp
-// fills slot k & 1 with cluster k's partner table, recurrence coefficients,
-// digit exponents, the factors V_l mu_t of its coefficients and the column
-// scales of those products (the largest magnitude of each of the 16 data
-// columns over the degrees).  Same converter schedule as the forward.
-//   dynamic smem: A planes [7] | B operand [2] | staging |
-//                 slot [2] { rA, rAc, rG [B doubles], alpha [B ints] }
+// inv_order[blockIdx.x + k gridDim.x]; tiles of 128 beta samples, K chunks of
+// 32 degrees.  Here M = the beta samples = the TMEM lanes, so the A operand
+// (the Wigner-d digits) lives in tensor memory, and each producer -- the
+// thread of sample j, TMEM lane j -- cuts its own recurrence values into
+// digits and stores them with tcgen05.st, two degrees per 32-bit column;
+// there is no staging ring and the converters only build the B operand and
+// run the epilogue.  TMEM: accumulators in columns 0..111, A buffer a
+// (a = chunk & 1) in columns kAcol0 + a kAbufCols + 16 i + k / 2 for digit i
+// and chunk-relative degree k.  The set-up warp fills slot k & 1 with cluster
+// k's partner table, recurrence coefficients, digit exponents, the factors
+// V_l mu_t of its coefficients and the column scales of those products (the
+// largest magnitude of each of the 16 data columns over the degrees).
+// Hand-off: afull[a] (one arrival per producer warp after its tcgen05.st
+// completed), afree[a] (tcgen05.commit of the chunk's MMAs), ready and mma as
+// in the forward; every wait bounded.
+//   dynamic smem: B operand [2] | slot [2] { rA, rAc, rG [B doubles], alpha [B ints] }
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr size_t inv_slot_doubles(int B) { return 3 * (size_t)B + ((size_t)B + 1) / 2; }
+constexpr int kKCInv = 32;                        // degrees per K chunk of the inverse
+constexpr uint32_t kAcol0 = 128;                  // first TMEM column of the A buffers
+constexpr uint32_t kAbufCols = kDig * kKCInv / 2;  // 112 columns per A buffer
+constexpr uint32_t kTmemColsInv = 512;            // >= kAcol0 + 2 kAbufCols
+
+struct InvBars {
+    uint64_t afull[2], afree[2];
+};
+
+// One K chunk of MMAs with A in tensor memory (issued by one thread): for each
+// K step of 16 degrees, A digit i (TMEM columns acol + 16 i + 8 s ..) against
+// B digits 0..6-i into accumulator columns 16 i ..; completion committed to
+// both mbarriers.
+__device__ __forceinline__ void issue_levels_ta(uint32_t tmem, uint32_t acol, const unsigned char *Bop, uint32_t b_lbo,
+                                                bool first, int ksteps, uint64_t *mbar, uint64_t *mbar2) {
+    tc::fence_after_sync();
+    const uint64_t bd0 = tc::smem_desc(tc::smem_u32(Bop), b_lbo, 128);
+    for (int s = 0; s < ksteps; ++s) {
+        const uint64_t bd = bd0 + (uint64_t)((s * 2 * b_lbo) >> 4);
+#pragma unroll
+        for (int i = 0; i < kDig; ++i) {
+            constexpr uint32_t kIdesc0 = tc::instr_desc(1, 128, kCols * kDig);
+            const uint32_t idesc = kIdesc0 - ((uint32_t)(kCols * i) >> 3 << 17);  // N = 16 (7 - i)
+            tc::mma_bf16_ta(tmem + kCols * i, tmem + acol + 16 * i + 8 * s, bd, idesc,
+                            (first && s == 0 && i == 0) ? 0u : 1u);
+        }
+    }
+    tc::mma_commit(mbar);
+    tc::mma_commit(mbar2);
+}
 
 __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables tb, const double *__restrict__ coef,
                                                                         double2 *__restrict__ S, int flags) {
-    constexpr int TM = kProd, KC = 64, G = kGroup, SR = kGroup + 2;
-    constexpr int A_LBO = TM * 16 + 16, A_PLANE = (KC / 8) * A_LBO;
+    constexpr int TM = kProd, KC = kKCInv;
     constexpr int B_LBO = kNB * 16 + 16, B_BYTES = (KC / 8) * B_LBO;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ SlotHdr hdr[2];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) PipeBars pb;
+    __shared__ __align__(8) InvBars ib;
     __shared__ __align__(8) uint64_t slot_full[2], slot_empty[2];
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    unsigned char *A = smem;
-    unsigned char *X = smem + kDig * A_PLANE;  // [2][B_BYTES]
-    double *stage = reinterpret_cast<double *>(X + 2 * B_BYTES);  // [kStages][TM][SR]
-    double *slotd = stage + kStages * TM * SR;
+    unsigned char *X = smem;  // [2][B_BYTES]
+    double *slotd = reinterpret_cast<double *>(X + 2 * B_BYTES);
     const size_t SLOT = inv_slot_doubles(B);
     auto slot_rA = [&](int s) { return slotd + s * SLOT; };
     auto slot_rAc = [&](int s) { return slotd + s * SLOT + B; };
@@ -785,9 +818,13 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
         return true;
     };
 
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemColsInv);
     if (tid == 0) {
         init_pipe(pb);
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(&ib.afull[a], kProd / 32);
+            tc::mbar_init(&ib.afree[a], 1);
+        }
         for (int s2 = 0; s2 < 2; ++s2) {
             tc::mbar_init(&slot_full[s2], 32);
             tc::mbar_init(&slot_empty[s2], kProd + kConv);
@@ -851,81 +888,151 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             tc::mbar_arrive(&slot_full[s]);
         }
     } else if (tid < kProd) {
-        // ---- producers: beta sample j = jb + t walks the degrees ----
+        // ---- producers: beta sample j = jb + t (TMEM lane t) walks the degrees ----
+        // Two stages in one basic block per group of 8 degrees: the FP64 recurrence
+        // of the next group and the digit cutting and TMEM stores of the current
+        // one, so that the integer work fills the dependent FMA chain's stalls.
+        // Group counts and degree counts are warp-uniform (an idle lane's values
+        // are zero because its recurrence starts from zero), so every lane of a
+        // warp takes the same branches and meets each tcgen05.st.
         const int t = tid;
-        uint32_t gi = 0;
+        const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
+        uint32_t cc = 0;
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
             if (!cluster_of(k, cidx, m, mp)) break;
-            const int s = k & 1, l0 = m;
-            ok = tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls);
+            const int s = k & 1, L = B - m;
+            ok = __all_sync(0xffffffffu, tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls));
             if (!ok) break;
             const double *rA = slot_rA(s), *rAc = slot_rAc(s);
+            const int *ralpha = slot_alpha(s);
+            const int nch = (L + KC - 1) / KC;  // K chunks of a tile
+            auto ngroups_of = [&](int c) { return 2 * ((min(KC, L - c * KC) + 15) / 16); };
             for (int jb = 0; jb < n && ok; jb += TM) {
                 const int j = jb + t;
-                const bool active = j < n;
                 double x = 0.0, dc = 0.0, dp = 0.0;
-                if (active) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
-                for (int lb = l0; lb < B && ok; lb += KC) {
-                    const int cnt = min(KC, B - lb);
-                    const int ngroups = (cnt + G - 1) / G;  // K padded to whole MMA steps
-                    for (int g = 0; g < ngroups; ++g, ++gi) {
-                        ok = producer_acquire(pb, gi);
-                        if (!ok) break;
-                        double2 *st = reinterpret_cast<double2 *>(stage + ((gi % kStages) * TM + t) * SR);
-                        const int nvg = active ? max(0, min(G, cnt - G * g)) : 0;  // degrees of this group
+                if (j < n) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
+                // stage 1: the 8 values of the group at degree l0 + q0 (nv valid, the rest 0)
+                auto recur = [&](double (&v)[8], int q0, int nv) {
+                    if (nv == 8) {
+                        // a whole group: straight-line code, the first FMA of a row two rows
+                        // ahead of the dependent second
+                        double ca[8], cb[8];
 #pragma unroll
-                        for (int hh = 0; hh < G; hh += 8) {  // halves of 8 degrees
-                            double v[8];
-                            const int nv = max(0, min(8, nvg - hh));
-                            const int q0 = lb + G * g + hh - l0;
-                            if (nv == 8) {
-                                // a whole half: straight-line code, no predicated FP64 work; the
-                                // first FMA of a row runs two rows ahead of the dependent second
-                                // (as in the forward's producers)
-                                double ca[8], cb[8];
-#pragma unroll
-                                for (int u = 0; u < 8; ++u) {
-                                    ca[u] = rA[q0 + u];
-                                    cb[u] = rAc[q0 + u];
-                                }
-                                double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
-#pragma unroll
-                                for (int u = 0; u < 8; ++u) {
-                                    v[u] = dc;
-                                    const double nx = fma(u0, dc, -dp);
-                                    u0 = u1;
-                                    if (u + 2 < 8) u1 = fma(ca[u + 2], x, -cb[u + 2]);
-                                    dp = dc;
-                                    dc = nx;
-                                }
-                            } else {  // the chunk's last, partial half (at most one per chunk)
-#pragma unroll
-                                for (int u = 0; u < 8; ++u) {
-                                    v[u] = 0.0;
-                                    if (u < nv) {
-                                        v[u] = dc;
-                                        const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
-                                        dp = dc;
-                                        dc = nx;
-                                    }
-                                }
-                            }
-#pragma unroll
-                            for (int h = 0; h < 4; ++h) st[hh / 2 + h] = make_double2(v[2 * h], v[2 * h + 1]);
+                        for (int u = 0; u < 8; ++u) {
+                            ca[u] = rA[q0 + u];
+                            cb[u] = rAc[q0 + u];
                         }
-                        release_full(pb, gi);
+                        double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            v[u] = dc;
+                            const double nx = fma(u0, dc, -dp);
+                            u0 = u1;
+                            if (u + 2 < 8) u1 = fma(ca[u + 2], x, -cb[u + 2]);
+                            dp = dc;
+                            dc = nx;
+                        }
+                    } else {  // the tile's last, partial group, or padding
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            v[u] = 0.0;
+                            if (u < nv) {
+                                v[u] = dc;
+                                const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
+                                dp = dc;
+                                dc = nx;
+                            }
+                        }
                     }
+                };
+                // stage 2: the group's digits, two degrees per 32-bit column (the lower
+                // degree in the low half), into columns 4 g .. 4 g + 3 of each digit plane
+                auto store = [&](const double (&v)[8], int q0, uint32_t acol, int g) {
+                    uint32_t pk[kDig][4];
+#pragma unroll
+                    for (int c2 = 0; c2 < 4; ++c2) {
+                        const int q = q0 + 2 * c2;
+                        uint32_t d0[kDig], d1[kDig];
+                        digits7(v[2 * c2], q < L ? ralpha[q] : 0, d0);
+                        digits7(v[2 * c2 + 1], q + 1 < L ? ralpha[q + 1] : 0, d1);
+#pragma unroll
+                        for (int i = 0; i < kDig; ++i) pk[i][c2] = __byte_perm(d0[i], d1[i], 0x7632);
+                    }
+#pragma unroll
+                    for (int i = 0; i < kDig; ++i)
+                        tc::tmem_st4(acol + 16 * i + 4 * g, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+                };
+                // both stages for a whole next group, interleaved row by row in the source:
+                // row u of the recurrence, then the digits of value u of the stored group
+                auto recur_store = [&](double (&vn)[8], int qn, const double (&v)[8], int q0, uint32_t acol, int g) {
+                    double ca[8], cb[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        ca[u] = rA[qn + u];
+                        cb[u] = rAc[qn + u];
+                    }
+                    double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
+                    uint32_t pk[kDig][4], d0[kDig];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        vn[u] = dc;
+                        const double nx = fma(u0, dc, -dp);
+                        u0 = u1;
+                        if (u + 2 < 8) u1 = fma(ca[u + 2], x, -cb[u + 2]);
+                        dp = dc;
+                        dc = nx;
+                        const int q = q0 + u;
+                        if (u & 1) {
+                            uint32_t d1[kDig];
+                            digits7(v[u], q < L ? ralpha[q] : 0, d1);
+#pragma unroll
+                            for (int i = 0; i < kDig; ++i) pk[i][u >> 1] = __byte_perm(d0[i], d1[i], 0x7632);
+                        } else {
+                            digits7(v[u], q < L ? ralpha[q] : 0, d0);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < kDig; ++i)
+                        tc::tmem_st4(acol + 16 * i + 4 * g, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+                };
+                double vp[8];  // the values of the group in stage 2
+                recur(vp, 0, min(8, L));
+                for (int c = 0; c < nch && ok; ++c, ++cc) {
+                    const uint32_t a = cc & 1;
+                    // A buffer a is free once the MMAs of chunk cc - 2 completed
+                    ok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.afree[a], ((cc >> 1) & 1) ^ 1u, kWaitPolls));
+                    if (!ok) break;
+                    const int ng = ngroups_of(c);
+                    const uint32_t acol = tlane + kAcol0 + a * kAbufCols;
+                    for (int g = 0; g < ng; ++g) {
+                        // the next group: g + 1 of this chunk, else the first of the next chunk
+                        const int cn = g + 1 < ng ? c : c + 1, gn = g + 1 < ng ? g + 1 : 0;
+                        const int qn = cn * KC + 8 * gn;
+                        const int nvn = cn < nch ? max(0, min(8, min(KC, L - cn * KC) - 8 * gn)) : 0;
+                        double vn[8];
+                        if (nvn == 8) {
+                            recur_store(vn, qn, vp, c * KC + 8 * g, acol, g);
+                        } else {
+                            recur(vn, qn, nvn);
+                            store(vp, c * KC + 8 * g, acol, g);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) vp[u] = vn[u];
+                    }
+                    tc::tmem_wait_st();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&ib.afull[a]);
                 }
             }
             if (ok) tc::mbar_arrive(&slot_empty[s]);  // this producer is done with the slot's tables
         }
     } else if (tid < kIssuer) {
-        // ---- converters ----
+        // ---- converters: the B operand and the epilogue ----
         const int t = tid - kProd;
         const int wq = warp & 3;
-        const int row = t & 127, half = t >> 7;  // A operand: 8 of the 16 staged degrees of one row
-        uint32_t gi = 0, mph = 0, cc = 0;
+        uint32_t mph = 0, cc = 0;
         bool pending = false;
         // the tile whose last MMAs are pending (pjb >= 0) for the deferred epilogue, its
         // cluster's slot, and whether it is that cluster's last tile
@@ -963,15 +1070,15 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             }
             tc::fence_before_sync();
         };
-        // B operand task of this thread: column q2 (partner bp = q2 / 2, re or im),
+        // B operand task of converter t < 128: column q2 (partner bp = q2 / 2, re or im),
         // degrees lb + bk0 .. + 3 of a chunk.  The coefficients are loaded one
-        // (tile, chunk) step ahead, so their latency passes while the A operand is cut
-        // (a few kilobytes per chunk: bulk copies into shared memory measured slower).
-        const int q2 = t & 15, bp = q2 >> 1, bk0 = 4 * (t >> 4);
+        // (tile, chunk) step ahead, so their latency passes while the chunk runs.
+        const int q2 = t & 15, bp = q2 >> 1, bk0 = 4 * ((t & 127) >> 4);
+        const bool btask = t < 128;
         double cvn[4];
         auto load_cv = [&](const SlotHdr &h, int lb, int l0) {
             const int cnt = min(KC, B - lb);
-            const bool used = bp < h.cs.np && !((flags & kRealSym) && h.cs.np > 1 && (bp & 1));
+            const bool used = btask && bp < h.cs.np && !((flags & kRealSym) && h.cs.np > 1 && (bp & 1));
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 cvn[u] = used && bk0 + u < cnt ? coef[2 * (h.cs.off[bp] + lb + bk0 + u - l0) + (q2 & 1)] : 0.0;
@@ -988,16 +1095,13 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             }
             const SlotHdr &h = hdr[s];
             const double *rG = slot_rG(s);
-            const int *ralpha = slot_alpha(s);
             for (int jb = 0; jb < n && ok; jb += TM) {
-                const bool active = jb + row < n;
                 for (int lb = l0, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
                     const int cnt = min(KC, B - lb);
-                    const int ksteps = (cnt + 15) / 16;
-                    const int kfill = ksteps * 16;
+                    const int kfill = (cnt + 15) / 16 * 16;
                     unsigned char *Xc = X + (cc & 1) * B_BYTES;
                     if (!have_cv) load_cv(h, lb, l0);  // the cluster's first step
-                    if (bk0 < kfill) {
+                    if (btask && bk0 < kfill) {
                         // F = sign_p(l) V_l mu_t f(l, m_p, m'_p), formed here in FP64
                         double v[4];
                         int al[4];
@@ -1024,25 +1128,6 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                         if (pjb >= 0) epilogue();
                         if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
                     }
-                    for (int g = 0; g < ksteps; ++g, ++gi) {  // one staged group per K step
-                        ok = converter_acquire(pb, gi);
-                        if (!ok) break;
-                        if (active) {
-#pragma unroll
-                            for (int q4 = 0; q4 < 8; q4 += 4) {
-                                const int k0 = G * g + 8 * half + q4;  // first of 4 degrees (chunk-relative)
-                                const double2 *src = reinterpret_cast<const double2 *>(
-                                    stage + ((gi % kStages) * TM + row) * SR + 8 * half + q4);
-                                const double2 w0 = src[0], w1 = src[1];
-                                const double v[4] = {w0.x, w0.y, w1.x, w1.y};
-                                int al[4];
-#pragma unroll
-                                for (int u = 0; u < 4; ++u) al[u] = k0 + u < cnt ? ralpha[lb + k0 + u - l0] : 0;
-                                put_digits4(A, A_PLANE, A_LBO, row, k0, v, al);
-                            }
-                        }
-                        release_empty(pb, gi);
-                    }
                     tc::fence_proxy_async();
                     ok = chunk_done(ok);
                     if (!ok) break;
@@ -1059,8 +1144,9 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             if (ok && done && pjb >= 0) epilogue();
             ok = ok && done;
         }
-        // after a timeout: copies still in flight land before the CTA leaves
     } else if (tid == kIssuer) {
+        // ---- issuer: the MMAs of every chunk once the converters (B operand, the
+        // previous tile's epilogue) and the producers (A digits in TMEM) are ready ----
         uint32_t rph = 0, cc = 0;
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
@@ -1069,16 +1155,19 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                 for (int lb = m, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
                     ok = issuer_acquire(pb, rph);
                     if (!ok) break;
+                    const uint32_t a = cc & 1;
+                    ok = tc::mbar_wait(&ib.afull[a], (cc >> 1) & 1, kWaitPolls);
+                    if (!ok) break;
                     const int ksteps = (min(KC, B - lb) + 15) / 16;
-                    issue_levels<TM>(tmem, A, A_PLANE, A_LBO, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps,
-                                     &pb.mma);
+                    issue_levels_ta(tmem, kAcol0 + a * kAbufCols, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps,
+                                    &pb.mma, &ib.afree[a]);
                 }
         }
     }
     if (!ok && tb.err) atomicExch(tb.err, 2);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemColsInv);
 }
 
 // colexp[(m n + m') 2 + h] = the largest biased FP64 exponent of the real
@@ -1162,15 +1251,13 @@ cudaError_t launch_dwt_forward_tc(const Tables &tb, const double2 *S, double2 *c
 
 cudaError_t launch_dwt_inverse_tc(const Tables &tb, const double2 *coef, double2 *S, cudaStream_t s, int flags) {
     if (!tb.seedtab || !tb.rectab) return cudaErrorInvalidValue;
-    constexpr int TM = kProd, KC = 64, SR = kGroup + 2;
-    constexpr int A_PLANE = (KC / 8) * (TM * 16 + 16), B_BYTES = (KC / 8) * (kNB * 16 + 16);
+    constexpr int B_BYTES = (kKCInv / 8) * (kNB * 16 + 16);
     const int B = tb.B;
-    const size_t bytes = (size_t)kDig * A_PLANE + 2 * (size_t)B_BYTES +
-                         sizeof(double) * (kStages * (size_t)TM * SR + 2 * inv_slot_doubles(B));
+    const size_t bytes = 2 * (size_t)B_BYTES + sizeof(double) * 2 * inv_slot_doubles(B);
     cudaError_t e =
         cudaFuncSetAttribute(dwt_inverse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;  // persistent: one CTA per SM
+    int dev = 0, sms = 0;  // persistent: one CTA per SM (its 512 TMEM columns)
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
