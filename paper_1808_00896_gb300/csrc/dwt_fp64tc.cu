@@ -324,10 +324,11 @@ __device__ __forceinline__ void release_empty(PipeBars &pb, uint32_t gi) {
 __device__ __forceinline__ bool chunk_done(bool ok) { return tc::group_and(kBarConv, kConv, ok); }
 
 // Converter: wait for the chunk MMAs committed last.
-__device__ __forceinline__ bool converter_wait_mma(PipeBars &pb, uint32_t &mph) {
+// `ok` joins this thread's own verdict so far into the group's.
+__device__ __forceinline__ bool converter_wait_mma(PipeBars &pb, uint32_t &mph, bool ok = true) {
     const bool done = tc::mbar_wait(&pb.mma, mph, kWaitPolls);
     mph ^= 1u;
-    return tc::group_and(kBarConv, kConv, done);
+    return tc::group_and(kBarConv, kConv, done && ok);
 }
 
 // ---------------------------------------------------------------------------
@@ -742,29 +743,39 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
 // Inverse DWT, persistent as the forward: one CTA per SM walks the clusters
 // inv_order[blockIdx.x + k gridDim.x]; tiles of 128 beta samples, K chunks of
 // 32 degrees.  Here M = the beta samples = the TMEM lanes, so the A operand
-// (the Wigner-d digits) lives in tensor memory, and each producer -- the
-// thread of sample j, TMEM lane j -- cuts its own recurrence values into
-// digits and stores them with tcgen05.st, two degrees per 32-bit column;
-// there is no staging ring and the converters only build the B operand and
-// run the epilogue.  TMEM: accumulators in columns 0..111, A buffer a
-// (a = chunk & 1) in columns kAcol0 + a kAbufCols + 16 i + k / 2 for digit i
-// and chunk-relative degree k.  The set-up warp fills slot k & 1 with cluster
-// k's partner table, recurrence coefficients, digit exponents, the factors
-// V_l mu_t of its coefficients and the column scales of those products (the
-// largest magnitude of each of the 16 data columns over the degrees).
-// Hand-off: afull[a] (one arrival per producer warp after its tcgen05.st
-// completed), afree[a] (tcgen05.commit of the chunk's MMAs), ready and mma as
-// in the forward; every wait bounded.
-//   dynamic smem: B operand [2] | slot [2] { rA, rAc, rG [B doubles], alpha [B ints] }
+// (the Wigner-d digits) lives in tensor memory, and no shared-memory digit
+// planes are needed: the freed shared memory holds a deep staging ring.
+//   producers  (warps 0-3; thread t = sample jb + t) run the FP64 recurrence
+//              and stage 8 degrees per group in ring slot [t][8] (rows of 10
+//              doubles, the pad spreads them over the banks);
+//   converters (warps 4-11; warp 4 + q + 4 h takes lane quarter q and the
+//              groups g = h mod 2 of each chunk) read the values of their own
+//              lanes' samples, cut them into digits and store them with
+//              tcgen05.st, two degrees per 32-bit column; they also build the
+//              B operand (warps 8-11) and run the epilogue (warps 4-7);
+//   issuer and set-up warp as in the forward.
+// TMEM: accumulators in columns 0..111, A buffer a (a = chunk & 1) in columns
+// kAcol0 + a kAbufCols + 16 i + k / 2 for digit i and chunk-relative degree k.
+// The set-up warp fills slot k & 1 with cluster k's partner table, recurrence
+// coefficients, digit exponents, the factors V_l mu_t of its coefficients and
+// the column scales of those products (the largest magnitude of each of the 16
+// data columns over the degrees).  Hand-off: ring full (one arrival per
+// producer warp) / empty (one per converter warp that read the slot), afull[a]
+// (one arrival per converter warp after its tcgen05.st completed), afree[a]
+// (tcgen05.commit of the chunk's MMAs), ready and mma as in the forward;
+// every wait bounded.
+//   dynamic smem: B operand [2] | ring [kRingInv][128][10] | slot [2] { rA, rAc, rG [B doubles], alpha [B ints] }
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr size_t inv_slot_doubles(int B) { return 3 * (size_t)B + ((size_t)B + 1) / 2; }
 constexpr int kKCInv = 32;                        // degrees per K chunk of the inverse
 constexpr uint32_t kAcol0 = 128;                  // first TMEM column of the A buffers
 constexpr uint32_t kAbufCols = kDig * kKCInv / 2;  // 112 columns per A buffer
 constexpr uint32_t kTmemColsInv = 512;            // >= kAcol0 + 2 kAbufCols
+constexpr int kRingInv = 8;                       // staging ring depth of the inverse (groups of 8 degrees)
+constexpr int kRowInv = 10;                       // doubles per sample row of a ring slot (8 used)
 
 struct InvBars {
-    uint64_t afull[2], afree[2];
+    uint64_t afull[2], afree[2], full[kRingInv], empty[kRingInv];
 };
 
 // One K chunk of MMAs with A in tensor memory (issued by one thread): for each
@@ -802,7 +813,8 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     unsigned char *X = smem;  // [2][B_BYTES]
-    double *slotd = reinterpret_cast<double *>(X + 2 * B_BYTES);
+    double *ring = reinterpret_cast<double *>(X + 2 * B_BYTES);  // [kRingInv][TM][kRowInv]
+    double *slotd = ring + kRingInv * TM * kRowInv;
     const size_t SLOT = inv_slot_doubles(B);
     auto slot_rA = [&](int s) { return slotd + s * SLOT; };
     auto slot_rAc = [&](int s) { return slotd + s * SLOT + B; };
@@ -822,8 +834,12 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
     if (tid == 0) {
         init_pipe(pb);
         for (int a = 0; a < 2; ++a) {
-            tc::mbar_init(&ib.afull[a], kProd / 32);
+            tc::mbar_init(&ib.afull[a], kConv / 32);
             tc::mbar_init(&ib.afree[a], 1);
+        }
+        for (int r = 0; r < kRingInv; ++r) {
+            tc::mbar_init(&ib.full[r], kProd / 32);
+            tc::mbar_init(&ib.empty[r], kConv / 64);
         }
         for (int s2 = 0; s2 < 2; ++s2) {
             tc::mbar_init(&slot_full[s2], 32);
@@ -888,16 +904,11 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             tc::mbar_arrive(&slot_full[s]);
         }
     } else if (tid < kProd) {
-        // ---- producers: beta sample j = jb + t (TMEM lane t) walks the degrees ----
-        // Two stages in one basic block per group of 8 degrees: the FP64 recurrence
-        // of the next group and the digit cutting and TMEM stores of the current
-        // one, so that the integer work fills the dependent FMA chain's stalls.
+        // ---- producers: beta sample j = jb + t walks the degrees ----
         // Group counts and degree counts are warp-uniform (an idle lane's values
-        // are zero because its recurrence starts from zero), so every lane of a
-        // warp takes the same branches and meets each tcgen05.st.
+        // are zero because its recurrence starts from zero).
         const int t = tid;
-        const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
-        uint32_t cc = 0;
+        uint32_t gi = 0;
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
             if (!cluster_of(k, cidx, m, mp)) break;
@@ -905,134 +916,69 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             ok = __all_sync(0xffffffffu, tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls));
             if (!ok) break;
             const double *rA = slot_rA(s), *rAc = slot_rAc(s);
-            const int *ralpha = slot_alpha(s);
             const int nch = (L + KC - 1) / KC;  // K chunks of a tile
-            auto ngroups_of = [&](int c) { return 2 * ((min(KC, L - c * KC) + 15) / 16); };
             for (int jb = 0; jb < n && ok; jb += TM) {
                 const int j = jb + t;
                 double x = 0.0, dc = 0.0, dp = 0.0;
                 if (j < n) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
-                // stage 1: the 8 values of the group at degree l0 + q0 (nv valid, the rest 0)
-                auto recur = [&](double (&v)[8], int q0, int nv) {
-                    if (nv == 8) {
-                        // a whole group: straight-line code, the first FMA of a row two rows
-                        // ahead of the dependent second
-                        double ca[8], cb[8];
+                for (int c = 0; c < nch && ok; ++c) {
+                    const int cnt = min(KC, L - c * KC);
+                    const int ng = 2 * ((cnt + 15) / 16);  // groups of 8 degrees up to the padded K
+                    for (int g = 0; g < ng; ++g, ++gi) {
+                        const int r = gi % kRingInv;
+                        ok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.empty[r], ((gi / kRingInv) & 1) ^ 1u, kWaitPolls));
+                        if (!ok) break;
+                        double v[8];
+                        const int nv = max(0, min(8, cnt - 8 * g));  // degrees of this group
+                        const int q0 = c * KC + 8 * g;
+                        if (nv == 8) {
+                            // a whole group: straight-line code, no predicated FP64 work; the
+                            // first FMA of a row runs two rows ahead of the dependent second
+                            double ca[8], cb[8];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            ca[u] = rA[q0 + u];
-                            cb[u] = rAc[q0 + u];
-                        }
-                        double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
+                            for (int u = 0; u < 8; ++u) {
+                                ca[u] = rA[q0 + u];
+                                cb[u] = rAc[q0 + u];
+                            }
+                            double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            v[u] = dc;
-                            const double nx = fma(u0, dc, -dp);
-                            u0 = u1;
-                            if (u + 2 < 8) u1 = fma(ca[u + 2], x, -cb[u + 2]);
-                            dp = dc;
-                            dc = nx;
-                        }
-                    } else {  // the tile's last, partial group, or padding
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            v[u] = 0.0;
-                            if (u < nv) {
+                            for (int u = 0; u < 8; ++u) {
                                 v[u] = dc;
-                                const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
+                                const double nx = fma(u0, dc, -dp);
+                                u0 = u1;
+                                if (u + 2 < 8) u1 = fma(ca[u + 2], x, -cb[u + 2]);
                                 dp = dc;
                                 dc = nx;
                             }
+                        } else {  // the tile's last, partial group, or padding
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                v[u] = 0.0;
+                                if (u < nv) {
+                                    v[u] = dc;
+                                    const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
+                                    dp = dc;
+                                    dc = nx;
+                                }
+                            }
                         }
+                        double2 *st = reinterpret_cast<double2 *>(ring + ((size_t)r * TM + t) * kRowInv);
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) st[h] = make_double2(v[2 * h], v[2 * h + 1]);
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&ib.full[r]);
                     }
-                };
-                // stage 2: the group's digits, two degrees per 32-bit column (the lower
-                // degree in the low half), into columns 4 g .. 4 g + 3 of each digit plane
-                auto store = [&](const double (&v)[8], int q0, uint32_t acol, int g) {
-                    uint32_t pk[kDig][4];
-#pragma unroll
-                    for (int c2 = 0; c2 < 4; ++c2) {
-                        const int q = q0 + 2 * c2;
-                        uint32_t d0[kDig], d1[kDig];
-                        digits7(v[2 * c2], q < L ? ralpha[q] : 0, d0);
-                        digits7(v[2 * c2 + 1], q + 1 < L ? ralpha[q + 1] : 0, d1);
-#pragma unroll
-                        for (int i = 0; i < kDig; ++i) pk[i][c2] = __byte_perm(d0[i], d1[i], 0x7632);
-                    }
-#pragma unroll
-                    for (int i = 0; i < kDig; ++i)
-                        tc::tmem_st4(acol + 16 * i + 4 * g, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
-                };
-                // both stages for a whole next group, interleaved row by row in the source:
-                // row u of the recurrence, then the digits of value u of the stored group
-                auto recur_store = [&](double (&vn)[8], int qn, const double (&v)[8], int q0, uint32_t acol, int g) {
-                    double ca[8], cb[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        ca[u] = rA[qn + u];
-                        cb[u] = rAc[qn + u];
-                    }
-                    double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
-                    uint32_t pk[kDig][4], d0[kDig];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        vn[u] = dc;
-                        const double nx = fma(u0, dc, -dp);
-                        u0 = u1;
-                        if (u + 2 < 8) u1 = fma(ca[u + 2], x, -cb[u + 2]);
-                        dp = dc;
-                        dc = nx;
-                        const int q = q0 + u;
-                        if (u & 1) {
-                            uint32_t d1[kDig];
-                            digits7(v[u], q < L ? ralpha[q] : 0, d1);
-#pragma unroll
-                            for (int i = 0; i < kDig; ++i) pk[i][u >> 1] = __byte_perm(d0[i], d1[i], 0x7632);
-                        } else {
-                            digits7(v[u], q < L ? ralpha[q] : 0, d0);
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < kDig; ++i)
-                        tc::tmem_st4(acol + 16 * i + 4 * g, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
-                };
-                double vp[8];  // the values of the group in stage 2
-                recur(vp, 0, min(8, L));
-                for (int c = 0; c < nch && ok; ++c, ++cc) {
-                    const uint32_t a = cc & 1;
-                    // A buffer a is free once the MMAs of chunk cc - 2 completed
-                    ok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.afree[a], ((cc >> 1) & 1) ^ 1u, kWaitPolls));
-                    if (!ok) break;
-                    const int ng = ngroups_of(c);
-                    const uint32_t acol = tlane + kAcol0 + a * kAbufCols;
-                    for (int g = 0; g < ng; ++g) {
-                        // the next group: g + 1 of this chunk, else the first of the next chunk
-                        const int cn = g + 1 < ng ? c : c + 1, gn = g + 1 < ng ? g + 1 : 0;
-                        const int qn = cn * KC + 8 * gn;
-                        const int nvn = cn < nch ? max(0, min(8, min(KC, L - cn * KC) - 8 * gn)) : 0;
-                        double vn[8];
-                        if (nvn == 8) {
-                            recur_store(vn, qn, vp, c * KC + 8 * g, acol, g);
-                        } else {
-                            recur(vn, qn, nvn);
-                            store(vp, c * KC + 8 * g, acol, g);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) vp[u] = vn[u];
-                    }
-                    tc::tmem_wait_st();
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&ib.afull[a]);
                 }
             }
             if (ok) tc::mbar_arrive(&slot_empty[s]);  // this producer is done with the slot's tables
         }
     } else if (tid < kIssuer) {
-        // ---- converters: the B operand and the epilogue ----
+        // ---- converters: the A digits into TMEM, the B operand and the epilogue ----
         const int t = tid - kProd;
-        const int wq = warp & 3;
-        uint32_t mph = 0, cc = 0;
+        const int wq = warp & 3;              // TMEM lane quarter of this warp
+        const int ah = (warp - 4) >> 2;       // the groups g = ah mod 2 of each chunk are this warp's
+        const uint32_t tlane = tmem + ((uint32_t)(wq * 32) << 16);
+        uint32_t mph = 0, cc = 0, gi = 0;
         bool pending = false;
         // the tile whose last MMAs are pending (pjb >= 0) for the deferred epilogue, its
         // cluster's slot, and whether it is that cluster's last tile
@@ -1070,11 +1016,11 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             }
             tc::fence_before_sync();
         };
-        // B operand task of converter t < 128: column q2 (partner bp = q2 / 2, re or im),
-        // degrees lb + bk0 .. + 3 of a chunk.  The coefficients are loaded one
+        // B operand task of converter t >= 128 (warps 8-11): column q2 (partner bp = q2 / 2,
+        // re or im), degrees lb + bk0 .. + 3 of a chunk.  The coefficients are loaded one
         // (tile, chunk) step ahead, so their latency passes while the chunk runs.
         const int q2 = t & 15, bp = q2 >> 1, bk0 = 4 * ((t & 127) >> 4);
-        const bool btask = t < 128;
+        const bool btask = t >= 128;
         double cvn[4];
         auto load_cv = [&](const SlotHdr &h, int lb, int l0) {
             const int cnt = min(KC, B - lb);
@@ -1095,6 +1041,7 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             }
             const SlotHdr &h = hdr[s];
             const double *rG = slot_rG(s);
+            const int *ralpha = slot_alpha(s);
             for (int jb = 0; jb < n && ok; jb += TM) {
                 for (int lb = l0, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
                     const int cnt = min(KC, B - lb);
@@ -1121,8 +1068,50 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                     // the next step of this cluster: the next degree chunk, else the first of the next tile
                     have_cv = lb + KC < B || jb + TM < n;
                     if (have_cv) load_cv(h, lb + KC < B ? lb + KC : l0, l0);
+                    // A digits of this chunk's groups g = ah mod 2 into TMEM A buffer cc & 1 (free once
+                    // the MMAs of chunk cc - 2 completed), two degrees per 32-bit column
+                    {
+                        const uint32_t a = cc & 1;
+                        bool aok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.afree[a], ((cc >> 1) & 1) ^ 1u, kWaitPolls));
+                        const int ng = kfill / 8;
+                        const uint32_t acol = tlane + kAcol0 + a * kAbufCols;
+                        for (int g = ah; g < ng && aok; g += 2) {
+                            const uint32_t gg = gi + g, r = gg % kRingInv;
+                            aok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.full[r], (gg / kRingInv) & 1, kWaitPolls));
+                            if (!aok) break;
+                            const double2 *src = reinterpret_cast<const double2 *>(ring + ((size_t)r * TM + wq * 32 + lane) * kRowInv);
+                            double v[8];
+#pragma unroll
+                            for (int h2 = 0; h2 < 4; ++h2) {
+                                const double2 w2 = src[h2];
+                                v[2 * h2] = w2.x;
+                                v[2 * h2 + 1] = w2.y;
+                            }
+                            __syncwarp();
+                            if (lane == 0) tc::mbar_arrive(&ib.empty[r]);
+                            uint32_t pk[kDig][4];
+#pragma unroll
+                            for (int c2 = 0; c2 < 4; ++c2) {
+                                const int q = lb - l0 + 8 * g + 2 * c2;  // degree - l0
+                                uint32_t d0[kDig], d1[kDig];
+                                digits7(v[2 * c2], q < B - l0 ? ralpha[q] : 0, d0);
+                                digits7(v[2 * c2 + 1], q + 1 < B - l0 ? ralpha[q + 1] : 0, d1);
+#pragma unroll
+                                for (int i = 0; i < kDig; ++i) pk[i][c2] = __byte_perm(d0[i], d1[i], 0x7632);
+                            }
+#pragma unroll
+                            for (int i = 0; i < kDig; ++i)
+                                tc::tmem_st4(acol + 16 * i + 4 * g, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+                        }
+                        gi += ng;
+                        tc::tmem_wait_st();
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&ib.afull[a]);
+                        ok = ok && aok;
+                    }
                     if (pending) {
-                        ok = converter_wait_mma(pb, mph);
+                        ok = converter_wait_mma(pb, mph, ok);
                         pending = false;
                         if (!ok) break;
                         if (pjb >= 0) epilogue();
@@ -1145,8 +1134,8 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             ok = ok && done;
         }
     } else if (tid == kIssuer) {
-        // ---- issuer: the MMAs of every chunk once the converters (B operand, the
-        // previous tile's epilogue) and the producers (A digits in TMEM) are ready ----
+        // ---- issuer: the MMAs of every chunk once its B operand, the previous tile's
+        // epilogue (ready) and its A digits in TMEM (afull) are done ----
         uint32_t rph = 0, cc = 0;
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
@@ -1253,7 +1242,7 @@ cudaError_t launch_dwt_inverse_tc(const Tables &tb, const double2 *coef, double2
     if (!tb.seedtab || !tb.rectab) return cudaErrorInvalidValue;
     constexpr int B_BYTES = (kKCInv / 8) * (kNB * 16 + 16);
     const int B = tb.B;
-    const size_t bytes = 2 * (size_t)B_BYTES + sizeof(double) * 2 * inv_slot_doubles(B);
+    const size_t bytes = 2 * (size_t)B_BYTES + sizeof(double) * ((size_t)kRingInv * kProd * kRowInv + 2 * inv_slot_doubles(B));
     cudaError_t e =
         cudaFuncSetAttribute(dwt_inverse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
