@@ -746,10 +746,10 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
 // (the Wigner-d digits) lives in tensor memory, and no shared-memory digit
 // planes are needed: the freed shared memory holds a deep staging ring.
 //   producers  (warps 0-3; thread t = sample jb + t) run the FP64 recurrence
-//              and stage 8 degrees per group in ring slot [t][8] (rows of 10
-//              doubles, the pad spreads them over the banks);
+//              and stage 16 degrees (one MMA K step) per group in ring slot
+//              [t][16] (rows of 18 doubles, the pad spreads them over the banks);
 //   converters (warps 4-11; warp 4 + q + 4 h takes lane quarter q and the
-//              groups g = h mod 2 of each chunk) read the values of their own
+//              group g = h of each chunk) read the values of their own
 //              lanes' samples, cut them into digits and store them with
 //              tcgen05.st, two degrees per 32-bit column; they also build the
 //              B operand (warps 8-11) and run the epilogue (warps 4-7);
@@ -764,15 +764,15 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
 // (one arrival per converter warp after its tcgen05.st completed), afree[a]
 // (tcgen05.commit of the chunk's MMAs), ready and mma as in the forward;
 // every wait bounded.
-//   dynamic smem: B operand [2] | ring [kRingInv][128][10] | slot [2] { rA, rAc, rG [B doubles], alpha [B ints] }
+//   dynamic smem: B operand [2] | ring [kRingInv][128][18] | slot [2] { rA, rAc, rG [B doubles], alpha [B ints] }
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr size_t inv_slot_doubles(int B) { return 3 * (size_t)B + ((size_t)B + 1) / 2; }
 constexpr int kKCInv = 32;                        // degrees per K chunk of the inverse
 constexpr uint32_t kAcol0 = 128;                  // first TMEM column of the A buffers
 constexpr uint32_t kAbufCols = kDig * kKCInv / 2;  // 112 columns per A buffer
 constexpr uint32_t kTmemColsInv = 512;            // >= kAcol0 + 2 kAbufCols
-constexpr int kRingInv = 8;                       // staging ring depth of the inverse (groups of 8 degrees)
-constexpr int kRowInv = 10;                       // doubles per sample row of a ring slot (8 used)
+constexpr int kRingInv = 6;                       // staging ring depth of the inverse (groups of 16 degrees)
+constexpr int kRowInv = 18;                       // doubles per sample row of a ring slot (16 used)
 
 struct InvBars {
     uint64_t afull[2], afree[2], full[kRingInv], empty[kRingInv];
@@ -923,48 +923,51 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                 if (j < n) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
                 for (int c = 0; c < nch && ok; ++c) {
                     const int cnt = min(KC, L - c * KC);
-                    const int ng = 2 * ((cnt + 15) / 16);  // groups of 8 degrees up to the padded K
+                    const int ng = (cnt + 15) / 16;  // groups of 16 degrees up to the padded K
                     for (int g = 0; g < ng; ++g, ++gi) {
                         const int r = gi % kRingInv;
                         ok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.empty[r], ((gi / kRingInv) & 1) ^ 1u, kWaitPolls));
                         if (!ok) break;
-                        double v[8];
-                        const int nv = max(0, min(8, cnt - 8 * g));  // degrees of this group
-                        const int q0 = c * KC + 8 * g;
-                        if (nv == 8) {
-                            // a whole group: straight-line code, no predicated FP64 work; the
-                            // first FMA of a row runs two rows ahead of the dependent second
-                            double ca[8], cb[8];
+                        double2 *st = reinterpret_cast<double2 *>(ring + ((size_t)r * TM + t) * kRowInv);
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                ca[u] = rA[q0 + u];
-                                cb[u] = rAc[q0 + u];
-                            }
-                            double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
+                        for (int hh = 0; hh < 16; hh += 8) {  // halves of 8 degrees
+                            double v[8];
+                            const int nv = max(0, min(8, cnt - 16 * g - hh));  // degrees of this half
+                            const int q0 = c * KC + 16 * g + hh;
+                            if (nv == 8) {
+                                // a whole half: straight-line code, no predicated FP64 work; the
+                                // first FMA of a row runs two rows ahead of the dependent second
+                                double ca[8], cb[8];
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                v[u] = dc;
-                                const double nx = fma(u0, dc, -dp);
-                                u0 = u1;
-                                if (u + 2 < 8) u1 = fma(ca[u + 2], x, -cb[u + 2]);
-                                dp = dc;
-                                dc = nx;
-                            }
-                        } else {  // the tile's last, partial group, or padding
+                                for (int u = 0; u < 8; ++u) {
+                                    ca[u] = rA[q0 + u];
+                                    cb[u] = rAc[q0 + u];
+                                }
+                                double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                v[u] = 0.0;
-                                if (u < nv) {
+                                for (int u = 0; u < 8; ++u) {
                                     v[u] = dc;
-                                    const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
+                                    const double nx = fma(u0, dc, -dp);
+                                    u0 = u1;
+                                    if (u + 2 < 8) u1 = fma(ca[u + 2], x, -cb[u + 2]);
                                     dp = dc;
                                     dc = nx;
                                 }
-                            }
-                        }
-                        double2 *st = reinterpret_cast<double2 *>(ring + ((size_t)r * TM + t) * kRowInv);
+                            } else {  // the tile's last, partial half, or padding
 #pragma unroll
-                        for (int h = 0; h < 4; ++h) st[h] = make_double2(v[2 * h], v[2 * h + 1]);
+                                for (int u = 0; u < 8; ++u) {
+                                    v[u] = 0.0;
+                                    if (u < nv) {
+                                        v[u] = dc;
+                                        const double nx = fma(fma(rA[q0 + u], x, -rAc[q0 + u]), dc, -dp);
+                                        dp = dc;
+                                        dc = nx;
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) st[hh / 2 + h] = make_double2(v[2 * h], v[2 * h + 1]);
+                        }
                         __syncwarp();
                         if (lane == 0) tc::mbar_arrive(&ib.full[r]);
                     }
@@ -1068,40 +1071,43 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                     // the next step of this cluster: the next degree chunk, else the first of the next tile
                     have_cv = lb + KC < B || jb + TM < n;
                     if (have_cv) load_cv(h, lb + KC < B ? lb + KC : l0, l0);
-                    // A digits of this chunk's groups g = ah mod 2 into TMEM A buffer cc & 1 (free once
+                    // A digits of this chunk's group g = ah into TMEM A buffer cc & 1 (free once
                     // the MMAs of chunk cc - 2 completed), two degrees per 32-bit column
                     {
                         const uint32_t a = cc & 1;
                         bool aok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.afree[a], ((cc >> 1) & 1) ^ 1u, kWaitPolls));
-                        const int ng = kfill / 8;
+                        const int ng = kfill / 16;
                         const uint32_t acol = tlane + kAcol0 + a * kAbufCols;
                         for (int g = ah; g < ng && aok; g += 2) {
                             const uint32_t gg = gi + g, r = gg % kRingInv;
                             aok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.full[r], (gg / kRingInv) & 1, kWaitPolls));
                             if (!aok) break;
                             const double2 *src = reinterpret_cast<const double2 *>(ring + ((size_t)r * TM + wq * 32 + lane) * kRowInv);
-                            double v[8];
+                            double v[16];
 #pragma unroll
-                            for (int h2 = 0; h2 < 4; ++h2) {
+                            for (int h2 = 0; h2 < 8; ++h2) {
                                 const double2 w2 = src[h2];
                                 v[2 * h2] = w2.x;
                                 v[2 * h2 + 1] = w2.y;
                             }
                             __syncwarp();
                             if (lane == 0) tc::mbar_arrive(&ib.empty[r]);
-                            uint32_t pk[kDig][4];
 #pragma unroll
-                            for (int c2 = 0; c2 < 4; ++c2) {
-                                const int q = lb - l0 + 8 * g + 2 * c2;  // degree - l0
-                                uint32_t d0[kDig], d1[kDig];
-                                digits7(v[2 * c2], q < B - l0 ? ralpha[q] : 0, d0);
-                                digits7(v[2 * c2 + 1], q + 1 < B - l0 ? ralpha[q + 1] : 0, d1);
+                            for (int hh = 0; hh < 16; hh += 8) {
+                                uint32_t pk[kDig][4];
 #pragma unroll
-                                for (int i = 0; i < kDig; ++i) pk[i][c2] = __byte_perm(d0[i], d1[i], 0x7632);
+                                for (int c2 = 0; c2 < 4; ++c2) {
+                                    const int q = lb - l0 + 16 * g + hh + 2 * c2;  // degree - l0
+                                    uint32_t d0[kDig], d1[kDig];
+                                    digits7(v[hh + 2 * c2], q < B - l0 ? ralpha[q] : 0, d0);
+                                    digits7(v[hh + 2 * c2 + 1], q + 1 < B - l0 ? ralpha[q + 1] : 0, d1);
+#pragma unroll
+                                    for (int i = 0; i < kDig; ++i) pk[i][c2] = __byte_perm(d0[i], d1[i], 0x7632);
+                                }
+#pragma unroll
+                                for (int i = 0; i < kDig; ++i)
+                                    tc::tmem_st4(acol + 16 * i + 8 * g + hh / 2, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
                             }
-#pragma unroll
-                            for (int i = 0; i < kDig; ++i)
-                                tc::tmem_st4(acol + 16 * i + 4 * g, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
                         }
                         gi += ng;
                         tc::tmem_wait_st();
