@@ -741,49 +741,61 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
 
 // ---------------------------------------------------------------------------
 // Inverse DWT, persistent as the forward: one CTA per SM walks the clusters
-// inv_order[blockIdx.x + k gridDim.x]; tiles of 128 beta samples, K chunks of
-// 32 degrees.  Here M = the beta samples = the TMEM lanes, so the A operand
-// (the Wigner-d digits) lives in tensor memory, and no shared-memory digit
-// planes are needed: the freed shared memory holds a deep staging ring.
-//   producers  (warps 0-3; thread t = sample jb + t) run the FP64 recurrence
-//              and stage 16 degrees (one MMA K step) per group in ring slot
-//              [t][16] (rows of 18 doubles, the pad spreads them over the banks);
-//   converters (warps 4-11; warp 4 + q + 4 h takes lane quarter q and the
-//              group g = h of each chunk) read the values of their own
-//              lanes' samples, cut them into digits and store them with
-//              tcgen05.st, two degrees per 32-bit column; they also build the
-//              B operand (warps 8-11) and run the epilogue (warps 4-7);
-//   issuer and set-up warp as in the forward.
-// TMEM: accumulators in columns 0..111, A buffer a (a = chunk & 1) in columns
-// kAcol0 + a kAbufCols + 16 i + k / 2 for digit i and chunk-relative degree k.
+// inv_order[blockIdx.x + k gridDim.x].  M = the beta samples = the TMEM lanes,
+// so the A operand (the Wigner-d digits) lives in tensor memory; the shared
+// memory that the forward spends on digit planes holds staging rings instead.
+// Two tiles of 128 beta samples are in flight (tile slot tau = 0, 1; samples
+// jb0 + 128 tau + 0..127 of a pair of tiles), K chunks of 32 degrees:
+//   producers  (warps 0-7; warp w takes tile slot w / 4, two warps per
+//              scheduler) run the FP64 recurrence of one sample per thread and
+//              stage 16 degrees (one MMA K step) per group in their tile's ring
+//              slot [128][18] (16 used; the pad spreads the rows over the banks);
+//   converters (warps 8-15; warp 8 + 4 tau + q takes tile slot tau and TMEM
+//              lane quarter q) read their own lanes' staged values, cut them
+//              into digits and store them with tcgen05.st, two degrees per
+//              32-bit column; they run their tile's epilogue, and warps 12-15
+//              build the B operand (shared by both tiles: one cluster);
+//   issuer     (lane 0 of warp 16) and set-up warp (warp 17) as in the forward.
+// TMEM: tile tau's accumulators in columns 128 tau + 0..111, its A buffer in
+// columns kAcolInv + tau kAbufCols + 16 i + k / 2 (digit i, chunk-relative
+// degree k).  Per step (one chunk of both tiles): converters wait for their
+// tile's previous MMAs (mdone[tau]) and run a closed tile's epilogue; all
+// converters meet (so the other tile's MMAs and the B buffers are done too)
+// and signal `ready`; they write the next step's B operand and then this
+// step's A digits (afull[tau]).  The issuer waits for ready and afull[0],
+// issues tile 0's MMAs (committed to mdone[0]), then waits for afull[1] and
+// issues tile 1's.  Both tiles of a pair share each chunk's B operand, and a
+// pair's second tile past the last sample runs on zeros (it is not stored).
 // The set-up warp fills slot k & 1 with cluster k's partner table, recurrence
 // coefficients, digit exponents, the factors V_l mu_t of its coefficients and
 // the column scales of those products (the largest magnitude of each of the 16
-// data columns over the degrees).  Hand-off: ring full (one arrival per
-// producer warp) / empty (one per converter warp that read the slot), afull[a]
-// (one arrival per converter warp after its tcgen05.st completed), afree[a]
-// (tcgen05.commit of the chunk's MMAs), ready and mma as in the forward;
-// every wait bounded.
-//   dynamic smem: B operand [2] | ring [kRingInv][128][18] | slot [2] { rA, rAc, rG [B doubles], alpha [B ints] }
+// data columns over the degrees).  Every wait bounded.
+//   dynamic smem: B operand [2] | rings [2][kRingInv][128][kRowInv] |
+//                 slot [2] { rA, rAc, rG [B doubles], alpha [B ints] }
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr size_t inv_slot_doubles(int B) { return 3 * (size_t)B + ((size_t)B + 1) / 2; }
-constexpr int kKCInv = 32;                        // degrees per K chunk of the inverse
-constexpr uint32_t kAcol0 = 128;                  // first TMEM column of the A buffers
-constexpr uint32_t kAbufCols = kDig * kKCInv / 2;  // 112 columns per A buffer
-constexpr uint32_t kTmemColsInv = 512;            // >= kAcol0 + 2 kAbufCols
-constexpr int kRingInv = 6;                       // staging ring depth of the inverse (groups of 16 degrees)
-constexpr int kRowInv = 18;                       // doubles per sample row of a ring slot (16 used)
+constexpr int kKCInv = 32;                         // degrees per K chunk of the inverse
+constexpr uint32_t kAbufCols = kDig * kKCInv / 2;  // 112 TMEM columns per A buffer
+constexpr uint32_t kAcolInv = 256;                 // first TMEM column of the A buffers
+constexpr uint32_t kTmemColsInv = 512;             // >= kAcolInv + 2 kAbufCols
+constexpr int kRingInv = 3;                        // staging ring depth per tile (groups of 16 degrees)
+constexpr int kRowInv = 18;                        // doubles per sample row of a ring slot (16 used)
+constexpr int kProdInv = 256;                      // producer threads (warps 0-7)
+constexpr int kConvInv = 256;                      // converter threads (warps 8-15)
+constexpr int kIssuerInv = kProdInv + kConvInv;    // lane 0 of warp 16
+constexpr int kSetupInv = kIssuerInv + 32;         // warp 17
+constexpr int kThreadsInv = kSetupInv + 32;        // 576 threads
 
 struct InvBars {
-    uint64_t afull[2], afree[2], full[kRingInv], empty[kRingInv];
+    uint64_t full[2][kRingInv], empty[2][kRingInv], afull[2], mdone[2], ready;
 };
 
 // One K chunk of MMAs with A in tensor memory (issued by one thread): for each
 // K step of 16 degrees, A digit i (TMEM columns acol + 16 i + 8 s ..) against
-// B digits 0..6-i into accumulator columns 16 i ..; completion committed to
-// both mbarriers.
-__device__ __forceinline__ void issue_levels_ta(uint32_t tmem, uint32_t acol, const unsigned char *Bop, uint32_t b_lbo,
-                                                bool first, int ksteps, uint64_t *mbar, uint64_t *mbar2) {
+// B digits 0..6-i into accumulator columns dcol + 16 i ..; completion
+// committed to mbar.
+__device__ __forceinline__ void issue_levels_ta(uint32_t tmem, uint32_t dcol, uint32_t acol, const unsigned char *Bop,
+                                                uint32_t b_lbo, bool first, int ksteps, uint64_t *mbar) {
     tc::fence_after_sync();
     const uint64_t bd0 = tc::smem_desc(tc::smem_u32(Bop), b_lbo, 128);
     for (int s = 0; s < ksteps; ++s) {
@@ -792,34 +804,36 @@ __device__ __forceinline__ void issue_levels_ta(uint32_t tmem, uint32_t acol, co
         for (int i = 0; i < kDig; ++i) {
             constexpr uint32_t kIdesc0 = tc::instr_desc(1, 128, kCols * kDig);
             const uint32_t idesc = kIdesc0 - ((uint32_t)(kCols * i) >> 3 << 17);  // N = 16 (7 - i)
-            tc::mma_bf16_ta(tmem + kCols * i, tmem + acol + 16 * i + 8 * s, bd, idesc,
+            tc::mma_bf16_ta(tmem + dcol + kCols * i, tmem + acol + 16 * i + 8 * s, bd, idesc,
                             (first && s == 0 && i == 0) ? 0u : 1u);
         }
     }
     tc::mma_commit(mbar);
-    tc::mma_commit(mbar2);
 }
 
-__global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables tb, const double *__restrict__ coef,
+__global__ void __launch_bounds__(kThreadsInv, 1) dwt_inverse_tc_kernel(Tables tb, const double *__restrict__ coef,
                                                                         double2 *__restrict__ S, int flags) {
-    constexpr int TM = kProd, KC = kKCInv;
+    constexpr int TM = 128, KC = kKCInv;
     constexpr int B_LBO = kNB * 16 + 16, B_BYTES = (KC / 8) * B_LBO;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ SlotHdr hdr[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ __align__(8) PipeBars pb;
     __shared__ __align__(8) InvBars ib;
     __shared__ __align__(8) uint64_t slot_full[2], slot_empty[2];
     const int B = tb.B, n = 2 * B, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int npairs = (n + 2 * TM - 1) / (2 * TM);  // pairs of sample tiles per cluster
 
     unsigned char *X = smem;  // [2][B_BYTES]
-    double *ring = reinterpret_cast<double *>(X + 2 * B_BYTES);  // [kRingInv][TM][kRowInv]
-    double *slotd = ring + kRingInv * TM * kRowInv;
+    double *ring = reinterpret_cast<double *>(X + 2 * B_BYTES);  // [2][kRingInv][TM][kRowInv]
+    double *slotd = ring + 2 * kRingInv * TM * kRowInv;
     const size_t SLOT = inv_slot_doubles(B);
     auto slot_rA = [&](int s) { return slotd + s * SLOT; };
     auto slot_rAc = [&](int s) { return slotd + s * SLOT + B; };
     auto slot_rG = [&](int s) { return slotd + s * SLOT + 2 * B; };
     auto slot_alpha = [&](int s) { return reinterpret_cast<int *>(slotd + s * SLOT + 3 * B); };
+    auto ring_row = [&](int tau, int r, int row) {
+        return ring + (((size_t)tau * kRingInv + r) * TM + row) * kRowInv;
+    };
     auto cluster_of = [&](int k, int &cidx, int &m, int &mp) {
         const int idx = blockIdx.x + k * gridDim.x;
         if (idx >= tb.ncl) return false;
@@ -832,18 +846,18 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
 
     if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemColsInv);
     if (tid == 0) {
-        init_pipe(pb);
-        for (int a = 0; a < 2; ++a) {
-            tc::mbar_init(&ib.afull[a], kConv / 32);
-            tc::mbar_init(&ib.afree[a], 1);
+        for (int tau = 0; tau < 2; ++tau) {
+            for (int r = 0; r < kRingInv; ++r) {
+                tc::mbar_init(&ib.full[tau][r], 4);   // the tile's 4 producer warps
+                tc::mbar_init(&ib.empty[tau][r], 4);  // the tile's 4 converter warps
+            }
+            tc::mbar_init(&ib.afull[tau], 4);
+            tc::mbar_init(&ib.mdone[tau], 1);
         }
-        for (int r = 0; r < kRingInv; ++r) {
-            tc::mbar_init(&ib.full[r], kProd / 32);
-            tc::mbar_init(&ib.empty[r], kConv / 64);
-        }
+        tc::mbar_init(&ib.ready, 1);
         for (int s2 = 0; s2 < 2; ++s2) {
             tc::mbar_init(&slot_full[s2], 32);
-            tc::mbar_init(&slot_empty[s2], kProd + kConv);
+            tc::mbar_init(&slot_empty[s2], kProdInv + kConvInv);
         }
     }
     tc::fence_before_sync();
@@ -852,7 +866,7 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
     const uint32_t tmem = tmem_slot;
     bool ok = true;
 
-    if (warp == kSetup / 32) {
+    if (warp == kSetupInv / 32) {
         // ---- set-up: the tables of cluster k into slot k & 1 ----
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
@@ -903,11 +917,11 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             }
             tc::mbar_arrive(&slot_full[s]);
         }
-    } else if (tid < kProd) {
-        // ---- producers: beta sample j = jb + t walks the degrees ----
+    } else if (tid < kProdInv) {
+        // ---- producers: sample jb0 + 128 tau + tp walks the degrees ----
         // Group counts and degree counts are warp-uniform (an idle lane's values
         // are zero because its recurrence starts from zero).
-        const int t = tid;
+        const int tau = warp >> 2, tp = tid & 127;
         uint32_t gi = 0;
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
@@ -917,8 +931,8 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
             if (!ok) break;
             const double *rA = slot_rA(s), *rAc = slot_rAc(s);
             const int nch = (L + KC - 1) / KC;  // K chunks of a tile
-            for (int jb = 0; jb < n && ok; jb += TM) {
-                const int j = jb + t;
+            for (int jp = 0; jp < npairs && ok; ++jp) {
+                const int j = 2 * TM * jp + TM * tau + tp;
                 double x = 0.0, dc = 0.0, dp = 0.0;
                 if (j < n) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
                 for (int c = 0; c < nch && ok; ++c) {
@@ -926,9 +940,10 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                     const int ng = (cnt + 15) / 16;  // groups of 16 degrees up to the padded K
                     for (int g = 0; g < ng; ++g, ++gi) {
                         const int r = gi % kRingInv;
-                        ok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.empty[r], ((gi / kRingInv) & 1) ^ 1u, kWaitPolls));
+                        ok = __all_sync(0xffffffffu,
+                                        tc::mbar_wait(&ib.empty[tau][r], ((gi / kRingInv) & 1) ^ 1u, kWaitPolls));
                         if (!ok) break;
-                        double2 *st = reinterpret_cast<double2 *>(ring + ((size_t)r * TM + t) * kRowInv);
+                        double2 *st = reinterpret_cast<double2 *>(ring_row(tau, r, tp));
 #pragma unroll
                         for (int hh = 0; hh < 16; hh += 8) {  // halves of 8 degrees
                             double v[8];
@@ -969,193 +984,183 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_inverse_tc_kernel(Tables t
                             for (int h = 0; h < 4; ++h) st[hh / 2 + h] = make_double2(v[2 * h], v[2 * h + 1]);
                         }
                         __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&ib.full[r]);
+                        if (lane == 0) tc::mbar_arrive(&ib.full[tau][r]);
                     }
                 }
             }
             if (ok) tc::mbar_arrive(&slot_empty[s]);  // this producer is done with the slot's tables
         }
-    } else if (tid < kIssuer) {
-        // ---- converters: the A digits into TMEM, the B operand and the epilogue ----
-        const int t = tid - kProd;
-        const int wq = warp & 3;              // TMEM lane quarter of this warp
-        const int ah = (warp - 4) >> 2;       // the groups g = ah mod 2 of each chunk are this warp's
+    } else if (tid < kIssuerInv) {
+        // ---- converters: A digits into TMEM, the epilogue, the B operand ----
+        const int t = tid - kProdInv;             // 0..255
+        const int tau = (warp - 8) >> 2, wq = warp & 3;
+        const int tl = wq * 32 + lane;            // this thread's TMEM lane = sample within the tile
         const uint32_t tlane = tmem + ((uint32_t)(wq * 32) << 16);
         uint32_t mph = 0, cc = 0, gi = 0;
         bool pending = false;
-        // the tile whose last MMAs are pending (pjb >= 0) for the deferred epilogue, its
-        // cluster's slot, and whether it is that cluster's last tile
+        // the tile pair whose last MMAs are pending (pjb >= 0: its first sample) for the
+        // deferred epilogue, its cluster's slot, and whether it is that cluster's last pair
         int pjb = -1, pslot = 0;
         bool plast = false;
         auto epilogue = [&]() {
-            // Beta sample pjb + t sits in TMEM lane t (warps 4-7).
+            // Sample pjb + 128 tau + tl sits in TMEM lane tl of tile tau's accumulators.
             tc::fence_after_sync();
-            if (t < 128) {
-                const SlotHdr &h = hdr[pslot];
-                const int np = h.cs.np;
-                const bool real = (flags & kRealSym) && np > 1;
-                const int jt = pjb + t;
-                double v16[kCols];
-                epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), h.colexp, v16);
-                if (jt < n) {
+            const SlotHdr &h = hdr[pslot];
+            const int np = h.cs.np;
+            const bool real = (flags & kRealSym) && np > 1;
+            const int jt = pjb + TM * tau + tl;
+            double v16[kCols];
+            epilogue_levels(tlane + 128 * tau, h.colexp, v16);
+            if (jt < n) {
 #pragma unroll
-                    for (int p = 0; p < 8; ++p) {
-                        if (p >= np) break;
-                        if (real && (p & 1)) continue;  // written from its pair below
-                        const int jj = h.cs.mir[p] ? n - 1 - jt : jt;
-                        double re = v16[2 * p], im = v16[2 * p + 1];
-                        if (flags & kApplyW) {
-                            const double wj = tb.w[jj];
-                            re *= wj;
-                            im *= wj;
-                        }
-                        S[((int64_t)jj * n + mod_n(h.cs.pm[p], n)) * n + mod_n(h.cs.pmp[p], n)] =
-                            make_double2(re, im);
-                        if (real)  // partner p + 1 = (-m, -m'): the conjugate, at the same beta sample
-                            S[((int64_t)jj * n + mod_n(h.cs.pm[p + 1], n)) * n + mod_n(h.cs.pmp[p + 1], n)] =
-                                make_double2(re, -im);
+                for (int p = 0; p < 8; ++p) {
+                    if (p >= np) break;
+                    if (real && (p & 1)) continue;  // written from its pair below
+                    const int jj = h.cs.mir[p] ? n - 1 - jt : jt;
+                    double re = v16[2 * p], im = v16[2 * p + 1];
+                    if (flags & kApplyW) {
+                        const double wj = tb.w[jj];
+                        re *= wj;
+                        im *= wj;
                     }
+                    S[((int64_t)jj * n + mod_n(h.cs.pm[p], n)) * n + mod_n(h.cs.pmp[p], n)] = make_double2(re, im);
+                    if (real)  // partner p + 1 = (-m, -m'): the conjugate, at the same beta sample
+                        S[((int64_t)jj * n + mod_n(h.cs.pm[p + 1], n)) * n + mod_n(h.cs.pmp[p + 1], n)] =
+                            make_double2(re, -im);
                 }
             }
             tc::fence_before_sync();
         };
-        // B operand task of converter t >= 128 (warps 8-11): column q2 (partner bp = q2 / 2,
-        // re or im), degrees lb + bk0 .. + 3 of a chunk.  The coefficients are loaded one
-        // (tile, chunk) step ahead, so their latency passes while the chunk runs.
-        const int q2 = t & 15, bp = q2 >> 1, bk0 = 4 * ((t & 127) >> 4);
+        // B operand task of warps 12-15 (bt = 0..127): column q2 (partner bp = q2 / 2, re
+        // or im), degrees bk0 .. + 3 of a chunk, written one step ahead of its MMAs
+        const int bt = t - 128, q2 = bt & 15, bp = q2 >> 1, bk0 = 4 * ((bt & 127) >> 4);
         const bool btask = t >= 128;
-        double cvn[4];
-        auto load_cv = [&](const SlotHdr &h, int lb, int l0) {
-            const int cnt = min(KC, B - lb);
-            const bool used = btask && bp < h.cs.np && !((flags & kRealSym) && h.cs.np > 1 && (bp & 1));
+        auto put_b = [&](const SlotHdr &h, const double *rG, int lb, int l0, unsigned char *Xb) {
+            if (!btask) return;
+            const int cnt = min(KC, B - lb), kfill = (cnt + 15) / 16 * 16;
+            if (bk0 >= kfill) return;
+            const bool used = bp < h.cs.np && !((flags & kRealSym) && h.cs.np > 1 && (bp & 1));
+            // F = sign_p(l) V_l mu_t f(l, m_p, m'_p), formed here in FP64
+            double v[4];
+            int al[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                cvn[u] = used && bk0 + u < cnt ? coef[2 * (h.cs.off[bp] + lb + bk0 + u - l0) + (q2 & 1)] : 0.0;
+            for (int u = 0; u < 4; ++u) {
+                al[u] = -h.colexp[q2];
+                const int kk = bk0 + u;
+                v[u] = 0.0;
+                if (used && kk < cnt) {
+                    const int q = lb + kk - l0, l = lb + kk;
+                    const bool neg = (h.cs.sign[bp] < 0.0) != (h.cs.lpar[bp] && (l & 1));
+                    v[u] = (neg ? -rG[q] : rG[q]) * coef[2 * (h.cs.off[bp] + q) + (q2 & 1)];
+                }
+            }
+            put_digits4(Xb, 16 * kCols, B_LBO, q2, bk0, v, al);
+            tc::fence_proxy_async();
         };
-        bool have_cv = false;  // cvn holds the next step's coefficients
+        bool b_ready = false;  // the current step's B operand is written
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
             if (!cluster_of(k, cidx, m, mp)) break;
             const int s = k & 1, l0 = m;
             {
                 const bool done = tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls);
-                ok = tc::group_and(kBarConv, kConv, done);
+                ok = tc::group_and(kBarConv, kConvInv, done);
                 if (!ok) break;
             }
             const SlotHdr &h = hdr[s];
             const double *rG = slot_rG(s);
             const int *ralpha = slot_alpha(s);
-            for (int jb = 0; jb < n && ok; jb += TM) {
+            for (int jp = 0; jp < npairs && ok; ++jp) {
                 for (int lb = l0, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
                     const int cnt = min(KC, B - lb);
-                    const int kfill = (cnt + 15) / 16 * 16;
-                    unsigned char *Xc = X + (cc & 1) * B_BYTES;
-                    if (!have_cv) load_cv(h, lb, l0);  // the cluster's first step
-                    if (btask && bk0 < kfill) {
-                        // F = sign_p(l) V_l mu_t f(l, m_p, m'_p), formed here in FP64
-                        double v[4];
-                        int al[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            al[u] = -h.colexp[q2];
-                            const int kk = bk0 + u;
-                            v[u] = 0.0;
-                            if (kk < cnt) {
-                                const int q = lb + kk - l0, l = lb + kk;
-                                const bool neg = (h.cs.sign[bp] < 0.0) != (h.cs.lpar[bp] && (l & 1));
-                                v[u] = (neg ? -rG[q] : rG[q]) * cvn[u];
-                            }
-                        }
-                        put_digits4(Xc, 16 * kCols, B_LBO, q2, bk0, v, al);
-                    }
-                    // the next step of this cluster: the next degree chunk, else the first of the next tile
-                    have_cv = lb + KC < B || jb + TM < n;
-                    if (have_cv) load_cv(h, lb + KC < B ? lb + KC : l0, l0);
-                    // A digits of this chunk's group g = ah into TMEM A buffer cc & 1 (free once
-                    // the MMAs of chunk cc - 2 completed), two degrees per 32-bit column
-                    {
-                        const uint32_t a = cc & 1;
-                        bool aok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.afree[a], ((cc >> 1) & 1) ^ 1u, kWaitPolls));
-                        const int ng = kfill / 16;
-                        const uint32_t acol = tlane + kAcol0 + a * kAbufCols;
-                        for (int g = ah; g < ng && aok; g += 2) {
-                            const uint32_t gg = gi + g, r = gg % kRingInv;
-                            aok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.full[r], (gg / kRingInv) & 1, kWaitPolls));
-                            if (!aok) break;
-                            const double2 *src = reinterpret_cast<const double2 *>(ring + ((size_t)r * TM + wq * 32 + lane) * kRowInv);
-                            double v[16];
-#pragma unroll
-                            for (int h2 = 0; h2 < 8; ++h2) {
-                                const double2 w2 = src[h2];
-                                v[2 * h2] = w2.x;
-                                v[2 * h2 + 1] = w2.y;
-                            }
-                            __syncwarp();
-                            if (lane == 0) tc::mbar_arrive(&ib.empty[r]);
-#pragma unroll
-                            for (int hh = 0; hh < 16; hh += 8) {
-                                uint32_t pk[kDig][4];
-#pragma unroll
-                                for (int c2 = 0; c2 < 4; ++c2) {
-                                    const int q = lb - l0 + 16 * g + hh + 2 * c2;  // degree - l0
-                                    uint32_t d0[kDig], d1[kDig];
-                                    digits7(v[hh + 2 * c2], q < B - l0 ? ralpha[q] : 0, d0);
-                                    digits7(v[hh + 2 * c2 + 1], q + 1 < B - l0 ? ralpha[q + 1] : 0, d1);
-#pragma unroll
-                                    for (int i = 0; i < kDig; ++i) pk[i][c2] = __byte_perm(d0[i], d1[i], 0x7632);
-                                }
-#pragma unroll
-                                for (int i = 0; i < kDig; ++i)
-                                    tc::tmem_st4(acol + 16 * i + 8 * g + hh / 2, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
-                            }
-                        }
-                        gi += ng;
-                        tc::tmem_wait_st();
-                        tc::fence_before_sync();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&ib.afull[a]);
-                        ok = ok && aok;
-                    }
-                    if (pending) {
-                        ok = converter_wait_mma(pb, mph, ok);
+                    const int ng = (cnt + 15) / 16;
+                    bool wok = true;
+                    if (pending) {  // this tile's previous MMAs; the epilogue if they closed a tile pair
+                        wok = tc::mbar_wait(&ib.mdone[tau], mph, kWaitPolls);
+                        mph ^= 1u;
                         pending = false;
-                        if (!ok) break;
-                        if (pjb >= 0) epilogue();
-                        if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
+                        if (wok && pjb >= 0) epilogue();
                     }
-                    tc::fence_proxy_async();
-                    ok = chunk_done(ok);
+                    if (!b_ready) put_b(h, rG, lb, l0, X + (cc & 1) * B_BYTES);  // the cluster's first step
+                    // both tiles' previous MMAs and epilogues and this step's B operand are done
+                    ok = tc::group_and(kBarConv, kConvInv, ok && wok);
                     if (!ok) break;
-                    if (t == 0) tc::mbar_arrive(&pb.ready);
+                    if (t == 0) tc::mbar_arrive(&ib.ready);
+                    // the next step's B operand (the other buffer, free now): the next degree
+                    // chunk, else the first of the next tile pair
+                    b_ready = lb + KC < B || jp + 1 < npairs;
+                    if (b_ready) put_b(h, rG, lb + KC < B ? lb + KC : l0, l0, X + ((cc + 1) & 1) * B_BYTES);
+                    // this tile's A digits (its buffer is free: its previous MMAs are done)
+                    bool aok = true;
+                    const uint32_t acol = tlane + kAcolInv + tau * kAbufCols;
+                    for (int g = 0; g < ng && aok; ++g) {
+                        const uint32_t gg = gi + g, r = gg % kRingInv;
+                        aok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.full[tau][r], (gg / kRingInv) & 1, kWaitPolls));
+                        if (!aok) break;
+                        const double2 *src = reinterpret_cast<const double2 *>(ring_row(tau, r, tl));
+                        double v[16];
+#pragma unroll
+                        for (int h2 = 0; h2 < 8; ++h2) {
+                            const double2 w2 = src[h2];
+                            v[2 * h2] = w2.x;
+                            v[2 * h2 + 1] = w2.y;
+                        }
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&ib.empty[tau][r]);
+#pragma unroll
+                        for (int hh = 0; hh < 16; hh += 8) {
+                            uint32_t pk[kDig][4];
+#pragma unroll
+                            for (int c2 = 0; c2 < 4; ++c2) {
+                                const int q = lb - l0 + 16 * g + hh + 2 * c2;  // degree - l0
+                                uint32_t d0[kDig], d1[kDig];
+                                digits7(v[hh + 2 * c2], q < B - l0 ? ralpha[q] : 0, d0);
+                                digits7(v[hh + 2 * c2 + 1], q + 1 < B - l0 ? ralpha[q + 1] : 0, d1);
+#pragma unroll
+                                for (int i = 0; i < kDig; ++i) pk[i][c2] = __byte_perm(d0[i], d1[i], 0x7632);
+                            }
+#pragma unroll
+                            for (int i = 0; i < kDig; ++i)
+                                tc::tmem_st4(acol + 16 * i + 8 * g + hh / 2, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+                        }
+                    }
+                    gi += ng;
+                    tc::tmem_wait_st();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&ib.afull[tau]);
+                    ok = ok && aok;
                     pending = true;
-                    pjb = lb + KC >= B ? jb : -1;
-                    plast = lb + KC >= B && jb + TM >= n;
+                    pjb = lb + KC >= B ? 2 * TM * jp : -1;
+                    // the cluster's last step: its slot is released after this step's epilogue
+                    if (plast) tc::mbar_arrive(&slot_empty[pslot]);
+                    plast = lb + KC >= B && jp + 1 >= npairs;
                     pslot = s;
                 }
             }
         }
         if (pending) {
-            const bool done = converter_wait_mma(pb, mph);
+            const bool done = tc::mbar_wait(&ib.mdone[tau], mph, kWaitPolls);
             if (ok && done && pjb >= 0) epilogue();
             ok = ok && done;
         }
-    } else if (tid == kIssuer) {
-        // ---- issuer: the MMAs of every chunk once its B operand, the previous tile's
-        // epilogue (ready) and its A digits in TMEM (afull) are done ----
+    } else if (tid == kIssuerInv) {
+        // ---- issuer: per step, tile 0's MMAs once ready and its A digits are done, then tile 1's ----
         uint32_t rph = 0, cc = 0;
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
             if (!cluster_of(k, cidx, m, mp)) break;
-            for (int jb = 0; jb < n && ok; jb += TM)
+            for (int jp = 0; jp < npairs && ok; ++jp)
                 for (int lb = m, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
-                    ok = issuer_acquire(pb, rph);
-                    if (!ok) break;
-                    const uint32_t a = cc & 1;
-                    ok = tc::mbar_wait(&ib.afull[a], (cc >> 1) & 1, kWaitPolls);
-                    if (!ok) break;
+                    ok = tc::mbar_wait(&ib.ready, rph, kWaitPolls);
+                    rph ^= 1u;
                     const int ksteps = (min(KC, B - lb) + 15) / 16;
-                    issue_levels_ta(tmem, kAcol0 + a * kAbufCols, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps,
-                                    &pb.mma, &ib.afree[a]);
+                    for (int tau = 0; tau < 2 && ok; ++tau) {
+                        ok = tc::mbar_wait(&ib.afull[tau], cc & 1, kWaitPolls);
+                        if (!ok) break;
+                        issue_levels_ta(tmem, 128 * tau, kAcolInv + tau * kAbufCols, X + (cc & 1) * B_BYTES, B_LBO,
+                                        c == 0, ksteps, &ib.mdone[tau]);
+                    }
                 }
         }
     }
@@ -1248,7 +1253,8 @@ cudaError_t launch_dwt_inverse_tc(const Tables &tb, const double2 *coef, double2
     if (!tb.seedtab || !tb.rectab) return cudaErrorInvalidValue;
     constexpr int B_BYTES = (kKCInv / 8) * (kNB * 16 + 16);
     const int B = tb.B;
-    const size_t bytes = 2 * (size_t)B_BYTES + sizeof(double) * ((size_t)kRingInv * kProd * kRowInv + 2 * inv_slot_doubles(B));
+    const size_t bytes =
+        2 * (size_t)B_BYTES + sizeof(double) * (2 * (size_t)kRingInv * 128 * kRowInv + 2 * inv_slot_doubles(B));
     cudaError_t e =
         cudaFuncSetAttribute(dwt_inverse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -1257,7 +1263,7 @@ cudaError_t launch_dwt_inverse_tc(const Tables &tb, const double2 *coef, double2
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(tb.ncl, sms));
-    dwt_inverse_tc_kernel<<<grid, kThreadsFwd, bytes, s>>>(tb, reinterpret_cast<const double *>(coef), S, flags);
+    dwt_inverse_tc_kernel<<<grid, kThreadsInv, bytes, s>>>(tb, reinterpret_cast<const double *>(coef), S, flags);
     count_launch();
     return cudaGetLastError();
 }
