@@ -112,6 +112,43 @@ def test_full_parity_B128():
     assert synth.rel_l2(g, oracle.inverse(B, coef)) < TOL
 
 
+@pytest.mark.parametrize("B", [80, 96])
+def test_partial_second_sample_tile(B):
+    """The inverse runs two 128-beta-sample tiles at a time; at 2B = 160 and 192
+    the second tile of the pair is partly past the last sample (its idle lanes
+    run on zeros and are not stored).  Full parity, both directions."""
+    grid = synth.random_grid(B, seed=27000 + B)
+    coef = synth.coefficients(B, "gauss_decay", seed=27100 + B)
+    with Plan(B, MODE, device=DEV) as p:
+        f = p.forward(torch.from_numpy(grid).to(DEV), out=nan_coef(B)).cpu().numpy()
+        g = p.inverse(torch.from_numpy(coef).to(DEV), out=nan_grid(B)).cpu().numpy()
+        p.sync()
+    assert synth.rel_l2(f, oracle.forward(B, grid)) < TOL
+    assert synth.rel_l2(g, oracle.inverse(B, coef)) < TOL
+
+
+@pytest.mark.parametrize("B", [160, 192])
+def test_odd_number_of_sample_tiles(B):
+    """2B = 320 and 384: three 128-sample tiles, so the inverse's second pair
+    has a second tile wholly (192) or partly (160) past the last sample.
+    Every grid value of sampled beta slices in both pairs against the oracle's
+    one-by-one sums, and the round trip."""
+    rng = np.random.default_rng(B)
+    coef = synth.coefficients(B, "gauss_decay", seed=27200 + B)
+    n = 2 * B
+    with Plan(B, MODE, device=DEV) as p:
+        g = p.inverse(torch.from_numpy(coef).to(DEV), out=nan_grid(B))
+        back = p.forward(g).cpu().numpy()
+        p.sync()
+        # beta slices j in each tile, the last sample, and random (alpha, gamma) points
+        js = [0, 127, 128, 255, 256, n - 1]
+        pts = [(int(rng.integers(0, n)), j, int(rng.integers(0, n))) for j in js for _ in range(2)]
+        g_pts = np.array([g[j, i, k].item() for (i, j, k) in pts])
+    assert np.isfinite(g_pts).all()
+    assert synth.rel_l2(g_pts, oracle.inverse_points(B, coef, pts)) < TOL
+    assert synth.rel_l2(back, coef) < TOL
+
+
 @pytest.mark.parametrize("B", [256, 512])
 def test_sampled_parity_large(B):
     """Full-size bandwidths in the benchmark's launch configuration: forward
