@@ -54,7 +54,7 @@ namespace {
 constexpr int kDig = 7;              // digits per operand entry (and levels kept)
 constexpr int kCols = 16;            // 8 partners x (re, im)
 constexpr int kNB = kDig * kCols;    // 112 B-operand rows: digit k of column c at row 16 k + c
-constexpr uint32_t kTmemCols = 128;  // >= 112 accumulator columns
+constexpr uint32_t kTmemCols = 512;  // the forward's 4 tile accumulators of 112 (128) columns
 constexpr uint32_t kWaitPolls = 1u << 22;
 
 __device__ __forceinline__ int mod_n(int a, int n) { return a < 0 ? a + n : a; }
@@ -335,10 +335,15 @@ __device__ __forceinline__ bool converter_wait_mma(PipeBars &pb, uint32_t &mph, 
 // Forward DWT, persistent.  One CTA per SM walks the clusters
 // fwd_order[blockIdx.x + k gridDim.x], k = 0, 1, ... (longest first, dealt out
 // round robin); tiles of TM = 64 degrees (M), K chunks of KC = 128 beta
-// samples, one producer per sample; the producers keep the recurrence state
-// of their (up to 8) samples in registers.  The roles of the one-cluster
-// design run on across cluster boundaries, and a fourth one prepares each
-// cluster's tables ahead of use:
+// samples, one producer per sample.  The tiles of a cluster are taken in
+// passes of up to four, whose accumulators stay in TMEM (columns 128 t + 0..111
+// for the pass's tile t), and each pass runs chunk by chunk: for chunk c the
+// producers carry their samples' recurrence through all the pass's tiles, and
+// the converters cut the chunk's data operand once for all of them.  The
+// producers keep the recurrence state of their samples at the end of a pass
+// in registers for the next (only clusters of more than 256 degrees have a
+// second pass).  The roles run on across cluster boundaries, and a fourth one
+// prepares each cluster's tables ahead of use:
 //   set-up     (warp 13) fills slot k & 1 with cluster k's partner table,
 //              column scales, recurrence coefficients and digit exponents as
 //              soon as cluster k-2 has released it, so the prologue of a
@@ -347,10 +352,11 @@ __device__ __forceinline__ bool converter_wait_mma(PipeBars &pb, uint32_t &mph, 
 // instead of once per cluster.  Slot hand-off by mbarriers: slot_full (the
 // set-up warp's 32 arrivals), slot_empty (every producer after its last
 // group of the cluster, every converter after the cluster's last epilogue).
-// Converter schedule per chunk: B operand of c into buffer c % 2 (while the
-// MMAs of c - 1 run), wait for those MMAs (then the epilogue when c - 1 closed
-// a tile, possibly of the previous cluster), A digits of the staged groups,
-// MMAs of c.
+// Converter schedule per step (pass, chunk, tile): at the chunk's first tile,
+// its data operand into B buffer (chunk step) % 2 (TMA copies issued one chunk
+// ahead, cut into digits in place); wait for the previous step's MMAs (then the
+// epilogue when they closed a tile, possibly of the previous cluster); A digits
+// of the staged groups; MMAs of the step.
 //   dynamic smem: A planes [7] | B operand [2] | staging [kStages][kGroup rows][KC] |
 //                 slot [2] { rA, rAc [B doubles], alpha [B ints] }
 // ---------------------------------------------------------------------------
@@ -448,12 +454,6 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
     } else if (tid < kProd) {
         // ---- producers: sample j = c KC + t of every chunk c, rows in groups of G ----
         const int t = tid;
-        double xr[MAXC];
-#pragma unroll
-        for (int c = 0; c < MAXC; ++c) {
-            const int j = c * KC + t;
-            xr[c] = j < n ? tb.cosb[j] : 0.0;
-        }
         uint32_t gi = 0;
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
@@ -462,72 +462,81 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
             ok = tc::mbar_wait(&slot_full[s], (k >> 1) & 1, kWaitPolls);
             if (!ok) break;
             const double *rA = slot_rA(s), *rAc = slot_rAc(s);
-            double dc[MAXC], dp[MAXC];
-#pragma unroll
-            for (int c = 0; c < MAXC; ++c) {
-                const int j = c * KC + t;
-                dc[c] = 0.0;
-                dp[c] = 0.0;
-                if (j < n) {
-                    const double sd = tb.seedtab[(size_t)cidx * n + j];
-                    dc[c] = (flags & kApplyW) ? sd * tb.w[j] : sd;
-                }
-            }
-            for (int lb = l0; lb < B && ok; lb += TM) {
-                const int rows = min(TM, B - lb);
-                const int ngroups = (rows + G - 1) / G;  // groups past the cluster's last degree are skipped
+            const int ntile = (B - l0 + TM - 1) / TM, npass = (ntile + 3) / 4;
+            double dcs[MAXC], dps[MAXC];  // each chunk's recurrence state at the end of a pass
+            for (int pp = 0; pp < npass && ok; ++pp) {
+                const int t0 = 4 * pp, nt = min(4, ntile - t0);
 #pragma unroll
                 for (int c = 0; c < MAXC; ++c) {
                     if (c >= nchunks || !ok) break;
-                    const bool col = c * KC + t < n;
-#pragma unroll 1
-                    for (int g = 0; g < ngroups; ++g, ++gi) {  // rolled: the chunk loop around it is unrolled
-                        ok = producer_acquire(pb, gi);
-                        if (!ok) break;
-                        double *st = stage + (gi % kStages) * G * KC + t;
-                        const int nv = min(G, rows - g * G);  // warp-uniform
-                        const int q0 = lb + g * G - l0;
-                        if (!col) {
-                            for (int rr = 0; rr < nv; ++rr) st[rr * KC] = 0.0;
-                        } else if (nv == G) {
-                            // a whole group: straight-line code, no predicated FP64 work, in
-                            // halves of 8 rows.  A half's coefficients are loaded before its
-                            // first staging store (a store could alias them, so later loads
-                            // would wait for it), and the first FMA of a row, which does not
-                            // depend on the recurrence, runs two rows ahead of the second, so
-                            // that the dependent chain finds the FP64 pipe busy rather than
-                            // idle while it waits.
-#pragma unroll
-                            for (int hh = 0; hh < G; hh += 8) {
-                                double ca[8], cb[8];
-#pragma unroll
-                                for (int rr = 0; rr < 8; ++rr) {
-                                    ca[rr] = rA[q0 + hh + rr];
-                                    cb[rr] = rAc[q0 + hh + rr];
-                                }
-                                double u0 = fma(ca[0], xr[c], -cb[0]), u1 = fma(ca[1], xr[c], -cb[1]);
-#pragma unroll
-                                for (int rr = 0; rr < 8; ++rr) {
-                                    st[(hh + rr) * KC] = dc[c];
-                                    const double nx = fma(u0, dc[c], -dp[c]);
-                                    u0 = u1;
-                                    if (rr + 2 < 8) u1 = fma(ca[rr + 2], xr[c], -cb[rr + 2]);
-                                    dp[c] = dc[c];
-                                    dc[c] = nx;
-                                }
-                            }
-                        } else {
-#pragma unroll 1
-                            for (int rr = 0; rr < nv; ++rr) {
-                                st[rr * KC] = dc[c];
-                                const double nx = fma(fma(rA[q0 + rr], xr[c], -rAc[q0 + rr]), dc[c], -dp[c]);
-                                dp[c] = dc[c];
-                                dc[c] = nx;
-                            }
+                    const int j = c * KC + t;
+                    const bool col = j < n;
+                    const double x = col ? tb.cosb[j] : 0.0;
+                    double dc = 0.0, dp = 0.0;
+                    if (pp == 0) {
+                        if (col) {
+                            const double sd = tb.seedtab[(size_t)cidx * n + j];
+                            dc = (flags & kApplyW) ? sd * tb.w[j] : sd;
                         }
-                        // staged rows nv..G-1 are never read: the converters take rows < `rows` only
-                        release_full(pb, gi);
+                    } else {
+                        dc = dcs[c];
+                        dp = dps[c];
                     }
+#pragma unroll 1
+                    for (int tt = 0; tt < nt && ok; ++tt) {
+                        const int lb = l0 + TM * (t0 + tt), rows = min(TM, B - lb);
+                        const int ngroups = (rows + G - 1) / G;  // groups past the cluster's last degree are skipped
+#pragma unroll 1
+                        for (int g = 0; g < ngroups; ++g, ++gi) {  // rolled: the chunk loop around it is unrolled
+                            ok = producer_acquire(pb, gi);
+                            if (!ok) break;
+                            double *st = stage + (gi % kStages) * G * KC + t;
+                            const int nv = min(G, rows - g * G);  // warp-uniform
+                            const int q0 = lb + g * G - l0;
+                            if (!col) {
+                                for (int rr = 0; rr < nv; ++rr) st[rr * KC] = 0.0;
+                            } else if (nv == G) {
+                                // a whole group: straight-line code, no predicated FP64 work, in
+                                // halves of 8 rows.  A half's coefficients are loaded before its
+                                // first staging store (a store could alias them, so later loads
+                                // would wait for it), and the first FMA of a row, which does not
+                                // depend on the recurrence, runs two rows ahead of the second, so
+                                // that the dependent chain finds the FP64 pipe busy rather than
+                                // idle while it waits.
+#pragma unroll
+                                for (int hh = 0; hh < G; hh += 8) {
+                                    double ca[8], cb[8];
+#pragma unroll
+                                    for (int rr = 0; rr < 8; ++rr) {
+                                        ca[rr] = rA[q0 + hh + rr];
+                                        cb[rr] = rAc[q0 + hh + rr];
+                                    }
+                                    double u0 = fma(ca[0], x, -cb[0]), u1 = fma(ca[1], x, -cb[1]);
+#pragma unroll
+                                    for (int rr = 0; rr < 8; ++rr) {
+                                        st[(hh + rr) * KC] = dc;
+                                        const double nx = fma(u0, dc, -dp);
+                                        u0 = u1;
+                                        if (rr + 2 < 8) u1 = fma(ca[rr + 2], x, -cb[rr + 2]);
+                                        dp = dc;
+                                        dc = nx;
+                                    }
+                                }
+                            } else {
+#pragma unroll 1
+                                for (int rr = 0; rr < nv; ++rr) {
+                                    st[rr * KC] = dc;
+                                    const double nx = fma(fma(rA[q0 + rr], x, -rAc[q0 + rr]), dc, -dp);
+                                    dp = dc;
+                                    dc = nx;
+                                }
+                            }
+                            // staged rows nv..G-1 are never read: the converters take rows < `rows` only
+                            release_full(pb, gi);
+                        }
+                    }
+                    dcs[c] = dc;
+                    dps[c] = dp;
                 }
             }
             if (ok) tc::mbar_arrive(&slot_empty[s]);  // this producer is done with the slot's tables
@@ -536,10 +545,11 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
         // ---- converters ----
         const int t = tid - kProd;
         const int wq = warp & 3;  // TMEM lane quarter of this warp
-        uint32_t gi = 0, mph = 0, cc = 0;
+        uint32_t gi = 0, mph = 0, bc = 0;  // bc: chunk steps (B buffer bc & 1)
         bool pending = false;     // MMAs committed and not yet waited for
-        // the tile those MMAs close (prows > 0), for the deferred epilogue, and its cluster
-        int plb = 0, prows = 0, pslot = 0, pl0 = 0, pcidx = 0;
+        // the tile those MMAs close (prows > 0), for the deferred epilogue: its first degree,
+        // rows, accumulator (128 ptile), cluster slot, first degree of the cluster and index
+        int plb = 0, prows = 0, ptile = 0, pslot = 0, pl0 = 0, pcidx = 0;
         bool plast = false;       // ... and whether that tile is its cluster's last
         auto epilogue = [&]() {
             // Degree plb + 16 w + i sits in TMEM lane 32 w + i (i < 16), w = lane quarter (warps 4-7).
@@ -551,7 +561,7 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
                 const int r = 16 * wq + lane;
                 const int l = plb + r, q = l - pl0;
                 double v16[kCols];
-                epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16), h.colexp, v16);
+                epilogue_levels(tmem + ((uint32_t)(wq * 32) << 16) + 128 * ptile, h.colexp, v16);
                 if (lane < 16 && r < prows) {
                     // V_l sig_t 2^-alpha_t
                     const double V = (flags & kApplyV) ? (2.0 * l + 1.0) / (8.0 * M_PI * B) : 1.0;
@@ -625,88 +635,95 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
             }
             const SlotHdr &h = hdr[s];
             const int *alpha = slot_alpha(s);
-            for (int lb = l0; lb < B && ok; lb += TM) {
-                const int rows = min(TM, B - lb);
-                for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+            const int ntile = (B - l0 + TM - 1) / TM, npass = (ntile + 3) / 4;
+            for (int pp = 0; pp < npass && ok; ++pp) {
+                const int t0 = 4 * pp, nt = min(4, ntile - t0);
+                for (int c = 0; c < nchunks && ok; ++c, ++bc) {
                     const int kvalid = min(KC, n - c * KC);
                     const int ksteps = (kvalid + 15) / 16;
                     const int kfill = ksteps * 16;
-                    const int buf = cc & 1;
+                    const int buf = bc & 1;
                     unsigned char *Xc = X + buf * B_BYTES;
-                    if (inflight != buf) {  // the cluster's first step: copy now (the buffer's MMAs are done)
-                        if (t == 0) issue_b(h, c, buf);
-                        inflight = buf;
-                    }
-                    {
-                        const bool done = tc::mbar_wait(&pb.data[buf], (dph >> buf) & 1, kWaitPolls);
-                        if (done) {
-                            dph ^= 1u << buf;
-                            inflight = -1;
-                        }
-                        read_raw(h, c, Xc, wn);
-                        ok = tc::group_and(kBarConv, kConv, done);  // every raw value read before any digit lands
-                        if (!ok) break;
-                    }
-                    if (bk0 < kfill) {
-                        double vr[4], vi[4];
+                    for (int tt = 0; tt < nt && ok; ++tt) {
+                        const int lb = l0 + TM * (t0 + tt), rows = min(TM, B - lb);
+                        if (tt == 0) {
+                            // the chunk's data operand, once for all the pass's tiles
+                            if (inflight != buf) {  // the cluster's first chunk: copy now (the buffer's MMAs are done)
+                                if (t == 0) issue_b(h, c, buf);
+                                inflight = buf;
+                            }
+                            const bool done = tc::mbar_wait(&pb.data[buf], (dph >> buf) & 1, kWaitPolls);
+                            if (done) {
+                                dph ^= 1u << buf;
+                                inflight = -1;
+                            }
+                            read_raw(h, c, Xc, wn);
+                            ok = tc::group_and(kBarConv, kConv, done);  // every raw value read before any digit lands
+                            if (!ok) break;
+                            if (bk0 < kfill) {
+                                double vr[4], vi[4];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const int q = (k - brot) & 3;
-                            const double2 x = q == 0 ? wn[0] : q == 1 ? wn[1] : q == 2 ? wn[2] : wn[3];
-                            vr[k] = x.x;
-                            vi[k] = x.y;
-                        }
-                        const int ar = -h.colexp[2 * bp], ai = -h.colexp[2 * bp + 1];
-                        const int alr[4] = {ar, ar, ar, ar}, ali[4] = {ai, ai, ai, ai};
-                        put_digits4(Xc, 16 * kCols, B_LBO, 2 * bp, bk0, vr, alr);
-                        put_digits4(Xc, 16 * kCols, B_LBO, 2 * bp + 1, bk0, vi, ali);
-                    }
-                    if (pending) {
-                        ok = converter_wait_mma(pb, mph);
-                        pending = false;
-                        if (!ok) break;
-                        if (prows > 0) epilogue();
-                        if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
-                    }
-                    // the other B buffer's MMAs (the previous step's) are done: the next step's copies
-                    if (!(c == nchunks - 1 && lb + TM >= B)) {  // a next step in this cluster
-                        if (t == 0) issue_b(h, c + 1 == nchunks ? 0 : c + 1, buf ^ 1);
-                        inflight = buf ^ 1;
-                    }
-                    // A operand: staged rows G g + t / 32 and G g + t / 32 + 8, samples
-                    // 4 (t % 32) .. + 3; the groups past the cluster's last degree are
-                    // neither staged nor read
-                    const int rr = t >> 5, k4 = 4 * (t & 31);
-                    const int ngroups = (rows + G - 1) / G;
-                    for (int g = 0; g < ngroups; ++g, ++gi) {
-                        ok = converter_acquire(pb, gi);
-                        if (!ok) break;
-#pragma unroll
-                        for (int hh = 0; hh < G; hh += 8) {
-                            const int r = g * G + hh + rr;
-                            if (r < rows && k4 < kfill) {
-                                const double2 *src = reinterpret_cast<const double2 *>(
-                                    stage + (gi % kStages) * G * KC + (hh + rr) * KC + k4);
-                                const double2 w0 = src[0], w1 = src[1];
-                                const double v[4] = {w0.x, w0.y, w1.x, w1.y};
-                                const int a = alpha[lb + r - l0];
-                                const int al[4] = {a, a, a, a};
-                                put_digits4(A, A_PLANE, A_LBO, r, k4, v, al);
+                                for (int k = 0; k < 4; ++k) {
+                                    const int q = (k - brot) & 3;
+                                    const double2 x = q == 0 ? wn[0] : q == 1 ? wn[1] : q == 2 ? wn[2] : wn[3];
+                                    vr[k] = x.x;
+                                    vi[k] = x.y;
+                                }
+                                const int ar = -h.colexp[2 * bp], ai = -h.colexp[2 * bp + 1];
+                                const int alr[4] = {ar, ar, ar, ar}, ali[4] = {ai, ai, ai, ai};
+                                put_digits4(Xc, 16 * kCols, B_LBO, 2 * bp, bk0, vr, alr);
+                                put_digits4(Xc, 16 * kCols, B_LBO, 2 * bp + 1, bk0, vi, ali);
                             }
                         }
-                        release_empty(pb, gi);
+                        if (pending) {
+                            ok = converter_wait_mma(pb, mph);
+                            pending = false;
+                            if (!ok) break;
+                            if (prows > 0) epilogue();
+                            if (plast) tc::mbar_arrive(&slot_empty[pslot]);  // the previous cluster is finished
+                        }
+                        // the previous chunk's MMAs (the other B buffer's) are done: the next chunk's
+                        // copies (the next of this pass, else the first of the next pass)
+                        if (tt == 0 && !(c == nchunks - 1 && pp + 1 >= npass)) {
+                            if (t == 0) issue_b(h, c + 1 == nchunks ? 0 : c + 1, buf ^ 1);
+                            inflight = buf ^ 1;
+                        }
+                        // A operand: staged rows G g + t / 32 and G g + t / 32 + 8, samples
+                        // 4 (t % 32) .. + 3; the groups past the cluster's last degree are
+                        // neither staged nor read
+                        const int rr = t >> 5, k4 = 4 * (t & 31);
+                        const int ngroups = (rows + G - 1) / G;
+                        for (int g = 0; g < ngroups; ++g, ++gi) {
+                            ok = converter_acquire(pb, gi);
+                            if (!ok) break;
+#pragma unroll
+                            for (int hh = 0; hh < G; hh += 8) {
+                                const int r = g * G + hh + rr;
+                                if (r < rows && k4 < kfill) {
+                                    const double2 *src = reinterpret_cast<const double2 *>(
+                                        stage + (gi % kStages) * G * KC + (hh + rr) * KC + k4);
+                                    const double2 w0 = src[0], w1 = src[1];
+                                    const double v[4] = {w0.x, w0.y, w1.x, w1.y};
+                                    const int a = alpha[lb + r - l0];
+                                    const int al[4] = {a, a, a, a};
+                                    put_digits4(A, A_PLANE, A_LBO, r, k4, v, al);
+                                }
+                            }
+                            release_empty(pb, gi);
+                        }
+                        tc::fence_proxy_async();
+                        ok = chunk_done(ok);
+                        if (!ok) break;
+                        if (t == 0) tc::mbar_arrive(&pb.ready);
+                        pending = true;
+                        plb = lb;
+                        prows = c == nchunks - 1 ? rows : 0;
+                        ptile = tt;
+                        plast = c == nchunks - 1 && pp + 1 >= npass && tt + 1 >= nt;
+                        pslot = s;
+                        pl0 = l0;
+                        pcidx = cidx;
                     }
-                    tc::fence_proxy_async();
-                    ok = chunk_done(ok);
-                    if (!ok) break;
-                    if (t == 0) tc::mbar_arrive(&pb.ready);
-                    pending = true;
-                    plb = lb;
-                    prows = c == nchunks - 1 ? rows : 0;
-                    plast = c == nchunks - 1 && lb + TM >= B;
-                    pslot = s;
-                    pl0 = l0;
-                    pcidx = cidx;
                 }
             }
         }
@@ -719,18 +736,25 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
         // after a timeout: copies still in flight land before the CTA leaves
         if (inflight >= 0) tc::mbar_wait(&pb.data[inflight], (dph >> inflight) & 1, kWaitPolls);
     } else if (tid == kIssuer) {
-        // ---- issuer: the MMAs of every chunk, in the converters' order ----
-        uint32_t rph = 0, cc = 0;
+        // ---- issuer: the MMAs of every step, in the converters' order, into the
+        // accumulator of the step's tile ----
+        uint32_t rph = 0, bc = 0;
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
             if (!cluster_of(k, cidx, m, mp)) break;
-            for (int lb = m; lb < B && ok; lb += TM)
-                for (int c = 0; c < nchunks && ok; ++c, ++cc) {
-                    ok = issuer_acquire(pb, rph);
-                    if (!ok) break;
+            const int ntile = (B - m + TM - 1) / TM, npass = (ntile + 3) / 4;
+            for (int pp = 0; pp < npass && ok; ++pp) {
+                const int nt = min(4, ntile - 4 * pp);
+                for (int c = 0; c < nchunks && ok; ++c, ++bc) {
                     const int ksteps = (min(KC, n - c * KC) + 15) / 16;
-                    issue_levels<TM>(tmem, A, A_PLANE, A_LBO, X + (cc & 1) * B_BYTES, B_LBO, c == 0, ksteps, &pb.mma);
+                    for (int tt = 0; tt < nt && ok; ++tt) {
+                        ok = issuer_acquire(pb, rph);
+                        if (!ok) break;
+                        issue_levels<TM>(tmem + 128 * tt, A, A_PLANE, A_LBO, X + (bc & 1) * B_BYTES, B_LBO, c == 0,
+                                         ksteps, &pb.mma);
+                    }
                 }
+            }
         }
     }
     if (!ok && tb.err) atomicExch(tb.err, 2);
