@@ -788,8 +788,9 @@ __global__ void __launch_bounds__(kThreadsFwd, 1) dwt_forward_tc_kernel(Tables t
 // and signal `ready`; they write the next step's B operand and then this
 // step's A digits (afull[tau]).  The issuer waits for ready and afull[0],
 // issues tile 0's MMAs (committed to mdone[0]), then waits for afull[1] and
-// issues tile 1's.  Both tiles of a pair share each chunk's B operand, and a
-// pair's second tile past the last sample runs on zeros (it is not stored).
+// issues tile 1's.  Both tiles of a pair share each chunk's B operand; a
+// pair's second tile wholly past the last sample is skipped by every role, and
+// the idle lanes of a partly filled tile run on zeros and are not stored.
 // The set-up warp fills slot k & 1 with cluster k's partner table, recurrence
 // coefficients, digit exponents, the factors V_l mu_t of its coefficients and
 // the column scales of those products (the largest magnitude of each of the 16
@@ -956,6 +957,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) dwt_inverse_tc_kernel(Tables t
             const double *rA = slot_rA(s), *rAc = slot_rAc(s);
             const int nch = (L + KC - 1) / KC;  // K chunks of a tile
             for (int jp = 0; jp < npairs && ok; ++jp) {
+                if (2 * TM * jp + TM * tau >= n) continue;  // the pair's second tile lies past the last sample
                 const int j = 2 * TM * jp + TM * tau + tp;
                 double x = 0.0, dc = 0.0, dp = 0.0;
                 if (j < n) { x = tb.cosb[j]; dc = tb.seedtab[(size_t)cidx * n + j]; }
@@ -1095,6 +1097,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) dwt_inverse_tc_kernel(Tables t
             const double *rG = slot_rG(s);
             const int *ralpha = slot_alpha(s);
             for (int jp = 0; jp < npairs && ok; ++jp) {
+                const bool live = 2 * TM * jp + TM * tau < n;  // else this tile slot idles for the pair
                 for (int lb = l0, c = 0; lb < B && ok; lb += KC, ++c, ++cc) {
                     const int cnt = min(KC, B - lb);
                     const int ng = (cnt + 15) / 16;
@@ -1116,45 +1119,47 @@ __global__ void __launch_bounds__(kThreadsInv, 1) dwt_inverse_tc_kernel(Tables t
                     if (b_ready) put_b(h, rG, lb + KC < B ? lb + KC : l0, l0, X + ((cc + 1) & 1) * B_BYTES);
                     // this tile's A digits (its buffer is free: its previous MMAs are done)
                     bool aok = true;
-                    const uint32_t acol = tlane + kAcolInv + tau * kAbufCols;
-                    for (int g = 0; g < ng && aok; ++g) {
-                        const uint32_t gg = gi + g, r = gg % kRingInv;
-                        aok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.full[tau][r], (gg / kRingInv) & 1, kWaitPolls));
-                        if (!aok) break;
-                        const double2 *src = reinterpret_cast<const double2 *>(ring_row(tau, r, tl));
-                        double v[16];
+                    if (live) {
+                        const uint32_t acol = tlane + kAcolInv + tau * kAbufCols;
+                        for (int g = 0; g < ng && aok; ++g) {
+                            const uint32_t gg = gi + g, r = gg % kRingInv;
+                            aok = __all_sync(0xffffffffu, tc::mbar_wait(&ib.full[tau][r], (gg / kRingInv) & 1, kWaitPolls));
+                            if (!aok) break;
+                            const double2 *src = reinterpret_cast<const double2 *>(ring_row(tau, r, tl));
+                            double v[16];
 #pragma unroll
-                        for (int h2 = 0; h2 < 8; ++h2) {
-                            const double2 w2 = src[h2];
-                            v[2 * h2] = w2.x;
-                            v[2 * h2 + 1] = w2.y;
-                        }
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&ib.empty[tau][r]);
-#pragma unroll
-                        for (int hh = 0; hh < 16; hh += 8) {
-                            uint32_t pk[kDig][4];
-#pragma unroll
-                            for (int c2 = 0; c2 < 4; ++c2) {
-                                const int q = lb - l0 + 16 * g + hh + 2 * c2;  // degree - l0
-                                uint32_t d0[kDig], d1[kDig];
-                                digits7(v[hh + 2 * c2], q < B - l0 ? ralpha[q] : 0, d0);
-                                digits7(v[hh + 2 * c2 + 1], q + 1 < B - l0 ? ralpha[q + 1] : 0, d1);
-#pragma unroll
-                                for (int i = 0; i < kDig; ++i) pk[i][c2] = __byte_perm(d0[i], d1[i], 0x7632);
+                            for (int h2 = 0; h2 < 8; ++h2) {
+                                const double2 w2 = src[h2];
+                                v[2 * h2] = w2.x;
+                                v[2 * h2 + 1] = w2.y;
                             }
+                            __syncwarp();
+                            if (lane == 0) tc::mbar_arrive(&ib.empty[tau][r]);
 #pragma unroll
-                            for (int i = 0; i < kDig; ++i)
-                                tc::tmem_st4(acol + 16 * i + 8 * g + hh / 2, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+                            for (int hh = 0; hh < 16; hh += 8) {
+                                uint32_t pk[kDig][4];
+#pragma unroll
+                                for (int c2 = 0; c2 < 4; ++c2) {
+                                    const int q = lb - l0 + 16 * g + hh + 2 * c2;  // degree - l0
+                                    uint32_t d0[kDig], d1[kDig];
+                                    digits7(v[hh + 2 * c2], q < B - l0 ? ralpha[q] : 0, d0);
+                                    digits7(v[hh + 2 * c2 + 1], q + 1 < B - l0 ? ralpha[q + 1] : 0, d1);
+#pragma unroll
+                                    for (int i = 0; i < kDig; ++i) pk[i][c2] = __byte_perm(d0[i], d1[i], 0x7632);
+                                }
+#pragma unroll
+                                for (int i = 0; i < kDig; ++i)
+                                    tc::tmem_st4(acol + 16 * i + 8 * g + hh / 2, pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+                            }
                         }
+                        gi += ng;
+                        tc::tmem_wait_st();
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&ib.afull[tau]);
                     }
-                    gi += ng;
-                    tc::tmem_wait_st();
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&ib.afull[tau]);
                     ok = ok && aok;
-                    pending = true;
+                    pending = live;
                     pjb = lb + KC >= B ? 2 * TM * jp : -1;
                     // the cluster's last step: its slot is released after this step's epilogue
                     if (plast) tc::mbar_arrive(&slot_empty[pslot]);
@@ -1170,7 +1175,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) dwt_inverse_tc_kernel(Tables t
         }
     } else if (tid == kIssuerInv) {
         // ---- issuer: per step, tile 0's MMAs once ready and its A digits are done, then tile 1's ----
-        uint32_t rph = 0, cc = 0;
+        uint32_t rph = 0, cc = 0, aph = 0;  // aph bit tau: parity of afull[tau]'s next completion
         for (int k = 0; ok; ++k) {
             int cidx, m, mp;
             if (!cluster_of(k, cidx, m, mp)) break;
@@ -1180,7 +1185,9 @@ __global__ void __launch_bounds__(kThreadsInv, 1) dwt_inverse_tc_kernel(Tables t
                     rph ^= 1u;
                     const int ksteps = (min(KC, B - lb) + 15) / 16;
                     for (int tau = 0; tau < 2 && ok; ++tau) {
-                        ok = tc::mbar_wait(&ib.afull[tau], cc & 1, kWaitPolls);
+                        if (2 * TM * jp + TM * tau >= n) continue;  // an idle tile slot
+                        ok = tc::mbar_wait(&ib.afull[tau], (aph >> tau) & 1, kWaitPolls);
+                        aph ^= 1u << tau;
                         if (!ok) break;
                         issue_levels_ta(tmem, 128 * tau, kAcolInv + tau * kAbufCols, X + (cc & 1) * B_BYTES, B_LBO,
                                         c == 0, ksteps, &ib.mdone[tau]);
