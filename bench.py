@@ -121,7 +121,7 @@ SM_MAX_MHZ = 2070.0
 TRAFFIC = {
     ("dwt_forward_fp64_kernel", 64): (36_887_552 + 12_032, "dwt_fp64.cu", "0589e4d08494f908"),
     ("dwt_forward_fp64_kernel", 256): (3_089_268_992 + 362_294_016, "dwt_fp64.cu", "1fc2456028276ded"),
-    ("dwt_forward_tc_kernel", 128): (295_112_192 + 45_680_384, "dwt_fp64tc.cu", "5a9e1badbe004aaf"),
+    ("dwt_forward_tc_kernel", 128): (294_756_608 + 45_407_488, "dwt_fp64tc.cu", "270df8a4ce56ca42"),
 }
 
 
