@@ -138,9 +138,10 @@ soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *st
  * and S(-m,-m';j) = conj S(m,m';j).  In each symmetry cluster the partners
  * come in such conjugate pairs, and these calls contract one partner of each
  * pair: half the DWT / iDWT contraction work.  Every contracted partner has
- * m' >= 0, so the slice FFTs (FP64 in both modes) run on that half of the
- * spectrum: real-row DFTs of half length, and the column DFTs of m' = 0..B-1
- * only.
+ * m' >= 0, so the slice FFTs (FP64 for SOFT_FP64 plans, double-float for
+ * SOFT_FP64_TC plans with B >= 2, as their complex-grid FFTs) run on that
+ * half of the spectrum: real-row DFTs of half length, and the column DFTs of
+ * m' = 0..B-1 only.
  *   soft_forward_real: grid (device, (2B)^3 doubles, layout [j][i][k] as the
  *     complex grid) -> coef (device, B(4B^2-1)/3 complex), the same values as
  *     soft_forward of the grid with zero imaginary parts (the conjugate

@@ -20,6 +20,8 @@
 //            in place on the double-float data, FP64 out.
 // Each DFT is an in-place radix-2 decimation-in-time transform in shared
 // memory: bit-reversed load, log2(n) butterfly stages, natural-order store.
+// Real grids take the half-spectrum form of the same passes (below): half-
+// length row DFTs of packed sample pairs, and the columns m' = 0..B-1 only.
 #include "soft_internal.cuh"
 #include "tcgen05.cuh"
 
@@ -222,18 +224,19 @@ __global__ void __launch_bounds__(kFftThreads) fft_rows_kernel(const double2 *in
     }
 }
 
-// Columns pass: for every slice and column, the length-n DFT along the middle
-// index (stride n), `kb` adjacent columns per block; double-float in, FP64
-// (double2) out, possibly to the same memory (each block reads its whole
-// tile before writing it).
+// Columns pass: for every slice and each of its first `ncols` columns (n,
+// or B for the m' >= 0 half of a real grid's spectrum), the length-n DFT
+// along the middle index (stride n), `kb` adjacent columns per block;
+// double-float in, FP64 (double2) out, possibly to the same memory (each
+// block reads its whole tile before writing it).
 __global__ void __launch_bounds__(kFftThreads) fft_cols_kernel(const float4 *in, double2 *out, int n, int logn, int kb,
-                                                                const float4 *__restrict__ twg, int conj,
+                                                                int ncols, const float4 *__restrict__ twg, int conj,
                                                                 const int *__restrict__ rexp) {
     extern __shared__ __align__(16) float4 sm[];
     float4 *tw = sm;              // [n/2]
     float4 *s = sm + (n >> 1);    // [kb][n], column-major: column c at s + c n
     for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) tw[t] = twg[t];
-    const int tiles = n / kb;
+    const int tiles = ncols / kb;
     const int64_t js = blockIdx.x / tiles;
     const int k0 = (blockIdx.x % tiles) * kb;
     const int64_t base = js * n * n + k0;
@@ -263,6 +266,182 @@ __global__ void __launch_bounds__(kFftThreads) fft_cols_kernel(const float4 *in,
         const int i = e / kb, c = e % kb;
         const dcomplex v = load_df(s[c * n + i]);
         out[base + (int64_t)i * n + c] = make_double2(scale2(join_f64(v.re), sh), scale2(join_f64(v.im), sh));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Real grids.  A real row x[0..n) has X[n-k] = conj X[k], so only X[0..N),
+// N = n/2, is formed, from one N-point DFT of the packed samples
+// z[t] = x[2t] + i x[2t+1]:
+//   X[k] = E[k] + w^k O[k],  w = exp(s 2 pi i / n),
+//   E[k] = (Z[k] + conj Z[N-k]) / 2,  O[k] = (Z[k] - conj Z[N-k]) / (2i)  (indices of Z mod N),
+// E and O being the DFTs of the even and odd samples.  Backwards, for a
+// Hermitian row whose Nyquist term X[N] is zero (as in the plan's S), the
+// samples come from one N-point DFT of
+//   Z[k] = (X[k] + conj X[N-k]) + i v^k (X[k] - conj X[N-k]),  v = exp(s 2 pi i / n),
+// as x[2t] = Re z[t], x[2t+1] = Im z[t] (the sum over k split into k < N and
+// k + N, with X[k + N] = conj X[N - k] and v^N = -1).
+// The forward runs the rows (r2c, every row scaled by its own power of two as
+// in fft_rows_kernel), then fft_cols_kernel on the columns m' = 0..N-1.  The
+// inverse runs those columns first (FP64 in, every column scaled by its own
+// power of two), then the rows (c2r), which bring a slice's columns to their
+// common scale before the packing.
+// ---------------------------------------------------------------------------
+
+// Biased exponent of the larger part of v (0 for zeros and subnormals).
+__device__ __forceinline__ int biased_exponent2(double2 v) {
+    return (int)max(((unsigned long long)__double_as_longlong(v.x) >> 52) & 0x7FF,
+                    ((unsigned long long)__double_as_longlong(v.y) >> 52) & 0x7FF);
+}
+
+__device__ __forceinline__ dfloat df_half(dfloat a) { return {0.5f * a.hi, 0.5f * a.lo}; }
+__device__ __forceinline__ dcomplex dc_scale(dcomplex a, float f) {
+    return {{a.re.hi * f, a.re.lo * f}, {a.im.hi * f, a.im.lo * f}};
+}
+
+// The real-row kernels' twiddles: tw[k] = w^k (k < N), twN[t] = w^(2t) =
+// exp(+2 pi i t / N) (t < N/2), from the n-point table.
+__device__ void load_real_twiddles_df(float4 *tw, float4 *twN, const float4 *__restrict__ twg, int N) {
+    for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
+    for (int t = threadIdx.x; t < (N >> 1); t += blockDim.x) twN[t] = twg[2 * t];
+}
+
+// Rows pass of a real grid: nrows real rows of n samples (`in`, FP64) ->
+// X[0..N) of each row, double-float, at out + row n (columns N..n-1 are not
+// written); every row scaled by its own power of two, recorded in rexp as in
+// fft_rows_kernel.  `rpb` rows per block (rpb <= 256).
+__global__ void __launch_bounds__(kFftThreads) fft_rows_r2c_kernel(const double *in, float4 *out, int64_t nrows, int n,
+                                                                    int logN, int rpb, const float4 *__restrict__ twg,
+                                                                    int conj, int *__restrict__ rexp) {
+    extern __shared__ __align__(16) float4 sm[];
+    const int N = n >> 1;
+    float4 *tw = sm;                // [N]
+    float4 *twN = sm + N;           // [N/2]
+    float4 *s = twN + (N >> 1);     // [rpb][N]
+    load_real_twiddles_df(tw, twN, twg, N);
+    __shared__ int rmax[256];  // largest biased exponent of each row
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int rows = (int)min((int64_t)rpb, nrows - r0);
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) rmax[t] = 0;
+    __syncthreads();
+    // the packed pairs, still FP64, into their bit-reversed slots (a double2
+    // fills a float4 slot), and the row maxima
+    const double2 *zin = reinterpret_cast<const double2 *>(in) + r0 * N;
+    double2 *sd = reinterpret_cast<double2 *>(s);
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+        const double2 z = zin[e];
+        const int ex = biased_exponent2(z);
+        if (ex) atomicMax(&rmax[e >> logN], ex);
+        sd[(e >> logN) * N + bitrev(e & (N - 1), logN)] = z;
+    }
+    __syncthreads();
+    // scaled and split in place, each slot by the thread that filled it
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+        const int rl = e >> logN, i = rl * N + bitrev(e & (N - 1), logN);
+        const int sh = rmax[rl] ? 1023 - rmax[rl] : 0;
+        const double2 z = sd[i];
+        const dfloat re = split_f64(scale2(z.x, sh)), im = split_f64(scale2(z.y, sh));
+        s[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) rexp[r0 + t] = rmax[t] ? rmax[t] - 1023 : kZeroRow;
+    dft_stages(s, rows, N, logN, twN, conj != 0);
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+        const int rl = e >> logN, k = e & (N - 1);
+        const dcomplex a = load_df(s[rl * N + k]), b = load_df(s[rl * N + ((N - k) & (N - 1))]);
+        const dcomplex E = {df_half(df_add(a.re, b.re)), df_half(df_add(a.im, df_neg(b.im)))};
+        const dcomplex O = {df_half(df_add(a.im, b.im)), df_half(df_add(b.re, df_neg(a.re)))};
+        out[(r0 + rl) * n + k] = store_df(cadd(E, cmul(load_df(tw[k]), O, conj != 0)));
+    }
+}
+
+// Columns pass of the inverse on the m' >= 0 half of a Hermitian spectrum:
+// for every slice, the length-n DFT along the middle index of columns
+// 0..ncols-1, `kb` (<= 64) adjacent columns per block; FP64 in, double-float
+// out, possibly to the same memory (each block reads its whole tile before
+// writing it).  Every column is scaled by the power of two of its own largest
+// magnitude, recorded in cexp[slice ncols + column] (kZeroRow when all zero).
+__global__ void __launch_bounds__(kFftThreads) fft_cols_f64_kernel(const double2 *in, float4 *out, int n, int logn,
+                                                                    int kb, int ncols, const float4 *__restrict__ twg,
+                                                                    int conj, int *__restrict__ cexp) {
+    extern __shared__ __align__(16) float4 sm[];
+    float4 *tw = sm;              // [n/2]
+    float4 *s = sm + (n >> 1);    // [kb][n], column c at s + c n
+    for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) tw[t] = twg[t];
+    __shared__ int cmax[64];
+    const int tiles = ncols / kb;
+    const int64_t js = blockIdx.x / tiles;
+    const int k0 = (blockIdx.x % tiles) * kb;
+    const int64_t base = js * n * n + k0;
+    for (int t = threadIdx.x; t < kb; t += blockDim.x) cmax[t] = 0;
+    __syncthreads();
+    double2 *sd = reinterpret_cast<double2 *>(s);
+    for (int e = threadIdx.x; e < n * kb; e += blockDim.x) {
+        const int i = e / kb, c = e % kb;
+        const double2 v = in[base + (int64_t)i * n + c];
+        const int ex = biased_exponent2(v);
+        if (ex) atomicMax(&cmax[c], ex);
+        sd[c * n + bitrev(i, logn)] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * kb; e += blockDim.x) {
+        const int i = e / kb, c = e % kb, idx = c * n + bitrev(i, logn);
+        const int sh = cmax[c] ? 1023 - cmax[c] : 0;
+        const double2 v = sd[idx];
+        const dfloat re = split_f64(scale2(v.x, sh)), im = split_f64(scale2(v.y, sh));
+        s[idx] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    for (int t = threadIdx.x; t < kb; t += blockDim.x) cexp[js * ncols + k0 + t] = cmax[t] ? cmax[t] - 1023 : kZeroRow;
+    dft_stages(s, kb, n, logn, tw, conj != 0);
+    for (int e = threadIdx.x; e < n * kb; e += blockDim.x) {
+        const int i = e / kb, c = e % kb;
+        out[base + (int64_t)i * n + c] = s[c * n + i];
+    }
+}
+
+// Rows pass back to a real grid: X[0..N) of each row at in + row n
+// (double-float, column k of slice j scaled by 2^-cexp[j N + k]; X[N] = 0) ->
+// nrows real rows of n samples in `out` (FP64).  `rpb` divides n, so a
+// block's rows lie in one slice, whose columns are brought to their largest
+// scale by exact power-of-two products.
+__global__ void __launch_bounds__(kFftThreads) fft_rows_c2r_kernel(const float4 *in, double *out, int64_t nrows, int n,
+                                                                    int logN, int rpb, const float4 *__restrict__ twg,
+                                                                    int conj, const int *__restrict__ cexp) {
+    extern __shared__ __align__(16) float4 sm[];
+    const int N = n >> 1;
+    float4 *tw = sm;                // [N]
+    float4 *twN = sm + N;           // [N/2]
+    float4 *s = twN + (N >> 1);     // [rpb][N]
+    load_real_twiddles_df(tw, twN, twg, N);
+    __shared__ float fs[kMaxB];     // per column: 2^(cexp - the slice's largest)
+    __shared__ int smax;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t js = r0 / n;
+    const int rows = (int)min((int64_t)rpb, nrows - r0);
+    if (threadIdx.x == 0) smax = kZeroRow;
+    __syncthreads();
+    int lm = kZeroRow;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) lm = max(lm, cexp[js * N + k]);
+    atomicMax(&smax, lm);
+    __syncthreads();
+    const int sref = smax;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) fs[k] = pow2f(cexp[js * N + k] - sref);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+        const int rl = e >> logN, k = e & (N - 1);
+        const float4 *row = in + (r0 + rl) * n;
+        const dcomplex a = dc_scale(load_df(row[k]), fs[k]);
+        const dcomplex b = k ? dc_scale(load_df(row[N - k]), fs[N - k]) : dcomplex{{0.f, 0.f}, {0.f, 0.f}};
+        const dcomplex A = {df_add(a.re, b.re), df_add(a.im, df_neg(b.im))};  // X[k] + conj X[N-k]
+        const dcomplex D = {df_add(a.re, df_neg(b.re)), df_add(a.im, b.im)};  // X[k] - conj X[N-k]
+        const dcomplex C = cmul(load_df(tw[k]), D, conj != 0);
+        s[rl * N + bitrev(k, logN)] = store_df(cadd(A, mul_i(C, true)));  // A + i C
+    }
+    dft_stages(s, rows, N, logN, twN, conj != 0);
+    const int sh = sref == kZeroRow ? 0 : sref;
+    double2 *o = reinterpret_cast<double2 *>(out) + r0 * N;  // (x[2t], x[2t+1]) = (Re z[t], Im z[t])
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+        const dcomplex z = load_df(s[e]);
+        o[e] = make_double2(scale2(join_f64(z.re), sh), scale2(join_f64(z.im), sh));
     }
 }
 
@@ -320,8 +499,71 @@ cudaError_t launch_df_fft2(int B, const double2 *in, double2 *out, float4 *work,
     const size_t cbytes = sizeof(float4) * ((size_t)n / 2 + (size_t)kb * n);
     e = cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
     if (e != cudaSuccess) return e;
-    fft_cols_kernel<<<(unsigned)((int64_t)nslices * (n / kb)), kFftThreads, cbytes, s>>>(work, out, n, logn, kb, tw,
-                                                                                          conj, rexp);
+    fft_cols_kernel<<<(unsigned)((int64_t)nslices * (n / kb)), kFftThreads, cbytes, s>>>(work, out, n, logn, kb, n,
+                                                                                          tw, conj, rexp);
+    count_launch();
+    return cudaGetLastError();
+}
+
+bool df_real_fft_supported(int B) { return B >= 2 && df_fft_supported(B); }
+
+// Real grid `in` ((2B)^3 doubles, layout [j][i][k]) -> the m' = 0..B-1 half
+// of S ([j][m][m'], columns B..2B-1 of every slice left as they are),
+// exp(sign i ...): real-row DFTs into S's memory as double-float, then the B
+// columns back to FP64 in place.  `rexp`: n^2 ints of scratch.
+cudaError_t launch_df_fft2_r2c(int B, const double *in, double2 *S, const float4 *tw, int sign, int *rexp,
+                               cudaStream_t s) {
+    if (!df_real_fft_supported(B)) return cudaErrorInvalidValue;
+    const int n = 2 * B, N = B, logn = ilog2_exact(n);
+    const int conj = sign < 0 ? 1 : 0;
+    const int64_t nrows = (int64_t)n * n;
+    float4 *work = reinterpret_cast<float4 *>(S);
+    const int rpb = std::min(256, std::max(1, 1024 / N));  // 1024 values, one radix-4 step per thread and stage
+    const size_t rbytes = sizeof(float4) * ((size_t)N + (size_t)(N / 2) + (size_t)rpb * N);
+    cudaError_t e = cudaFuncSetAttribute(fft_rows_r2c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rbytes);
+    if (e != cudaSuccess) return e;
+    fft_rows_r2c_kernel<<<(unsigned)((nrows + rpb - 1) / rpb), kFftThreads, rbytes, s>>>(in, work, nrows, n, logn - 1,
+                                                                                         rpb, tw, conj, rexp);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int kb = std::min(N, std::max(4, 4096 / n));
+    const size_t cbytes = sizeof(float4) * ((size_t)n / 2 + (size_t)kb * n);
+    e = cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
+    if (e != cudaSuccess) return e;
+    fft_cols_kernel<<<(unsigned)((int64_t)n * (N / kb)), kFftThreads, cbytes, s>>>(work, S, n, logn, kb, N, tw, conj,
+                                                                                   rexp);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// The m' = 0..B-1 half of a Hermitian S (S(-m,-m') = conj S(m,m'), the
+// m' = -B column zero) -> the real grid `out`, exp(sign i ...): the B columns
+// in place into double-float, then the rows to FP64 real samples.  S's
+// columns 0..B-1 are overwritten.  `cexp`: 2B^2 ints of scratch.
+cudaError_t launch_df_fft2_c2r(int B, double2 *S, double *out, const float4 *tw, int sign, int *cexp,
+                               cudaStream_t s) {
+    if (!df_real_fft_supported(B)) return cudaErrorInvalidValue;
+    const int n = 2 * B, N = B, logn = ilog2_exact(n);
+    const int conj = sign < 0 ? 1 : 0;
+    const int64_t nrows = (int64_t)n * n;
+    float4 *work = reinterpret_cast<float4 *>(S);
+    const int kb = std::min(N, std::max(4, 4096 / n));
+    if (kb > 64) return cudaErrorInvalidValue;
+    const size_t cbytes = sizeof(float4) * ((size_t)n / 2 + (size_t)kb * n);
+    cudaError_t e = cudaFuncSetAttribute(fft_cols_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
+    if (e != cudaSuccess) return e;
+    fft_cols_f64_kernel<<<(unsigned)((int64_t)n * (N / kb)), kFftThreads, cbytes, s>>>(S, work, n, logn, kb, N, tw,
+                                                                                       conj, cexp);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int rpb = std::min(n, std::max(1, 1024 / N));  // a power of two dividing n
+    const size_t rbytes = sizeof(float4) * ((size_t)N + (size_t)(N / 2) + (size_t)rpb * N);
+    e = cudaFuncSetAttribute(fft_rows_c2r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rbytes);
+    if (e != cudaSuccess) return e;
+    fft_rows_c2r_kernel<<<(unsigned)(nrows / rpb), kFftThreads, rbytes, s>>>(work, out, nrows, n, logn - 1, rpb, tw,
+                                                                             conj, cexp);
     count_launch();
     return cudaGetLastError();
 }

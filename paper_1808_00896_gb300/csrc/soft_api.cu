@@ -59,7 +59,7 @@ struct soft_plan_s {
     double *seedtab, *rectab;  // per-cluster seeds and recurrence coefficients, built at creation
     int *fwd_order, *inv_order;  // FP64 and FP64-TC plans: the DWT and iDWT dispatch orders (Tables)
     float4 *dftw;              // FP64-TC plans with power-of-two 2B: double-float FFT twiddles (else null)
-    int *dfexp;                // and its row scales (n^2 ints)
+    int *dfexp;                // and its row (real-grid inverse: column) scales (n^2 ints)
     FftTw64 *tw64;             // FP64 / FP64-TC plans with power-of-two 2B: FP64 FFT twiddles (FP64 plans'
                                // slice FFT, both plans' real-grid FFT; else null: cuFFT Z2Z)
     int *colexp;               // FP64-TC plans: per-(m, m') exponents of S for the DWT's column scales
@@ -1082,10 +1082,10 @@ soft_status soft_inverse(soft_plan p, const double *coef, double *grid, void *st
 }
 
 // Real grids (FP64 and FP64-TC plans with power-of-two 2B): the slice FFTs
-// (in FP64 for both) run on the
-// m' >= 0 half of the spectrum (real-row DFTs of half length; every
-// contracted partner has m' >= 0) and the DWT / iDWT contract only one
-// partner of each conjugate pair (kRealSym).
+// (FP64 for FP64 plans, double-float for FP64-TC plans from B = 2 on, as
+// their complex-grid FFTs) run on the m' >= 0 half of the spectrum (real-row
+// DFTs of half length; every contracted partner has m' >= 0) and the DWT /
+// iDWT contract only one partner of each conjugate pair (kRealSym).
 soft_status soft_forward_real(soft_plan p, const double *grid, double *coef, void *stream) {
     soft_status st = check_plan_args(p, grid, coef);
     if (st != SOFT_OK) return st;
@@ -1094,8 +1094,11 @@ soft_status soft_forward_real(soft_plan p, const double *grid, double *coef, voi
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t *ev = timing_slot(p, 0);
     if (ev) cudaEventRecord(ev[0], s);
-    cudaError_t e = launch_fft64_2d_r2c(p->B, grid, p->S, p->tw64, +1, s);  // the m' >= 0 half the DWT reads
-    if (e != cudaSuccess) return fail_cuda("FP64 FFT launch", e);
+    // the m' >= 0 half the DWT reads
+    cudaError_t e = p->dftw && df_real_fft_supported(p->B)
+                        ? launch_df_fft2_r2c(p->B, grid, p->S, p->dftw, +1, p->dfexp, s)
+                        : launch_fft64_2d_r2c(p->B, grid, p->S, p->tw64, +1, s);
+    if (e != cudaSuccess) return fail_cuda("real-grid FFT launch", e);
     if (ev) cudaEventRecord(ev[1], s);
     e = launch_dwt_forward_plan(p, p->S, reinterpret_cast<double2 *>(coef), s, kApplyW | kApplyV | kRealSym);
     if (e != cudaSuccess) return fail_cuda("DWT kernel launch", e);
@@ -1116,8 +1119,9 @@ soft_status soft_inverse_real(soft_plan p, const double *coef, double *grid, voi
     e = launch_dwt_inverse_plan(p, reinterpret_cast<const double2 *>(coef), p->S, s, kRealSym);
     if (e != cudaSuccess) return fail_cuda("iDWT kernel launch", e);
     if (ev) cudaEventRecord(ev[1], s);
-    e = launch_fft64_2d_c2r(p->B, p->S, grid, p->tw64, -1, s);
-    if (e != cudaSuccess) return fail_cuda("FP64 FFT launch", e);
+    e = p->dftw && df_real_fft_supported(p->B) ? launch_df_fft2_c2r(p->B, p->S, grid, p->dftw, -1, p->dfexp, s)
+                                               : launch_fft64_2d_c2r(p->B, p->S, grid, p->tw64, -1, s);
+    if (e != cudaSuccess) return fail_cuda("real-grid FFT launch", e);
     if (ev) cudaEventRecord(ev[2], s);
     return SOFT_OK;
 }

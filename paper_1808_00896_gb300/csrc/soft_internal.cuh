@@ -296,6 +296,15 @@ bool df_fft_supported(int B);
 cudaError_t launch_df_twiddles(int B, float4 *tw, cudaStream_t s);
 cudaError_t launch_df_fft2(int B, const double2 *in, double2 *out, float4 *work, const float4 *tw, int sign,
                            int *rexp, cudaStream_t s, int nslices);
+// Its half-spectrum forms for real grids (B >= 2): real `in` -> columns
+// m' = 0..B-1 of every slice of S (the rest untouched; S's memory is the
+// double-float work buffer), and the Hermitian S's columns 0..B-1
+// (overwritten) -> the real `out`.  `rexp` / `cexp`: n^2 / n B ints of scratch.
+bool df_real_fft_supported(int B);
+cudaError_t launch_df_fft2_r2c(int B, const double *in, double2 *S, const float4 *tw, int sign, int *rexp,
+                               cudaStream_t s);
+cudaError_t launch_df_fft2_c2r(int B, double2 *S, double *out, const float4 *tw, int sign, int *cexp,
+                               cudaStream_t s);
 // FP64 2-D FFT of `nslices` consecutive beta slices (fft_fp64.cu), for
 // power-of-two 2B: same layouts and sign convention; `out` may be `in`; both
 // at the range's first slice.  The twiddle table holds

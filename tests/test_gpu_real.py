@@ -5,9 +5,10 @@ symmetries of Eq. (Wigner_symmetries)); the real entry points contract one
 partner of each such conjugate pair.  The oracle has no real mode: it runs the
 complex transforms on the same data (zero imaginary parts in, real part out),
 so every comparison here is against the plain definition.  Bound: rel-L2
-<= 1e-10, as the FP64 path, for FP64 and FP64-TC plans alike (both run the
-half-spectrum FP64 slice FFT; the FP64-TC kernels contract the even partners
-on the tensor cores).
+<= 1e-10, as the FP64 path, for FP64 and FP64-TC plans alike (FP64 plans run
+the half-spectrum slice FFT in FP64, FP64-TC plans from B = 2 on in
+double-float arithmetic, and their kernels contract the even partners on the
+tensor cores).
 """
 import numpy as np
 import pytest
@@ -173,3 +174,64 @@ def test_real_entry_points_unsupported(B, mode):
         c = p.empty_coef()
         assert capi.soft_forward_real(p.handle, g.data_ptr(), c.data_ptr(), 0) == capi.SOFT_ERR_UNSUPPORTED
         assert capi.soft_inverse_real(p.handle, c.data_ptr(), g.data_ptr(), 0) == capi.SOFT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("scale", [1e-150, 1e150])
+def test_fp64tc_real_inputs_far_outside_the_fp32_range(scale):
+    """The double-float half-spectrum FFT scales every row (forward) or
+    column (inverse) by the power of two of its largest magnitude, so grids
+    and coefficients far outside the FP32 exponent range keep the bound."""
+    B = 16
+    g = real_grid(B, 8700) * scale
+    c = symmetrize(B, synth.coefficients(B, "gauss_decay", seed=8701)) * scale
+    with Plan(B, "fp64_tc", device=DEV) as p:
+        f = p.forward_real(torch.from_numpy(g).to(DEV)).cpu().numpy()
+        back = p.inverse_real(torch.from_numpy(c).to(DEV)).cpu().numpy()
+        p.sync()
+    assert synth.rel_l2(f, oracle.forward(B, g.astype(np.complex128))) < TOL
+    assert synth.rel_l2(back, oracle.inverse(B, c).real) < TOL
+
+
+def test_fp64tc_real_zero_slices_and_rows():
+    """All-zero rows and slices take the zero-scale branch of the row and
+    column scales; the rest of the grid must be unaffected."""
+    B = 8
+    g = real_grid(B, 8800)
+    g[3] = 0.0           # one whole beta slice
+    g[5, 2] = 0.0        # one row of another slice
+    c = symmetrize(B, synth.coefficients(B, "gauss_decay", seed=8801))
+    with Plan(B, "fp64_tc", device=DEV) as p:
+        f = p.forward_real(torch.from_numpy(g).to(DEV)).cpu().numpy()
+        z = p.forward_real(torch.zeros((2 * B,) * 3, dtype=torch.float64, device=DEV)).cpu().numpy()
+        back = p.inverse_real(torch.from_numpy(c).to(DEV)).cpu().numpy()
+        p.sync()
+    assert synth.rel_l2(f, oracle.forward(B, g.astype(np.complex128))) < TOL
+    assert np.all(z == 0)
+    assert synth.rel_l2(back, oracle.inverse(B, c).real) < TOL
+
+
+def test_fp64tc_real_B512_against_the_fp64_path():
+    """Every coefficient and grid value of the real-grid calls at B = 512
+    (1024^3 grid; the double-float FFT's largest row and column shapes)
+    against the FP64 plan's real-grid calls, whose agreement with the oracle
+    the smaller and sampled cases establish.  Norms on the device."""
+    B = 512
+    gen = torch.Generator(device=DEV).manual_seed(8900)
+    g = torch.randn((2 * B,) * 3, dtype=torch.float64, device=DEV, generator=gen)
+    # the real-grid inverse reads one partner of each conjugate pair, the same in both plans
+    c = torch.from_numpy(synth.coefficients(B, "gauss_decay", seed=8901)).to(DEV)
+
+    def rel(x, ref):
+        return (torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref)).item()
+
+    with Plan(B, "fp64", device=DEV) as a:
+        fa = a.forward_real(g)
+        ga = a.inverse_real(c)
+        a.sync()
+    with Plan(B, "fp64_tc", device=DEV) as b:
+        fb = b.forward_real(g)
+        gb = b.inverse_real(c)
+        b.sync()
+    del g
+    assert rel(fb, fa) < TOL
+    assert rel(gb, ga) < TOL
