@@ -10,7 +10,12 @@ themselves with the oracle):
 * the forward FP64 DWT's contraction lanes (csrc/dwt_fp64.cu): for every tile
   shape and partner count, every output column of every degree receives every
   beta sample exactly once, the combining shuffles stay inside a warp, and one
-  lane writes each output.
+  lane writes each output;
+* the real-grid form of the double-float slice FFT (csrc/fft_df.cu): the
+  blocks, bit-reversed slots, power-of-two scales and unpacking / packing of
+  fft_rows_r2c_kernel, fft_cols_kernel on m' < B, fft_cols_f64_kernel and
+  fft_rows_c2r_kernel, in complex128, against numpy.fft on whole grids, with
+  every index bounds-checked and the launch shapes checked for B = 2..512.
 """
 import math
 from collections import Counter
@@ -290,3 +295,215 @@ def test_real_row_c2r_packing(n, s):
     x = np.empty(n)
     x[0::2], x[1::2] = z.real, z.imag
     assert np.allclose(x, want.real, rtol=0, atol=1e-12 * n)
+
+
+
+# ---------------------------------------------------------------------------
+# Real-grid double-float slice FFT (fft_df.cu): the kernels' loops over blocks,
+# bit-reversed slots and scales, in complex128.  Launch shapes as the host
+# code computes them: n = 2B, N = B; r2c rows rpb = min(256, max(1, 1024 / N)),
+# c2r rows rpb = min(n, max(1, 1024 / N)), columns kb = min(N, max(4, 4096 / n)).
+# ---------------------------------------------------------------------------
+ZERO_ROW = -100000
+
+
+def _df_shapes(B):
+    n, N = 2 * B, B
+    return (n, N, min(256, max(1, 1024 // N)), min(n, max(1, 1024 // N)), min(N, max(4, 4096 // n)))
+
+
+def _df_stages(s, cnt, n, logn, tw, conj):
+    """dft_stages of fft_df.cu: radix-4 passes (sub-stages 2h and 4h), then a
+    last radix-2 stage when log2 n is odd; tw[t] = exp(+2 pi i t / n)."""
+    T = np.conj(tw) if conj else tw
+    h, lh = 1, 0
+    while 4 * h <= n:
+        for q in range(cnt * (n >> 2)):
+            row, qq = q >> (logn - 2), q & ((n >> 2) - 1)
+            k, g = qq & (h - 1), qq >> lh
+            i0 = row * n + g * 4 * h + k
+            assert i0 + 3 * h < cnt * n and (k << (logn - 1 - lh)) < len(T)
+            w1, w2 = T[k << (logn - 1 - lh)], T[k << (logn - 2 - lh)]
+            x0, x1, x2, x3 = s[i0], s[i0 + h], s[i0 + 2 * h], s[i0 + 3 * h]
+            t1, t3 = w1 * x1, w1 * x3
+            a0, a1, a2, a3 = x0 + t1, x0 - t1, x2 + t3, x2 - t3
+            u2, u3 = w2 * a2, (w2 * a3) * (-1j if conj else 1j)
+            s[i0], s[i0 + 2 * h], s[i0 + h], s[i0 + 3 * h] = a0 + u2, a0 - u2, a1 + u3, a1 - u3
+        h, lh = 4 * h, lh + 2
+    if 2 * h == n:
+        for b in range(cnt * (n >> 1)):
+            row, k = b >> (logn - 1), b & (h - 1)
+            i, j = row * n + k, row * n + k + h
+            t = T[k] * s[j]
+            s[i], s[j] = s[i] + t, s[i] - t
+
+
+def _exp_of(v):
+    """Biased FP64 exponent of the larger part (0 for zero), as the kernels read it."""
+    m = max(abs(v.real), abs(v.imag))
+    return 0 if m == 0 else math.frexp(m)[1] - 1 + 1023
+
+
+def _df_r2c(B, x, sign):
+    """fft_rows_r2c_kernel, then fft_cols_kernel on the columns m' < B; returns
+    S (n, n, n) with the columns >= B left NaN, and the row scales."""
+    n, N, rpb, _, kb = _df_shapes(B)
+    logn, logN, conj = n.bit_length() - 1, N.bit_length() - 1, sign < 0
+    tw = np.exp(2j * np.pi * np.arange(n // 2) / n)
+    twN = tw[0:2 * (N >> 1):2]
+    z = x.reshape(-1)[0::2] + 1j * x.reshape(-1)[1::2]
+    work = np.full(n ** 3, np.nan + 0j)
+    rexp = np.full(n * n, 7777)
+    nrows = n * n
+    written = np.zeros(n ** 3, dtype=int)
+    for blk in range((nrows + rpb - 1) // rpb):
+        r0 = blk * rpb
+        rows = min(rpb, nrows - r0)
+        assert rows <= 256
+        sm = np.full(rpb * N, np.nan + 0j)
+        rmax = [0] * rows
+        for e in range(rows * N):
+            assert r0 * N + e < len(z)
+            rmax[e >> logN] = max(rmax[e >> logN], _exp_of(z[r0 * N + e]))
+            sm[(e >> logN) * N + _brev(e & (N - 1), logN)] = z[r0 * N + e]
+        for e in range(rows * N):
+            rl = e >> logN
+            i = rl * N + _brev(e & (N - 1), logN)
+            sm[i] *= 2.0 ** ((1023 - rmax[rl]) if rmax[rl] else 0)
+        for t in range(rows):
+            rexp[r0 + t] = rmax[t] - 1023 if rmax[t] else ZERO_ROW
+        _df_stages(sm, rows, N, logN, twN, conj)
+        for e in range(rows * N):
+            rl, k = e >> logN, e & (N - 1)
+            a, b = sm[rl * N + k], sm[rl * N + ((N - k) & (N - 1))]
+            E = complex(0.5 * (a.real + b.real), 0.5 * (a.imag - b.imag))
+            O = complex(0.5 * (a.imag + b.imag), 0.5 * (b.real - a.real))
+            o = (r0 + rl) * n + k
+            assert k < N and o < n ** 3
+            work[o] = E + (np.conj(tw[k]) if conj else tw[k]) * O
+            written[o] += 1
+    S = np.full(n ** 3, np.nan + 0j)
+    tiles = N // kb
+    assert tiles * kb == N and kb <= 64
+    for blk in range(n * tiles):
+        js, k0 = blk // tiles, (blk % tiles) * kb
+        base = js * n * n + k0
+        sref = max(rexp[js * n + i] for i in range(n))
+        sm = np.full(kb * n, np.nan + 0j)
+        for e in range(n * kb):
+            i, c = e // kb, e % kb
+            f = 0.0 if rexp[js * n + i] - sref < -126 else 2.0 ** (rexp[js * n + i] - sref)
+            sm[c * n + _brev(i, logn)] = work[base + i * n + c] * f
+        _df_stages(sm, kb, n, logn, tw, conj)
+        sh = 0 if sref == ZERO_ROW else sref
+        for e in range(n * kb):
+            i, c = e // kb, e % kb
+            S[base + i * n + c] = sm[c * n + i] * 2.0 ** sh
+    return S.reshape(n, n, n), written.reshape(n, n, n)
+
+
+def _df_c2r(B, S, sign):
+    """fft_cols_f64_kernel on the columns m' < B, then fft_rows_c2r_kernel."""
+    n, N, _, rpb, kb = _df_shapes(B)
+    logn, logN, conj = n.bit_length() - 1, N.bit_length() - 1, sign < 0
+    tw = np.exp(2j * np.pi * np.arange(n // 2) / n)
+    twN = tw[0:2 * (N >> 1):2]
+    Sf = S.reshape(-1)
+    work = np.full(n ** 3, np.nan + 0j)
+    cexp = np.full(n * N, 7777)
+    tiles = N // kb
+    for blk in range(n * tiles):
+        js, k0 = blk // tiles, (blk % tiles) * kb
+        base = js * n * n + k0
+        sm = np.full(kb * n, np.nan + 0j)
+        cmax = [0] * kb
+        for e in range(n * kb):
+            i, c = e // kb, e % kb
+            v = Sf[base + i * n + c]
+            cmax[c] = max(cmax[c], _exp_of(v))
+            sm[c * n + _brev(i, logn)] = v
+        for e in range(n * kb):
+            i, c = e // kb, e % kb
+            sm[c * n + _brev(i, logn)] *= 2.0 ** ((1023 - cmax[c]) if cmax[c] else 0)
+        for t in range(kb):
+            assert js * N + k0 + t < n * N
+            cexp[js * N + k0 + t] = cmax[t] - 1023 if cmax[t] else ZERO_ROW
+        _df_stages(sm, kb, n, logn, tw, conj)
+        for e in range(n * kb):
+            i, c = e // kb, e % kb
+            work[base + i * n + c] = sm[c * n + i]
+    out = np.full(n ** 3, np.nan)
+    nrows = n * n
+    assert n % rpb == 0
+    for blk in range(nrows // rpb):
+        r0 = blk * rpb
+        js, rows = r0 // n, min(rpb, nrows - r0)
+        assert (r0 + rows - 1) // n == js  # a block's rows lie in one slice
+        sref = max(cexp[js * N + k] for k in range(N))
+        fs = [0.0 if cexp[js * N + k] - sref < -126 else 2.0 ** (cexp[js * N + k] - sref) for k in range(N)]
+        sm = np.full(rpb * N, np.nan + 0j)
+        for e in range(rows * N):
+            rl, k = e >> logN, e & (N - 1)
+            row = (r0 + rl) * n
+            a = work[row + k] * fs[k]
+            b = work[row + N - k] * fs[N - k] if k else 0j
+            A = complex(a.real + b.real, a.imag - b.imag)
+            D = complex(a.real - b.real, a.imag + b.imag)
+            C = (np.conj(tw[k]) if conj else tw[k]) * D
+            sm[rl * N + _brev(k, logN)] = A + 1j * C
+        _df_stages(sm, rows, N, logN, twN, conj)
+        sh = 0 if sref == ZERO_ROW else sref
+        for e in range(rows * N):
+            o = r0 * N + e
+            assert 2 * o + 1 < n ** 3
+            out[2 * o], out[2 * o + 1] = sm[e].real * 2.0 ** sh, sm[e].imag * 2.0 ** sh
+    return out.reshape(n, n, n)
+
+
+@pytest.mark.parametrize("B", [2, 4, 8, 16])
+def test_df_real_forward_model_matches_numpy(B):
+    n = 2 * B
+    rng = np.random.default_rng(900 + B)
+    x = rng.standard_normal((n, n, n)) * np.exp(rng.uniform(-30, 30, size=(n, n, 1)))  # rows of mixed scales
+    x[1] = 0.0          # an all-zero slice: the zero-row branch
+    S, written = _df_r2c(B, x, +1)
+    ref = np.fft.ifft2(x, axes=(1, 2)) * n * n  # exp(+i ...), unnormalised
+    assert np.isnan(S[:, :, B:]).all()          # the columns m' >= B are never written
+    assert (written[:, :, :B] == 1).all() and (written[:, :, B:] == 0).all()
+    err = np.linalg.norm(S[:, :, :B] - ref[:, :, :B]) / np.linalg.norm(ref[:, :, :B])
+    assert err < 1e-13
+
+
+@pytest.mark.parametrize("B", [2, 4, 8, 16])
+def test_df_real_inverse_model_matches_numpy(B):
+    n = 2 * B
+    rng = np.random.default_rng(950 + B)
+    X = np.fft.fft2(rng.standard_normal((n, n, n)), axes=(1, 2))
+    X[:, :, B] = 0.0    # the m' = -B column and m = -B row, cleared as the iDWT leaves them
+    X[:, B, :] = 0.0
+    X *= np.exp(rng.uniform(-30, 30, size=(n, 1, 1)))
+    X[2] = 0.0          # an all-zero slice
+    want = np.fft.fft2(X, axes=(1, 2))  # exp(-i ...): real up to rounding
+    assert np.abs(want.imag).max() <= 1e-12 * np.abs(want).max()
+    S = X.copy()
+    S[:, :, B:] = np.nan  # the kernels must not read the columns m' >= B
+    g = _df_c2r(B, S, -1)
+    assert np.isfinite(g).all()
+    assert np.linalg.norm(g - want.real) <= 1e-13 * np.linalg.norm(want.real)
+
+
+def test_df_real_launch_shapes():
+    """For every power-of-two B the host code accepts (2..512): the r2c row
+    blocks stay within the 256-entry row-maximum array, the c2r row blocks
+    divide a slice, the column tiles divide B and fit the 64-entry column
+    array, shared memory fits, and every grid is below 2^31 blocks."""
+    for lb in range(1, 10):
+        B = 1 << lb
+        n, N, rpb_r, rpb_c, kb = _df_shapes(B)
+        assert 1 <= rpb_r <= 256 and 1 <= rpb_c and n % rpb_c == 0
+        assert N % kb == 0 and kb <= 64
+        rbytes = 16 * (N + N // 2 + max(rpb_r, rpb_c) * N)
+        cbytes = 16 * (n // 2 + kb * n)
+        assert rbytes <= 227 * 1024 and cbytes <= 227 * 1024
+        assert (n * n + rpb_r - 1) // rpb_r < 2 ** 31 and n * (N // kb) < 2 ** 31
+        assert rpb_r * N <= 4096 and rpb_c * N <= 4096
