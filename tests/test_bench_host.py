@@ -76,7 +76,9 @@ def test_oracle_ref_indexing_against_the_oracle_itself():
     import torch
 
     import oracle
+    from paper_1808_00896_gb300 import build as build_mod
     from paper_1808_00896_gb300 import synth
+    build_mod.build()  # OracleRef reads run offsets through the library's host-only soft_coef_index
     B = 8
     coef = synth.coefficients(B, "gauss_decay", seed=3)
     grid = oracle.inverse(B, coef)
