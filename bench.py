@@ -67,7 +67,7 @@ for _B in (64, 128, 256, 512):
     WORKLOADS[f"b{_B}_fp64tc_real"] = (_B, "fp64_tc_real", "gauss_decay",
                                        f"FP64-accurate SOFT forward+inverse of a real function, B={_B}: "
                                        f"soft_forward_real / soft_inverse_real on an FP64-TC plan (tensor-core "
-                                       f"contraction of one partner per conjugate pair, FP64 half-spectrum FFT)")
+                                       f"contraction of one partner per conjugate pair, double-float half-spectrum FFT)")
     WORKLOADS[f"b{_B}_clenshaw"] = (_B, "fp64_clenshaw", "gauss_decay",
                                     f"FP64 SOFT forward+inverse, B={_B}, inverse DWT by Clenshaw's algorithm "
                                     f"(backward summation over the degrees, the iDWT's last tile-shape variant)")
