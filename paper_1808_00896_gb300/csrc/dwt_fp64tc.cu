@@ -232,7 +232,9 @@ __device__ __forceinline__ void issue_levels(uint32_t tmem, const unsigned char 
 }
 
 // ---------------------------------------------------------------------------
-// Both kernels split the CTA into two warp-specialised groups:
+// Both kernels split the CTA into warp-specialised roles; the forward's are
+// below (the inverse runs eight producer and eight converter warps over two
+// sample tiles, laid out at its kernel):
 //   producers  (128 threads, warps 0-3) run the FP64 recurrence -- two FMAs
 //              per Wigner-d entry and nothing else -- and write the raw FP64
 //              values into a staging ring of kStages groups, kGroup rows
@@ -254,17 +256,17 @@ __device__ __forceinline__ void issue_levels(uint32_t tmem, const unsigned char 
 // the tcgen05 commit); every wait is bounded and its verdict warp-uniform.
 // A ring of two 16-row groups hands off half as often as four 8-row ones
 // for the same staging bytes: each hand-off costs the single producer warp
-// of a scheduler FP64-pipe time that no other warp fills.  Converters, which synchronise among themselves once
-// per chunk to agree that the operands are complete, take that barrier as an
-// AND reduction of their wait verdicts so that a timeout makes the whole group
-// leave together; producers and the issuer synchronise with nobody but the
-// mbarriers and leave individually.
+// of a scheduler FP64-pipe time that no other warp fills.  Converters, which
+// synchronise among themselves once per chunk to agree that the operands are
+// complete, take that barrier as an AND reduction of their wait verdicts so
+// that a timeout makes the whole group leave together; producers and the
+// issuer synchronise with nobody but the mbarriers and leave individually.
 // ---------------------------------------------------------------------------
 constexpr int kProd = 128;    // producer threads (warps 0-3)
 constexpr int kConv = 256;    // converter threads (warps 4-11)
 constexpr int kIssuer = kProd + kConv;  // lane 0 of warp 12 issues the MMAs
 constexpr int kSetup = kIssuer + 32;    // warp 13 prepares the next cluster's tables
-constexpr int kThreadsFwd = kSetup + 32;  // 448 threads (both kernels)
+constexpr int kThreadsFwd = kSetup + 32;  // 448 threads (the forward)
 constexpr int kBarConv = 1;   // named barrier of the converters
 
 constexpr int kStages = 2;    // staging ring depth (groups)
