@@ -34,6 +34,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -116,18 +117,24 @@ SM_MAX_MHZ = 2070.0
 
 # DRAM traffic per launch of the dominant kernels from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel and bandwidth,
-# with the source file and the SHA-256 prefix of it that the capture was taken
-# on; reported as null once that file has changed.
+# with the source file and the SHA-256 prefix of its code (comments and blank
+# lines removed) that the capture was taken on; reported as null once that
+# code has changed.
 TRAFFIC = {
-    ("dwt_forward_fp64_kernel", 64): (36_887_552 + 12_032, "dwt_fp64.cu", "0589e4d08494f908"),
-    ("dwt_forward_fp64_kernel", 256): (3_089_268_992 + 362_294_016, "dwt_fp64.cu", "1fc2456028276ded"),
-    ("dwt_forward_tc_kernel", 128): (294_756_608 + 45_407_488, "dwt_fp64tc.cu", "270df8a4ce56ca42"),
+    ("dwt_forward_fp64_kernel", 64): (36_887_552 + 12_032, "dwt_fp64.cu", "1047c03e36d8df50"),
+    ("dwt_forward_fp64_kernel", 256): (3_089_268_992 + 362_294_016, "dwt_fp64.cu", "eb315583bf94423f"),
+    ("dwt_forward_tc_kernel", 128): (294_756_608 + 45_407_488, "dwt_fp64tc.cu", "c443e7c0222d361b"),
 }
 
 
 def kernel_source_sha(name: str = "dwt_fp64.cu") -> str:
+    """SHA-256 prefix of a CUDA source's code: /* */ and // comments, trailing
+    spaces and blank lines removed, so that comment edits keep a capture valid."""
     path = os.path.join(ROOT, "paper_1808_00896_gb300", "csrc", name)
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    text = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def dwt_flops(B: int) -> dict:

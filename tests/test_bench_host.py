@@ -57,6 +57,25 @@ def test_traffic_entries_name_existing_sources():
         assert len(sha) == 16
 
 
+def test_source_sha_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    """A recorded traffic figure stays valid across comment edits of its
+    kernel's source and is voided by any change of the code."""
+    d = tmp_path / "paper_1808_00896_gb300" / "csrc"
+    d.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    versions = {
+        "base": "// header\nint f(int a) {  /* old */\n  return a + 1;\n}\n",
+        "comments": "// a longer header\n// over two lines\n\nint f(int a) {  /* new\n  text */\n  return a + 1;  // sum\n}\n",
+        "code": "// header\nint f(int a) {  /* old */\n  return a + 2;\n}\n",
+    }
+    sha = {}
+    for k, text in versions.items():
+        (d / "k.cu").write_text(text)
+        sha[k] = bench.kernel_source_sha("k.cu")
+    assert sha["base"] == sha["comments"]
+    assert sha["base"] != sha["code"]
+
+
 @pytest.mark.parametrize("B", [1, 2, 3, 8, 64, 512])
 def test_sampled_pairs_and_points_are_in_range(B):
     pairs = bench.sample_pairs(B, seed=B)
