@@ -101,9 +101,14 @@ const char *soft_status_string(int status);
 const char *soft_last_error(void);
 
 /* Create a plan for bandwidth B on the current CUDA device.  Allocates the
- * plan's device workspace ((2B)^3 complex doubles for S plus small tables),
- * builds the slice-FFT tables (the library's own FFT when 2B is a power of
- * two, else a cuFFT plan) and computes the quadrature weights of Eq. (weights)
+ * plan's device workspace ((2B)^3 complex doubles for S -- mixed plans: S and
+ * a grid copy in complex floats instead --, 5B doubles of seeds and rescaled
+ * recurrence coefficients per symmetry cluster, 2.7 GB at B = 512, and small
+ * beta tables; SOFT_FP64_TC plans add 2 ints per order pair and (2B)^2 ints
+ * of FFT scales),
+ * builds the slice-FFT tables (FP64 and FP64-TC plans: the library's own FFT
+ * when 2B is a power of two, else a cuFFT plan; mixed plans: FP32 cuFFT
+ * plans) and computes the quadrature weights of Eq. (weights)
  * and the other beta tables on the device.  *out receives the handle, or NULL
  * on failure.  Returns SOFT_ERR_INVALID_ARG for B < 1 or out == NULL,
  * SOFT_ERR_UNSUPPORTED for B > soft_max_bandwidth() or an unbuilt dtype. */
@@ -116,8 +121,10 @@ soft_status soft_destroy(soft_plan p);
 /* Bandwidth of a plan, or -1 for NULL. */
 int soft_plan_bandwidth(soft_plan p);
 
-/* Wait for all work on the plan's device and read the device error word.
- * Returns SOFT_ERR_DEVICE if a kernel flagged an error since the last call. */
+/* Wait for all work on the plan's device and read (and clear) the device
+ * error word: SOFT_ERR_TIMEOUT if a tensor-core kernel's bounded wait gave up
+ * since the last call (its results are then not to be used; the context stays
+ * usable), SOFT_ERR_DEVICE if a kernel flagged another inconsistency. */
 soft_status soft_plan_sync(soft_plan p);
 
 /* Forward transform (FSOFT, Sec. 2.4): grid (device, (2B)^3 complex) ->
