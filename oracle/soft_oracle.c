@@ -39,7 +39,7 @@ static int g_threads = 1;
 void oracle_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
 int oracle_get_threads(void) { return g_threads; }
 
-/* 1 when this build runs its loops with OpenMP. */
+/* 1 when the oracle was compiled with OpenMP (its loops then run on threads). */
 int oracle_openmp(void)
 {
 #ifdef _OPENMP
