@@ -345,7 +345,7 @@ def workload_config(args, B: int, dtype: str, kind: str, world: int) -> dict:
 
 
 def run_reference(args) -> None:
-    """--impl reference: the CPU oracle timed as it stands on the machine's host
+    """--impl reference: the CPU oracle timed as it stands on this machine's host
     cores (OpenMP over order pairs and slices), on the same workload, metric,
     unit and config.  Each step is a bounded sample: the oracle's strided
     round trip over every stride-th row of order pairs and beta slice, with
