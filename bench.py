@@ -334,13 +334,15 @@ def cpu_baseline_oracle(B: int, kind: str, budget_s: float, seed: int) -> dict:
 def workload_config(args, B: int, dtype: str, kind: str, world: int) -> dict:
     """The `config` dict of a workload, the same for both arms."""
     n = 2 * B
-    grid_bytes = 16 * n ** 3
+    grid_bytes = (8 if dtype in ("fp64_real", "fp64_tc_real") else 16) * n ** 3  # real grids: doubles
     coef_bytes = 16 * (B * (4 * B * B - 1) // 3)
-    R = 1 if B >= 256 else max(1, min(8, math.ceil(2 * L2_BYTES / (grid_bytes + coef_bytes))))
+    set_bytes = grid_bytes + coef_bytes
+    # enough input sets that one pass over them is at least twice the L2
+    R = max(1, math.ceil(2 * L2_BYTES / set_bytes))
     return {"workload": WORKLOADS[args.workload][3], "B": B, "mode": dtype, "coefficients": kind,
             "inputs_rotated": R, "tile_variants": None,
-            "l2": f"{R} rotating input sets of {(grid_bytes + coef_bytes) / 2**20:.1f} MiB (> 129 MB L2 per pass)"
-            if R > 1 else "single input larger than L2",
+            "l2": f"{R} rotating input sets of {set_bytes / 2**20:.1f} MiB ({R * set_bytes / 2**20:.0f} MiB "
+                  f"per pass, > 129 MB L2)" if R > 1 else "single input larger than L2",
             "parallelism": f"replicas x{world}"}
 
 
