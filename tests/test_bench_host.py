@@ -108,3 +108,19 @@ def test_oracle_ref_indexing_against_the_oracle_itself():
     bad = oracle.forward(B, grid)
     bad[ref.coef_idx[0]] += 1.0
     assert ref.errors(torch.from_numpy(bad), torch.from_numpy(grid))["forward"] > 1e-3
+
+
+def test_every_single_workload_exceeds_l2_per_pass():
+    """The timing rule: between timed steps the inputs are not L2-resident.
+    For every single-transform workload the rotated input sets span at least
+    twice the L2, or one set alone exceeds it, and the config says which."""
+    import types
+    for name, (B, dtype, kind, _) in bench.WORKLOADS.items():
+        if name in bench.BATCHED:
+            continue
+        c = bench.workload_config(types.SimpleNamespace(workload=name), B, dtype, kind, 1)
+        n = 2 * B
+        set_bytes = (8 if "real" in dtype else 16) * n ** 3 + 16 * (B * (4 * B * B - 1) // 3)
+        R = c["inputs_rotated"]
+        assert R * set_bytes >= 2 * bench.L2_BYTES or (R == 1 and set_bytes > bench.L2_BYTES), name
+        assert ("single input larger than L2" in c["l2"]) == (R == 1), name
